@@ -1,0 +1,107 @@
+/*
+ * FP64 CPU oracle for the chemical-potential multiphase LBM step
+ * (Qin, Chen, Qin, Xu, Wen, "Spurious currents suppression by accurate
+ * difference schemes in multiphase lattice Boltzmann method").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include,
+ * link or call this code: only the tests, the package's smoke check and
+ * the benchmark's CPU-baseline leg use it.  It shares no header, table or
+ * helper with the CUDA library.
+ *
+ * Everything is plain double precision, plain nested loops, in the order the
+ * paper states the algorithm (Sec. 2.1-2.3).  Built with -ffp-contract=off so
+ * that results do not depend on whether the host has FMA.
+ *
+ * Parity pins: every function here is pinned by a CPU test against a
+ * property fixed by the paper or by mathematics (see tests/test_oracle_*.py).
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* lattices */
+#define OR_D2Q9 0
+#define OR_D3Q19 1
+
+/* finite-difference schemes (Sec. 2.3) */
+#define OR_EFDS2 0  /* Eq. 18 */
+#define OR_EFDS4 1  /* Eq. 19 */
+#define OR_EFDS6 2  /* Eq. 20 */
+#define OR_CFDS4 3  /* Eq. 22 */
+#define OR_CFDS6 4  /* Eq. 23 */
+#define OR_CFDS8 5  /* Eq. 24 */
+#define OR_OCFDS4 6 /* Sec. 3.1 optimal fourth-order compact */
+#define OR_E4 7     /* Eq. 25, fourth-order isotropic */
+#define OR_E8 8     /* Eq. 25, eighth-order isotropic (2D only) */
+#define OR_NSCHEMES 9
+
+/* status codes */
+#define OR_OK 0
+#define OR_EINVAL -1
+#define OR_ENOMEM -2
+#define OR_EUNSTABLE -4
+
+typedef struct {
+  int lattice;          /* OR_D2Q9 or OR_D3Q19 */
+  int nx, ny, nz;       /* nz = 1 for D2Q9; x fastest */
+  double a, b, R, Tr;   /* Carnahan-Starling constants and reduced temperature */
+  double k, kappa, tau; /* proportional coefficient (Eq. 16), kappa-hat, BGK tau */
+  int scheme;           /* OR_EFDS2 .. OR_E8 */
+} or_params;
+
+typedef struct {
+  double max_v, max_u, rho_center, rho_corner, mass, max_drho;
+  long long step;
+  int status;
+} or_obs;
+
+typedef struct or_sim or_sim;
+
+/* ---- lattice, equilibrium, forcing (Sec. 2.1) ---- */
+int or_lattice_q(int lattice);
+void or_lattice_e(int lattice, int* e /* Q*3 */, double* w /* Q */);
+void or_feq(int lattice, double rho, const double u[3], double* feq);
+void or_edm(int lattice, double rho, const double u[3], const double F[3], double* Fi);
+
+/* ---- Carnahan-Starling EOS and chemical potential (Eq. 10-13, 16) ---- */
+double or_cs_pressure(double rho, double a, double b, double R, double T);
+double or_cs_mu(double rho, double a, double b, double R, double T);
+int or_cs_critical(double a, double b, double R, double* rho_c, double* T_c);
+int or_maxwell(double a, double b, double R, double T, double* rho_g, double* rho_l);
+
+/* ---- finite differences on periodic lattices (Sec. 2.3) ---- */
+void or_scheme_coeffs(int scheme, double* alpha, double* a, double* b, double* c);
+int or_deriv_line(int scheme, const double* f, int n, double* d);
+int or_deriv2_line(int scheme, const double* f, int n, double* d2);
+int or_gradient(int scheme, int dim, int nx, int ny, int nz, const double* phi, double* g /* dim*N */);
+int or_laplacian(int scheme, int dim, int nx, int ny, int nz, const double* phi, double* lap);
+
+/* ---- the simulation ---- */
+or_sim* or_create(const or_params* p);
+void or_destroy(or_sim* s);
+int or_init_droplet(or_sim* s, const double center[3], double radius, double width, double rho_l, double rho_g);
+int or_init_slab(or_sim* s, int axis, double thickness, double width, double rho_l, double rho_g);
+int or_init_profile(or_sim* s, const double center[3], const double* r, const double* rho, int n);
+int or_set_f(or_sim* s, const double* f);
+int or_get_f(const or_sim* s, double* f);
+int or_get_density(const or_sim* s, double* rho);
+int or_get_fields(or_sim* s, double* rho, double* u, double* F, double* mu);
+int or_step(or_sim* s, long long n);
+int or_observables(or_sim* s, or_obs* out);
+double or_temperature(const or_sim* s);
+
+/* ---- warm-start MLP (FP64 reference of the network the solver trains) ---- */
+int or_mlp_forward(const int* sizes, int nlayers, const double* params, const double* x, int batch,
+                   double* y, double* acts);
+int or_mlp_loss_grad(const int* sizes, int nlayers, const double* params, const double* x,
+                     const double* target, int batch, double* loss, double* grad);
+int or_adam_step(int n, double* params, double* m, double* v, const double* grad, double lr,
+                 double beta1, double beta2, double eps, int t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
