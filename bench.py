@@ -1,0 +1,240 @@
+#!/usr/bin/env python
+"""Benchmark: fused D3Q19 chemical-potential LBM step on one GB300.
+
+Workload (one step = one full time step of the hot path over the lattice):
+D3Q19, 256^3 periodic, droplet r0 = 60, Carnahan-Starling EOS (a=1, b=4,
+R=1), T_r = 0.8, k = 0.25, kappa = 0.1, tau = 1, sixth-order central
+differences (EFDS6), populations stored in FP32 as deviations from w_i rho_g
+with an FP64 density field.  The f arrays (1.27 GB) are far larger than L2,
+so no flush is needed between steps.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead,
+on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM-peak fraction of fused step; device-s to converged sweep vs plain"
+UNIT = "MLUPS"
+WORKLOAD = dict(lattice="D3Q19", nx=256, ny=256, nz=256, radius=60.0, Tr=0.8, k=0.25, kappa=0.1, tau=1.0,
+                scheme="EFDS6", precision="FP32DEV", mu="fp32")
+# algorithmic bytes per lattice update: read + write 19 FP32 populations, read + write the FP64 density
+B_ALG = 19 * 4 * 2 + 8 * 2
+SAMPLE_N = 128  # oracle sample lattice (same parameters, radius scaled)
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[2:]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(steps, n=SAMPLE_N):
+    """Time the FP64 oracle on an n^3 sample with the workload's parameters."""
+    import oracle as O
+    w = WORKLOAD
+    s = O.Sim(lattice=O.D3Q19, nx=n, ny=n, nz=n, Tr=w["Tr"], k=w["k"], kappa=w["kappa"], tau=w["tau"],
+              scheme=w["scheme"])
+    s.init_droplet(w["radius"] * n / w["nx"])
+    t = time.perf_counter()
+    rc = s.step(steps)
+    dt = time.perf_counter() - t
+    assert rc == 0
+    return n ** 3 * steps / dt / 1e6, dt
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    vals = []
+    total = 0.0
+    for _ in range(args.steps):
+        v, dt = oracle_sample(1)
+        vals.append(v)
+        total += dt
+    value = SAMPLE_N ** 3 * args.steps / total / 1e6
+    sample = "%d^3 lattice, same parameters (r0 scaled), one oracle step per timed step" % SAMPLE_N
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(workload="D3Q19 droplet, FP64 CPU oracle sample", **WORKLOAD),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import paper_2205_09186_gb300 as pkg
+    if rank == 0 or world == 1:
+        pkg.build()
+    if dist:
+        dist.barrier()
+    from paper_2205_09186_gb300 import lbm as L
+    w = WORKLOAD
+    params = L.make_params(lattice=L.LBM_D3Q19, nx=w["nx"], ny=w["ny"], nz=w["nz"], Tr=w["Tr"], k=w["k"],
+                           kappa=w["kappa"], tau=w["tau"], scheme=w["scheme"], precision=L.LBM_FP32DEV, mu_fp64=0)
+    stream = torch.cuda.current_stream()
+    sim = L.Sim(params)
+    sim.lbm_init_droplet(w["radius"])
+    N = w["nx"] * w["ny"] * w["nz"]
+    for _ in range(args.warmup):
+        sim.lbm_step(1)
+    torch.cuda.synchronize()
+    obs0 = sim.lbm_observables()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for i in range(args.steps):
+            sim.lbm_step(1)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    obs = sim.lbm_observables()
+    ok = obs["status"] == 0 and abs(obs["mass"] / obs0["mass"] - 1) < 1e-6
+    mlups = N * args.steps * world / (total_ms * 1e-3) / 1e6
+    launch_ms = statistics.mean(per)
+    achieved = B_ALG * N / (launch_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+
+    # end to end through the public API with host buffers: upload the initial
+    # density (H2D), step, read the observables every step (D2H), read back
+    # the final density (D2H)
+    rho0 = np.ascontiguousarray(sim.lbm_get_density())
+    host_rho = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.lbm_init_density(rho0)
+    for _ in range(args.steps):
+        sim.lbm_step(1)
+        sim.lbm_observables()
+    host_rho[:] = sim.lbm_get_density().reshape(-1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": N * args.steps * world / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": N * 8 / args.steps, "d2h_bytes_per_step": 64 + N * 8 / args.steps}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, dt = oracle_sample(args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d^3 lattice with the same parameters (r0 scaled), %d FP64 oracle steps, %.1f s"
+                         % (SAMPLE_N, args.cpu_steps, dt)}
+    line = {"metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload="D3Q19 droplet 256^3 r0=60, CS EOS, EFDS6, FP32-deviation populations, "
+                                    "FP64 density; inputs larger than L2 (no flush)", parallelism="replicas",
+                           **WORKLOAD),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_lu": B_ALG, "kernel": "k_step3d (fused mu+grad+force+collide+stream+density)"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clk.summary(), "check": {"status": obs["status"], "mass_rel_change": obs["mass"] / obs0["mass"] - 1,
+                                               "ok": ok}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

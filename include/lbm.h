@@ -1,0 +1,206 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) chemical-potential multiphase lattice
+ * Boltzmann library.
+ *
+ * Method: Qin, Chen, Qin, Xu, Wen, "Spurious currents suppression by accurate
+ * difference schemes in multiphase lattice Boltzmann method".  One time step
+ * evaluates the bulk chemical potential from the equation of state (Eq. 10-13,
+ * 16), adds the density-Laplacian term (Eq. 11, 16), takes grad mu and grad
+ * rho with a selectable difference scheme (Eq. 17-25), forms the nonideal
+ * force F = -rho grad mu + c_s^2 grad rho (Eq. 12), applies single-relaxation
+ * (BGK) collision with exact-difference forcing (Eq. 1, 6, 8) and streams
+ * (Eq. 1, left side) on a periodic D2Q9 or D3Q19 lattice.
+ *
+ * Conventions
+ *  - Lattice units: dx = dt = c = 1, c_s^2 = 1/3.  Node (x, y, z) has linear
+ *    index x + nx*(y + ny*z) (x fastest).  Fields are structure-of-arrays:
+ *    population i of node n at f[i*N + n], N = nx*ny*nz.
+ *  - D2Q9 velocity order is that of Eq. 2 (rest; +x, +y, -x, -y; (1,1),
+ *    (-1,1), (-1,-1), (1,-1)).  D3Q19 order: rest; +x, -x, +y, -y, +z, -z;
+ *    (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1),
+ *    (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).
+ *  - All functions return 0 on success or a negative LBM_E* code; no call
+ *    falls back to the CPU.  Host arrays passed in are borrowed for the
+ *    duration of the call only.  Calls on one handle are not thread-safe;
+ *    distinct handles are independent.
+ *  - Device work is enqueued on the stream given at creation; functions that
+ *    return host data synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define LBM_OK 0
+#define LBM_EINVAL -1     /* invalid argument or parameter combination */
+#define LBM_ENOMEM -2     /* the allocator returned NULL */
+#define LBM_ECUDA -3      /* a CUDA runtime call failed */
+#define LBM_EUNSTABLE -4  /* a density became non-positive or NaN; see lbm_obs.step */
+#define LBM_ETIMEOUT -5   /* a bounded device-side wait gave up */
+#define LBM_ENOTSUP -6    /* combination not provided (e.g. E8 on D3Q19) */
+
+/* ---- enumerations ---- */
+#define LBM_D2Q9 0
+#define LBM_D3Q19 1
+
+#define LBM_EOS_CS 0 /* Carnahan-Starling */
+
+/* difference schemes (Sec. 2.3) */
+#define LBM_EFDS2 0  /* Eq. 18, second-order central */
+#define LBM_EFDS4 1  /* Eq. 19 */
+#define LBM_EFDS6 2  /* Eq. 20 */
+#define LBM_CFDS4 3  /* Eq. 22, Pade; periodic tridiagonal line solves */
+#define LBM_CFDS6 4  /* Eq. 23 */
+#define LBM_CFDS8 5  /* Eq. 24 */
+#define LBM_OCFDS4 6 /* Sec. 3.1 optimal fourth-order compact, alpha = 0.446776, c = -0.0541132 */
+#define LBM_E4 7     /* Eq. 25, fourth-order isotropic */
+#define LBM_E8 8     /* Eq. 25, eighth-order isotropic (D2Q9 only) */
+
+/* storage precision */
+#define LBM_FP64 0    /* populations, density and all arithmetic in FP64 */
+#define LBM_FP32DEV 1 /* populations stored in FP32 as f_i - w_i rho_ref; density FP64 */
+
+/*
+ * Simulation parameters.
+ *  lattice   LBM_D2Q9 (nz must be 1) or LBM_D3Q19
+ *  nx,ny,nz  periodic lattice size; each >= 8 (D2Q9: nx, ny >= 8)
+ *  eos       LBM_EOS_CS
+ *  a,b,R     CS constants: p0 = rho R T (1+eta+eta^2-eta^3)/(1-eta)^3 - a rho^2, eta = b rho/4
+ *  Tr        reduced temperature T/T_c (T_c computed from a, b, R), 0 < Tr
+ *  k         proportional coefficient of Eq. 16 (mu-hat = k^2 psi' - kappa lap rho)
+ *  kappa     kappa-hat of Eq. 16
+ *  tau       BGK relaxation time (> 0.5)
+ *  scheme    LBM_EFDS2 .. LBM_E8
+ *  precision LBM_FP64 or LBM_FP32DEV
+ *  mu_fp64   FP32DEV only: evaluate the EOS chemical potential in FP64
+ *            (slower on GB300, whose FP64 rate is a small fraction of FP32)
+ *  rho_ref   FP32DEV only: reference density of the stored deviations;
+ *            <= 0 selects the Maxwell gas density at Tr
+ */
+typedef struct {
+  int lattice;
+  int nx, ny, nz;
+  int eos;
+  double a, b, R, Tr;
+  double k, kappa, tau;
+  int scheme;
+  int precision;
+  int mu_fp64;
+  double rho_ref;
+} lbm_params;
+
+/*
+ * Observables at the current time step t (Sec. 3.3 and 3.4):
+ *  max_v       max over nodes of |v|, v = u + F/(2 rho) (Sec. 2.1, after Eq. 8)
+ *  max_u       max over nodes of |u|, u = sum e_i f_i / rho (Eq. 7)
+ *  rho_center  rho at node (nx/2, ny/2, nz/2)
+ *  rho_corner  rho at node (0, 0, 0)
+ *  mass        sum of rho over all nodes (FP64)
+ *  max_drho    max over nodes |rho(t) - rho(t0)| / (t - t0), t0 the time of the
+ *              previous lbm_observables call (or of initialisation); 0 if t == t0
+ *  step        t; for status LBM_EUNSTABLE the first step at which a
+ *              non-positive or NaN density was seen
+ *  status      LBM_OK or LBM_EUNSTABLE
+ */
+typedef struct {
+  double max_v, max_u, rho_center, rho_corner, mass, max_drho;
+  long long step;
+  int status;
+} lbm_obs;
+
+/*
+ * Device-memory allocator supplied by the caller (for example one backed by a
+ * framework's caching allocator).  alloc returns a device pointer aligned to
+ * at least 256 bytes or NULL; free releases it.  If the allocator argument of
+ * lbm_create is NULL the library uses cudaMalloc / cudaFree.
+ */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* ctx);
+  void* ctx;
+} lbm_allocator;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Create a simulation.  stream: a cudaStream_t (NULL = legacy default
+ * stream) on the current device, on which all work of this handle runs.
+ * The handle owns every device buffer it allocates through `alloc`.
+ * Errors: LBM_EINVAL (bad parameters), LBM_ENOTSUP, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* alloc, lbm_handle** out);
+
+/* Release all device memory of the handle (after synchronising its stream). */
+void lbm_destroy(lbm_handle* h);
+
+/* Initialise a droplet by Eq. 26: rho = (rho_l+rho_g)/2 - (rho_l-rho_g)/2
+ * tanh(2 (r - radius)/width), r = Euclidean distance to center (no periodic
+ * image); center NULL = node (nx/2, ny/2, nz/2); rho_l or rho_g <= 0 selects
+ * the Maxwell coexistence densities.  Populations start at equilibrium with
+ * u = 0.  Resets the step counter and status. */
+int lbm_init_droplet(lbm_handle* h, const double center[3], double radius, double width, double rho_l,
+                     double rho_g);
+
+/* Flat liquid slab of the given thickness centred on the mid-plane of axis
+ * (0 = x, 1 = y, 2 = z) with a tanh interface of the given width (the
+ * coexistence test of Sec. 3.4). */
+int lbm_init_slab(lbm_handle* h, int axis, double thickness, double width, double rho_l, double rho_g);
+
+/* Radial profile: rho(node) is linearly interpolated in r between samples
+ * (r[j], rho[j]), j < n, r strictly increasing, held at the end values
+ * outside [r[0], r[n-1]]. */
+int lbm_init_profile(lbm_handle* h, const double center[3], const double* r, const double* rho, int n);
+
+/* Arbitrary initial density field: host_rho[N] (FP64, all > 0), u = 0. */
+int lbm_init_density(lbm_handle* h, const double* host_rho);
+
+/* Set all populations from host FP64 f[Q*N] (full values, not deviations).
+ * Resets the step counter. */
+int lbm_set_f(lbm_handle* h, const double* host_f);
+
+/* Advance n >= 0 time steps; asynchronous on the handle's stream. */
+int lbm_step(lbm_handle* h, long long n);
+
+/* Observables of the current state (synchronises the stream).  Returns
+ * LBM_EUNSTABLE (and fills out->status, out->step) once a non-positive or
+ * NaN density has been seen. */
+int lbm_observables(lbm_handle* h, lbm_obs* out);
+
+/* Copy the density field rho[N] (FP64) to host memory (synchronises). */
+int lbm_get_density(lbm_handle* h, double* host_rho);
+
+/* Copy the populations as full FP64 values f[Q*N] to host memory. */
+int lbm_get_f(lbm_handle* h, double* host_f);
+
+/* Nonideal force F[dim*N] (component-major) and chemical potential mu[N] of
+ * the current state, FP64 on the host; either pointer may be NULL. */
+int lbm_get_force(lbm_handle* h, double* host_F, double* host_mu);
+
+/* Current step counter. */
+long long lbm_get_step(const lbm_handle* h);
+
+/* Device pointers of the current populations and density (for callers that
+ * keep data on the GPU).  Valid until the next lbm_step. */
+int lbm_device_state(lbm_handle* h, void** f, void** rho);
+
+/* Carnahan-Starling critical point for constants (a, b, R), solving
+ * dp0/drho = d2p0/drho2 = 0. */
+int lbm_critical(double a, double b, double R, double* rho_c, double* T_c);
+
+/* Maxwell equal-area coexistence densities for params->(a, b, R, Tr):
+ * equal chemical potential and pressure in both bulk phases. */
+int lbm_maxwell(const lbm_params* params, double* rho_g, double* rho_l);
+
+/* Lattice size Q (9 or 19) of a lattice id, 0 if unknown. */
+int lbm_lattice_q(int lattice);
+
+/* Static text for an error code. */
+const char* lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

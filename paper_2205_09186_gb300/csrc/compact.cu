@@ -1,0 +1,256 @@
+// Compact-scheme path: mu field, PCR line solves for the periodic tridiagonal
+// systems of Eq. 21 (beta = 0), and the fused collide/stream kernels that read
+// the resulting gradient fields.
+#include <cmath>
+
+#include "compact.cuh"
+#include "step2d.cuh"
+#include "step3d.cuh"
+
+namespace lbmd {
+
+void compact_coeffs(int scheme, double* alpha, double* a, double* b, double* c) {
+  *alpha = *a = *b = *c = 0.0;
+  switch (scheme) {
+    case S_CFDS4: *alpha = 0.25; *a = 1.5; break;                               // Eq. 22
+    case S_CFDS6: *alpha = 1.0 / 3.0; *a = 14.0 / 9.0; *b = 1.0 / 9.0; break;   // Eq. 23
+    case S_CFDS8: *alpha = 0.375; *a = 25.0 / 16.0; *b = 0.2; *c = -1.0 / 80.0; break;  // Eq. 24
+    case S_OCFDS4: {
+      const double al = 0.446776, cc = -0.0541132;
+      // a + b + c = 1 + 2 alpha and a + 4 b + 9 c = 6 alpha
+      const double bb = ((6.0 * al - 9.0 * cc) - (1.0 + 2.0 * al - cc)) / 3.0;
+      *alpha = al; *c = cc; *b = bb; *a = (1.0 + 2.0 * al - cc) - bb;
+      break;
+    }
+    default: break;
+  }
+}
+
+// PCR on x_i + al (x_{i-s} + x_{i+s}) = d_i: combining rows i-s, i, i+s gives
+// x_i + al' (x_{i-2s} + x_{i+2s}) = d'_i with al' = -al^2/(1 - 2 al^2) and
+// d'_i = (d_i - al (d_{i-s} + d_{i+s}))/(1 - 2 al^2); exact for circulant
+// systems of any length (indices modulo the line length).
+LineCoef make_line_coef(int scheme) {
+  LineCoef lc{};
+  double al, a, b, c;
+  compact_coeffs(scheme, &al, &a, &b, &c);
+  lc.A1 = 0.5 * a;
+  lc.A2 = 0.25 * b;
+  lc.A3 = c / 6.0;
+  int k = 0;
+  while (std::fabs(al) > 1e-17 && k < 16) {
+    lc.alpha[k] = al;
+    lc.inv[k] = 1.0 / (1.0 - 2.0 * al * al);
+    al = -al * al * lc.inv[k];
+    ++k;
+  }
+  lc.nlev = k;
+  return lc;
+}
+
+namespace {
+
+__device__ __forceinline__ int lmod(long long a, int n) {
+  long long r = a % n;
+  return int(r < 0 ? r + n : r);
+}
+
+// mu = k^2 psi'(rho) - kappa lap rho with the explicit central second
+// derivative of order LO along each axis (the compact scheme's Laplacian).
+template <typename Tm, int LO>
+__global__ void k_mu_field(KParams p, int D, const double* __restrict__ rho, Tm* __restrict__ mu) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.n) return;
+  constexpr int R = LO / 2;
+  const double l0 = LO == 4 ? -2.5 : (LO == 6 ? -49.0 / 18.0 : -205.0 / 72.0);
+  const double lc[5] = {l0, LO == 4 ? 4.0 / 3.0 : (LO == 6 ? 1.5 : 1.6), LO == 4 ? -1.0 / 12.0 : (LO == 6 ? -0.15 : -0.2),
+                        LO == 6 ? 1.0 / 90.0 : (LO == 8 ? 8.0 / 315.0 : 0.0), LO == 8 ? -1.0 / 560.0 : 0.0};
+  const int x = int(n % p.nx), y = int((n / p.nx) % p.ny), z = int(n / ((long long)p.nx * p.ny));
+  const double ref = p.rho_ref;
+  const Tm c0 = Tm(rho[n] - ref);
+  Tm lap = Tm(D * lc[0]) * c0;
+#pragma unroll
+  for (int m = 1; m <= R; ++m) {
+    const long long row = (long long)z * p.nx * p.ny + (long long)y * p.nx;
+    Tm s = Tm(rho[row + lmod(x + m, p.nx)] - ref) + Tm(rho[row + lmod(x - m, p.nx)] - ref);
+    s += Tm(rho[(long long)z * p.nx * p.ny + (long long)lmod(y + m, p.ny) * p.nx + x] - ref) +
+         Tm(rho[(long long)z * p.nx * p.ny + (long long)lmod(y - m, p.ny) * p.nx + x] - ref);
+    if (D == 3)
+      s += Tm(rho[(long long)lmod(z + m, p.nz) * p.nx * p.ny + (long long)y * p.nx + x] - ref) +
+           Tm(rho[(long long)lmod(z - m, p.nz) * p.nx * p.ny + (long long)y * p.nx + x] - ref);
+    lap += Tm(lc[m]) * s;
+  }
+  mu[n] = Tm(p.k2) * cs_mu<Tm>(Tm(rho[n]), Tm(p.RT), Tm(p.b4), Tm(p.two_a)) - Tm(p.kappa) * lap;
+}
+
+// Derivative along `axis` of lines of `in` (minus ref), LPB lines per CTA held
+// in shared memory; explicit right side of Eq. 21 then PCR levels.
+template <typename Tin, typename T>
+__global__ void k_lines(int axis, int nx, int ny, int nz, const Tin* __restrict__ in, double ref, T* __restrict__ out,
+                        const LineCoef lc, int LPB) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = axis == 0 ? nx : (axis == 1 ? ny : nz);
+  const int LP = L + 1;
+  T* A = reinterpret_cast<T*>(smem);
+  T* B = A + LPB * LP;
+  const long long NXY = (long long)nx * ny;
+  // line j of this CTA: base offset and element stride
+  const long long stride = axis == 0 ? 1 : (axis == 1 ? nx : NXY);
+  const int groups_x = (nx + LPB - 1) / LPB;  // for y/z lines: groups of LPB consecutive x
+  auto line_base = [&](int j, bool& ok) -> long long {
+    if (axis == 0) {
+      const long long row = (long long)blockIdx.x * LPB + j;  // (y, z) row
+      ok = row < (long long)ny * nz;
+      return row * nx;
+    }
+    const int gx = (blockIdx.x % groups_x) * LPB + j;
+    const long long r = blockIdx.x / groups_x;  // z (axis 1) or y (axis 2)
+    ok = gx < nx;
+    return axis == 1 ? r * NXY + gx : r * nx + gx;
+  };
+  const int tot = LPB * L;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int j, i;
+    if (axis == 0) { j = idx / L; i = idx - j * L; } else { i = idx / LPB; j = idx - i * LPB; }
+    bool ok;
+    const long long b = line_base(j, ok);
+    A[j * LP + i] = ok ? T(double(in[b + i * stride]) - ref) : T(0);
+  }
+  __syncthreads();
+  // explicit side: a (f[i+1]-f[i-1])/2 + b (f[i+2]-f[i-2])/4 + c (f[i+3]-f[i-3])/6
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int j = idx / L, i = idx - j * L;
+    const T* f = A + j * LP;
+    const int p1 = i + 1 >= L ? i + 1 - L : i + 1, m1 = i - 1 < 0 ? i - 1 + L : i - 1;
+    T r = T(lc.A1) * (f[p1] - f[m1]);
+    if (lc.A2 != 0.0) r += T(lc.A2) * (f[lmod(i + 2, L)] - f[lmod(i - 2, L)]);
+    if (lc.A3 != 0.0) r += T(lc.A3) * (f[lmod(i + 3, L)] - f[lmod(i - 3, L)]);
+    B[j * LP + i] = r;
+  }
+  __syncthreads();
+  T* cur = B;
+  T* nxt = A;
+  int s = 1 % L;
+  for (int k = 0; k < lc.nlev; ++k) {
+    const T al = T(lc.alpha[k]), iv = T(lc.inv[k]);
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      const int j = idx / L, i = idx - j * L;
+      const T* d = cur + j * LP;
+      int ip = i + s; if (ip >= L) ip -= L;
+      int im = i - s; if (im < 0) im += L;
+      nxt[j * LP + i] = (d[i] - al * (d[im] + d[ip])) * iv;
+    }
+    __syncthreads();
+    T* t = cur; cur = nxt; nxt = t;
+    s = (2 * s) % L;
+  }
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int j, i;
+    if (axis == 0) { j = idx / L; i = idx - j * L; } else { i = idx / LPB; j = idx - i * LPB; }
+    bool ok;
+    const long long b = line_base(j, ok);
+    if (ok) out[b + i * stride] = cur[j * LP + i];
+  }
+}
+
+template <typename Tin, typename T>
+cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T* out, const LineCoef& lc,
+                      cudaStream_t st) {
+  const int L = axis == 0 ? kp.nx : (axis == 1 ? kp.ny : kp.nz);
+  int LPB = 16;
+  while (LPB > 1 && size_t(2) * LPB * (L + 1) * sizeof(T) > 200 * 1024) LPB /= 2;
+  const size_t smem = size_t(2) * LPB * (L + 1) * sizeof(T);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  static int set_bytes = 0;
+  if (int(smem) > set_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_lines<Tin, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    if (e != cudaSuccess) return e;
+    set_bytes = 220 * 1024;
+  }
+  long long nlines;
+  unsigned grid;
+  if (axis == 0) {
+    nlines = (long long)kp.ny * kp.nz;
+    grid = unsigned((nlines + LPB - 1) / LPB);
+  } else {
+    const int gx = (kp.nx + LPB - 1) / LPB;
+    grid = unsigned((long long)gx * (axis == 1 ? kp.nz : kp.ny));
+  }
+  k_lines<Tin, T><<<grid, 256, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, in, ref, out, lc, LPB);
+  return cudaGetLastError();
+}
+
+constexpr int TXc = 32, TYc = 8, ZCc = 32;
+
+template <class P, int MODE>
+cudaError_t launch_gf(const Launch& c, int D, int* nblocks) {
+  using Tf = typename P::Tf;
+  if (D == 2) {
+    using Sh = Step2DShape<S_CFDS4, P, TXc, TYc>;
+    auto k = k_step2d<S_CFDS4, P, TXc, TYc, MODE>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    dim3 grid((c.kp.nx + TXc - 1) / TXc, (c.kp.ny + TYc - 1) / TYc, 1);
+    if (nblocks) *nblocks = int(grid.x * grid.y);
+    k<<<grid, NT2, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), c.rin, c.rout,
+                                          c.aux, c.fo, c.gi);
+  } else {
+    using Sh = Step3DShape<S_CFDS4, P, TXc, TYc>;
+    auto k = k_step3d<S_CFDS4, P, TXc, TYc, ZCc, MODE>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    dim3 grid((c.kp.nx + TXc - 1) / TXc, (c.kp.ny + TYc - 1) / TYc, (c.kp.nz + ZCc - 1) / ZCc);
+    if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
+    k<<<grid, NT3, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), c.rin, c.rout,
+                                          c.aux, c.fo, c.gi);
+  }
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nblocks) {
+  using Tm = typename P::Tm;
+  using Tc = typename P::Tc;
+  const KParams& kp = c.kp;
+  const int bs = 256;
+  const unsigned g = unsigned((kp.n + bs - 1) / bs);
+  Tm* mu = static_cast<Tm*>(cb.mu);
+  if (cb.lap_order == 4) k_mu_field<Tm, 4><<<g, bs, 0, c.stream>>>(kp, D, c.rin, mu);
+  else if (cb.lap_order == 6) k_mu_field<Tm, 6><<<g, bs, 0, c.stream>>>(kp, D, c.rin, mu);
+  else k_mu_field<Tm, 8><<<g, bs, 0, c.stream>>>(kp, D, c.rin, mu);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  Tm* gmu = static_cast<Tm*>(cb.gmu);
+  Tc* grho = static_cast<Tc*>(cb.grho);
+  for (int ax = 0; ax < D; ++ax) {
+    e = run_lines<Tm, Tm>(ax, kp, mu, 0.0, gmu + size_t(ax) * kp.n, cb.lc, c.stream);
+    if (e != cudaSuccess) return e;
+    e = run_lines<double, Tc>(ax, kp, c.rin, P::DEV ? kp.rho_ref : 0.0, grho + size_t(ax) * kp.n, cb.lc, c.stream);
+    if (e != cudaSuccess) return e;
+  }
+  c.gi.gmu = gmu;
+  c.gi.grho = grho;
+  c.gi.mu = mu;
+  if (mode == MODE_STEP) return launch_gf<P, MODE_STEP>(c, D, nblocks);
+  if (mode == MODE_OBS) return launch_gf<P, MODE_OBS>(c, D, nblocks);
+  return launch_gf<P, MODE_FIELDS>(c, D, nblocks);
+}
+
+}  // namespace
+
+cudaError_t compact_step(const CompactBufs& cb, Launch c, int D, int scheme, int prec, int mode, int* nblocks) {
+  (void)scheme;
+  if (prec == 0) return step_prec<PrecF64>(cb, c, D, mode, nblocks);
+  if (prec == 1) return step_prec<PrecF32>(cb, c, D, mode, nblocks);
+  return step_prec<PrecF32M64>(cb, c, D, mode, nblocks);
+}
+
+}  // namespace lbmd

@@ -1,0 +1,650 @@
+// C ABI of the GB300 chemical-potential multiphase LBM library (include/lbm.h).
+// Host-side handle management, initialisation kernels, the step loop and the
+// observables reduction.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbm.h"
+#include "launch.cuh"
+#include "compact.cuh"
+
+using namespace lbmd;
+
+struct lbm_handle {
+  lbm_params p;
+  int Q = 0, D = 0, prec = 0;
+  long long N = 0;
+  cudaStream_t stream = nullptr;
+  lbm_allocator alloc{};
+  bool own_alloc = false;
+  void* f[2] = {nullptr, nullptr};
+  double* rho[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* rho_snap = nullptr;
+  unsigned long long* d_bad = nullptr;
+  double* d_partials = nullptr;
+  int n_partials = 0;
+  double* d_obs = nullptr;   // 8 doubles
+  long long t = 0, t_snap = 0;
+  KParams kp{};
+  StepFn fn = nullptr;
+  CompactBufs cb{};
+  bool compact = false;
+};
+
+// ------------------------------------------------------------------ allocation
+static void* dalloc(lbm_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  return h->alloc.alloc(bytes, h->alloc.ctx);
+}
+static void dfree(lbm_handle* h, void* p, size_t bytes) {
+  if (p) h->alloc.free(p, bytes == 0 ? 256 : bytes, h->alloc.ctx);
+}
+static void* cuda_alloc_cb(size_t bytes, void*) {
+  void* p = nullptr;
+  return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+static void cuda_free_cb(void* p, size_t, void*) { cudaFree(p); }
+
+static size_t f_bytes(const lbm_handle* h) {
+  return size_t(h->Q) * size_t(h->N) * (h->p.precision == LBM_FP64 ? sizeof(double) : sizeof(float));
+}
+
+// ------------------------------------------------------------------ EOS on the host
+// Carnahan-Starling: p0 = rho R T C0(eta) - a rho^2 with eta = b rho / 4 and
+// C0 = (1 + eta + eta^2 - eta^3)/(1 - eta)^3.  dp0/drho = R T C1(eta) - 2 a rho,
+// C1 = d(eta C0)/d eta = (1 + 4eta + 4eta^2 - 4eta^3 + eta^4)/(1 - eta)^4.
+static double cs_p(double rho, double a, double b, double R, double T) {
+  const double e = 0.25 * b * rho, q = 1.0 - e;
+  return rho * R * T * (1.0 + e * (1.0 + e * (1.0 - e))) / (q * q * q) - a * rho * rho;
+}
+static double cs_c1(double e) {
+  const double q = 1.0 - e;
+  return (1.0 + e * (4.0 + e * (4.0 + e * (-4.0 + e)))) / (q * q * q * q);
+}
+static double cs_c1p(double e) {  // d C1 / d eta
+  const double q = 1.0 - e;
+  const double num = 1.0 + e * (4.0 + e * (4.0 + e * (-4.0 + e)));
+  const double dnum = 4.0 + e * (8.0 + e * (-12.0 + 4.0 * e));
+  return dnum / (q * q * q * q) + 4.0 * num / (q * q * q * q * q);
+}
+static double cs_dp(double rho, double a, double b, double R, double T) {
+  return R * T * cs_c1(0.25 * b * rho) - 2.0 * a * rho;
+}
+static double cs_mub(double rho, double a, double b, double R, double T) {
+  const double e = 0.25 * b * rho, q = 1.0 - e;
+  return R * T * (std::log(rho) + e * (8.0 + e * (-9.0 + 3.0 * e)) / (q * q * q)) - 2.0 * a * rho;
+}
+
+extern "C" int lbm_critical(double a, double b, double R, double* rho_c, double* T_c) {
+  if (!(a > 0 && b > 0 && R > 0) || !rho_c || !T_c) return LBM_EINVAL;
+  // dp0/drho = 0 and d2p0/drho2 = 0  <=>  C1(eta) = eta C1'(eta);  R T_c = 8 a / (b C1'(eta_c))
+  double lo = 1e-8, hi = 0.5;
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (lo + hi);
+    if (cs_c1(m) - m * cs_c1p(m) > 0) lo = m; else hi = m;
+  }
+  const double e = 0.5 * (lo + hi);
+  *rho_c = 4.0 * e / b;
+  *T_c = 8.0 * a / (b * R * cs_c1p(e));
+  return LBM_OK;
+}
+
+// Coexistence by bisection on the common chemical potential m: on the gas
+// branch (0, spinodal_g) and the liquid branch (spinodal_l, 4/b) mu is
+// increasing in rho, so each branch has one root of mu = m; by Gibbs-Duhem
+// (dp = rho dmu) p_gas(m) - p_liq(m) decreases with m, which brackets the
+// equal-pressure level.
+static int maxwell_T(double a, double b, double R, double T, double* rg, double* rl) {
+  double rc, Tc;
+  if (lbm_critical(a, b, R, &rc, &Tc) != LBM_OK) return LBM_EINVAL;
+  if (!(T > 0 && T < Tc)) return LBM_EINVAL;
+  double lo = std::log(rc) - 800.0, hi = std::log(rc);  // ln rho on the gas side
+  for (int it = 0; it < 400; ++it) {
+    const double m = 0.5 * (lo + hi);
+    if (cs_dp(std::exp(m), a, b, R, T) > 0) lo = m; else hi = m;
+  }
+  const double sg = std::exp(lo);
+  lo = rc; hi = 4.0 / b;
+  for (int it = 0; it < 400; ++it) {
+    const double m = 0.5 * (lo + hi);
+    if (cs_dp(m, a, b, R, T) < 0) lo = m; else hi = m;
+  }
+  const double sl = hi;
+  auto gas = [&](double m) {
+    double l = std::log(rc) - 800.0, u = std::log(sg);
+    for (int it = 0; it < 400; ++it) {
+      const double c = 0.5 * (l + u);
+      if (cs_mub(std::exp(c), a, b, R, T) < m) l = c; else u = c;
+    }
+    return std::exp(0.5 * (l + u));
+  };
+  auto liq = [&](double m) {
+    double l = sl, u = 4.0 / b;
+    for (int it = 0; it < 400; ++it) {
+      const double c = 0.5 * (l + u);
+      if (cs_mub(c, a, b, R, T) < m) l = c; else u = c;
+    }
+    return 0.5 * (l + u);
+  };
+  double mlo = cs_mub(sl, a, b, R, T), mhi = cs_mub(sg, a, b, R, T);
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (mlo + mhi);
+    const double g = gas(m), l = liq(m);
+    if (cs_p(g, a, b, R, T) - cs_p(l, a, b, R, T) > 0) mlo = m; else mhi = m;
+    if (mhi - mlo <= 1e-17 * std::fabs(m)) break;
+  }
+  const double m = 0.5 * (mlo + mhi);
+  *rg = gas(m);
+  *rl = liq(m);
+  return LBM_OK;
+}
+
+extern "C" int lbm_maxwell(const lbm_params* p, double* rho_g, double* rho_l) {
+  if (!p || !rho_g || !rho_l) return LBM_EINVAL;
+  double rc, Tc;
+  if (lbm_critical(p->a, p->b, p->R, &rc, &Tc) != LBM_OK) return LBM_EINVAL;
+  return maxwell_T(p->a, p->b, p->R, p->Tr * Tc, rho_g, rho_l);
+}
+
+extern "C" int lbm_lattice_q(int lattice) { return lattice == LBM_D2Q9 ? 9 : (lattice == LBM_D3Q19 ? 19 : 0); }
+
+extern "C" const char* lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "device allocation failed";
+    case LBM_ECUDA: return "CUDA runtime error";
+    case LBM_EUNSTABLE: return "simulation unstable (non-positive or NaN density)";
+    case LBM_ETIMEOUT: return "device-side wait timed out";
+    case LBM_ENOTSUP: return "unsupported lattice/scheme combination";
+    default: return "unknown error";
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+namespace {
+
+__constant__ double c_w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+__constant__ double c_w19[19] = {1.0 / 3,  1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18,
+                                 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36,
+                                 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+struct InitSpec {
+  int kind;  // 0 droplet, 1 slab, 2 radial profile, 3 density array
+  double cx, cy, cz, radius, width, rho_l, rho_g;
+  int axis;
+  const double* r;
+  const double* prof;
+  int nprof;
+  const double* dens;
+};
+
+__device__ double init_density(const InitSpec& s, int x, int y, int z, long long node) {
+  if (s.kind == 3) return s.dens[node];
+  if (s.kind == 1) {
+    const double c = s.axis == 0 ? x - s.cx : (s.axis == 1 ? y - s.cy : z - s.cz);
+    return 0.5 * (s.rho_l + s.rho_g) - 0.5 * (s.rho_l - s.rho_g) * tanh(2.0 * (fabs(c) - 0.5 * s.radius) / s.width);
+  }
+  const double dx = x - s.cx, dy = y - s.cy, dz = z - s.cz;
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  if (s.kind == 0) return 0.5 * (s.rho_l + s.rho_g) - 0.5 * (s.rho_l - s.rho_g) * tanh(2.0 * (r - s.radius) / s.width);
+  // radial profile, linear interpolation
+  if (r <= s.r[0]) return s.prof[0];
+  if (r >= s.r[s.nprof - 1]) return s.prof[s.nprof - 1];
+  int lo = 0, hi = s.nprof - 1;
+  while (hi - lo > 1) {
+    const int m = (lo + hi) / 2;
+    if (s.r[m] < r) lo = m; else hi = m;
+  }
+  const double t = (r - s.r[lo]) / (s.r[hi] - s.r[lo]);
+  return s.prof[lo] + t * (s.prof[hi] - s.prof[lo]);
+}
+
+// f_i = w_i rho0 (u = 0); the density field is the sum of the stored populations
+template <typename Tf>
+__global__ void k_init(KParams p, int Q, InitSpec s, Tf* f, double* rho) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.n) return;
+  const int x = int(n % p.nx), y = int((n / p.nx) % p.ny), z = int(n / ((long long)p.nx * p.ny));
+  const double r0 = init_density(s, x, y, z, n);
+  const double* w = Q == 9 ? c_w9 : c_w19;
+  if constexpr (sizeof(Tf) == 8) {
+    double acc = 0;
+    for (int i = 0; i < Q; ++i) {
+      const double fi = w[i] * r0;
+      f[i * p.n + n] = Tf(fi);
+      acc += fi;
+    }
+    rho[n] = acc;
+  } else {
+    FSum acc;
+    for (int i = 0; i < Q; ++i) {
+      const float d = float(w[i] * (r0 - p.rho_ref));
+      f[i * p.n + n] = d;
+      acc.add(d);
+    }
+    rho[n] = p.rho_ref + acc.value();
+  }
+}
+
+// density field from the stored populations
+template <typename Tf>
+__global__ void k_density(KParams p, int Q, const Tf* f, double* rho) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.n) return;
+  if constexpr (sizeof(Tf) == 8) {
+    double acc = 0;
+    for (int i = 0; i < Q; ++i) acc += double(f[i * p.n + n]);
+    rho[n] = acc;
+  } else {
+    FSum acc;
+    for (int i = 0; i < Q; ++i) acc.add(float(f[i * p.n + n]));
+    rho[n] = p.rho_ref + acc.value();
+  }
+}
+
+// full FP64 populations <-> stored form
+template <typename Tf>
+__global__ void k_export_f(KParams p, int Q, const Tf* f, double* out) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.n) return;
+  const double* w = Q == 9 ? c_w9 : c_w19;
+  for (int i = 0; i < Q; ++i) out[i * p.n + n] = double(f[i * p.n + n]) + (sizeof(Tf) == 8 ? 0.0 : w[i] * p.rho_ref);
+}
+template <typename Tf>
+__global__ void k_import_f(KParams p, int Q, const double* in, Tf* f) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.n) return;
+  const double* w = Q == 9 ? c_w9 : c_w19;
+  for (int i = 0; i < Q; ++i) f[i * p.n + n] = Tf(in[i * p.n + n] - (sizeof(Tf) == 8 ? 0.0 : w[i] * p.rho_ref));
+}
+
+// final reduction of per-CTA observables, fixed order (deterministic)
+__global__ void k_obs_final(const double* part, int nb, const double* rho, long long center, const unsigned long long* bad,
+                            double* out) {
+  __shared__ double red[4][256];
+  double a = 0, b = 0, c = 0, d = 0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    a = fmax(a, part[4 * i]);
+    b = fmax(b, part[4 * i + 1]);
+    c += part[4 * i + 2];
+    d = fmax(d, part[4 * i + 3]);
+  }
+  red[0][threadIdx.x] = a; red[1][threadIdx.x] = b; red[2][threadIdx.x] = c; red[3][threadIdx.x] = d;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + s]);
+      red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + s]);
+      red[2][threadIdx.x] += red[2][threadIdx.x + s];
+      red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = red[0][0]; out[1] = red[1][0]; out[2] = red[2][0]; out[3] = red[3][0];
+    out[4] = rho[center];
+    out[5] = rho[0];
+    unsigned long long bs = *bad;
+    reinterpret_cast<unsigned long long*>(out)[6] = bs;
+  }
+}
+
+inline unsigned grid1(long long n, int bs) { return unsigned((n + bs - 1) / bs); }
+
+}  // namespace
+
+static int ck(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+// ------------------------------------------------------------------ create/destroy
+extern "C" void lbm_destroy(lbm_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  dfree(h, h->f[0], f_bytes(h));
+  dfree(h, h->f[1], f_bytes(h));
+  dfree(h, h->rho[0], h->N * 8);
+  dfree(h, h->rho[1], h->N * 8);
+  dfree(h, h->rho_snap, h->N * 8);
+  dfree(h, h->d_bad, 8);
+  dfree(h, h->d_partials, size_t(h->n_partials) * 4 * 8);
+  dfree(h, h->d_obs, 64);
+  compact_free(h->cb, [&](void* p, size_t b) { dfree(h, p, b); });
+  delete h;
+}
+
+static int validate(const lbm_params* p) {
+  if (!p) return LBM_EINVAL;
+  if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return LBM_EINVAL;
+  if (p->nx < 8 || p->ny < 8) return LBM_EINVAL;
+  if (p->lattice == LBM_D2Q9 && p->nz != 1) return LBM_EINVAL;
+  if (p->lattice == LBM_D3Q19 && p->nz < 8) return LBM_EINVAL;
+  if ((long long)p->nx * p->ny * p->nz > (1LL << 31) / 19) return LBM_EINVAL;
+  if (p->eos != LBM_EOS_CS) return LBM_EINVAL;
+  if (!(p->a > 0 && p->b > 0 && p->R > 0 && p->Tr > 0)) return LBM_EINVAL;
+  if (!(p->k > 0) || !(p->kappa >= 0) || !(p->tau > 0.5)) return LBM_EINVAL;
+  if (p->scheme < LBM_EFDS2 || p->scheme > LBM_E8) return LBM_EINVAL;
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32DEV) return LBM_EINVAL;
+  if (p->scheme == LBM_E8 && p->lattice != LBM_D2Q9) return LBM_ENOTSUP;
+  return LBM_OK;
+}
+
+extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allocator* alloc, lbm_handle** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  int rc = validate(params);
+  if (rc != LBM_OK) return rc;
+  lbm_handle* h = new (std::nothrow) lbm_handle();
+  if (!h) return LBM_ENOMEM;
+  h->p = *params;
+  h->Q = lbm_lattice_q(params->lattice);
+  h->D = params->lattice == LBM_D2Q9 ? 2 : 3;
+  h->N = (long long)params->nx * params->ny * params->nz;
+  h->stream = static_cast<cudaStream_t>(stream);
+  if (alloc && alloc->alloc && alloc->free) {
+    h->alloc = *alloc;
+  } else {
+    h->alloc.alloc = cuda_alloc_cb;
+    h->alloc.free = cuda_free_cb;
+    h->alloc.ctx = nullptr;
+    h->own_alloc = true;
+  }
+  double rc_, Tc;
+  lbm_critical(params->a, params->b, params->R, &rc_, &Tc);
+  const double T = params->Tr * Tc;
+  double rho_ref = 0.0;
+  if (params->precision == LBM_FP32DEV) {
+    rho_ref = params->rho_ref;
+    if (!(rho_ref > 0)) {
+      double rg, rl;
+      if (maxwell_T(params->a, params->b, params->R, T, &rg, &rl) != LBM_OK) { delete h; return LBM_EINVAL; }
+      rho_ref = rg;
+    }
+  }
+  h->prec = params->precision == LBM_FP64 ? 0 : (params->mu_fp64 ? 2 : 1);
+  h->compact = (params->scheme >= LBM_CFDS4 && params->scheme <= LBM_OCFDS4);
+  h->kp.nx = params->nx; h->kp.ny = params->ny; h->kp.nz = params->nz; h->kp.n = h->N;
+  h->kp.RT = params->R * T; h->kp.b4 = 0.25 * params->b; h->kp.two_a = 2.0 * params->a;
+  h->kp.k2 = params->k * params->k; h->kp.kappa = params->kappa; h->kp.omega = 1.0 / params->tau;
+  h->kp.rho_ref = rho_ref;
+  h->p.rho_ref = rho_ref;
+  if (h->compact) {
+    h->fn = nullptr;
+  } else {
+    h->fn = h->D == 2 ? step2d_fn(params->scheme, h->prec) : step3d_fn(params->scheme, h->prec);
+    if (!h->fn) { delete h; return LBM_ENOTSUP; }
+  }
+  const size_t fb = f_bytes(h);
+  h->f[0] = dalloc(h, fb);
+  h->f[1] = dalloc(h, fb);
+  h->rho[0] = static_cast<double*>(dalloc(h, h->N * 8));
+  h->rho[1] = static_cast<double*>(dalloc(h, h->N * 8));
+  h->rho_snap = static_cast<double*>(dalloc(h, h->N * 8));
+  h->d_bad = static_cast<unsigned long long*>(dalloc(h, 8));
+  h->d_obs = static_cast<double*>(dalloc(h, 64));
+  // partials: one per CTA of the observation pass (upper bound over tilings used)
+  h->n_partials = int((params->nx / 8 + 2) * (params->ny / 8 + 2) * (params->lattice == LBM_D2Q9 ? 1 : (params->nz / 8 + 2)));
+  h->d_partials = static_cast<double*>(dalloc(h, size_t(h->n_partials) * 4 * 8));
+  bool ok = h->f[0] && h->f[1] && h->rho[0] && h->rho[1] && h->rho_snap && h->d_bad && h->d_obs && h->d_partials;
+  if (ok && h->compact) {
+    rc = compact_alloc(h->cb, h->kp, h->D, params->scheme, h->prec, [&](size_t b) { return dalloc(h, b); });
+    if (rc != LBM_OK) ok = false;
+  }
+  if (!ok) {
+    lbm_destroy(h);
+    return LBM_ENOMEM;
+  }
+  unsigned long long init = ULLONG_MAX;
+  if (cudaMemcpyAsync(h->d_bad, &init, 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    lbm_destroy(h);
+    return LBM_ECUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+// ------------------------------------------------------------------ init
+static int run_init(lbm_handle* h, const InitSpec& s) {
+  const int bs = 256;
+  if (h->p.precision == LBM_FP64)
+    k_init<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, s, static_cast<double*>(h->f[0]), h->rho[0]);
+  else
+    k_init<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, s, static_cast<float*>(h->f[0]), h->rho[0]);
+  h->cur = 0;
+  h->t = 0;
+  h->t_snap = 0;
+  unsigned long long init = ULLONG_MAX;
+  if (cudaMemcpyAsync(h->d_bad, &init, 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return LBM_ECUDA;
+  if (cudaMemcpyAsync(h->rho_snap, h->rho[0], h->N * 8, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+    return LBM_ECUDA;
+  // host arrays referenced by the spec must outlive the kernel: synchronise
+  return ck(cudaStreamSynchronize(h->stream));
+}
+
+static int default_dens(lbm_handle* h, double& rl, double& rg) {
+  if (rl > 0 && rg > 0) return LBM_OK;
+  double g, l;
+  if (lbm_maxwell(&h->p, &g, &l) != LBM_OK) return LBM_EINVAL;
+  rl = l;
+  rg = g;
+  return LBM_OK;
+}
+
+static void set_center(lbm_handle* h, InitSpec& s, const double* c) {
+  s.cx = c ? c[0] : double(h->p.nx / 2);
+  s.cy = c ? c[1] : double(h->p.ny / 2);
+  s.cz = c ? c[2] : double(h->p.nz / 2);
+  if (h->D == 2) s.cz = 0;
+}
+
+extern "C" int lbm_init_droplet(lbm_handle* h, const double center[3], double radius, double width, double rho_l,
+                                double rho_g) {
+  if (!h || !(width > 0) || !(radius >= 0)) return LBM_EINVAL;
+  if (default_dens(h, rho_l, rho_g) != LBM_OK) return LBM_EINVAL;
+  InitSpec s{};
+  s.kind = 0;
+  set_center(h, s, center);
+  s.radius = radius; s.width = width; s.rho_l = rho_l; s.rho_g = rho_g;
+  return run_init(h, s);
+}
+
+extern "C" int lbm_init_slab(lbm_handle* h, int axis, double thickness, double width, double rho_l, double rho_g) {
+  if (!h || axis < 0 || axis >= h->D || !(width > 0) || !(thickness >= 0)) return LBM_EINVAL;
+  if (default_dens(h, rho_l, rho_g) != LBM_OK) return LBM_EINVAL;
+  InitSpec s{};
+  s.kind = 1;
+  s.axis = axis;
+  set_center(h, s, nullptr);
+  s.radius = thickness; s.width = width; s.rho_l = rho_l; s.rho_g = rho_g;
+  return run_init(h, s);
+}
+
+extern "C" int lbm_init_profile(lbm_handle* h, const double center[3], const double* r, const double* rho, int n) {
+  if (!h || !r || !rho || n < 2) return LBM_EINVAL;
+  for (int j = 0; j < n; ++j) {
+    if (!(rho[j] > 0)) return LBM_EINVAL;
+    if (j > 0 && !(r[j] > r[j - 1])) return LBM_EINVAL;
+  }
+  double* d = static_cast<double*>(dalloc(h, size_t(2 * n) * 8));
+  if (!d) return LBM_ENOMEM;
+  int rc = ck(cudaMemcpyAsync(d, r, size_t(n) * 8, cudaMemcpyHostToDevice, h->stream));
+  if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(d + n, rho, size_t(n) * 8, cudaMemcpyHostToDevice, h->stream));
+  if (rc == LBM_OK) {
+    InitSpec s{};
+    s.kind = 2;
+    set_center(h, s, center);
+    s.r = d; s.prof = d + n; s.nprof = n;
+    rc = run_init(h, s);
+  }
+  cudaStreamSynchronize(h->stream);
+  dfree(h, d, size_t(2 * n) * 8);
+  return rc;
+}
+
+extern "C" int lbm_init_density(lbm_handle* h, const double* host_rho) {
+  if (!h || !host_rho) return LBM_EINVAL;
+  // stage through the second density buffer (it is rewritten by the first step)
+  int rc = ck(cudaMemcpyAsync(h->rho[1], host_rho, h->N * 8, cudaMemcpyHostToDevice, h->stream));
+  if (rc != LBM_OK) return rc;
+  InitSpec s{};
+  s.kind = 3;
+  s.dens = h->rho[1];
+  return run_init(h, s);
+}
+
+extern "C" int lbm_set_f(lbm_handle* h, const double* host_f) {
+  if (!h || !host_f) return LBM_EINVAL;
+  const size_t bytes = size_t(h->Q) * h->N * 8;
+  double* tmp = static_cast<double*>(dalloc(h, bytes));
+  if (!tmp) return LBM_ENOMEM;
+  int rc = ck(cudaMemcpyAsync(tmp, host_f, bytes, cudaMemcpyHostToDevice, h->stream));
+  const int bs = 256;
+  if (rc == LBM_OK) {
+    h->cur = 0;
+    if (h->p.precision == LBM_FP64) {
+      k_import_f<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, tmp, static_cast<double*>(h->f[0]));
+      k_density<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, static_cast<double*>(h->f[0]), h->rho[0]);
+    } else {
+      k_import_f<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, tmp, static_cast<float*>(h->f[0]));
+      k_density<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, static_cast<float*>(h->f[0]), h->rho[0]);
+    }
+    rc = ck(cudaGetLastError());
+  }
+  h->t = 0;
+  h->t_snap = 0;
+  unsigned long long init = ULLONG_MAX;
+  if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(h->d_bad, &init, 8, cudaMemcpyHostToDevice, h->stream));
+  if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(h->rho_snap, h->rho[0], h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
+  cudaStreamSynchronize(h->stream);
+  dfree(h, tmp, bytes);
+  return rc;
+}
+
+// ------------------------------------------------------------------ stepping
+static Launch make_launch(lbm_handle* h, int out_buf) {
+  Launch c{};
+  c.kp = h->kp;
+  c.fin = h->f[h->cur];
+  c.fout = h->f[out_buf];
+  c.rin = h->rho[h->cur];
+  c.rout = h->rho[out_buf];
+  c.aux.t = h->t;
+  c.aux.bad_step = h->d_bad;
+  c.aux.partials = h->d_partials;
+  c.aux.rho_snap = h->rho_snap;
+  c.stream = h->stream;
+  return c;
+}
+
+extern "C" int lbm_step(lbm_handle* h, long long n) {
+  if (!h || n < 0) return LBM_EINVAL;
+  for (long long s = 0; s < n; ++s) {
+    Launch c = make_launch(h, 1 - h->cur);
+    cudaError_t e;
+    if (h->compact)
+      e = compact_step(h->cb, c, h->D, h->p.scheme, h->prec, MODE_STEP, nullptr);
+    else
+      e = h->fn(c, MODE_STEP, nullptr);
+    if (e != cudaSuccess) return LBM_ECUDA;
+    h->cur = 1 - h->cur;
+    h->t += 1;
+  }
+  return LBM_OK;
+}
+
+extern "C" long long lbm_get_step(const lbm_handle* h) { return h ? h->t : -1; }
+
+extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
+  if (!h || !out) return LBM_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  Launch c = make_launch(h, h->cur);
+  c.fout = nullptr;
+  c.rout = nullptr;
+  int nb = 0;
+  cudaError_t e = h->compact ? compact_step(h->cb, c, h->D, h->p.scheme, h->prec, MODE_OBS, &nb)
+                             : h->fn(c, MODE_OBS, &nb);
+  if (e != cudaSuccess) return LBM_ECUDA;
+  if (nb > h->n_partials) return LBM_ECUDA;
+  const long long center =
+      (long long)(h->p.nz / 2) * h->p.nx * h->p.ny + (long long)(h->p.ny / 2) * h->p.nx + h->p.nx / 2;
+  k_obs_final<<<1, 256, 0, h->stream>>>(h->d_partials, nb, h->rho[h->cur], center, h->d_bad, h->d_obs);
+  double host[8];
+  if (cudaMemcpyAsync(host, h->d_obs, 64, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return LBM_ECUDA;
+  if (cudaMemcpyAsync(h->rho_snap, h->rho[h->cur], h->N * 8, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+    return LBM_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+  unsigned long long bad;
+  std::memcpy(&bad, &host[6], 8);
+  out->max_v = host[0];
+  out->max_u = host[1];
+  out->mass = host[2];
+  out->max_drho = h->t > h->t_snap ? host[3] / double(h->t - h->t_snap) : 0.0;
+  out->rho_center = host[4];
+  out->rho_corner = host[5];
+  out->step = h->t;
+  out->status = LBM_OK;
+  h->t_snap = h->t;
+  if (bad != ULLONG_MAX) {
+    out->status = LBM_EUNSTABLE;
+    out->step = (long long)bad;
+    return LBM_EUNSTABLE;
+  }
+  return LBM_OK;
+}
+
+extern "C" int lbm_get_density(lbm_handle* h, double* host_rho) {
+  if (!h || !host_rho) return LBM_EINVAL;
+  int rc = ck(cudaMemcpyAsync(host_rho, h->rho[h->cur], h->N * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (rc == LBM_OK) rc = ck(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+extern "C" int lbm_get_f(lbm_handle* h, double* host_f) {
+  if (!h || !host_f) return LBM_EINVAL;
+  const size_t bytes = size_t(h->Q) * h->N * 8;
+  double* tmp = static_cast<double*>(dalloc(h, bytes));
+  if (!tmp) return LBM_ENOMEM;
+  const int bs = 256;
+  if (h->p.precision == LBM_FP64)
+    k_export_f<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, static_cast<double*>(h->f[h->cur]), tmp);
+  else
+    k_export_f<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, static_cast<float*>(h->f[h->cur]), tmp);
+  int rc = ck(cudaGetLastError());
+  if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(host_f, tmp, bytes, cudaMemcpyDeviceToHost, h->stream));
+  cudaStreamSynchronize(h->stream);
+  dfree(h, tmp, bytes);
+  return rc;
+}
+
+extern "C" int lbm_get_force(lbm_handle* h, double* host_F, double* host_mu) {
+  if (!h) return LBM_EINVAL;
+  const size_t bytes = size_t(h->D + 1) * h->N * 8;
+  double* tmp = static_cast<double*>(dalloc(h, bytes));
+  if (!tmp) return LBM_ENOMEM;
+  Launch c = make_launch(h, h->cur);
+  c.fout = nullptr;
+  c.rout = nullptr;
+  c.fo.F = tmp;
+  c.fo.mu = tmp + size_t(h->D) * h->N;
+  cudaError_t e = h->compact ? compact_step(h->cb, c, h->D, h->p.scheme, h->prec, MODE_FIELDS, nullptr)
+                             : h->fn(c, MODE_FIELDS, nullptr);
+  int rc = ck(e);
+  if (rc == LBM_OK && host_F) rc = ck(cudaMemcpyAsync(host_F, tmp, size_t(h->D) * h->N * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (rc == LBM_OK && host_mu) rc = ck(cudaMemcpyAsync(host_mu, c.fo.mu, size_t(h->N) * 8, cudaMemcpyDeviceToHost, h->stream));
+  cudaStreamSynchronize(h->stream);
+  dfree(h, tmp, bytes);
+  return rc;
+}
+
+extern "C" int lbm_device_state(lbm_handle* h, void** f, void** rho) {
+  if (!h) return LBM_EINVAL;
+  if (f) *f = h->f[h->cur];
+  if (rho) *rho = h->rho[h->cur];
+  return LBM_OK;
+}

@@ -1,0 +1,260 @@
+// Device-side building blocks of the chemical-potential multiphase LBM step:
+// lattice tables, the Carnahan-Starling chemical potential, the difference
+// stencils of Sec. 2.3 and the BGK + exact-difference-method collision.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmd {
+
+// ------------------------------------------------------------------ lattices
+// D2Q9 in the order of Eq. 2; D3Q19: rest, +-x, +-y, +-z, twelve edges.
+template <int LAT>
+struct Lattice;
+
+template <>
+struct Lattice<0> {
+  static constexpr int Q = 9, D = 2;
+  __host__ __device__ static constexpr int ex(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
+  __host__ __device__ static constexpr int ey(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0; }
+  __host__ __device__ static constexpr int ez(int) { return 0; }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+};
+
+template <>
+struct Lattice<1> {
+  static constexpr int Q = 19, D = 3;
+  // rows: rest; +x -x +y -y +z -z; (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+  //       (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+  __host__ __device__ static constexpr int ex(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1 : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int ey(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1 : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int ez(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1 : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+};
+
+// ------------------------------------------------------------------ precision policies
+// FP64: everything double.  FP32DEV: populations stored as f_i - w_i rho_ref in
+// float, collision and stencils in float, density field double; Tm is the type
+// of the chemical potential.
+struct PrecF64 {
+  using Tf = double;  // stored population
+  using Tc = double;  // collision / force arithmetic
+  using Ts = double;  // density stencil operand
+  using Tm = double;  // chemical potential
+  static constexpr bool DEV = false;
+};
+struct PrecF32 {
+  using Tf = float;
+  using Tc = float;
+  using Ts = float;
+  using Tm = float;
+  static constexpr bool DEV = true;
+};
+struct PrecF32M64 {
+  using Tf = float;
+  using Tc = float;
+  using Ts = float;
+  using Tm = double;
+  static constexpr bool DEV = true;
+};
+
+// ------------------------------------------------------------------ parameters
+struct KParams {
+  int nx, ny, nz;
+  long long n;            // nodes
+  double RT, b4, two_a;   // R*T, b/4, 2a of the CS chemical potential
+  double k2, kappa;       // k^2 and kappa-hat (Eq. 16)
+  double omega;           // 1/tau
+  double rho_ref;         // FP32DEV reference density (0 in FP64 mode)
+};
+
+struct StepAux {
+  long long t;                     // step index of the state being advanced
+  unsigned long long* bad_step;    // atomicMin target: first step with rho <= 0 or NaN
+  double* partials;                // observables: per-block partial results
+  const double* rho_snap;          // observables: density at the previous observation
+};
+
+__device__ __forceinline__ float lg(float x) { return logf(x); }
+__device__ __forceinline__ double lg(double x) { return log(x); }
+
+// Bulk chemical potential psi'(rho) of the Carnahan-Starling fluid, from
+// Eq. 10 and Eq. 13:  R T [ln rho + eta (8 - 9 eta + 3 eta^2)/(1 - eta)^3] - 2 a rho.
+template <typename T>
+__device__ __forceinline__ T cs_mu(T rho, T RT, T b4, T two_a) {
+  T eta = b4 * rho;
+  T om = T(1) - eta;
+  T hs = eta * (T(8) + eta * (T(-9) + T(3) * eta)) / (om * om * om);
+  return RT * (lg(rho) + hs) - two_a * rho;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ------------------------------------------------------------------ difference stencils
+// Line schemes (Eq. 18-20): derivative = sum_m g(m) (phi[+m] - phi[-m]);
+// matching-order central second derivative sum_m l(m) (phi[+m] + phi[-m]) + l(0) phi.
+// Isotropic schemes (Eq. 25): gradient sum_i w(|e_i|^2) e_i phi(x + e_i),
+// Laplacian 2 sum_i w(|e_i|^2) (phi(x + e_i) - phi(x)).
+enum { S_EFDS2 = 0, S_EFDS4 = 1, S_EFDS6 = 2, S_CFDS4 = 3, S_CFDS6 = 4, S_CFDS8 = 5, S_OCFDS4 = 6, S_E4 = 7, S_E8 = 8 };
+
+template <int S>
+struct Sch;
+
+// GF: gradients are read from precomputed fields (compact schemes, solved by
+// line kernels); the fused kernel then needs no stencil halo (R = 0).
+template <>
+struct Sch<S_EFDS2> {
+  static constexpr int R = 1;
+  static constexpr bool ISO = false, GF = false;
+  __host__ __device__ static constexpr double g(int) { return 0.5; }
+  __host__ __device__ static constexpr double l(int m) { return m == 0 ? -2.0 : 1.0; }
+};
+template <>
+struct Sch<S_EFDS4> {
+  static constexpr int R = 2;
+  static constexpr bool ISO = false, GF = false;
+  __host__ __device__ static constexpr double g(int m) { return m == 1 ? 2.0 / 3.0 : -1.0 / 12.0; }
+  __host__ __device__ static constexpr double l(int m) { return m == 0 ? -2.5 : (m == 1 ? 4.0 / 3.0 : -1.0 / 12.0); }
+};
+template <>
+struct Sch<S_EFDS6> {
+  static constexpr int R = 3;
+  static constexpr bool ISO = false, GF = false;
+  __host__ __device__ static constexpr double g(int m) { return m == 1 ? 0.75 : (m == 2 ? -0.15 : 1.0 / 60.0); }
+  __host__ __device__ static constexpr double l(int m) {
+    return m == 0 ? -49.0 / 18.0 : (m == 1 ? 1.5 : (m == 2 ? -0.15 : 1.0 / 90.0));
+  }
+};
+// isotropic: weight of offset (dx, dy, dz); 0 outside the stencil
+template <>
+struct Sch<S_E4> {
+  static constexpr int R = 1;
+  static constexpr bool ISO = true, GF = false;
+  __host__ __device__ static constexpr double w2d(int dx, int dy) {
+    return (dx * dx + dy * dy == 1) ? 1.0 / 3.0 : (dx * dx + dy * dy == 2 ? 1.0 / 12.0 : 0.0);
+  }
+  __host__ __device__ static constexpr double w3d(int dx, int dy, int dz) {
+    return (dx * dx + dy * dy + dz * dz == 1) ? 1.0 / 6.0 : (dx * dx + dy * dy + dz * dz == 2 ? 1.0 / 12.0 : 0.0);
+  }
+};
+template <>
+struct Sch<S_E8> {
+  static constexpr int R = 2;
+  static constexpr bool ISO = true, GF = false;
+  __host__ __device__ static constexpr double w2d(int dx, int dy) {
+    return (dx * dx + dy * dy == 1) ? 4.0 / 21.0
+         : (dx * dx + dy * dy == 2) ? 4.0 / 45.0
+         : (dx * dx + dy * dy == 4) ? 1.0 / 60.0
+         : (dx * dx + dy * dy == 5) ? 2.0 / 315.0
+         : (dx * dx + dy * dy == 8) ? 1.0 / 5040.0 : 0.0;
+  }
+  __host__ __device__ static constexpr double w3d(int, int, int) { return 0.0; }
+};
+
+// compact schemes in the fused kernel: gradients come from fields
+template <>
+struct Sch<S_CFDS4> {
+  static constexpr int R = 0;
+  static constexpr bool ISO = false, GF = true;
+  __host__ __device__ static constexpr double g(int) { return 0.0; }
+  __host__ __device__ static constexpr double l(int) { return 0.0; }
+};
+
+// precomputed gradient fields (component-major, D*N) and mu (N) for GF schemes
+struct GradIn {
+  const void* gmu;
+  const void* grho;
+  const void* mu;
+};
+
+// 2D gradient and Laplacian on a row-major shared array at (cx, cy), row stride W.
+template <int S, typename T, typename A>
+__device__ __forceinline__ void grad2d(const A* s, int W, int cx, int cy, T& gx, T& gy) {
+  using Sc = Sch<S>;
+  constexpr int R = Sc::R;
+  T ax = 0, ay = 0;
+  if constexpr (Sc::ISO) {
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx) {
+        const double w = Sc::w2d(dx, dy);
+        if (w != 0.0) {
+          T v = T(s[(cy + dy) * W + cx + dx]);
+          if (dx != 0) ax += T(w * dx) * v;
+          if (dy != 0) ay += T(w * dy) * v;
+        }
+      }
+  } else {
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+      ax += T(Sc::g(m)) * (T(s[cy * W + cx + m]) - T(s[cy * W + cx - m]));
+      ay += T(Sc::g(m)) * (T(s[(cy + m) * W + cx]) - T(s[(cy - m) * W + cx]));
+    }
+  }
+  gx = ax;
+  gy = ay;
+}
+
+template <int S, typename T, typename A>
+__device__ __forceinline__ T lap2d(const A* s, int W, int cx, int cy) {
+  using Sc = Sch<S>;
+  constexpr int R = Sc::R;
+  T c = T(s[cy * W + cx]);
+  T acc = 0;
+  if constexpr (Sc::ISO) {
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx) {
+        const double w = Sc::w2d(dx, dy);
+        if (w != 0.0) acc += T(2.0 * w) * (T(s[(cy + dy) * W + cx + dx]) - c);
+      }
+  } else {
+    acc = T(2.0 * Sc::l(0)) * c;
+#pragma unroll
+    for (int m = 1; m <= R; ++m)
+      acc += T(Sc::l(m)) * ((T(s[cy * W + cx + m]) + T(s[cy * W + cx - m])) + (T(s[(cy + m) * W + cx]) + T(s[(cy - m) * W + cx])));
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------------ collision
+// Post-collision population in deviation form (rho_ref = 0 gives the plain form):
+//   d*_i = (1 - omega) d_i + omega w_i (rho - rho_ref) + w_i rho [omega A_i(u) + A_i(u + du) - A_i(u)],
+//   A_i(U) = 3 e_i.U + 4.5 (e_i.U)^2 - 1.5 U.U,
+// which is f_i - (f_i - f_i^eq(rho,u))/tau + [f_i^eq(rho,u+du) - f_i^eq(rho,u)] (Eq. 1, 6, 8)
+// with f_i^eq - w_i rho_ref written out.
+template <int LAT, typename T>
+__device__ __forceinline__ T coll_one(int i, T d, T dr, T rho, T omega, T ux, T uy, T uz, T vx, T vy, T vz) {
+  using L = Lattice<LAT>;
+  const T ei_u = T(L::ex(i)) * ux + T(L::ey(i)) * uy + T(L::ez(i)) * uz;
+  const T ei_v = T(L::ex(i)) * vx + T(L::ey(i)) * vy + T(L::ez(i)) * vz;
+  const T uu = ux * ux + uy * uy + uz * uz;
+  const T vv = vx * vx + vy * vy + vz * vz;
+  const T Au = T(3) * ei_u + T(4.5) * ei_u * ei_u - T(1.5) * uu;
+  const T Av = T(3) * ei_v + T(4.5) * ei_v * ei_v - T(1.5) * vv;
+  const T w = T(L::w(i));
+  return (T(1) - omega) * d + omega * w * dr + w * rho * (omega * Au + Av - Au);
+}
+
+// Error-free float summation (TwoSum accumulation) used for densities in
+// FP32DEV mode: returns s_hi + s_lo ~= exact sum of the terms.
+struct FSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t = s + x;
+    float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+}  // namespace lbmd

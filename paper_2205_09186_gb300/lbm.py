@@ -1,0 +1,240 @@
+"""ctypes binding of include/lbm.h (argument marshalling only).
+
+Every function of the C ABI is exposed under the same name.  PyTorch provides
+device memory (through an lbm_allocator backed by its caching allocator) and
+the CUDA stream; all arithmetic runs in liblbm.so.  Importing this module on
+a machine without the built library raises ImportError: there is no CPU path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_EOS_CS = 0
+SCHEMES = {"EFDS2": 0, "EFDS4": 1, "EFDS6": 2, "CFDS4": 3, "CFDS6": 4, "CFDS8": 5, "OCFDS4": 6, "E4": 7, "E8": 8}
+LBM_FP64, LBM_FP32DEV = 0, 1
+
+
+class lbm_params(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("eos", C.c_int),
+                ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("Tr", C.c_double),
+                ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double),
+                ("scheme", C.c_int), ("precision", C.c_int), ("mu_fp64", C.c_int), ("rho_ref", C.c_double)]
+
+
+class lbm_obs(C.Structure):
+    _fields_ = [("max_v", C.c_double), ("max_u", C.c_double), ("rho_center", C.c_double),
+                ("rho_corner", C.c_double), ("mass", C.c_double), ("max_drho", C.c_double),
+                ("step", C.c_longlong), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class lbm_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+_dp = C.POINTER(C.c_double)
+_h = C.c_void_p
+
+# name -> (restype, argtypes); every entry point declared in include/lbm.h
+SIGNATURES = {
+    "lbm_create": (C.c_int, [C.POINTER(lbm_params), C.c_void_p, C.POINTER(lbm_allocator), C.POINTER(C.c_void_p)]),
+    "lbm_destroy": (None, [_h]),
+    "lbm_init_droplet": (C.c_int, [_h, _dp, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "lbm_init_slab": (C.c_int, [_h, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "lbm_init_profile": (C.c_int, [_h, _dp, _dp, _dp, C.c_int]),
+    "lbm_init_density": (C.c_int, [_h, _dp]),
+    "lbm_set_f": (C.c_int, [_h, _dp]),
+    "lbm_step": (C.c_int, [_h, C.c_longlong]),
+    "lbm_observables": (C.c_int, [_h, C.POINTER(lbm_obs)]),
+    "lbm_get_density": (C.c_int, [_h, _dp]),
+    "lbm_get_f": (C.c_int, [_h, _dp]),
+    "lbm_get_force": (C.c_int, [_h, _dp, _dp]),
+    "lbm_get_step": (C.c_longlong, [_h]),
+    "lbm_device_state": (C.c_int, [_h, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "lbm_critical": (C.c_int, [C.c_double, C.c_double, C.c_double, _dp, _dp]),
+    "lbm_maxwell": (C.c_int, [C.POINTER(lbm_params), _dp, _dp]),
+    "lbm_lattice_q": (C.c_int, [C.c_int]),
+    "lbm_strerror": (C.c_char_p, [C.c_int]),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load liblbm.so (built by paper_2205_09186_gb300.build); no fallback."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("liblbm.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, lib().lbm_strerror(code).decode(), code))
+        self.code = code
+
+
+def check(rc, what):
+    if rc != LBM_OK:
+        raise LBMError(rc, what)
+    return rc
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_params(lattice=LBM_D2Q9, nx=64, ny=64, nz=1, a=1.0, b=4.0, R=1.0, Tr=0.7, k=0.25, kappa=0.1, tau=1.0,
+                scheme="EFDS2", precision=LBM_FP64, mu_fp64=0, rho_ref=0.0):
+    s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    return lbm_params(lattice, nx, ny, nz, LBM_EOS_CS, a, b, R, Tr, k, kappa, tau, s, precision, int(mu_fp64), rho_ref)
+
+
+def lbm_critical(a=1.0, b=4.0, R=1.0):
+    rc, Tc = C.c_double(), C.c_double()
+    check(lib().lbm_critical(a, b, R, C.byref(rc), C.byref(Tc)), "lbm_critical")
+    return rc.value, Tc.value
+
+
+def lbm_maxwell(params):
+    g, l = C.c_double(), C.c_double()
+    check(lib().lbm_maxwell(C.byref(params), C.byref(g), C.byref(l)), "lbm_maxwell")
+    return g.value, l.value
+
+
+class TorchAllocator:
+    """lbm_allocator backed by PyTorch's CUDA caching allocator."""
+
+    def __init__(self, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = stream
+
+        def _alloc(nbytes, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:  # out of memory -> NULL -> LBM_ENOMEM
+                return None
+
+        def _free(ptr, nbytes, ctx):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.struct = lbm_allocator(self._a, self._f, None)
+
+
+class Sim:
+    """One periodic simulation handle (C ABI: lbm_create ... lbm_destroy)."""
+
+    def __init__(self, params=None, stream=None, allocator="torch", **kw):
+        self.params = params if params is not None else make_params(**kw)
+        self.Q = lib().lbm_lattice_q(self.params.lattice)
+        self.D = 2 if self.params.lattice == LBM_D2Q9 else 3
+        p = self.params
+        self.shape = (p.ny, p.nx) if self.D == 2 else (p.nz, p.ny, p.nx)
+        self.N = p.nx * p.ny * p.nz
+        st = None
+        self._alloc = None
+        if stream is not None:
+            st = C.c_void_p(int(stream))
+        if allocator == "torch":
+            import torch
+            if stream is None:
+                st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+            self._alloc = TorchAllocator(stream=torch.cuda.current_stream() if stream is None else None)
+        h = C.c_void_p()
+        check(lib().lbm_create(C.byref(p), st, C.byref(self._alloc.struct) if self._alloc else None, C.byref(h)),
+              "lbm_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def lbm_init_droplet(self, radius, width=10.0, center=None, rho_l=0.0, rho_g=0.0):
+        c = _f64(center) if center is not None else None
+        return check(lib().lbm_init_droplet(self.h, _ptr(c) if c is not None else None, radius, width, rho_l, rho_g),
+                     "lbm_init_droplet")
+
+    def lbm_init_slab(self, axis, thickness, width=10.0, rho_l=0.0, rho_g=0.0):
+        return check(lib().lbm_init_slab(self.h, axis, thickness, width, rho_l, rho_g), "lbm_init_slab")
+
+    def lbm_init_profile(self, r, rho, center=None):
+        r, rho = _f64(r), _f64(rho)
+        c = _f64(center) if center is not None else None
+        return check(lib().lbm_init_profile(self.h, _ptr(c) if c is not None else None, _ptr(r), _ptr(rho), r.size),
+                     "lbm_init_profile")
+
+    def lbm_init_density(self, rho):
+        rho = _f64(rho).reshape(-1)
+        assert rho.size == self.N
+        return check(lib().lbm_init_density(self.h, _ptr(rho)), "lbm_init_density")
+
+    def lbm_set_f(self, f):
+        f = _f64(f).reshape(-1)
+        assert f.size == self.Q * self.N
+        return check(lib().lbm_set_f(self.h, _ptr(f)), "lbm_set_f")
+
+    def lbm_step(self, n=1):
+        return check(lib().lbm_step(self.h, n), "lbm_step")
+
+    def lbm_observables(self, raise_unstable=False):
+        o = lbm_obs()
+        rc = lib().lbm_observables(self.h, C.byref(o))
+        if rc not in (LBM_OK, LBM_EUNSTABLE) or (raise_unstable and rc == LBM_EUNSTABLE):
+            check(rc, "lbm_observables")
+        return o.as_dict()
+
+    def lbm_get_density(self):
+        out = np.empty(self.shape)
+        check(lib().lbm_get_density(self.h, _ptr(out)), "lbm_get_density")
+        return out
+
+    def lbm_get_f(self):
+        out = np.empty((self.Q,) + self.shape)
+        check(lib().lbm_get_f(self.h, _ptr(out)), "lbm_get_f")
+        return out
+
+    def lbm_get_force(self):
+        F = np.empty((self.D,) + self.shape)
+        mu = np.empty(self.shape)
+        check(lib().lbm_get_force(self.h, _ptr(F), _ptr(mu)), "lbm_get_force")
+        return F, mu
+
+    def lbm_get_step(self):
+        return lib().lbm_get_step(self.h)
+
+    def lbm_device_state(self):
+        f, r = C.c_void_p(), C.c_void_p()
+        check(lib().lbm_device_state(self.h, C.byref(f), C.byref(r)), "lbm_device_state")
+        return f.value, r.value

@@ -1,0 +1,61 @@
+"""CPU-side checks of the C ABI library: it builds for sm_103a, loads, and
+exports every entry point declared in include/lbm.h (no GPU calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(lbm_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import paper_2205_09186_gb300 as pkg
+    return pkg.build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2205_09186_gb300 import lbm
+    assert set(declared_functions()) <= set(lbm.SIGNATURES)
+
+
+def test_host_only_entry_points(libpath):
+    # the EOS helpers of the C ABI run on the host and need no GPU
+    from paper_2205_09186_gb300 import lbm
+    import oracle as O
+    rc, Tc = lbm.lbm_critical()
+    orc, oTc = O.cs_critical()
+    assert abs(rc - orc) < 1e-12 and abs(Tc - oTc) < 1e-14
+    for tr in (0.9, 0.7, 0.5, 0.3, 0.2):
+        g, l = lbm.lbm_maxwell(lbm.make_params(Tr=tr))
+        og, ol = O.maxwell_tr(tr)
+        assert abs(g / og - 1) < 1e-9 and abs(l / ol - 1) < 1e-12
+    assert lbm.lib().lbm_lattice_q(0) == 9 and lbm.lib().lbm_lattice_q(1) == 19
+    assert lbm.lib().lbm_strerror(-4).decode().startswith("simulation unstable")
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    from paper_2205_09186_gb300 import lbm
+    monkeypatch.setattr(lbm, "_LIB", None)
+    monkeypatch.setattr(lbm, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(ImportError):
+        lbm.lib()

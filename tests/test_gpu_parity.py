@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs.  FP64 mode: 1e-12 relative; FP32 deviation storage:
+1e-5 on densities relative to the liquid density."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2205_09186_gb300 as pkg
+    pkg.build()
+    from paper_2205_09186_gb300 import lbm
+    return lbm
+
+
+def pair(L, lattice, precision=0, mu_fp64=0, **kw):
+    lat_g = L.LBM_D2Q9 if lattice == 2 else L.LBM_D3Q19
+    lat_o = O.D2Q9 if lattice == 2 else O.D3Q19
+    g = L.Sim(L.make_params(lattice=lat_g, precision=precision, mu_fp64=mu_fp64, **kw))
+    o = O.Sim(lattice=lat_o, **kw)
+    return g, o
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+SCHEMES_2D = ["EFDS2", "EFDS4", "EFDS6", "E4", "E8", "CFDS4", "CFDS6", "CFDS8", "OCFDS4"]
+SCHEMES_3D = ["EFDS2", "EFDS4", "EFDS6", "E4", "CFDS4", "CFDS6", "CFDS8", "OCFDS4"]
+
+
+@pytest.mark.parametrize("scheme", SCHEMES_2D)
+def test_d2q9_fp64_fields_and_steps(L, scheme):
+    # 40 x 24: one full and one ragged tile in x (32 + 8), three tiles in y
+    kw = dict(nx=40, ny=24, Tr=0.8, k=0.25, kappa=0.1, scheme=scheme)
+    g, o = pair(L, 2, **kw)
+    g.lbm_init_droplet(7.0, center=[19.0, 11.5, 0.0])
+    o.init_droplet(7.0, center=[19.0, 11.5, 0.0])
+    F, mu = g.lbm_get_force()
+    fo = o.fields()
+    assert relerr(mu, fo["mu"]) < TOL64
+    assert relerr(F, fo["F"]) < 1e-11
+    for n in (1, 9, 40):
+        g.lbm_step(n)
+        assert o.step(n) == 0
+        assert relerr(g.lbm_get_density(), o.density()) < TOL64, (scheme, n)
+    assert relerr(g.lbm_get_f(), o.get_f()) < TOL64
+
+
+@pytest.mark.parametrize("scheme", SCHEMES_3D)
+def test_d3q19_fp64_steps(L, scheme):
+    # 36 x 20 x 40: ragged tiles in x and y, two z chunks (32 + 8)
+    kw = dict(nx=36, ny=20, nz=40, Tr=0.8, k=0.25, kappa=0.1, scheme=scheme)
+    g, o = pair(L, 3, **kw)
+    g.lbm_init_droplet(6.0, center=[17.0, 9.0, 21.0])
+    o.init_droplet(6.0, center=[17.0, 9.0, 21.0])
+    F, mu = g.lbm_get_force()
+    fo = o.fields()
+    assert relerr(mu, fo["mu"]) < TOL64
+    assert relerr(F, fo["F"]) < 1e-11
+    g.lbm_step(6)
+    assert o.step(6) == 0
+    assert relerr(g.lbm_get_density(), o.density()) < TOL64
+    assert relerr(g.lbm_get_f(), o.get_f()) < TOL64
+
+
+@pytest.mark.parametrize("lattice,shape,scheme", [(2, (64, 48, 1), "EFDS6"), (2, (64, 48, 1), "OCFDS4"),
+                                                  (3, (32, 24, 40), "EFDS6"), (3, (32, 24, 40), "E4")])
+@pytest.mark.parametrize("mu_fp64", [0, 1])
+def test_fp32dev_against_oracle(L, lattice, shape, scheme, mu_fp64):
+    nx, ny, nz = shape
+    kw = dict(nx=nx, ny=ny, nz=nz, Tr=0.8, k=0.25, kappa=0.1, scheme=scheme)
+    g, o = pair(L, lattice, precision=L.LBM_FP32DEV, mu_fp64=mu_fp64, **kw)
+    g.lbm_init_droplet(10.0)
+    o.init_droplet(10.0)
+    rl = O.maxwell_tr(0.8)[1]
+    g.lbm_step(100)
+    assert o.step(100) == 0
+    err = np.max(np.abs(g.lbm_get_density() - o.density())) / rl
+    assert err < TOL32, err
+
+
+def test_observables_parity(L):
+    kw = dict(nx=48, ny=40, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS4")
+    g, o = pair(L, 2, **kw)
+    g.lbm_init_droplet(10.0)
+    o.init_droplet(10.0)
+    for n in (0, 30, 200):
+        g.lbm_step(n)
+        o.step(n)
+        og, oo = g.lbm_observables(), o.observables()
+        assert og["status"] == 0 and og["step"] == oo["step"]
+        for key in ("max_v", "max_u", "rho_center", "rho_corner", "mass", "max_drho"):
+            assert og[key] == pytest.approx(oo[key], rel=1e-11, abs=1e-300), key
+
+
+def test_first_config_instability_agrees(L):
+    # 64 x 64, r0 = 16, T_r = 0.7, second-order scheme, tau = 1: the oracle
+    # reports a non-positive density; the GPU must report it at the same step
+    kw = dict(nx=64, ny=64, Tr=0.7, k=0.25, kappa=0.1, scheme="EFDS2")
+    g, o = pair(L, 2, **kw)
+    g.lbm_init_droplet(16.0)
+    o.init_droplet(16.0)
+    g.lbm_step(40)
+    o.step(40)
+    assert relerr(g.lbm_get_density(), o.density()) < 1e-11
+    assert o.step(3000) == O.EUNSTABLE
+    oo = o.observables()
+    g.lbm_step(3000 - 40)
+    og = g.lbm_observables()
+    assert og["status"] == L.LBM_EUNSTABLE
+    assert abs(og["step"] - oo["step"]) <= 2, (og["step"], oo["step"])
+
+
+def test_deterministic_fp64(L):
+    kw = dict(nx=40, ny=40, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6")
+    outs = []
+    for _ in range(2):
+        g = L.Sim(L.make_params(lattice=L.LBM_D2Q9, **kw))
+        g.lbm_init_droplet(9.0)
+        g.lbm_step(25)
+        outs.append((g.lbm_get_f(), g.lbm_observables()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+
+
+def test_init_variants_match_oracle(L):
+    kw = dict(nx=33, ny=27, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS4")
+    g, o = pair(L, 2, **kw)
+    g.lbm_init_slab(1, 12.0, width=6.0)
+    o.init_slab(1, 12.0, width=6.0)
+    assert relerr(g.lbm_get_density(), o.density()) < 1e-14
+    r = np.linspace(0.0, 20.0, 41)
+    prof = 0.2 + 0.1 * np.tanh(8.0 - r)
+    g.lbm_init_profile(r, prof)
+    o.init_profile(r, prof)
+    assert relerr(g.lbm_get_density(), o.density()) < 1e-14
+    rng = np.random.default_rng(7)
+    rho = 0.2 + 0.01 * rng.standard_normal((27, 33))
+    g.lbm_init_density(rho)
+    f = np.stack([w * rho for w in O.lattice(O.D2Q9)[1]])
+    o.set_f(f)
+    g.lbm_step(5)
+    o.step(5)
+    assert relerr(g.lbm_get_density(), o.density()) < TOL64
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 1), (65, 33, 1), (8, 8, 8), (9, 13, 11)])
+def test_small_and_ragged_lattices(L, shape):
+    nx, ny, nz = shape
+    lat = 2 if nz == 1 else 3
+    kw = dict(nx=nx, ny=ny, nz=nz, Tr=0.9, k=0.3, kappa=0.1, scheme="EFDS4")
+    g, o = pair(L, lat, **kw)
+    rng = np.random.default_rng(nx * 100 + ny)
+    shp = (ny, nx) if lat == 2 else (nz, ny, nx)
+    rho = 0.15 + 0.01 * rng.standard_normal(shp)
+    g.lbm_init_density(rho)
+    o.set_f(np.stack([w * rho for w in O.lattice(O.D2Q9 if lat == 2 else O.D3Q19)[1]]))
+    g.lbm_step(7)
+    o.step(7)
+    assert relerr(g.lbm_get_density(), o.density()) < TOL64
+    assert relerr(g.lbm_get_f(), o.get_f()) < TOL64
+
+
+def test_zero_steps_and_invalid_arguments(L):
+    g = L.Sim(L.make_params(lattice=L.LBM_D2Q9, nx=16, ny=16, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS4"))
+    g.lbm_init_droplet(4.0)
+    r0 = g.lbm_get_density()
+    g.lbm_step(0)
+    assert np.array_equal(r0, g.lbm_get_density())
+    with pytest.raises(L.LBMError) as e:
+        g.lbm_step(-1)
+    assert e.value.code == L.LBM_EINVAL
+    for bad in (dict(nx=4), dict(tau=0.5), dict(Tr=-1.0), dict(scheme=99), dict(nz=2)):
+        kw = dict(lattice=L.LBM_D2Q9, nx=16, ny=16, Tr=0.8)
+        kw.update(bad)
+        with pytest.raises(L.LBMError) as e:
+            L.Sim(L.make_params(**kw))
+        assert e.value.code == L.LBM_EINVAL
+    with pytest.raises(L.LBMError) as e:
+        L.Sim(L.make_params(lattice=L.LBM_D3Q19, nx=16, ny=16, nz=16, scheme="E8"))
+    assert e.value.code == L.LBM_ENOTSUP
