@@ -63,7 +63,7 @@ extern "C" {
 
 /* storage precision */
 #define LBM_FP64 0    /* populations, density and all arithmetic in FP64 */
-#define LBM_FP32DEV 1 /* populations stored in FP32 as f_i - w_i rho_ref; density FP64 */
+#define LBM_FP32DEV 1 /* populations stored in FP32 as f_i - w_i rho_ref, density as rho - rho_ref */
 
 /*
  * Simulation parameters.
@@ -182,9 +182,22 @@ int lbm_get_force(lbm_handle* h, double* host_F, double* host_mu);
 /* Current step counter. */
 long long lbm_get_step(const lbm_handle* h);
 
-/* Device pointers of the current populations and density (for callers that
- * keep data on the GPU).  Valid until the next lbm_step. */
+/* Device pointers of the current populations and density field (for callers
+ * that keep data on the GPU).  Stored forms: LBM_FP64 f and rho as double;
+ * LBM_FP32DEV f_i - w_i rho_ref and rho - rho_ref as float.  Valid until the
+ * next lbm_step. */
 int lbm_device_state(lbm_handle* h, void** f, void** rho);
+
+/* Work decomposition of the D3Q19 FP32DEV step (explicit schemes): each CTA
+ * marches through a chunk of zc planes.  lbm_set_zchunk fixes zc (0 = the
+ * built-in heuristic, which balances the last wave of CTAs against the
+ * per-chunk prologue).  lbm_autotune times the candidate chunk lengths over a
+ * few steps each on this handle's lattice and keeps the fastest; the steps
+ * run on the handle's state, which is left undefined (initialise after
+ * tuning).  *zc_out receives the choice, 0 if the handle has nothing to
+ * tune. */
+int lbm_set_zchunk(lbm_handle* h, int zc);
+int lbm_autotune(lbm_handle* h, int* zc_out);
 
 /* Carnahan-Starling critical point for constants (a, b, R), solving
  * dp0/drho = d2p0/drho2 = 0. */
@@ -199,6 +212,88 @@ int lbm_lattice_q(int lattice);
 
 /* Static text for an error code. */
 const char* lbm_strerror(int code);
+
+/* ==================================================================== batches
+ * Many independent D2Q9 droplets of different sizes and parameters advanced
+ * together (the parameter sweeps of Sec. 3.3-3.4 run as one job).  All cases
+ * must share lattice (LBM_D2Q9), precision and mu_fp64; schemes may differ
+ * among LBM_EFDS2/4/6, LBM_E4, LBM_E8 (compact schemes: LBM_ENOTSUP).  Each
+ * case owns its own populations and density; lbm_batch_step runs n steps of
+ * every case in ONE persistent kernel launch whose resident CTAs fetch
+ * (case, tile) work items dynamically and meet at a device-wide barrier
+ * between steps; the launch is captured in a CUDA graph (one per distinct n)
+ * and replayed.  Barrier waits are bounded (about one second): if a wait runs
+ * out the kernel returns and lbm_batch_observables reports LBM_ETIMEOUT.
+ */
+typedef struct lbm_batch lbm_batch;
+
+/* cases[n] as for lbm_create; stream/alloc as for lbm_create. */
+int lbm_batch_create(const lbm_params* cases, int n, void* stream, const lbm_allocator* alloc, lbm_batch** out);
+void lbm_batch_destroy(lbm_batch* b);
+
+/* Every case: droplet of Eq. 26 centred on node (nx/2, ny/2) with radius[c],
+ * interface width `width` and its Maxwell densities; resets the step counter. */
+int lbm_batch_init_droplets(lbm_batch* b, const double* radius, double width);
+
+/* Advance every case by n steps (asynchronous on the batch stream). */
+int lbm_batch_step(lbm_batch* b, long long n);
+
+/* Observables of every case into out[n] (lbm_obs as above; synchronises).
+ * Returns LBM_ETIMEOUT if a barrier wait of the last launch ran out;
+ * per-case instability is reported in out[c].status without failing. */
+int lbm_batch_observables(lbm_batch* b, lbm_obs* out);
+
+/* Density field of case c (nx*ny FP64) to host memory (synchronises). */
+int lbm_batch_get_density(lbm_batch* b, int c, double* host_rho);
+
+long long lbm_batch_get_step(const lbm_batch* b);
+
+/* Sizes: number of cases, of (case, tile) work items and of resident CTAs. */
+int lbm_batch_size(const lbm_batch* b, int* ncases, int* nitems, int* grid);
+
+/* Failure-detection aid for tests: CTA `cta` (0 <= cta < grid) will leave at
+ * its first barrier without arriving, so the others' bounded waits run out;
+ * -1 clears the injection and the error status. */
+int lbm_batch_inject_stall(lbm_batch* b, int cta);
+
+/* ================================================================ warm start
+ * A small fully connected network (FP32; GELU hidden layers, linear output)
+ * that maps droplet parameters to an initial radial density profile, trained
+ * by Adam on profiles the solver itself produced.  The paper has no
+ * counterpart: it only seeds lbm_init_profile, and the solver relaxes the
+ * state from there.  Parameters are packed per layer as W (out x in,
+ * row-major) followed by b.  Layers are at most 128 wide, at most 8 deep.
+ * Host arrays are row-major, one sample per row.
+ */
+typedef struct lbm_mlp lbm_mlp;
+
+/* sizes[0..nlayers]: widths from input to output; max_batch: the largest
+ * batch (and data set) used with this handle. */
+int lbm_mlp_create(const int* sizes, int nlayers, int max_batch, void* stream, const lbm_allocator* alloc,
+                   lbm_mlp** out);
+void lbm_mlp_destroy(lbm_mlp* m);
+long long lbm_mlp_param_count(const lbm_mlp* m);
+
+/* Copy parameters in (resets the Adam state) or out (FP32, packed). */
+int lbm_mlp_set_params(lbm_mlp* m, const float* host_params);
+int lbm_mlp_get_params(lbm_mlp* m, float* host_params);
+
+/* y[batch x out] = network(x[batch x in]). */
+int lbm_mlp_forward(lbm_mlp* m, const float* host_x, int batch, float* host_y);
+
+/* Mean-squared-error loss over batch x out entries and its gradient with
+ * respect to every parameter (same packing); either output may be NULL. */
+int lbm_mlp_loss_grad(lbm_mlp* m, const float* host_x, const float* host_t, int batch, float* host_loss,
+                      float* host_grad);
+
+/* Keep a training set of n samples on the device. */
+int lbm_mlp_set_data(lbm_mlp* m, const float* host_x, const float* host_t, int n);
+
+/* iters full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, step size
+ * lr) on the stored data; *host_loss (may be NULL) receives the loss of the
+ * last evaluated parameters. */
+int lbm_mlp_train(lbm_mlp* m, int iters, float lr, float* host_loss);
+
 
 #ifdef __cplusplus
 }

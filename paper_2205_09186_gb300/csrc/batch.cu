@@ -1,0 +1,564 @@
+// Batched D2Q9 droplets of uneven sizes and parameters in one persistent
+// launch.  The (case, tile) work items of all cases are fetched dynamically
+// by resident CTAs (an atomic counter per step); steps are separated by a
+// device-wide barrier whose waits are bounded (about one second), after which
+// the kernel records LBM_ETIMEOUT and returns.  lbm_batch_step captures the
+// launch (plus the counter reset) in a CUDA graph and replays it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "launch.cuh"
+#include "step2d.cuh"
+
+using namespace lbmd;
+
+namespace {
+
+constexpr int TXB = 32, TYB = 8;
+
+struct CaseDev {
+  KParams kp;
+  void* f[2];
+  void* rho[2];  // density field: double (FP64) or float rho - rho_ref (FP32DEV)
+  void* snap;
+  unsigned long long* bad;
+  int scheme;
+  int tiles_x, tiles_y;
+  int item_begin, item_end;
+};
+
+struct Item {
+  int c, tile;
+};
+
+struct BatchCtl {
+  unsigned int count;
+  unsigned int gen;
+  unsigned int work[2];
+  int status;
+  int skip_block;  // fault injection for tests: this CTA never arrives (-1: none)
+  long long t;     // step counter of the batch
+};
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Device-wide barrier with a bounded wait.  Returns false (for every thread of
+// the CTA) when the wait timed out or another CTA already reported an error.
+__device__ bool grid_barrier(BatchCtl* ctl, unsigned long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (int(blockIdx.x) == ctl->skip_block) {
+      ok = 0;  // injected non-arrival: leave without arriving
+    } else {
+      __threadfence();
+      const unsigned gen = ld_acquire(&ctl->gen);
+      __threadfence();
+      const unsigned arrived = atomicAdd(&ctl->count, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(&ctl->count, 0u);
+        __threadfence();
+        atomicAdd(&ctl->gen, 1u);
+      } else {
+        const unsigned long long t0 = gtime();
+        while (ld_acquire(&ctl->gen) == gen) {
+          if (gtime() - t0 > timeout_ns) {
+            atomicExch(&ctl->status, LBM_ETIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
+      __threadfence();
+      if (atomicAdd(&ctl->status, 0) != 0) ok = 0;
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <class P>
+__device__ void run_item(const CaseDev& cd, int tile, long long t, unsigned char* smem, int mode, double* partial) {
+  using Tf = typename P::Tf;
+  using Tr = typename P::Tr;
+  const int par = int(t & 1);
+  const int x0 = (tile % cd.tiles_x) * TXB, y0 = (tile / cd.tiles_x) * TYB;
+  StepAux aux;
+  aux.t = t;
+  aux.bad_step = cd.bad;
+  aux.partials = nullptr;
+  aux.rho_snap = cd.snap;
+  FieldOut fo{nullptr, nullptr};
+  GradIn gi{nullptr, nullptr, nullptr};
+  const Tf* fin = static_cast<const Tf*>(cd.f[par]);
+  Tf* fout = static_cast<Tf*>(cd.f[par ^ 1]);
+  const Tr* rin = static_cast<const Tr*>(cd.rho[par]);
+  Tr* rout = static_cast<Tr*>(cd.rho[par ^ 1]);
+#define LBM_ITEM_CASE(S)                                                                                   \
+  case S:                                                                                                  \
+    if (mode == MODE_STEP)                                                                                 \
+      step2d_tile<S, P, TXB, TYB, MODE_STEP>(cd.kp, fin, fout, rin, rout, aux, fo, gi, x0, y0, smem, partial); \
+    else                                                                                                   \
+      step2d_tile<S, P, TXB, TYB, MODE_OBS>(cd.kp, fin, fout, rin, rout, aux, fo, gi, x0, y0, smem, partial);  \
+    break;
+  switch (cd.scheme) {
+    LBM_ITEM_CASE(S_EFDS2)
+    LBM_ITEM_CASE(S_EFDS4)
+    LBM_ITEM_CASE(S_EFDS6)
+    LBM_ITEM_CASE(S_E4)
+    LBM_ITEM_CASE(S_E8)
+    default: break;
+  }
+#undef LBM_ITEM_CASE
+}
+
+template <class P>
+__global__ void __launch_bounds__(NT2) k_batch_persistent(const CaseDev* __restrict__ cases,
+                                                          const Item* __restrict__ items, int nitems, int nsteps,
+                                                          BatchCtl* ctl, unsigned long long timeout_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  const long long t0 = *((volatile long long*)&ctl->t);
+  for (int s = 0; s < nsteps; ++s) {
+    const long long t = t0 + s;
+    for (;;) {
+      if (threadIdx.x == 0) s_item = int(atomicAdd(&ctl->work[s & 1], 1u));
+      __syncthreads();
+      const int it = s_item;
+      __syncthreads();
+      if (it >= nitems) break;
+      const Item itm = items[it];
+      run_item<P>(cases[itm.c], itm.tile, t, smem, MODE_STEP, nullptr);
+      __syncthreads();
+    }
+    // the counter of the next step was last used two steps ago: reset it
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[(s + 1) & 1] = 0u;
+    if (!grid_barrier(ctl, timeout_ns)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t = t0 + nsteps;
+}
+
+// observation pass: one CTA per work item (not persistent)
+template <class P>
+__global__ void __launch_bounds__(NT2) k_batch_obs(const CaseDev* __restrict__ cases, const Item* __restrict__ items,
+                                                   const BatchCtl* ctl, double* partials) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Item itm = items[blockIdx.x];
+  run_item<P>(cases[itm.c], itm.tile, ctl->t, smem, MODE_OBS, partials + 4 * blockIdx.x);
+}
+
+// per case: reduce its items' partials; out[c*8 + ...]
+__global__ void k_batch_obs_final(const CaseDev* __restrict__ cases, const BatchCtl* ctl, const double* partials,
+                                  double* out, int dev) {
+  __shared__ double red[4][256];
+  const CaseDev& cd = cases[blockIdx.x];
+  double a = 0, b = 0, c = 0, d = 0;
+  for (int i = cd.item_begin + threadIdx.x; i < cd.item_end; i += blockDim.x) {
+    a = fmax(a, partials[4 * i]);
+    b = fmax(b, partials[4 * i + 1]);
+    c += partials[4 * i + 2];
+    d = fmax(d, partials[4 * i + 3]);
+  }
+  red[0][threadIdx.x] = a; red[1][threadIdx.x] = b; red[2][threadIdx.x] = c; red[3][threadIdx.x] = d;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + s]);
+      red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + s]);
+      red[2][threadIdx.x] += red[2][threadIdx.x + s];
+      red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int par = int(ctl->t & 1);
+    const long long center = (long long)(cd.kp.ny / 2) * cd.kp.nx + cd.kp.nx / 2;
+    double* o = out + 8 * blockIdx.x;
+    o[0] = red[0][0]; o[1] = red[1][0]; o[2] = red[2][0]; o[3] = red[3][0];
+    if (dev) {
+      const float* r = static_cast<const float*>(cd.rho[par]);
+      o[4] = cd.kp.rho_ref + double(r[center]);
+      o[5] = cd.kp.rho_ref + double(r[0]);
+    } else {
+      const double* r = static_cast<const double*>(cd.rho[par]);
+      o[4] = r[center];
+      o[5] = r[0];
+    }
+    reinterpret_cast<unsigned long long*>(o)[6] = *cd.bad;
+  }
+}
+
+// rho snapshot of every case (for the max |d rho / dt| observable)
+template <typename Tr>
+__global__ void k_batch_snap(const CaseDev* __restrict__ cases, const BatchCtl* ctl) {
+  const CaseDev& cd = cases[blockIdx.y];
+  const int par = int(ctl->t & 1);
+  const Tr* r = static_cast<const Tr*>(cd.rho[par]);
+  Tr* s = static_cast<Tr*>(cd.snap);
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < cd.kp.n; n += (long long)gridDim.x * blockDim.x)
+    s[n] = r[n];
+}
+
+template <class P>
+size_t batch_smem() {
+  size_t m = Step2DShape<S_EFDS2, P, TXB, TYB>::bytes;
+  m = std::max(m, Step2DShape<S_EFDS4, P, TXB, TYB>::bytes);
+  m = std::max(m, Step2DShape<S_EFDS6, P, TXB, TYB>::bytes);
+  m = std::max(m, Step2DShape<S_E4, P, TXB, TYB>::bytes);
+  m = std::max(m, Step2DShape<S_E8, P, TXB, TYB>::bytes);
+  return m;
+}
+
+}  // namespace
+
+struct lbm_batch {
+  int n = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  lbm_allocator alloc{};
+  std::vector<lbm_params> p;
+  std::vector<CaseDev> host_cases;
+  std::vector<int> order;  // case c is host index order[k]... (identity: cases keep input order)
+  CaseDev* d_cases = nullptr;
+  Item* d_items = nullptr;
+  int nitems = 0;
+  BatchCtl* ctl = nullptr;
+  double* d_partials = nullptr;
+  double* d_out = nullptr;
+  long long t = 0, t_snap = 0;
+  int grid = 0;
+  size_t smem = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_steps = -1;
+  std::vector<std::pair<void*, size_t>> blocks;
+};
+
+static void* balloc(lbm_batch* b, size_t bytes) {
+  void* p = b->alloc.alloc(bytes ? bytes : 256, b->alloc.ctx);
+  if (p) b->blocks.push_back({p, bytes ? bytes : 256});
+  return p;
+}
+static void* cuda_alloc_b(size_t bytes, void*) {
+  void* p = nullptr;
+  return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+static void cuda_free_b(void* p, size_t, void*) { cudaFree(p); }
+
+extern "C" void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto& blk : b->blocks) b->alloc.free(blk.first, blk.second, b->alloc.ctx);
+  delete b;
+}
+
+extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, const lbm_allocator* alloc,
+                                lbm_batch** out) {
+  if (!out || !cases || n < 1) return LBM_EINVAL;
+  *out = nullptr;
+  const int prec0 = cases[0].precision;
+  const int mu0 = cases[0].mu_fp64;
+  for (int c = 0; c < n; ++c) {
+    const lbm_params& q = cases[c];
+    if (q.lattice != LBM_D2Q9 || q.nz != 1 || q.nx < 8 || q.ny < 8) return LBM_EINVAL;
+    if (!(q.a > 0 && q.b > 0 && q.R > 0 && q.Tr > 0 && q.k > 0 && q.kappa >= 0 && q.tau > 0.5)) return LBM_EINVAL;
+    if (q.precision != prec0 || q.mu_fp64 != mu0 || (q.precision != LBM_FP64 && q.precision != LBM_FP32DEV))
+      return LBM_EINVAL;
+    if (!(q.scheme == LBM_EFDS2 || q.scheme == LBM_EFDS4 || q.scheme == LBM_EFDS6 || q.scheme == LBM_E4 ||
+          q.scheme == LBM_E8))
+      return LBM_ENOTSUP;
+  }
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ENOMEM;
+  b->n = n;
+  b->stream = static_cast<cudaStream_t>(stream);
+  if (alloc && alloc->alloc && alloc->free) b->alloc = *alloc;
+  else { b->alloc.alloc = cuda_alloc_b; b->alloc.free = cuda_free_b; b->alloc.ctx = nullptr; }
+  b->prec = prec0 == LBM_FP64 ? 0 : (mu0 ? 2 : 1);
+  b->p.assign(cases, cases + n);
+  b->host_cases.resize(n);
+  // work items: cases grouped by scheme, larger cases first (dynamic fetch
+  // then ends with small items, which balances the step)
+  std::vector<int> idx(n);
+  for (int c = 0; c < n; ++c) idx[c] = c;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    if (cases[x].scheme != cases[y].scheme) return cases[x].scheme < cases[y].scheme;
+    return (long long)cases[x].nx * cases[x].ny > (long long)cases[y].nx * cases[y].ny;
+  });
+  std::vector<Item> items;
+  const size_t fs = prec0 == LBM_FP64 ? 8 : 4;
+  bool ok = true;
+  for (int k = 0; k < n && ok; ++k) {
+    const int c = idx[k];
+    const lbm_params& q = cases[c];
+    CaseDev& cd = b->host_cases[c];
+    double rc, Tc;
+    lbm_critical(q.a, q.b, q.R, &rc, &Tc);
+    const double T = q.Tr * Tc;
+    double rho_ref = 0.0;
+    if (q.precision == LBM_FP32DEV) {
+      rho_ref = q.rho_ref;
+      if (!(rho_ref > 0)) {
+        double g, l;
+        if (lbm_maxwell(&q, &g, &l) != LBM_OK) { ok = false; break; }
+        rho_ref = g;
+      }
+    }
+    const long long N = (long long)q.nx * q.ny;
+    cd.kp.nx = q.nx; cd.kp.ny = q.ny; cd.kp.nz = 1; cd.kp.n = N;
+    cd.kp.RT = q.R * T; cd.kp.b4 = 0.25 * q.b; cd.kp.two_a = 2.0 * q.a;
+    cd.kp.k2 = q.k * q.k; cd.kp.kappa = q.kappa; cd.kp.omega = 1.0 / q.tau; cd.kp.rho_ref = rho_ref;
+    b->p[c].rho_ref = rho_ref;
+    cd.scheme = q.scheme;
+    cd.tiles_x = (q.nx + TXB - 1) / TXB;
+    cd.tiles_y = (q.ny + TYB - 1) / TYB;
+    cd.item_begin = int(items.size());
+    for (int tl = 0; tl < cd.tiles_x * cd.tiles_y; ++tl) items.push_back({c, tl});
+    cd.item_end = int(items.size());
+    cd.f[0] = balloc(b, size_t(9) * N * fs);
+    cd.f[1] = balloc(b, size_t(9) * N * fs);
+    cd.rho[0] = balloc(b, size_t(N) * fs);
+    cd.rho[1] = balloc(b, size_t(N) * fs);
+    cd.snap = balloc(b, size_t(N) * fs);
+    cd.bad = static_cast<unsigned long long*>(balloc(b, 8));
+    ok = cd.f[0] && cd.f[1] && cd.rho[0] && cd.rho[1] && cd.snap && cd.bad;
+  }
+  if (!ok) { lbm_batch_destroy(b); return LBM_ENOMEM; }
+  b->nitems = int(items.size());
+  b->d_cases = static_cast<CaseDev*>(balloc(b, sizeof(CaseDev) * n));
+  b->d_items = static_cast<Item*>(balloc(b, sizeof(Item) * items.size()));
+  b->ctl = static_cast<BatchCtl*>(balloc(b, sizeof(BatchCtl)));
+  b->d_partials = static_cast<double*>(balloc(b, size_t(4) * 8 * items.size()));
+  b->d_out = static_cast<double*>(balloc(b, size_t(8) * 8 * n));
+  if (!b->d_cases || !b->d_items || !b->ctl || !b->d_partials || !b->d_out) { lbm_batch_destroy(b); return LBM_ENOMEM; }
+  BatchCtl c0{};
+  c0.skip_block = -1;
+  cudaError_t e = cudaMemcpyAsync(b->d_cases, b->host_cases.data(), sizeof(CaseDev) * n, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  // residency: CTAs per SM x SMs, all resident at once
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto setup = [&](auto kern, size_t smem) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT2, smem);
+  };
+  if (b->prec == 0) { b->smem = batch_smem<PrecF64>(); setup(k_batch_persistent<PrecF64>, b->smem);
+                      cudaFuncSetAttribute(k_batch_obs<PrecF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)); }
+  else if (b->prec == 1) { b->smem = batch_smem<PrecF32>(); setup(k_batch_persistent<PrecF32>, b->smem);
+                           cudaFuncSetAttribute(k_batch_obs<PrecF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)); }
+  else { b->smem = batch_smem<PrecF32M64>(); setup(k_batch_persistent<PrecF32M64>, b->smem);
+         cudaFuncSetAttribute(k_batch_obs<PrecF32M64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)); }
+  b->grid = std::max(1, std::min(per_sm * sms, b->nitems));
+  if (e != cudaSuccess || per_sm < 1 || cudaGetLastError() != cudaSuccess) { lbm_batch_destroy(b); return LBM_ECUDA; }
+  *out = b;
+  return LBM_OK;
+}
+
+namespace {
+__constant__ double cb_w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+// Eq. 26 droplet centred at node (nx/2, ny/2) for every case; f_i = w_i rho
+template <typename Tf>
+__global__ void k_batch_init(const CaseDev* __restrict__ cases, const double* radius, const double* rl,
+                             const double* rg, double width) {
+  const int c = blockIdx.y;
+  const CaseDev& cd = cases[c];
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < cd.kp.n; n += (long long)gridDim.x * blockDim.x) {
+    const int x = int(n % cd.kp.nx), y = int(n / cd.kp.nx);
+    const double dx = x - double(cd.kp.nx / 2), dy = y - double(cd.kp.ny / 2);
+    const double r = sqrt(dx * dx + dy * dy);
+    const double r0 = 0.5 * (rl[c] + rg[c]) - 0.5 * (rl[c] - rg[c]) * tanh(2.0 * (r - radius[c]) / width);
+    Tf* f = static_cast<Tf*>(cd.f[0]);
+    Tf* rho = static_cast<Tf*>(cd.rho[0]);
+    Tf* snap = static_cast<Tf*>(cd.snap);
+    if constexpr (sizeof(Tf) == 8) {
+      double acc = 0;
+      for (int i = 0; i < 9; ++i) { const double fi = cb_w9[i] * r0; f[i * cd.kp.n + n] = fi; acc += fi; }
+      rho[n] = acc;
+    } else {
+      FSum acc;
+      for (int i = 0; i < 9; ++i) { const float d = float(cb_w9[i] * (r0 - cd.kp.rho_ref)); f[i * cd.kp.n + n] = d; acc.add(d); }
+      rho[n] = acc.fvalue();
+    }
+    snap[n] = rho[n];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *cd.bad = ULLONG_MAX;
+}
+}  // namespace
+
+extern "C" int lbm_batch_init_droplets(lbm_batch* b, const double* radius, double width) {
+  if (!b || !radius || !(width > 0)) return LBM_EINVAL;
+  std::vector<double> host(3 * size_t(b->n));
+  long long maxn = 0;
+  for (int c = 0; c < b->n; ++c) {
+    double g, l;
+    if (!(radius[c] >= 0) || lbm_maxwell(&b->p[c], &g, &l) != LBM_OK) return LBM_EINVAL;
+    host[c] = radius[c];
+    host[b->n + c] = l;
+    host[2 * b->n + c] = g;
+    maxn = std::max(maxn, (long long)b->p[c].nx * b->p[c].ny);
+  }
+  double* d = static_cast<double*>(b->alloc.alloc(host.size() * 8, b->alloc.ctx));
+  if (!d) return LBM_ENOMEM;
+  cudaError_t e = cudaMemcpyAsync(d, host.data(), host.size() * 8, cudaMemcpyHostToDevice, b->stream);
+  dim3 grid(unsigned(std::min<long long>((maxn + 255) / 256, 1024)), unsigned(b->n));
+  if (e == cudaSuccess) {
+    if (b->prec == 0) k_batch_init<double><<<grid, 256, 0, b->stream>>>(b->d_cases, d, d + b->n, d + 2 * b->n, width);
+    else k_batch_init<float><<<grid, 256, 0, b->stream>>>(b->d_cases, d, d + b->n, d + 2 * b->n, width);
+    e = cudaGetLastError();
+  }
+  BatchCtl c0{};
+  c0.skip_block = -1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  b->alloc.free(d, host.size() * 8, b->alloc.ctx);
+  b->t = 0;
+  b->t_snap = 0;
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+static cudaError_t launch_persistent(lbm_batch* b, int nsteps) {
+  const unsigned long long timeout_ns = 1000000000ull;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned(b->grid));
+  cfg.blockDim = dim3(NT2);
+  cfg.dynamicSmemBytes = b->smem;
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (b->prec == 0)
+    return cudaLaunchKernelEx(&cfg, k_batch_persistent<PrecF64>, (const CaseDev*)b->d_cases, (const Item*)b->d_items,
+                              b->nitems, nsteps, b->ctl, timeout_ns);
+  if (b->prec == 1)
+    return cudaLaunchKernelEx(&cfg, k_batch_persistent<PrecF32>, (const CaseDev*)b->d_cases, (const Item*)b->d_items,
+                              b->nitems, nsteps, b->ctl, timeout_ns);
+  return cudaLaunchKernelEx(&cfg, k_batch_persistent<PrecF32M64>, (const CaseDev*)b->d_cases, (const Item*)b->d_items,
+                            b->nitems, nsteps, b->ctl, timeout_ns);
+}
+
+// n steps = one persistent launch (preceded by the reset of the barrier and
+// work counters), captured once in a CUDA graph per distinct n and replayed
+extern "C" int lbm_batch_step(lbm_batch* b, long long n) {
+  if (!b || n < 0 || n > INT_MAX) return LBM_EINVAL;
+  if (n == 0) return LBM_OK;
+  if (b->graph_steps != n) {
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
+    cudaStream_t saved = b->stream;
+    b->stream = cap;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      // counters and barrier state (status and skip_block are left as they are)
+      cudaMemsetAsync(b->ctl, 0, offsetof(BatchCtl, status), cap);
+      launch_persistent(b, int(n));
+      e = cudaStreamEndCapture(cap, &b->graph);
+    }
+    b->stream = saved;
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return LBM_ECUDA;
+    if (cudaGraphInstantiate(&b->gexec, b->graph, 0) != cudaSuccess) return LBM_ECUDA;
+    b->graph_steps = n;
+  }
+  if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) return LBM_ECUDA;
+  b->t += n;
+  return LBM_OK;
+}
+
+extern "C" int lbm_batch_observables(lbm_batch* b, lbm_obs* out) {
+  if (!b || !out) return LBM_EINVAL;
+  cudaError_t e;
+  if (b->prec == 0) k_batch_obs<PrecF64><<<b->nitems, NT2, b->smem, b->stream>>>(b->d_cases, b->d_items, b->ctl, b->d_partials);
+  else if (b->prec == 1) k_batch_obs<PrecF32><<<b->nitems, NT2, b->smem, b->stream>>>(b->d_cases, b->d_items, b->ctl, b->d_partials);
+  else k_batch_obs<PrecF32M64><<<b->nitems, NT2, b->smem, b->stream>>>(b->d_cases, b->d_items, b->ctl, b->d_partials);
+  k_batch_obs_final<<<b->n, 256, 0, b->stream>>>(b->d_cases, b->ctl, b->d_partials, b->d_out, b->prec != 0);
+  if (b->prec == 0) k_batch_snap<double><<<dim3(64, unsigned(b->n)), 256, 0, b->stream>>>(b->d_cases, b->ctl);
+  else k_batch_snap<float><<<dim3(64, unsigned(b->n)), 256, 0, b->stream>>>(b->d_cases, b->ctl);
+  e = cudaGetLastError();
+  std::vector<double> host(size_t(8) * b->n);
+  BatchCtl hc{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), b->d_out, host.size() * 8, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, b->ctl, sizeof(hc), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return LBM_ECUDA;
+  int rc = LBM_OK;
+  for (int c = 0; c < b->n; ++c) {
+    const double* o = host.data() + 8 * c;
+    lbm_obs& r = out[c];
+    r.max_v = o[0]; r.max_u = o[1]; r.mass = o[2];
+    r.max_drho = b->t > b->t_snap ? o[3] / double(b->t - b->t_snap) : 0.0;
+    r.rho_center = o[4]; r.rho_corner = o[5];
+    unsigned long long bad;
+    std::memcpy(&bad, &o[6], 8);
+    r.step = b->t;
+    r.status = LBM_OK;
+    if (bad != ULLONG_MAX) { r.status = LBM_EUNSTABLE; r.step = (long long)bad; }
+    if (hc.status != 0) r.status = hc.status;
+  }
+  b->t_snap = b->t;
+  if (hc.status != 0) rc = hc.status;
+  return rc;
+}
+
+extern "C" int lbm_batch_get_density(lbm_batch* b, int c, double* host) {
+  if (!b || !host || c < 0 || c >= b->n) return LBM_EINVAL;
+  const CaseDev& cd = b->host_cases[c];
+  const size_t n = size_t(cd.kp.n);
+  cudaError_t e;
+  if (b->prec == 0) {
+    e = cudaMemcpyAsync(host, cd.rho[b->t & 1], n * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+  }
+  std::vector<float> tmp(n);
+  e = cudaMemcpyAsync(tmp.data(), cd.rho[b->t & 1], n * 4, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  for (size_t i = 0; i < n; ++i) host[i] = cd.kp.rho_ref + double(tmp[i]);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+extern "C" long long lbm_batch_get_step(const lbm_batch* b) { return b ? b->t : -1; }
+
+extern "C" int lbm_batch_inject_stall(lbm_batch* b, int cta) {
+  if (!b || cta < -1 || cta >= b->grid) return LBM_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(&b->ctl->skip_block, &cta, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+  int zero = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&b->ctl->status, &zero, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+extern "C" int lbm_batch_size(const lbm_batch* b, int* ncases, int* nitems, int* grid) {
+  if (!b) return LBM_EINVAL;
+  if (ncases) *ncases = b->n;
+  if (nitems) *nitems = b->nitems;
+  if (grid) *grid = b->grid;
+  return LBM_OK;
+}

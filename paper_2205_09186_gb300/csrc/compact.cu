@@ -57,8 +57,8 @@ __device__ __forceinline__ int lmod(long long a, int n) {
 
 // mu = k^2 psi'(rho) - kappa lap rho with the explicit central second
 // derivative of order LO along each axis (the compact scheme's Laplacian).
-template <typename Tm, int LO>
-__global__ void k_mu_field(KParams p, int D, const double* __restrict__ rho, Tm* __restrict__ mu) {
+template <typename Tm, typename Tr, int LO>
+__global__ void k_mu_field(KParams p, int D, bool dev, const Tr* __restrict__ rho, Tm* __restrict__ mu) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= p.n) return;
   constexpr int R = LO / 2;
@@ -66,24 +66,25 @@ __global__ void k_mu_field(KParams p, int D, const double* __restrict__ rho, Tm*
   const double lc[5] = {l0, LO == 4 ? 4.0 / 3.0 : (LO == 6 ? 1.5 : 1.6), LO == 4 ? -1.0 / 12.0 : (LO == 6 ? -0.15 : -0.2),
                         LO == 6 ? 1.0 / 90.0 : (LO == 8 ? 8.0 / 315.0 : 0.0), LO == 8 ? -1.0 / 560.0 : 0.0};
   const int x = int(n % p.nx), y = int((n / p.nx) % p.ny), z = int(n / ((long long)p.nx * p.ny));
-  const double ref = p.rho_ref;
-  const Tm c0 = Tm(rho[n] - ref);
+  // rho holds rho - rho_ref when dev: the Laplacian needs no offset
+  const Tm c0 = Tm(rho[n]);
   Tm lap = Tm(D * lc[0]) * c0;
 #pragma unroll
   for (int m = 1; m <= R; ++m) {
     const long long row = (long long)z * p.nx * p.ny + (long long)y * p.nx;
-    Tm s = Tm(rho[row + lmod(x + m, p.nx)] - ref) + Tm(rho[row + lmod(x - m, p.nx)] - ref);
-    s += Tm(rho[(long long)z * p.nx * p.ny + (long long)lmod(y + m, p.ny) * p.nx + x] - ref) +
-         Tm(rho[(long long)z * p.nx * p.ny + (long long)lmod(y - m, p.ny) * p.nx + x] - ref);
+    Tm s = Tm(rho[row + lmod(x + m, p.nx)]) + Tm(rho[row + lmod(x - m, p.nx)]);
+    s += Tm(rho[(long long)z * p.nx * p.ny + (long long)lmod(y + m, p.ny) * p.nx + x]) +
+         Tm(rho[(long long)z * p.nx * p.ny + (long long)lmod(y - m, p.ny) * p.nx + x]);
     if (D == 3)
-      s += Tm(rho[(long long)lmod(z + m, p.nz) * p.nx * p.ny + (long long)y * p.nx + x] - ref) +
-           Tm(rho[(long long)lmod(z - m, p.nz) * p.nx * p.ny + (long long)y * p.nx + x] - ref);
+      s += Tm(rho[(long long)lmod(z + m, p.nz) * p.nx * p.ny + (long long)y * p.nx + x]) +
+           Tm(rho[(long long)lmod(z - m, p.nz) * p.nx * p.ny + (long long)y * p.nx + x]);
     lap += Tm(lc[m]) * s;
   }
-  mu[n] = Tm(p.k2) * cs_mu<Tm>(Tm(rho[n]), Tm(p.RT), Tm(p.b4), Tm(p.two_a)) - Tm(p.kappa) * lap;
+  const Tm rfull = dev ? Tm(p.rho_ref) + Tm(rho[n]) : Tm(rho[n]);
+  mu[n] = Tm(p.k2) * cs_mu<Tm>(rfull, Tm(p.RT), Tm(p.b4), Tm(p.two_a)) - Tm(p.kappa) * lap;
 }
 
-// Derivative along `axis` of lines of `in` (minus ref), LPB lines per CTA held
+// Derivative along `axis` of lines of `in`, LPB lines per CTA held
 // in shared memory; explicit right side of Eq. 21 then PCR levels.
 template <typename Tin, typename T>
 __global__ void k_lines(int axis, int nx, int ny, int nz, const Tin* __restrict__ in, double ref, T* __restrict__ out,
@@ -114,7 +115,7 @@ __global__ void k_lines(int axis, int nx, int ny, int nz, const Tin* __restrict_
     if (axis == 0) { j = idx / L; i = idx - j * L; } else { i = idx / LPB; j = idx - i * LPB; }
     bool ok;
     const long long b = line_base(j, ok);
-    A[j * LP + i] = ok ? T(double(in[b + i * stride]) - ref) : T(0);
+    A[j * LP + i] = ok ? T(in[b + i * stride]) : T(0);
   }
   __syncthreads();
   // explicit side: a (f[i+1]-f[i-1])/2 + b (f[i+2]-f[i-2])/4 + c (f[i+3]-f[i-3])/6
@@ -185,6 +186,9 @@ constexpr int TXc = 32, TYc = 8, ZCc = 32;
 template <class P, int MODE>
 cudaError_t launch_gf(const Launch& c, int D, int* nblocks) {
   using Tf = typename P::Tf;
+  using Tr = typename P::Tr;
+  const Tr* rin = static_cast<const Tr*>(c.rin);
+  Tr* rout = static_cast<Tr*>(c.rout);
   if (D == 2) {
     using Sh = Step2DShape<S_CFDS4, P, TXc, TYc>;
     auto k = k_step2d<S_CFDS4, P, TXc, TYc, MODE>;
@@ -196,7 +200,7 @@ cudaError_t launch_gf(const Launch& c, int D, int* nblocks) {
     }
     dim3 grid((c.kp.nx + TXc - 1) / TXc, (c.kp.ny + TYc - 1) / TYc, 1);
     if (nblocks) *nblocks = int(grid.x * grid.y);
-    k<<<grid, NT2, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), c.rin, c.rout,
+    k<<<grid, NT2, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), rin, rout,
                                           c.aux, c.fo, c.gi);
   } else {
     using Sh = Step3DShape<S_CFDS4, P, TXc, TYc>;
@@ -209,7 +213,7 @@ cudaError_t launch_gf(const Launch& c, int D, int* nblocks) {
     }
     dim3 grid((c.kp.nx + TXc - 1) / TXc, (c.kp.ny + TYc - 1) / TYc, (c.kp.nz + ZCc - 1) / ZCc);
     if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
-    k<<<grid, NT3, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), c.rin, c.rout,
+    k<<<grid, NT3, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), rin, rout,
                                           c.aux, c.fo, c.gi);
   }
   return cudaGetLastError();
@@ -219,13 +223,15 @@ template <class P>
 cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nblocks) {
   using Tm = typename P::Tm;
   using Tc = typename P::Tc;
+  using Tr = typename P::Tr;
+  const Tr* rin = static_cast<const Tr*>(c.rin);
   const KParams& kp = c.kp;
   const int bs = 256;
   const unsigned g = unsigned((kp.n + bs - 1) / bs);
   Tm* mu = static_cast<Tm*>(cb.mu);
-  if (cb.lap_order == 4) k_mu_field<Tm, 4><<<g, bs, 0, c.stream>>>(kp, D, c.rin, mu);
-  else if (cb.lap_order == 6) k_mu_field<Tm, 6><<<g, bs, 0, c.stream>>>(kp, D, c.rin, mu);
-  else k_mu_field<Tm, 8><<<g, bs, 0, c.stream>>>(kp, D, c.rin, mu);
+  if (cb.lap_order == 4) k_mu_field<Tm, Tr, 4><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
+  else if (cb.lap_order == 6) k_mu_field<Tm, Tr, 6><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
+  else k_mu_field<Tm, Tr, 8><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   Tm* gmu = static_cast<Tm*>(cb.gmu);
@@ -233,7 +239,7 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   for (int ax = 0; ax < D; ++ax) {
     e = run_lines<Tm, Tm>(ax, kp, mu, 0.0, gmu + size_t(ax) * kp.n, cb.lc, c.stream);
     if (e != cudaSuccess) return e;
-    e = run_lines<double, Tc>(ax, kp, c.rin, P::DEV ? kp.rho_ref : 0.0, grho + size_t(ax) * kp.n, cb.lc, c.stream);
+    e = run_lines<Tr, Tc>(ax, kp, rin, 0.0, grho + size_t(ax) * kp.n, cb.lc, c.stream);
     if (e != cudaSuccess) return e;
   }
   c.gi.gmu = gmu;

@@ -20,7 +20,9 @@ cudaError_t launch_mode(const Launch& c, int* nblocks) {
   dim3 grid((c.kp.nx + TX2 - 1) / TX2, (c.kp.ny + TY2 - 1) / TY2, 1);
   if (nblocks) *nblocks = int(grid.x * grid.y);
   using Tf = typename P::Tf;
-  k<<<grid, NT2, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), c.rin, c.rout,
+  using Tr = typename P::Tr;
+  k<<<grid, NT2, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout),
+                                        static_cast<const Tr*>(c.rin), static_cast<Tr*>(c.rout),
                                         c.aux, c.fo, c.gi);
   return cudaGetLastError();
 }

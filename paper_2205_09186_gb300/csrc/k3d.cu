@@ -1,8 +1,34 @@
 // Instantiations of the fused 2.5D D3Q19 step for the explicit and isotropic schemes.
+#include <type_traits>
+
 #include "launch.cuh"
 #include "step3d.cuh"
+#include "step3d_fast.cuh"
 
 namespace lbmd {
+
+int fast_zchunk_heuristic(const KParams& kp, int R) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const long long tiles = (long long)((kp.nx + FT - 1) / FT) * ((kp.ny + FT - 1) / FT);
+  const long long slots = 2LL * sms;  // two CTAs per SM
+  double best = 1e300;
+  int best_zc = kp.nz;
+  for (int nzc = 1; nzc <= kp.nz && nzc <= 128; ++nzc) {
+    const int zc = (kp.nz + nzc - 1) / nzc;
+    if (zc < 4 && nzc > 1) break;
+    const long long ctas = tiles * ((kp.nz + zc - 1) / zc);
+    const double waves = double((ctas + slots - 1) / slots);
+    const double cost = waves * (zc + 2 + 0.3 * 4 * R);
+    if (cost < best - 1e-9) { best = cost; best_zc = zc; }
+  }
+  return best_zc;
+}
 
 namespace {
 constexpr int TX3 = 32, TY3 = 8, ZC3 = 32;
@@ -20,13 +46,38 @@ cudaError_t launch_mode(const Launch& c, int* nblocks) {
   dim3 grid((c.kp.nx + TX3 - 1) / TX3, (c.kp.ny + TY3 - 1) / TY3, (c.kp.nz + ZC3 - 1) / ZC3);
   if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
   using Tf = typename P::Tf;
-  k<<<grid, NT3, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), c.rin, c.rout,
+  using Tr = typename P::Tr;
+  k<<<grid, NT3, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout),
+                                        static_cast<const Tr*>(c.rin), static_cast<Tr*>(c.rout),
                                         c.aux, c.fo, c.gi);
+  return cudaGetLastError();
+}
+
+// FP32 deviation storage with FP32 mu: the pipelined kernel (step mode)
+template <int S, bool TAU1>
+cudaError_t launch_fast(const Launch& c, int* nblocks) {
+  using Sh = FastShape<S>;
+  auto k = k_step3d_fast<S, TAU1>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int zc = c.zc > 0 ? c.zc : fast_zchunk_heuristic(c.kp, Sh::R);
+  dim3 grid((c.kp.nx + FT - 1) / FT, (c.kp.ny + FT - 1) / FT, (c.kp.nz + zc - 1) / zc);
+  if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
+  k<<<grid, FNT, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
+                                        static_cast<const float*>(c.rin), static_cast<float*>(c.rout), c.aux, zc);
   return cudaGetLastError();
 }
 
 template <int S, class P>
 cudaError_t launch(const Launch& c, int mode, int* nblocks) {
+  if constexpr (std::is_same<P, PrecF32>::value) {
+    if (mode == MODE_STEP)
+      return c.kp.omega == 1.0 ? launch_fast<S, true>(c, nblocks) : launch_fast<S, false>(c, nblocks);
+  }
   if (mode == MODE_STEP) return launch_mode<S, P, MODE_STEP>(c, nblocks);
   if (mode == MODE_OBS) return launch_mode<S, P, MODE_OBS>(c, nblocks);
   return launch_mode<S, P, MODE_FIELDS>(c, nblocks);

@@ -10,13 +10,19 @@ struct Launch {
   KParams kp;
   const void* fin;
   void* fout;
-  const double* rin;
-  double* rout;
+  const void* rin;   // density field, type P::Tr
+  void* rout;
   StepAux aux;
   FieldOut fo;
   GradIn gi;
   cudaStream_t stream;
+  int zc;  // z-chunk of the pipelined D3Q19 kernel; 0 = heuristic
 };
+
+// z-chunk length for the pipelined D3Q19 kernel: balances the last wave of
+// CTAs against the per-chunk prologue (4R + 2 extra planes, of which only 2
+// are collided)
+int fast_zchunk_heuristic(const KParams& kp, int R);
 
 // launch one fused step (mode MODE_STEP), an observation pass (MODE_OBS) or a
 // field dump (MODE_FIELDS); returns the number of CTAs through *nblocks

@@ -23,9 +23,9 @@ struct lbm_handle {
   lbm_allocator alloc{};
   bool own_alloc = false;
   void* f[2] = {nullptr, nullptr};
-  double* rho[2] = {nullptr, nullptr};
+  void* rho[2] = {nullptr, nullptr};  // FP64: density; FP32DEV: float rho - rho_ref
   int cur = 0;
-  double* rho_snap = nullptr;
+  void* rho_snap = nullptr;
   unsigned long long* d_bad = nullptr;
   double* d_partials = nullptr;
   int n_partials = 0;
@@ -35,6 +35,7 @@ struct lbm_handle {
   StepFn fn = nullptr;
   CompactBufs cb{};
   bool compact = false;
+  int zc = 0;  // z-chunk of the pipelined D3Q19 kernel (0 = heuristic)
 };
 
 // ------------------------------------------------------------------ allocation
@@ -53,6 +54,9 @@ static void cuda_free_cb(void* p, size_t, void*) { cudaFree(p); }
 
 static size_t f_bytes(const lbm_handle* h) {
   return size_t(h->Q) * size_t(h->N) * (h->p.precision == LBM_FP64 ? sizeof(double) : sizeof(float));
+}
+static size_t r_bytes(const lbm_handle* h) {
+  return size_t(h->N) * (h->p.precision == LBM_FP64 ? sizeof(double) : sizeof(float));
 }
 
 // ------------------------------------------------------------------ EOS on the host
@@ -208,7 +212,7 @@ __device__ double init_density(const InitSpec& s, int x, int y, int z, long long
 
 // f_i = w_i rho0 (u = 0); the density field is the sum of the stored populations
 template <typename Tf>
-__global__ void k_init(KParams p, int Q, InitSpec s, Tf* f, double* rho) {
+__global__ void k_init(KParams p, int Q, InitSpec s, Tf* f, Tf* rho) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= p.n) return;
   const int x = int(n % p.nx), y = int((n / p.nx) % p.ny), z = int(n / ((long long)p.nx * p.ny));
@@ -229,13 +233,13 @@ __global__ void k_init(KParams p, int Q, InitSpec s, Tf* f, double* rho) {
       f[i * p.n + n] = d;
       acc.add(d);
     }
-    rho[n] = p.rho_ref + acc.value();
+    rho[n] = acc.fvalue();
   }
 }
 
 // density field from the stored populations
 template <typename Tf>
-__global__ void k_density(KParams p, int Q, const Tf* f, double* rho) {
+__global__ void k_density(KParams p, int Q, const Tf* f, Tf* rho) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= p.n) return;
   if constexpr (sizeof(Tf) == 8) {
@@ -245,8 +249,16 @@ __global__ void k_density(KParams p, int Q, const Tf* f, double* rho) {
   } else {
     FSum acc;
     for (int i = 0; i < Q; ++i) acc.add(float(f[i * p.n + n]));
-    rho[n] = p.rho_ref + acc.value();
+    rho[n] = acc.fvalue();
   }
+}
+
+// density field (stored form) -> FP64 full density
+template <typename Tr>
+__global__ void k_export_rho(KParams p, const Tr* r, double* out) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= p.n) return;
+  out[n] = sizeof(Tr) == 8 ? double(r[n]) : p.rho_ref + double(r[n]);
 }
 
 // full FP64 populations <-> stored form
@@ -266,8 +278,9 @@ __global__ void k_import_f(KParams p, int Q, const double* in, Tf* f) {
 }
 
 // final reduction of per-CTA observables, fixed order (deterministic)
-__global__ void k_obs_final(const double* part, int nb, const double* rho, long long center, const unsigned long long* bad,
-                            double* out) {
+template <typename Tr>
+__global__ void k_obs_final(const double* part, int nb, const Tr* rho, double rho_ref, long long center,
+                            const unsigned long long* bad, double* out) {
   __shared__ double red[4][256];
   double a = 0, b = 0, c = 0, d = 0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -289,8 +302,8 @@ __global__ void k_obs_final(const double* part, int nb, const double* rho, long 
   }
   if (threadIdx.x == 0) {
     out[0] = red[0][0]; out[1] = red[1][0]; out[2] = red[2][0]; out[3] = red[3][0];
-    out[4] = rho[center];
-    out[5] = rho[0];
+    out[4] = sizeof(Tr) == 8 ? double(rho[center]) : rho_ref + double(rho[center]);
+    out[5] = sizeof(Tr) == 8 ? double(rho[0]) : rho_ref + double(rho[0]);
     unsigned long long bs = *bad;
     reinterpret_cast<unsigned long long*>(out)[6] = bs;
   }
@@ -308,9 +321,9 @@ extern "C" void lbm_destroy(lbm_handle* h) {
   cudaStreamSynchronize(h->stream);
   dfree(h, h->f[0], f_bytes(h));
   dfree(h, h->f[1], f_bytes(h));
-  dfree(h, h->rho[0], h->N * 8);
-  dfree(h, h->rho[1], h->N * 8);
-  dfree(h, h->rho_snap, h->N * 8);
+  dfree(h, h->rho[0], r_bytes(h));
+  dfree(h, h->rho[1], r_bytes(h));
+  dfree(h, h->rho_snap, r_bytes(h));
   dfree(h, h->d_bad, 8);
   dfree(h, h->d_partials, size_t(h->n_partials) * 4 * 8);
   dfree(h, h->d_obs, 64);
@@ -382,9 +395,9 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
   const size_t fb = f_bytes(h);
   h->f[0] = dalloc(h, fb);
   h->f[1] = dalloc(h, fb);
-  h->rho[0] = static_cast<double*>(dalloc(h, h->N * 8));
-  h->rho[1] = static_cast<double*>(dalloc(h, h->N * 8));
-  h->rho_snap = static_cast<double*>(dalloc(h, h->N * 8));
+  h->rho[0] = dalloc(h, r_bytes(h));
+  h->rho[1] = dalloc(h, r_bytes(h));
+  h->rho_snap = dalloc(h, r_bytes(h));
   h->d_bad = static_cast<unsigned long long*>(dalloc(h, 8));
   h->d_obs = static_cast<double*>(dalloc(h, 64));
   // partials: one per CTA of the observation pass (upper bound over tilings used)
@@ -413,15 +426,17 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
 static int run_init(lbm_handle* h, const InitSpec& s) {
   const int bs = 256;
   if (h->p.precision == LBM_FP64)
-    k_init<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, s, static_cast<double*>(h->f[0]), h->rho[0]);
+    k_init<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, s, static_cast<double*>(h->f[0]),
+                                                          static_cast<double*>(h->rho[0]));
   else
-    k_init<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, s, static_cast<float*>(h->f[0]), h->rho[0]);
+    k_init<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, s, static_cast<float*>(h->f[0]),
+                                                         static_cast<float*>(h->rho[0]));
   h->cur = 0;
   h->t = 0;
   h->t_snap = 0;
   unsigned long long init = ULLONG_MAX;
   if (cudaMemcpyAsync(h->d_bad, &init, 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return LBM_ECUDA;
-  if (cudaMemcpyAsync(h->rho_snap, h->rho[0], h->N * 8, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(h->rho_snap, h->rho[0], r_bytes(h), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return LBM_ECUDA;
   // host arrays referenced by the spec must outlive the kernel: synchronise
   return ck(cudaStreamSynchronize(h->stream));
@@ -489,13 +504,18 @@ extern "C" int lbm_init_profile(lbm_handle* h, const double center[3], const dou
 
 extern "C" int lbm_init_density(lbm_handle* h, const double* host_rho) {
   if (!h || !host_rho) return LBM_EINVAL;
-  // stage through the second density buffer (it is rewritten by the first step)
-  int rc = ck(cudaMemcpyAsync(h->rho[1], host_rho, h->N * 8, cudaMemcpyHostToDevice, h->stream));
-  if (rc != LBM_OK) return rc;
-  InitSpec s{};
-  s.kind = 3;
-  s.dens = h->rho[1];
-  return run_init(h, s);
+  double* tmp = static_cast<double*>(dalloc(h, size_t(h->N) * 8));
+  if (!tmp) return LBM_ENOMEM;
+  int rc = ck(cudaMemcpyAsync(tmp, host_rho, h->N * 8, cudaMemcpyHostToDevice, h->stream));
+  if (rc == LBM_OK) {
+    InitSpec s{};
+    s.kind = 3;
+    s.dens = tmp;
+    rc = run_init(h, s);
+  }
+  cudaStreamSynchronize(h->stream);
+  dfree(h, tmp, size_t(h->N) * 8);
+  return rc;
 }
 
 extern "C" int lbm_set_f(lbm_handle* h, const double* host_f) {
@@ -509,10 +529,12 @@ extern "C" int lbm_set_f(lbm_handle* h, const double* host_f) {
     h->cur = 0;
     if (h->p.precision == LBM_FP64) {
       k_import_f<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, tmp, static_cast<double*>(h->f[0]));
-      k_density<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, static_cast<double*>(h->f[0]), h->rho[0]);
+      k_density<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, static_cast<double*>(h->f[0]),
+                                                               static_cast<double*>(h->rho[0]));
     } else {
       k_import_f<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, tmp, static_cast<float*>(h->f[0]));
-      k_density<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, static_cast<float*>(h->f[0]), h->rho[0]);
+      k_density<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, static_cast<float*>(h->f[0]),
+                                                              static_cast<float*>(h->rho[0]));
     }
     rc = ck(cudaGetLastError());
   }
@@ -520,7 +542,7 @@ extern "C" int lbm_set_f(lbm_handle* h, const double* host_f) {
   h->t_snap = 0;
   unsigned long long init = ULLONG_MAX;
   if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(h->d_bad, &init, 8, cudaMemcpyHostToDevice, h->stream));
-  if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(h->rho_snap, h->rho[0], h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
+  if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(h->rho_snap, h->rho[0], r_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
   cudaStreamSynchronize(h->stream);
   dfree(h, tmp, bytes);
   return rc;
@@ -539,7 +561,50 @@ static Launch make_launch(lbm_handle* h, int out_buf) {
   c.aux.partials = h->d_partials;
   c.aux.rho_snap = h->rho_snap;
   c.stream = h->stream;
+  c.zc = h->zc;
   return c;
+}
+
+static bool tunable(const lbm_handle* h) {
+  return h->D == 3 && h->prec == 1 && !h->compact &&
+         (h->p.scheme == LBM_EFDS2 || h->p.scheme == LBM_EFDS4 || h->p.scheme == LBM_EFDS6 || h->p.scheme == LBM_E4);
+}
+
+extern "C" int lbm_set_zchunk(lbm_handle* h, int zc) {
+  if (!h || zc < 0) return LBM_EINVAL;
+  h->zc = zc > h->p.nz ? h->p.nz : zc;
+  return LBM_OK;
+}
+
+extern "C" int lbm_autotune(lbm_handle* h, int* zc_out) {
+  if (!h) return LBM_EINVAL;
+  if (zc_out) *zc_out = 0;
+  if (!tunable(h)) return LBM_OK;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LBM_ECUDA;
+  const long long t_saved = h->t;
+  int prev = 0, best_zc = 0;
+  float best = 1e30f;
+  for (int nzc = 1; nzc <= 32 && nzc <= h->p.nz; ++nzc) {
+    const int zc = (h->p.nz + nzc - 1) / nzc;
+    if (zc == prev || (zc < 4 && nzc > 1)) continue;
+    prev = zc;
+    h->zc = zc;
+    if (lbm_step(h, 1) != LBM_OK) break;
+    cudaEventRecord(e0, h->stream);
+    if (lbm_step(h, 3) != LBM_OK) break;
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_zc = zc; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->t = t_saved;
+  h->zc = best_zc;
+  if (zc_out) *zc_out = best_zc;
+  return best_zc > 0 ? LBM_OK : LBM_ECUDA;
 }
 
 extern "C" int lbm_step(lbm_handle* h, long long n) {
@@ -573,10 +638,15 @@ extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
   if (nb > h->n_partials) return LBM_ECUDA;
   const long long center =
       (long long)(h->p.nz / 2) * h->p.nx * h->p.ny + (long long)(h->p.ny / 2) * h->p.nx + h->p.nx / 2;
-  k_obs_final<<<1, 256, 0, h->stream>>>(h->d_partials, nb, h->rho[h->cur], center, h->d_bad, h->d_obs);
+  if (h->p.precision == LBM_FP64)
+    k_obs_final<double><<<1, 256, 0, h->stream>>>(h->d_partials, nb, static_cast<const double*>(h->rho[h->cur]), 0.0,
+                                                  center, h->d_bad, h->d_obs);
+  else
+    k_obs_final<float><<<1, 256, 0, h->stream>>>(h->d_partials, nb, static_cast<const float*>(h->rho[h->cur]),
+                                                 h->kp.rho_ref, center, h->d_bad, h->d_obs);
   double host[8];
   if (cudaMemcpyAsync(host, h->d_obs, 64, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return LBM_ECUDA;
-  if (cudaMemcpyAsync(h->rho_snap, h->rho[h->cur], h->N * 8, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(h->rho_snap, h->rho[h->cur], r_bytes(h), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return LBM_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
   unsigned long long bad;
@@ -600,8 +670,19 @@ extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
 
 extern "C" int lbm_get_density(lbm_handle* h, double* host_rho) {
   if (!h || !host_rho) return LBM_EINVAL;
-  int rc = ck(cudaMemcpyAsync(host_rho, h->rho[h->cur], h->N * 8, cudaMemcpyDeviceToHost, h->stream));
-  if (rc == LBM_OK) rc = ck(cudaStreamSynchronize(h->stream));
+  if (h->p.precision == LBM_FP64) {
+    int rc = ck(cudaMemcpyAsync(host_rho, h->rho[h->cur], h->N * 8, cudaMemcpyDeviceToHost, h->stream));
+    if (rc == LBM_OK) rc = ck(cudaStreamSynchronize(h->stream));
+    return rc;
+  }
+  double* tmp = static_cast<double*>(dalloc(h, size_t(h->N) * 8));
+  if (!tmp) return LBM_ENOMEM;
+  const int bs = 256;
+  k_export_rho<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, static_cast<const float*>(h->rho[h->cur]), tmp);
+  int rc = ck(cudaGetLastError());
+  if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(host_rho, tmp, h->N * 8, cudaMemcpyDeviceToHost, h->stream));
+  cudaStreamSynchronize(h->stream);
+  dfree(h, tmp, size_t(h->N) * 8);
   return rc;
 }
 

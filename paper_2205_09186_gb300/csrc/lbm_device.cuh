@@ -39,10 +39,12 @@ struct Lattice<1> {
 };
 
 // ------------------------------------------------------------------ precision policies
-// FP64: everything double.  FP32DEV: populations stored as f_i - w_i rho_ref in
-// float, collision and stencils in float, density field double; Tm is the type
-// of the chemical potential.
+// FP64: everything double.  FP32DEV: populations stored as f_i - w_i rho_ref and
+// the density field as rho - rho_ref, both in float; collision and stencils in
+// float; Tm is the type of the chemical potential.  No FP64 instruction is on
+// the FP32DEV step path unless Tm is double.
 struct PrecF64 {
+  using Tr = double;  // stored density field (full density)
   using Tf = double;  // stored population
   using Tc = double;  // collision / force arithmetic
   using Ts = double;  // density stencil operand
@@ -50,6 +52,7 @@ struct PrecF64 {
   static constexpr bool DEV = false;
 };
 struct PrecF32 {
+  using Tr = float;  // stored density field: rho - rho_ref
   using Tf = float;
   using Tc = float;
   using Ts = float;
@@ -57,6 +60,7 @@ struct PrecF32 {
   static constexpr bool DEV = true;
 };
 struct PrecF32M64 {
+  using Tr = float;
   using Tf = float;
   using Tc = float;
   using Ts = float;
@@ -78,7 +82,7 @@ struct StepAux {
   long long t;                     // step index of the state being advanced
   unsigned long long* bad_step;    // atomicMin target: first step with rho <= 0 or NaN
   double* partials;                // observables: per-block partial results
-  const double* rho_snap;          // observables: density at the previous observation
+  const void* rho_snap;            // observables: density field (type Tr) at the previous observation
 };
 
 __device__ __forceinline__ float lg(float x) { return logf(x); }
@@ -255,6 +259,7 @@ struct FSum {
     s = t;
   }
   __device__ __forceinline__ double value() const { return double(s) + double(c); }
+  __device__ __forceinline__ float fvalue() const { return s + c; }
 };
 
 }  // namespace lbmd

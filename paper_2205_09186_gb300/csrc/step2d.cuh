@@ -31,9 +31,7 @@ struct Step2DShape {
   static constexpr int RW = TX + 2 * H, RH = TY + 2 * H;          // density region
   static constexpr int MW = TX + 2 * R + 2, MH = TY + 2 * R + 2;  // mu region
   static constexpr int CW = TX + 2, CH = TY + 2;                  // collision region
-  static constexpr size_t off_ds = size_t(RH) * RW * sizeof(double);
-  static constexpr size_t sz_ds = P::DEV ? size_t(RH) * RW * sizeof(typename P::Ts) : 0;
-  static constexpr size_t off_mu = (off_ds + sz_ds + 15) / 16 * 16;
+  static constexpr size_t off_mu = (size_t(RH) * RW * sizeof(typename P::Tr) + 15) / 16 * 16;
   static constexpr size_t off_f = (off_mu + size_t(MH) * MW * sizeof(typename P::Tm) + 15) / 16 * 16;
   static constexpr size_t bytes = off_f + size_t(9) * CH * CW * sizeof(typename P::Tf);
 };
@@ -67,11 +65,14 @@ __device__ __forceinline__ void block_obs_reduce(double vmax, double umax, doubl
   }
 }
 
+// One TX x TY tile of the fused step (all threads of the CTA take part).
+// partial: where MODE_OBS writes this tile's 4 partial observables.
 template <int S, class P, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename P::Tf* __restrict__ fin,
-                                                typename P::Tf* __restrict__ fout, const double* __restrict__ rin,
-                                                double* __restrict__ rout, const StepAux aux, const FieldOut fo,
-                                                const GradIn gi) {
+__device__ __forceinline__ void step2d_tile(const KParams& p, const typename P::Tf* __restrict__ fin,
+                                            typename P::Tf* __restrict__ fout, const typename P::Tr* __restrict__ rin,
+                                            typename P::Tr* __restrict__ rout, const StepAux& aux, const FieldOut& fo,
+                                            const GradIn& gi, const int x0, const int y0, unsigned char* smem,
+                                            double* partial) {
   using Tf = typename P::Tf;
   using Tc = typename P::Tc;
   using Ts = typename P::Ts;
@@ -80,16 +81,14 @@ __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename 
   using Sh = Step2DShape<S, P, TX, TY>;
   constexpr int Q = 9, R = Sh::R, H = Sh::H, RW = Sh::RW, MW = Sh::MW, CW = Sh::CW, CH = Sh::CH;
 
-  extern __shared__ __align__(16) unsigned char smem[];
-  double* s_rho = reinterpret_cast<double*>(smem);
-  const Ts* s_ds = P::DEV ? reinterpret_cast<const Ts*>(smem + Sh::off_ds) : reinterpret_cast<const Ts*>(smem);
-  Ts* s_ds_w = reinterpret_cast<Ts*>(smem + Sh::off_ds);
+  using Tr = typename P::Tr;
+  // density (FP64 mode) or density deviation rho - rho_ref (FP32DEV) of the region
+  Tr* s_ds = reinterpret_cast<Tr*>(smem);
   Tm* s_mu = reinterpret_cast<Tm*>(smem + Sh::off_mu);
   Tf* s_f = reinterpret_cast<Tf*>(smem + Sh::off_f);
 
   const int nx = p.nx, ny = p.ny;
   const long long N = p.n;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int VW = min(TX, nx - x0), VH = min(TY, ny - y0);
   const int tid = threadIdx.x;
 
@@ -102,9 +101,7 @@ __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename 
       if (gx < 0) gx += nx;
       int gy = (y0 - H + ry) % ny;
       if (gy < 0) gy += ny;
-      const double v = rin[(long long)gy * nx + gx];
-      s_rho[ry * RW + rx] = v;
-      if constexpr (P::DEV) s_ds_w[ry * RW + rx] = Ts(v - p.rho_ref);
+      s_ds[ry * RW + rx] = rin[(long long)gy * nx + gx];
     }
   }
   __syncthreads();
@@ -116,7 +113,7 @@ __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename 
     for (int idx = tid; idx < mw * mh; idx += NT2) {
       const int my = idx / mw, mx = idx - my * mw;
       const int sx = mx + (H - R - 1), sy = my + (H - R - 1);
-      const Tm rho = Tm(s_rho[sy * RW + sx]);
+      const Tm rho = P::DEV ? Tm(p.rho_ref) + Tm(s_ds[sy * RW + sx]) : Tm(s_ds[sy * RW + sx]);
       const Tm lap = lap2d<S, Tm>(s_ds, RW, sx, sy);
       s_mu[my * MW + mx] = k2 * cs_mu<Tm>(rho, RT, b4, two_a) - kap * lap;
     }
@@ -138,14 +135,15 @@ __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename 
       Tf fv[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) fv[i] = fin[i * N + node];
-      const double rho = s_rho[(ly + H) * RW + lx + H];
+      const Tr dsv = s_ds[(ly + H) * RW + lx + H];
+      const double rho = P::DEV ? p.rho_ref + double(dsv) : double(dsv);
       Tc jx = 0, jy = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         if (L::ex(i) != 0) jx += Tc(L::ex(i)) * Tc(fv[i]);
         if (L::ey(i) != 0) jy += Tc(L::ey(i)) * Tc(fv[i]);
       }
-      const Tc rc = Tc(rho);
+      const Tc rc = P::DEV ? Tc(p.rho_ref) + Tc(dsv) : Tc(dsv);
       const Tc ux = jx / rc, uy = jy / rc;
       Tm gmx, gmy;
       Tc grx, gry;
@@ -160,9 +158,9 @@ __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename 
       }
       const Tc Fx = -rc * Tc(gmx) + grx / Tc(3), Fy = -rc * Tc(gmy) + gry / Tc(3);
       if constexpr (MODE == MODE_STEP) {
-        if (interior && !(rho > 0.0)) atomicMin(aux.bad_step, (unsigned long long)aux.t);
+        if (interior && !(rc > Tc(0))) atomicMin(aux.bad_step, (unsigned long long)aux.t);
         const Tc vx = ux + Fx / rc, vy = uy + Fy / rc;
-        const Tc dr = Tc(rho - p.rho_ref);
+        const Tc dr = P::DEV ? Tc(dsv) : rc;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const Tc fs = coll_one<0, Tc>(i, Tc(fv[i]), dr, rc, omega, ux, uy, Tc(0), vx, vy, Tc(0));
@@ -178,7 +176,7 @@ __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename 
         o_vmax = fmax(o_vmax, sqrt(vx * vx + vy * vy));
         o_umax = fmax(o_umax, sqrt(dux * dux + duy * duy));
         o_mass += rho;
-        o_dmax = fmax(o_dmax, fabs(rho - aux.rho_snap[node]));
+        o_dmax = fmax(o_dmax, fabs(double(dsv) - double(static_cast<const Tr*>(aux.rho_snap)[node])));
         if (!(rho > 0.0)) atomicMin(aux.bad_step, (unsigned long long)aux.t);
       } else {
         fo.F[node] = double(Fx);
@@ -190,7 +188,7 @@ __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename 
   }
 
   if constexpr (MODE == MODE_OBS) {
-    block_obs_reduce<NT2>(o_vmax, o_umax, o_mass, o_dmax, aux.partials + 4 * (blockIdx.y * gridDim.x + blockIdx.x));
+    block_obs_reduce<NT2>(o_vmax, o_umax, o_mass, o_dmax, partial);
     return;
   }
   if constexpr (MODE == MODE_STEP) {
@@ -199,23 +197,36 @@ __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename 
     for (int idx = tid; idx < VW * VH; idx += NT2) {
       const int ly = idx / VW, lx = idx - ly * VW;
       const int cx = lx + 1, cy = ly + 1;
-      double rn;
+      Tr rn;
+      bool ok;
       if constexpr (P::DEV) {
         FSum acc;
 #pragma unroll
         for (int i = 0; i < Q; ++i) acc.add(float(s_f[i * CH * CW + (cy - L::ey(i)) * CW + cx - L::ex(i)]));
-        rn = p.rho_ref + acc.value();
+        rn = acc.fvalue();
+        ok = float(p.rho_ref) + rn > 0.f;
       } else {
         double acc = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) acc += double(s_f[i * CH * CW + (cy - L::ey(i)) * CW + cx - L::ex(i)]);
         rn = acc;
+        ok = rn > 0.0;
       }
       const long long node = (long long)(y0 + ly) * nx + x0 + lx;
       rout[node] = rn;
-      if (!(rn > 0.0)) atomicMin(aux.bad_step, (unsigned long long)(aux.t + 1));
+      if (!ok) atomicMin(aux.bad_step, (unsigned long long)(aux.t + 1));
     }
   }
+}
+
+template <int S, class P, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename P::Tf* __restrict__ fin,
+                                                typename P::Tf* __restrict__ fout, const typename P::Tr* __restrict__ rin,
+                                                typename P::Tr* __restrict__ rout, const StepAux aux, const FieldOut fo,
+                                                const GradIn gi) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  step2d_tile<S, P, TX, TY, MODE>(p, fin, fout, rin, rout, aux, fo, gi, blockIdx.x * TX, blockIdx.y * TY, smem,
+                                  aux.partials + 4 * (blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 }  // namespace lbmd

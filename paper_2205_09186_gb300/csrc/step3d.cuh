@@ -30,7 +30,7 @@ struct Step3DShape {
   static constexpr int CW = TX + 2, CH = TY + 2;                  // collision region
   static constexpr size_t ds_plane = size_t(RH) * RW;
   static constexpr size_t mu_plane = size_t(MH) * MW;
-  static constexpr size_t off_mu = (NS * ds_plane * sizeof(typename P::Ts) + 15) / 16 * 16;
+  static constexpr size_t off_mu = (NS * ds_plane * sizeof(typename P::Tr) + 15) / 16 * 16;
   static constexpr size_t off_f = (off_mu + NS * mu_plane * sizeof(typename P::Tm) + 15) / 16 * 16;
   static constexpr size_t bytes = off_f + size_t(19) * CH * CW * sizeof(typename P::Tf);
   static constexpr int K = (TX * TY + NT3 - 1) / NT3;  // interior nodes per thread
@@ -105,9 +105,10 @@ __device__ __forceinline__ int pmod(int a, int n) {
 
 template <int S, class P, int TX, int TY, int ZC, int MODE>
 __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename P::Tf* __restrict__ fin,
-                                                typename P::Tf* __restrict__ fout, const double* __restrict__ rin,
-                                                double* __restrict__ rout, const StepAux aux, const FieldOut fo,
+                                                typename P::Tf* __restrict__ fout, const typename P::Tr* __restrict__ rin,
+                                                typename P::Tr* __restrict__ rout, const StepAux aux, const FieldOut fo,
                                                 const GradIn gi) {
+  using Tr = typename P::Tr;
   using Tf = typename P::Tf;
   using Tc = typename P::Tc;
   using Ts = typename P::Ts;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
   constexpr int K = Sh::K;
 
   extern __shared__ __align__(16) unsigned char smem[];
-  Ts* s_ds = reinterpret_cast<Ts*>(smem);
+  Tr* s_ds = reinterpret_cast<Tr*>(smem);  // density (FP64) or rho - rho_ref (FP32DEV)
   Tm* s_mu = reinterpret_cast<Tm*>(smem + Sh::off_mu);
   Tf* s_f = reinterpret_cast<Tf*>(smem + Sh::off_f);
 
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
     {
       const int slot = pmod(ql, NS);
       const long long zoff = (long long)pmod(ql, nz) * NXY;
-      Ts* dsp = s_ds + slot * Sh::ds_plane;
+      Tr* dsp = s_ds + slot * Sh::ds_plane;
       Tm* mup = s_mu + slot * Sh::mu_plane;
       for (int idx = tid; idx < rw * rh; idx += NT3) {
         const int ry = idx / rw, rx = idx - ry * rw;
@@ -158,11 +159,12 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
         if (gx < 0) gx += nx;
         int gy = (y0 - H + ry) % ny;
         if (gy < 0) gy += ny;
-        const double v = rin[zoff + (long long)gy * nx + gx];
-        dsp[ry * RW + rx] = Ts(v - p.rho_ref);
+        const Tr v = rin[zoff + (long long)gy * nx + gx];
+        dsp[ry * RW + rx] = v;
         const int mx = rx - (H - R - 1), my = ry - (H - R - 1);
         if constexpr (!Sch<S>::GF)
-          if (mx >= 0 && mx < mw && my >= 0 && my < mh) mup[my * MW + mx] = k2 * cs_mu<Tm>(Tm(v), RT, b4, two_a);
+          if (mx >= 0 && mx < mw && my >= 0 && my < mh)
+            mup[my * MW + mx] = k2 * cs_mu<Tm>(P::DEV ? Tm(p.rho_ref) + Tm(v) : Tm(v), RT, b4, two_a);
       }
     }
     __syncthreads();
@@ -206,8 +208,7 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
         Tf fv[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) fv[i] = fin[i * N + node];
-        const Ts dsv = s_ds[bds[R] + (ly + H) * RW + lx + H];
-        const double rho = P::DEV ? p.rho_ref + double(dsv) : double(dsv);
+        const Tr dsv = s_ds[bds[R] + (ly + H) * RW + lx + H];
         Tc jx = 0, jy = 0, jz = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
         }
         const Tc Fx = -rc * Tc(gmx) + grx / Tc(3), Fy = -rc * Tc(gmy) + gry / Tc(3), Fz = -rc * Tc(gmz) + grz / Tc(3);
         if constexpr (MODE == MODE_STEP) {
-          if (own && interior && !(rho > 0.0)) atomicMin(aux.bad_step, (unsigned long long)aux.t);
+          if (own && interior && !(rc > Tc(0))) atomicMin(aux.bad_step, (unsigned long long)aux.t);
           const Tc vx = ux + Fx / rc, vy = uy + Fy / rc, vz = uz + Fz / rc;
           const Tc dr = P::DEV ? Tc(dsv) : rc;
 #pragma unroll
@@ -243,14 +244,15 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
             }
           }
         } else if constexpr (MODE == MODE_OBS) {
+          const double rho = P::DEV ? p.rho_ref + double(dsv) : double(dsv);
           const double dux = double(ux), duy = double(uy), duz = double(uz);
           const double vx = dux + double(Fx) / (2.0 * rho), vy = duy + double(Fy) / (2.0 * rho),
                        vz = duz + double(Fz) / (2.0 * rho);
           o_vmax = fmax(o_vmax, sqrt(vx * vx + vy * vy + vz * vz));
           o_umax = fmax(o_umax, sqrt(dux * dux + duy * duy + duz * duz));
-          const double rtrue = rin[node];
+          const double rtrue = P::DEV ? p.rho_ref + double(rin[node]) : double(rin[node]);
           o_mass += rtrue;
-          o_dmax = fmax(o_dmax, fabs(rtrue - aux.rho_snap[node]));
+          o_dmax = fmax(o_dmax, fabs(double(rin[node]) - double(static_cast<const Tr*>(aux.rho_snap)[node])));
           if (!(rtrue > 0.0)) atomicMin(aux.bad_step, (unsigned long long)aux.t);
         } else {
           fo.F[node] = double(Fx);
@@ -261,8 +263,9 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
         }
       }
     }
+    // the next iteration's load overwrites the ring slot read by this collision
+    __syncthreads();
     if constexpr (MODE == MODE_STEP) {
-      __syncthreads();
       // ---- gather: populations of plane pc stream into planes pc-1, pc, pc+1
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -279,9 +282,12 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
           // plane pc-1 is complete
           const int zt = pc - 1;
           if (zt >= z0 && zt < z1) {
-            const double rn = P::DEV ? p.rho_ref + accD[k][0].value() : accS[k][0];
+            Tr rn;
+            bool okr;
+            if constexpr (P::DEV) { rn = accD[k][0].fvalue(); okr = float(p.rho_ref) + rn > 0.f; }
+            else { rn = accS[k][0]; okr = rn > 0.0; }
             rout[(long long)zt * NXY + (long long)(y0 + ly) * nx + x0 + lx] = rn;
-            if (!(rn > 0.0)) atomicMin(aux.bad_step, (unsigned long long)(aux.t + 1));
+            if (!okr) atomicMin(aux.bad_step, (unsigned long long)(aux.t + 1));
           }
         }
         accD[k][0] = accD[k][1]; accD[k][1] = accD[k][2]; accD[k][2] = FSum();

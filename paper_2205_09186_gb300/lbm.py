@@ -45,6 +45,7 @@ class lbm_allocator(C.Structure):
 
 
 _dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
 _h = C.c_void_p
 
 # name -> (restype, argtypes); every entry point declared in include/lbm.h
@@ -66,7 +67,29 @@ SIGNATURES = {
     "lbm_critical": (C.c_int, [C.c_double, C.c_double, C.c_double, _dp, _dp]),
     "lbm_maxwell": (C.c_int, [C.POINTER(lbm_params), _dp, _dp]),
     "lbm_lattice_q": (C.c_int, [C.c_int]),
+    "lbm_set_zchunk": (C.c_int, [_h, C.c_int]),
+    "lbm_autotune": (C.c_int, [_h, C.POINTER(C.c_int)]),
     "lbm_strerror": (C.c_char_p, [C.c_int]),
+    "lbm_batch_create": (C.c_int, [C.POINTER(lbm_params), C.c_int, C.c_void_p, C.POINTER(lbm_allocator),
+                                   C.POINTER(C.c_void_p)]),
+    "lbm_batch_destroy": (None, [_h]),
+    "lbm_batch_init_droplets": (C.c_int, [_h, _dp, C.c_double]),
+    "lbm_batch_step": (C.c_int, [_h, C.c_longlong]),
+    "lbm_batch_observables": (C.c_int, [_h, C.POINTER(lbm_obs)]),
+    "lbm_batch_get_density": (C.c_int, [_h, C.c_int, _dp]),
+    "lbm_batch_get_step": (C.c_longlong, [_h]),
+    "lbm_batch_size": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lbm_batch_inject_stall": (C.c_int, [_h, C.c_int]),
+    "lbm_mlp_create": (C.c_int, [C.POINTER(C.c_int), C.c_int, C.c_int, C.c_void_p, C.POINTER(lbm_allocator),
+                                 C.POINTER(C.c_void_p)]),
+    "lbm_mlp_destroy": (None, [_h]),
+    "lbm_mlp_param_count": (C.c_longlong, [_h]),
+    "lbm_mlp_set_params": (C.c_int, [_h, _fp]),
+    "lbm_mlp_get_params": (C.c_int, [_h, _fp]),
+    "lbm_mlp_forward": (C.c_int, [_h, _fp, C.c_int, _fp]),
+    "lbm_mlp_loss_grad": (C.c_int, [_h, _fp, _fp, C.c_int, _fp, _fp]),
+    "lbm_mlp_set_data": (C.c_int, [_h, _fp, _fp, C.c_int]),
+    "lbm_mlp_train": (C.c_int, [_h, C.c_int, C.c_float, _fp]),
 }
 
 _LIB = None
@@ -234,7 +257,137 @@ class Sim:
     def lbm_get_step(self):
         return lib().lbm_get_step(self.h)
 
+    def lbm_set_zchunk(self, zc):
+        return check(lib().lbm_set_zchunk(self.h, zc), "lbm_set_zchunk")
+
+    def lbm_autotune(self):
+        zc = C.c_int()
+        check(lib().lbm_autotune(self.h, C.byref(zc)), "lbm_autotune")
+        return zc.value
+
     def lbm_device_state(self):
         f, r = C.c_void_p(), C.c_void_p()
         check(lib().lbm_device_state(self.h, C.byref(f), C.byref(r)), "lbm_device_state")
         return f.value, r.value
+
+
+class Batch:
+    """Many D2Q9 droplets advanced together (C ABI: lbm_batch_*)."""
+
+    def __init__(self, params_list, stream=None, allocator="torch"):
+        import torch
+        n = len(params_list)
+        arr = (lbm_params * n)(*params_list)
+        self.params = list(params_list)
+        st = C.c_void_p(int(stream)) if stream is not None else C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        self._alloc = TorchAllocator(stream=torch.cuda.current_stream()) if allocator == "torch" else None
+        h = C.c_void_p()
+        check(lib().lbm_batch_create(arr, n, st, C.byref(self._alloc.struct) if self._alloc else None, C.byref(h)),
+              "lbm_batch_create")
+        self.h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def lbm_batch_init_droplets(self, radius, width=10.0):
+        r = _f64(radius)
+        assert r.size == self.n
+        return check(lib().lbm_batch_init_droplets(self.h, _ptr(r), width), "lbm_batch_init_droplets")
+
+    def lbm_batch_step(self, n=1):
+        return check(lib().lbm_batch_step(self.h, n), "lbm_batch_step")
+
+    def lbm_batch_observables(self, raise_errors=True):
+        out = (lbm_obs * self.n)()
+        rc = lib().lbm_batch_observables(self.h, out)
+        if raise_errors and rc != LBM_OK:
+            check(rc, "lbm_batch_observables")
+        return rc, [o.as_dict() for o in out]
+
+    def lbm_batch_get_density(self, c):
+        p = self.params[c]
+        out = np.empty((p.ny, p.nx))
+        check(lib().lbm_batch_get_density(self.h, c, _ptr(out)), "lbm_batch_get_density")
+        return out
+
+    def lbm_batch_get_step(self):
+        return lib().lbm_batch_get_step(self.h)
+
+    def lbm_batch_size(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        check(lib().lbm_batch_size(self.h, C.byref(a), C.byref(b), C.byref(c)), "lbm_batch_size")
+        return a.value, b.value, c.value
+
+    def lbm_batch_inject_stall(self, cta):
+        return check(lib().lbm_batch_inject_stall(self.h, cta), "lbm_batch_inject_stall")
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(_fp)
+
+
+class MLP:
+    """Warm-start network (C ABI: lbm_mlp_*)."""
+
+    def __init__(self, sizes, max_batch, stream=None, allocator="torch"):
+        import torch
+        sz = (C.c_int * len(sizes))(*sizes)
+        self.sizes = list(sizes)
+        st = C.c_void_p(int(stream)) if stream is not None else C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        self._alloc = TorchAllocator(stream=torch.cuda.current_stream()) if allocator == "torch" else None
+        h = C.c_void_p()
+        check(lib().lbm_mlp_create(sz, len(sizes) - 1, max_batch, st,
+                                   C.byref(self._alloc.struct) if self._alloc else None, C.byref(h)), "lbm_mlp_create")
+        self.h = h
+        self.nparam = lib().lbm_mlp_param_count(h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def lbm_mlp_set_params(self, p):
+        p = _f32(p)
+        assert p.size == self.nparam
+        return check(lib().lbm_mlp_set_params(self.h, _fptr(p)), "lbm_mlp_set_params")
+
+    def lbm_mlp_get_params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        check(lib().lbm_mlp_get_params(self.h, _fptr(out)), "lbm_mlp_get_params")
+        return out
+
+    def lbm_mlp_forward(self, x):
+        x = _f32(x)
+        y = np.empty((x.shape[0], self.sizes[-1]), dtype=np.float32)
+        check(lib().lbm_mlp_forward(self.h, _fptr(x), x.shape[0], _fptr(y)), "lbm_mlp_forward")
+        return y
+
+    def lbm_mlp_loss_grad(self, x, t):
+        x, t = _f32(x), _f32(t)
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        check(lib().lbm_mlp_loss_grad(self.h, _fptr(x), _fptr(t), x.shape[0], _fptr(loss), _fptr(g)),
+              "lbm_mlp_loss_grad")
+        return float(loss[0]), g
+
+    def lbm_mlp_set_data(self, x, t):
+        x, t = _f32(x), _f32(t)
+        return check(lib().lbm_mlp_set_data(self.h, _fptr(x), _fptr(t), x.shape[0]), "lbm_mlp_set_data")
+
+    def lbm_mlp_train(self, iters, lr=1e-3):
+        loss = np.zeros(1, dtype=np.float32)
+        check(lib().lbm_mlp_train(self.h, iters, lr, _fptr(loss)), "lbm_mlp_train")
+        return float(loss[0])

@@ -1,0 +1,95 @@
+"""Batched droplets in one persistent graph-captured launch: results equal
+the single-case path, replays continue the run, per-case instability is
+reported, and a stalled device barrier returns LBM_ETIMEOUT (no hang)."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2205_09186_gb300 as pkg
+    pkg.build()
+    from paper_2205_09186_gb300 import lbm
+    return lbm
+
+
+CASES = [dict(nx=64, ny=48, Tr=0.8, k=0.25, scheme="EFDS4", r=12.0),
+         dict(nx=40, ny=72, Tr=0.9, k=0.3, scheme="E4", r=10.0),
+         dict(nx=96, ny=96, Tr=0.8, k=0.2, scheme="EFDS6", r=20.0),
+         dict(nx=33, ny=35, Tr=0.85, k=0.25, scheme="E8", r=8.0),
+         dict(nx=64, ny=64, Tr=0.7, k=0.25, scheme="EFDS2", r=16.0)]  # goes unstable
+
+
+def params(L, c, precision):
+    return L.make_params(lattice=L.LBM_D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1,
+                         scheme=c["scheme"], precision=precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_single_case_path(L, precision):
+    b = L.Batch([params(L, c, precision) for c in CASES])
+    b.lbm_batch_init_droplets([c["r"] for c in CASES])
+    b.lbm_batch_step(30)
+    b.lbm_batch_step(30)  # graph replay continues the run
+    assert b.lbm_batch_get_step() == 60
+    rc, obs = b.lbm_batch_observables(raise_errors=False)
+    assert rc == 0
+    for i, c in enumerate(CASES[:4]):
+        s = L.Sim(params(L, c, precision))
+        s.lbm_init_droplet(c["r"])
+        s.lbm_step(60)
+        # same tile code, compiled in another unit: equal up to rounding
+        rb, rs = b.lbm_batch_get_density(i), s.lbm_get_density()
+        assert np.max(np.abs(rb - rs)) / np.max(rs) < (1e-12 if precision == 0 else 1e-6), c
+        o = s.lbm_observables()
+        assert obs[i]["status"] == 0
+        for key in ("max_v", "max_u", "mass", "rho_center", "rho_corner"):
+            assert obs[i][key] == pytest.approx(o[key], rel=1e-10 if precision == 0 else 1e-3), (c, key)
+
+
+def test_batch_fp64_matches_oracle(L):
+    c = CASES[0]
+    b = L.Batch([params(L, c, 0) for c in CASES[:2]])
+    b.lbm_batch_init_droplets([c["r"] for c in CASES[:2]])
+    b.lbm_batch_step(25)
+    o = O.Sim(lattice=O.D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1, scheme=c["scheme"])
+    o.init_droplet(c["r"])
+    assert o.step(25) == 0
+    ro = o.density()
+    assert np.max(np.abs(b.lbm_batch_get_density(0) - ro)) / np.max(ro) < 1e-12
+
+
+def test_batch_reports_unstable_case(L):
+    b = L.Batch([params(L, c, 1) for c in CASES])
+    b.lbm_batch_init_droplets([c["r"] for c in CASES])
+    b.lbm_batch_step(1500)
+    rc, obs = b.lbm_batch_observables(raise_errors=False)
+    assert rc == 0
+    assert obs[4]["status"] == L.LBM_EUNSTABLE and 0 < obs[4]["step"] < 1500
+    assert all(obs[i]["status"] == 0 for i in range(4))
+
+
+def test_stalled_barrier_times_out(L):
+    import time
+    b = L.Batch([params(L, c, 1) for c in CASES[:3]])
+    b.lbm_batch_init_droplets([c["r"] for c in CASES[:3]])
+    _, _, grid = b.lbm_batch_size()
+    b.lbm_batch_inject_stall(grid - 1)
+    t0 = time.time()
+    b.lbm_batch_step(3)
+    rc, _ = b.lbm_batch_observables(raise_errors=False)
+    assert rc == L.LBM_ETIMEOUT
+    assert time.time() - t0 < 30
+    b.lbm_batch_inject_stall(-1)
+    # the context stays usable
+    s = L.Sim(params(L, CASES[0], 1))
+    s.lbm_init_droplet(CASES[0]["r"])
+    s.lbm_step(5)
+    assert s.lbm_observables()["status"] == 0

@@ -190,3 +190,20 @@ def test_zero_steps_and_invalid_arguments(L):
     with pytest.raises(L.LBMError) as e:
         L.Sim(L.make_params(lattice=L.LBM_D3Q19, nx=16, ny=16, nz=16, scheme="E8"))
     assert e.value.code == L.LBM_ENOTSUP
+
+
+def test_zchunk_and_autotune_do_not_change_results(L):
+    kw = dict(lattice=L.LBM_D3Q19, nx=48, ny=40, nz=44, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
+              precision=L.LBM_FP32DEV)
+    outs = []
+    for zc in (0, 5, 11, 44, -1):
+        g = L.Sim(L.make_params(**kw))
+        if zc < 0:
+            assert g.lbm_autotune() > 0
+        else:
+            g.lbm_set_zchunk(zc)
+        g.lbm_init_droplet(9.0)
+        g.lbm_step(12)
+        outs.append(g.lbm_get_f())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
