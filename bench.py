@@ -27,8 +27,14 @@ METRIC = "MLUPS & HBM-peak fraction of fused step; device-s to converged sweep v
 UNIT = "MLUPS"
 WORKLOAD = dict(lattice="D3Q19", nx=256, ny=256, nz=256, radius=60.0, Tr=0.8, k=0.25, kappa=0.1, tau=1.0,
                 scheme="EFDS6", precision="FP32DEV", mu="fp32")
-# algorithmic bytes per lattice update: read + write 19 FP32 populations and the FP32 density deviation
-B_ALG = 19 * 4 * 2 + 4 * 2
+# algorithmic bytes per lattice update of the step: read + write the 19 FP32
+# populations (152), read + write the FP32 density deviation (8), write + read
+# the FP32 chemical potential field of the mu pass (8)
+B_ALG = 19 * 4 * 2 + 4 * 2 + 4 * 2
+# of which the collision/streaming pass (the dominant kernel) moves: populations
+# read + write, density read + write, mu read
+B_COLL = 19 * 4 * 2 + 4 * 2 + 4
+B_MU = 4 + 4
 SAMPLE_N = 128  # oracle sample lattice (same parameters, radius scaled)
 
 
@@ -90,6 +96,38 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+KERNEL_SOURCES = ["paper_2205_09186_gb300/csrc/step3d_split.cuh", "paper_2205_09186_gb300/csrc/lbm_device.cuh",
+                  "paper_2205_09186_gb300/csrc/step3d_fast.cuh", "paper_2205_09186_gb300/csrc/step3d.cuh"]
+TRAFFIC_FILE = "profiles/k_coll3d_d3q19_fp32dev_traffic.txt"
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(n_nodes):
+    """DRAM bytes per launch of the collision pass from the committed ncu
+    capture, scaled to n_nodes by bytes per lattice update; None when the
+    kernel sources changed since the capture."""
+    try:
+        kv = {}
+        with open(os.path.join(ROOT, TRAFFIC_FILE)) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha256_16") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_lu"]) * n_nodes
+    except Exception:
+        return None
+
+
 def oracle_sample(steps, n=SAMPLE_N):
     """Time the FP64 oracle on an n^3 sample with the workload's parameters."""
     import oracle as O
@@ -102,6 +140,53 @@ def oracle_sample(steps, n=SAMPLE_N):
     dt = time.perf_counter() - t
     assert rc == 0
     return n ** 3 * steps / dt / 1e6, dt
+
+
+def batch_cases(n=512, seed=2205):
+    """Seeded sweep of D2Q9 droplets: sizes uniform in {64..512}^2, radius uniform
+    in [8, L/4], T_r uniform in [0.2, 0.95], k log-uniform in [0.1, 0.4], scheme
+    uniform over the explicit and isotropic schemes."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    schemes = ["EFDS2", "EFDS4", "EFDS6", "E4", "E8"]
+    out = []
+    for _ in range(n):
+        lx, ly = int(rng.integers(64, 513)), int(rng.integers(64, 513))
+        r0 = float(rng.uniform(8, min(lx, ly) / 4))
+        tr = float(rng.uniform(0.2, 0.95))
+        k = float(np.exp(rng.uniform(np.log(0.1), np.log(0.4))))
+        sch = schemes[int(rng.integers(0, len(schemes)))]
+        out.append(dict(nx=lx, ny=ly, r=r0, Tr=tr, k=k, scheme=sch))
+    return out
+
+
+def run_batch(L, steps=50, warmup=10):
+    """512 D2Q9 droplets of uneven sizes in one persistent graph-captured launch
+    per lbm_batch_step (FP32 deviation storage); returns MLUPS and case counts."""
+    import torch
+    cases = batch_cases()
+    params = [L.make_params(lattice=L.LBM_D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1,
+                            scheme=c["scheme"], precision=L.LBM_FP32DEV) for c in cases]
+    b = L.Batch(params)
+    b.lbm_batch_init_droplets([c["r"] for c in cases])
+    nodes = sum(c["nx"] * c["ny"] for c in cases)
+    b.lbm_batch_step(warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.lbm_batch_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rc, obs = b.lbm_batch_observables(raise_errors=False)
+    stable = sum(1 for o in obs if o["status"] == 0)
+    ncases, nitems, grid = b.lbm_batch_size()
+    b.close()
+    return {"workload": "512 D2Q9 droplets, sizes U{64..512}^2 (seed 2205), FP32DEV, one persistent launch",
+            "nodes": nodes, "steps": steps, "ms": ms, "mlups": nodes * steps / (ms * 1e-3) / 1e6,
+            "hbm_frac": nodes * steps * (9 * 4 * 2 + 4 * 2) / (ms * 1e-3) / 1e9 / measured_peak()[0],
+            "stable_cases": stable, "work_items": nitems, "resident_ctas": grid, "status": rc}
 
 
 def run_reference(args):
@@ -149,7 +234,11 @@ def run_gpu(args):
                            kappa=w["kappa"], tau=w["tau"], scheme=w["scheme"], precision=L.LBM_FP32DEV, mu_fp64=0)
     stream = torch.cuda.current_stream()
     sim = L.Sim(params)
-    zc = sim.lbm_autotune()  # z-chunk of the D3Q19 kernel; leaves the state undefined
+    if args.zchunk > 0:
+        sim.lbm_set_zchunk(args.zchunk)
+        zc = args.zchunk
+    else:
+        zc = sim.lbm_autotune()  # z-chunk of the D3Q19 kernel; leaves the state undefined
     sim.lbm_init_droplet(w["radius"])
     N = w["nx"] * w["ny"] * w["nz"]
     for _ in range(args.warmup):
@@ -159,15 +248,15 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        ev[0].record(stream)
-        for i in range(args.steps):
-            sim.lbm_step(1)
-            ev[i + 1].record(stream)
+        e0.record(stream)
+        # one step per launch group; CUDA events between the mu pass and the
+        # collision pass time the dominant kernel on the handle's own stream
+        phase_ms = sim.lbm_step_timed(args.steps)
+        e1.record(stream)
         torch.cuda.synchronize()
-    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = e0.elapsed_time(e1)
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -176,8 +265,9 @@ def run_gpu(args):
     obs = sim.lbm_observables()
     ok = obs["status"] == 0 and abs(obs["mass"] / obs0["mass"] - 1) < 1e-6
     mlups = N * args.steps * world / (total_ms * 1e-3) / 1e6
-    launch_ms = statistics.mean(per)
-    achieved = B_ALG * N / (launch_ms * 1e-3) / 1e9
+    coll_ms = phase_ms[1] / args.steps   # collision/streaming pass (dominant kernel), per launch
+    mu_ms = phase_ms[0] / args.steps     # mu pass, per launch
+    achieved = B_COLL * N / (coll_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
 
     # end to end through the public API with host buffers: upload the initial
@@ -197,6 +287,10 @@ def run_gpu(args):
     e2e = {"value": N * args.steps * world / e2e_s / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": N * 8 / args.steps, "d2h_bytes_per_step": 64 + N * 8 / args.steps}
 
+    sim.close()
+    extra = {}
+    if not args.no_batch:
+        extra["batch2d"] = run_batch(L)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -215,11 +309,15 @@ def run_gpu(args):
                            parallelism="replicas", zchunk=zc,
                            **WORKLOAD),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "bytes_per_lu": B_ALG, "kernel": "k_step3d (fused mu+grad+force+collide+stream+density)"},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                         "frac": achieved / peak, "traffic": captured_traffic(N), "peak_kind": peak_kind,
+                         "bytes_per_lu": B_COLL, "kernel": "k_coll3d (grad mu, grad rho, force, BGK+EDM, push, next density)",
+                         "kernel_ms": coll_ms, "mu_pass": {"kernel": "k_mu3d", "ms": mu_ms, "bytes_per_lu": B_MU,
+                                                           "achieved": B_MU * N / (mu_ms * 1e-3) / 1e9 if mu_ms > 0 else None},
+                         "step_bytes_per_lu": B_ALG, "step_frac": B_ALG * N / (total_ms / args.steps * 1e-3) / 1e9 / peak},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(), "check": {"status": obs["status"], "mass_rel_change": obs["mass"] / obs0["mass"] - 1,
-                                               "ok": ok}}
+                                               "ok": ok},
+            "extra": extra}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -233,6 +331,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D sweep measurement")
+    ap.add_argument("--zchunk", type=int, default=0, help="fix the z-chunk instead of autotuning (profiling runs)")
     ap.add_argument("--size", type=int, default=256,
                     help="lattice edge (profiling runs only; the benchmark workload is 256)")
     args = ap.parse_args()

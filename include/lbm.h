@@ -164,6 +164,13 @@ int lbm_set_f(lbm_handle* h, const double* host_f);
 /* Advance n >= 0 time steps; asynchronous on the handle's stream. */
 int lbm_step(lbm_handle* h, long long n);
 
+/* As lbm_step (n <= 100000), timing every step on the handle's stream with
+ * CUDA events recorded between the launches; synchronises once at the end.
+ * ms[3] receives the summed
+ * milliseconds of the mu pass (0 when the step is a single fused kernel), of
+ * the collision/streaming pass (the whole step when fused), and of both. */
+int lbm_step_timed(lbm_handle* h, long long n, double* ms);
+
 /* Observables of the current state (synchronises the stream).  Returns
  * LBM_EUNSTABLE (and fills out->status, out->step) once a non-positive or
  * NaN density has been seen. */
@@ -212,6 +219,7 @@ int lbm_lattice_q(int lattice);
 
 /* Static text for an error code. */
 const char* lbm_strerror(int code);
+
 
 /* ==================================================================== batches
  * Many independent D2Q9 droplets of different sizes and parameters advanced

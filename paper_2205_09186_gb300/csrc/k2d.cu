@@ -4,8 +4,9 @@
 
 namespace lbmd {
 
-namespace {
 constexpr int TX2 = 32, TY2 = 8;
+
+namespace {
 
 template <int S, class P, int MODE>
 cudaError_t launch_mode(const Launch& c, int* nblocks) {

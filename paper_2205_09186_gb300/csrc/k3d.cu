@@ -4,10 +4,11 @@
 #include "launch.cuh"
 #include "step3d.cuh"
 #include "step3d_fast.cuh"
+#include "step3d_split.cuh"
 
 namespace lbmd {
 
-int fast_zchunk_heuristic(const KParams& kp, int R) {
+static int num_sms() {
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -15,6 +16,33 @@ int fast_zchunk_heuristic(const KParams& kp, int R) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
+  return sms;
+}
+
+bool split3d_scheme(int scheme, int prec) {
+  return prec == 1 && (scheme == S_EFDS2 || scheme == S_EFDS4 || scheme == S_EFDS6);
+}
+
+// z-chunk for the split collision pass: last-wave balance against the
+// prologue (2R planes of field loads and two extra collided planes)
+static int split_zchunk_heuristic(const KParams& kp, int R) {
+  const long long tiles = (long long)((kp.nx + TXC - 1) / TXC) * ((kp.ny + TYC - 1) / TYC);
+  const long long slots = 2LL * num_sms();
+  double best = 1e300;
+  int best_zc = kp.nz;
+  for (int nzc = 1; nzc <= kp.nz && nzc <= 128; ++nzc) {
+    const int zc = (kp.nz + nzc - 1) / nzc;
+    if (zc < 4 && nzc > 1) break;
+    const long long ctas = tiles * ((kp.nz + zc - 1) / zc);
+    const double waves = double((ctas + slots - 1) / slots);
+    const double cost = waves * (zc + 2 + 0.2 * 2 * R);
+    if (cost < best - 1e-9) { best = cost; best_zc = zc; }
+  }
+  return best_zc;
+}
+
+int fast_zchunk_heuristic(const KParams& kp, int R) {
+  const int sms = num_sms();
   const long long tiles = (long long)((kp.nx + FT - 1) / FT) * ((kp.ny + FT - 1) / FT);
   const long long slots = 2LL * sms;  // two CTAs per SM
   double best = 1e300;
@@ -30,8 +58,9 @@ int fast_zchunk_heuristic(const KParams& kp, int R) {
   return best_zc;
 }
 
-namespace {
 constexpr int TX3 = 32, TY3 = 8, ZC3 = 32;
+
+namespace {
 
 template <int S, class P, int MODE>
 cudaError_t launch_mode(const Launch& c, int* nblocks) {
@@ -72,11 +101,39 @@ cudaError_t launch_fast(const Launch& c, int* nblocks) {
   return cudaGetLastError();
 }
 
+// mu pass + collision pass (line schemes, FP32DEV, FP32 mu)
+template <int S, bool TAU1>
+cudaError_t launch_split(const Launch& c, int* nblocks) {
+  using Sh = CollShape<S>;
+  auto kc = k_coll3d<S, TAU1>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (!c.mu) return cudaErrorInvalidValue;
+  const int zmu = 32;
+  dim3 gm((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + zmu - 1) / zmu);
+  k_mu3d<S><<<gm, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu), zmu);
+  if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
+  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sh::R);
+  dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + TYC - 1) / TYC, (c.kp.nz + zc - 1) / zc);
+  if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
+  kc<<<grid, CNT, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
+                                         static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
+                                         static_cast<float*>(c.rout), c.aux, zc);
+  return cudaGetLastError();
+}
+
 template <int S, class P>
 cudaError_t launch(const Launch& c, int mode, int* nblocks) {
   if constexpr (std::is_same<P, PrecF32>::value) {
-    if (mode == MODE_STEP)
+    if (mode == MODE_STEP) {
+      if constexpr (!Sch<S>::ISO)
+        return c.kp.omega == 1.0 ? launch_split<S, true>(c, nblocks) : launch_split<S, false>(c, nblocks);
       return c.kp.omega == 1.0 ? launch_fast<S, true>(c, nblocks) : launch_fast<S, false>(c, nblocks);
+    }
   }
   if (mode == MODE_STEP) return launch_mode<S, P, MODE_STEP>(c, nblocks);
   if (mode == MODE_OBS) return launch_mode<S, P, MODE_OBS>(c, nblocks);

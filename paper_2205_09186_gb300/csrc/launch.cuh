@@ -16,8 +16,14 @@ struct Launch {
   FieldOut fo;
   GradIn gi;
   cudaStream_t stream;
-  int zc;  // z-chunk of the pipelined D3Q19 kernel; 0 = heuristic
+  int zc;       // z-chunk of the pipelined D3Q19 kernel; 0 = heuristic
+  void* mu;     // N floats: mu field of the split D3Q19 FP32DEV path (else unused)
+  cudaEvent_t ev_mid;  // if set: recorded between the mu pass and the collision pass
 };
+
+// the D3Q19 FP32DEV step of this scheme runs as mu pass + collision pass and
+// needs an N-float mu buffer in Launch::mu
+bool split3d_scheme(int scheme, int prec);
 
 // z-chunk length for the pipelined D3Q19 kernel: balances the last wave of
 // CTAs against the per-chunk prologue (4R + 2 extra planes, of which only 2

@@ -36,6 +36,7 @@ struct lbm_handle {
   CompactBufs cb{};
   bool compact = false;
   int zc = 0;  // z-chunk of the pipelined D3Q19 kernel (0 = heuristic)
+  void* mu = nullptr;  // mu field of the split D3Q19 FP32DEV path
 };
 
 // ------------------------------------------------------------------ allocation
@@ -327,6 +328,7 @@ extern "C" void lbm_destroy(lbm_handle* h) {
   dfree(h, h->d_bad, 8);
   dfree(h, h->d_partials, size_t(h->n_partials) * 4 * 8);
   dfree(h, h->d_obs, 64);
+  dfree(h, h->mu, size_t(h->N) * 4);
   compact_free(h->cb, [&](void* p, size_t b) { dfree(h, p, b); });
   delete h;
 }
@@ -404,6 +406,10 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
   h->n_partials = int((params->nx / 8 + 2) * (params->ny / 8 + 2) * (params->lattice == LBM_D2Q9 ? 1 : (params->nz / 8 + 2)));
   h->d_partials = static_cast<double*>(dalloc(h, size_t(h->n_partials) * 4 * 8));
   bool ok = h->f[0] && h->f[1] && h->rho[0] && h->rho[1] && h->rho_snap && h->d_bad && h->d_obs && h->d_partials;
+  if (ok && h->D == 3 && !h->compact && split3d_scheme(params->scheme, h->prec)) {
+    h->mu = dalloc(h, size_t(h->N) * 4);
+    ok = h->mu != nullptr;
+  }
   if (ok && h->compact) {
     rc = compact_alloc(h->cb, h->kp, h->D, params->scheme, h->prec, [&](size_t b) { return dalloc(h, b); });
     if (rc != LBM_OK) ok = false;
@@ -562,6 +568,7 @@ static Launch make_launch(lbm_handle* h, int out_buf) {
   c.aux.rho_snap = h->rho_snap;
   c.stream = h->stream;
   c.zc = h->zc;
+  c.mu = h->mu;
   return c;
 }
 
@@ -624,6 +631,47 @@ extern "C" int lbm_step(lbm_handle* h, long long n) {
 }
 
 extern "C" long long lbm_get_step(const lbm_handle* h) { return h ? h->t : -1; }
+
+extern "C" int lbm_step_timed(lbm_handle* h, long long n, double* ms) {
+  if (!h || n < 0 || n > 100000 || !ms) return LBM_EINVAL;
+  ms[0] = ms[1] = ms[2] = 0.0;
+  const bool split = h->mu != nullptr;
+  // three events per step, recorded back to back; one synchronisation at the end
+  const size_t ne = size_t(3 * n);
+  cudaEvent_t* e = new (std::nothrow) cudaEvent_t[ne > 0 ? ne : 1];
+  if (!e) return LBM_ENOMEM;
+  size_t made = 0;
+  int rc = LBM_OK;
+  for (; made < ne; ++made)
+    if (cudaEventCreate(&e[made]) != cudaSuccess) { rc = LBM_ECUDA; break; }
+  for (long long s = 0; s < n && rc == LBM_OK; ++s) {
+    Launch c = make_launch(h, 1 - h->cur);
+    c.ev_mid = split ? e[3 * s + 1] : nullptr;
+    cudaEventRecord(e[3 * s], h->stream);
+    cudaError_t err = h->compact ? compact_step(h->cb, c, h->D, h->p.scheme, h->prec, MODE_STEP, nullptr)
+                                 : h->fn(c, MODE_STEP, nullptr);
+    cudaEventRecord(e[3 * s + 2], h->stream);
+    if (err != cudaSuccess) rc = LBM_ECUDA;
+    h->cur = 1 - h->cur;
+    h->t += 1;
+  }
+  if (rc == LBM_OK && n > 0 && cudaEventSynchronize(e[3 * n - 1]) != cudaSuccess) rc = LBM_ECUDA;
+  for (long long s = 0; s < n && rc == LBM_OK; ++s) {
+    float a = 0.f, b = 0.f;
+    if (split) {
+      cudaEventElapsedTime(&a, e[3 * s], e[3 * s + 1]);
+      cudaEventElapsedTime(&b, e[3 * s + 1], e[3 * s + 2]);
+    } else {
+      cudaEventElapsedTime(&b, e[3 * s], e[3 * s + 2]);
+    }
+    ms[0] += a;
+    ms[1] += b;
+    ms[2] += a + b;
+  }
+  for (size_t k = 0; k < made; ++k) cudaEventDestroy(e[k]);
+  delete[] e;
+  return rc;
+}
 
 extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
   if (!h || !out) return LBM_EINVAL;

@@ -58,6 +58,7 @@ SIGNATURES = {
     "lbm_init_density": (C.c_int, [_h, _dp]),
     "lbm_set_f": (C.c_int, [_h, _dp]),
     "lbm_step": (C.c_int, [_h, C.c_longlong]),
+    "lbm_step_timed": (C.c_int, [_h, C.c_longlong, _dp]),
     "lbm_observables": (C.c_int, [_h, C.POINTER(lbm_obs)]),
     "lbm_get_density": (C.c_int, [_h, _dp]),
     "lbm_get_f": (C.c_int, [_h, _dp]),
@@ -230,6 +231,11 @@ class Sim:
 
     def lbm_step(self, n=1):
         return check(lib().lbm_step(self.h, n), "lbm_step")
+
+    def lbm_step_timed(self, n=1):
+        ms = np.zeros(3)
+        check(lib().lbm_step_timed(self.h, n, _ptr(ms)), "lbm_step_timed")
+        return ms
 
     def lbm_observables(self, raise_unstable=False):
         o = lbm_obs()
