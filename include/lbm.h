@@ -43,6 +43,7 @@ extern "C" {
 #define LBM_EUNSTABLE -4  /* a density became non-positive or NaN; see lbm_obs.step */
 #define LBM_ETIMEOUT -5   /* a bounded device-side wait gave up */
 #define LBM_ENOTSUP -6    /* combination not provided (e.g. E8 on D3Q19) */
+#define LBM_ESCRATCH -7   /* larger than the fixed scratch of lbm_observables_noalloc */
 
 /* ---- enumerations ---- */
 #define LBM_D2Q9 0
@@ -220,6 +221,35 @@ int lbm_lattice_q(int lattice);
 /* Static text for an error code. */
 const char* lbm_strerror(int code);
 
+/* ====================================================== no device allocation
+ * Observables (as lbm_observables) of a state the caller holds in its own
+ * device buffers, computed without allocating any device memory.  For callers
+ * that cannot let a library allocate: an application that owns all device
+ * memory under a fixed budget, or code running where a new cudaMalloc would
+ * stall or fail.  The paper has no counterpart; it is an interface choice.
+ *
+ *  p                 the parameters the state was produced with (explicit and
+ *                    isotropic schemes only: compact schemes -> LBM_ENOTSUP)
+ *  d_f, d_rho        device pointers to the populations and density field in
+ *                    the stored form of lbm_device_state (read only)
+ *  d_rho_prev        density field of an earlier step (stored form) for
+ *                    max_drho, or NULL (max_drho = 0)
+ *  steps_since_prev  steps between d_rho_prev and d_rho (max_drho divisor)
+ *  step              step index reported back in out->step
+ *  stream            cudaStream_t the work is ordered on (synchronised)
+ *
+ * The reduction's partial results live in a fixed file-scope device array of
+ * 65536 x 4 doubles plus 16 result words (about 2 MiB), held by every GPU that
+ * loads the library until the process exits.  Lattices whose observation pass
+ * needs more than 65536 CTAs (D2Q9 above about 16.7 M nodes, D3Q19 above
+ * about 537 M nodes) return LBM_ESCRATCH.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU race and must be serialised.
+ * Returns LBM_OK, or LBM_EUNSTABLE (out->status too) if a density is
+ * non-positive or NaN. */
+int lbm_observables_noalloc(const lbm_params* p, const void* d_f, const void* d_rho, const void* d_rho_prev,
+                            long long steps_since_prev, long long step, void* stream, lbm_obs* out);
 
 /* ==================================================================== batches
  * Many independent D2Q9 droplets of different sizes and parameters advanced

@@ -43,6 +43,10 @@ StepFn pick(int prec) {
 }
 }  // namespace
 
+long long step2d_obs_ctas(const KParams& kp) {
+  return (long long)((kp.nx + TX2 - 1) / TX2) * ((kp.ny + TY2 - 1) / TY2);
+}
+
 StepFn step2d_fn(int scheme, int prec) {
   switch (scheme) {
     case S_EFDS2: return pick<S_EFDS2>(prec);

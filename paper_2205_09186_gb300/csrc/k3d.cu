@@ -148,6 +148,10 @@ StepFn pick(int prec) {
 }
 }  // namespace
 
+long long step3d_obs_ctas(const KParams& kp) {
+  return (long long)((kp.nx + TX3 - 1) / TX3) * ((kp.ny + TY3 - 1) / TY3) * ((kp.nz + ZC3 - 1) / ZC3);
+}
+
 StepFn step3d_fn(int scheme, int prec) {
   switch (scheme) {
     case S_EFDS2: return pick<S_EFDS2>(prec);

@@ -38,4 +38,8 @@ using StepFn = cudaError_t (*)(const Launch&, int mode, int* nblocks);
 StepFn step2d_fn(int scheme, int prec);
 StepFn step3d_fn(int scheme, int prec);
 
+// number of CTAs (hence partial results) of the observation pass
+long long step2d_obs_ctas(const KParams& kp);
+long long step3d_obs_ctas(const KParams& kp);
+
 }  // namespace lbmd

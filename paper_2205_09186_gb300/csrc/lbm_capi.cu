@@ -168,6 +168,7 @@ extern "C" const char* lbm_strerror(int code) {
     case LBM_EUNSTABLE: return "simulation unstable (non-positive or NaN density)";
     case LBM_ETIMEOUT: return "device-side wait timed out";
     case LBM_ENOTSUP: return "unsupported lattice/scheme combination";
+    case LBM_ESCRATCH: return "lattice too large for the fixed scratch array of the non-allocating entry point";
     default: return "unknown error";
   }
 }

@@ -13,7 +13,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm.so")
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOTSUP, LBM_ESCRATCH = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_EOS_CS = 0
 SCHEMES = {"EFDS2": 0, "EFDS4": 1, "EFDS6": 2, "CFDS4": 3, "CFDS6": 4, "CFDS8": 5, "OCFDS4": 6, "E4": 7, "E8": 8}
@@ -71,6 +72,8 @@ SIGNATURES = {
     "lbm_set_zchunk": (C.c_int, [_h, C.c_int]),
     "lbm_autotune": (C.c_int, [_h, C.POINTER(C.c_int)]),
     "lbm_strerror": (C.c_char_p, [C.c_int]),
+    "lbm_observables_noalloc": (C.c_int, [C.POINTER(lbm_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong,
+                                          C.c_longlong, C.c_void_p, C.POINTER(lbm_obs)]),
     "lbm_batch_create": (C.c_int, [C.POINTER(lbm_params), C.c_int, C.c_void_p, C.POINTER(lbm_allocator),
                                    C.POINTER(C.c_void_p)]),
     "lbm_batch_destroy": (None, [_h]),
@@ -135,6 +138,17 @@ def make_params(lattice=LBM_D2Q9, nx=64, ny=64, nz=1, a=1.0, b=4.0, R=1.0, Tr=0.
                 scheme="EFDS2", precision=LBM_FP64, mu_fp64=0, rho_ref=0.0):
     s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     return lbm_params(lattice, nx, ny, nz, LBM_EOS_CS, a, b, R, Tr, k, kappa, tau, s, precision, int(mu_fp64), rho_ref)
+
+
+def lbm_observables_noalloc(params, d_f, d_rho, d_rho_prev=None, steps_since_prev=0, step=0, stream=None):
+    """Observables of a caller-held device state; the library allocates nothing.
+    Returns (status code, observables dict)."""
+    o = lbm_obs()
+    st = C.c_void_p(int(stream)) if stream is not None else None
+    rc = lib().lbm_observables_noalloc(C.byref(params), C.c_void_p(d_f), C.c_void_p(d_rho),
+                                       C.c_void_p(d_rho_prev) if d_rho_prev else None, steps_since_prev, step, st,
+                                       C.byref(o))
+    return rc, o.as_dict()
 
 
 def lbm_critical(a=1.0, b=4.0, R=1.0):
