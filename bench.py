@@ -38,6 +38,21 @@ B_MU = 4 + 4
 SAMPLE_N = 128  # oracle sample lattice (same parameters, radius scaled)
 
 
+def reduce_max_ms(total_ms, dist=None, device="cpu"):
+    """Max over ranks of a rank's timed-region milliseconds (all ranks get it)."""
+    if dist is None:
+        return total_ms
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank, steps, world, total_ms):
+    """Whole-job throughput: lattice updates of all ranks over the slowest rank's time."""
+    return nodes_per_rank * steps * world / (total_ms * 1e-3) / 1e6
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -258,13 +273,11 @@ def run_gpu(args):
         torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max_ms(total_ms, dist, "cuda")
         dist.barrier()
     obs = sim.lbm_observables()
     ok = obs["status"] == 0 and abs(obs["mass"] / obs0["mass"] - 1) < 1e-6
-    mlups = N * args.steps * world / (total_ms * 1e-3) / 1e6
+    mlups = job_mlups(N, args.steps, world, total_ms)
     coll_ms = phase_ms[1] / args.steps   # collision/streaming pass (dominant kernel), per launch
     mu_ms = phase_ms[0] / args.steps     # mu pass, per launch
     achieved = B_COLL * N / (coll_ms * 1e-3) / 1e9
@@ -291,6 +304,12 @@ def run_gpu(args):
     extra = {}
     if not args.no_batch:
         extra["batch2d"] = run_batch(L)
+    if not args.no_warmstart:
+        from paper_2205_09186_gb300 import warmstart as W
+        res, _ = W.experiment(n_train=32, n_test=12, n=80, tol=1e-7, iters=4000)
+        res["device_s_ratio_cold_over_warm"] = (res["cold_device_s"] / res["warm_device_s"]
+                                                if res["warm_device_s"] else None)
+        extra["warmstart"] = res
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -332,6 +351,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D sweep measurement")
+    ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start experiment")
     ap.add_argument("--zchunk", type=int, default=0, help="fix the z-chunk instead of autotuning (profiling runs)")
     ap.add_argument("--size", type=int, default=256,
                     help="lattice edge (profiling runs only; the benchmark workload is 256)")

@@ -15,6 +15,7 @@
 #include "../../include/lbm.h"
 #include "launch.cuh"
 #include "step2d.cuh"
+#include "step2d_split.cuh"
 
 using namespace lbmd;
 
@@ -27,10 +28,12 @@ struct CaseDev {
   void* f[2];
   void* rho[2];  // density field: double (FP64) or float rho - rho_ref (FP32DEV)
   void* snap;
+  float* mu;     // mu field (split FP32DEV path)
   unsigned long long* bad;
   int scheme;
   int tiles_x, tiles_y;
-  int item_begin, item_end;
+  int item_begin, item_end;      // observation / single-phase items
+  int mtiles_x, ctiles_x;        // split path: mu tiles (32 x 16) and collision tiles (30 x 14) per row
 };
 
 struct Item {
@@ -40,7 +43,7 @@ struct Item {
 struct BatchCtl {
   unsigned int count;
   unsigned int gen;
-  unsigned int work[2];
+  unsigned int work[4];  // [phase * 2 + step parity]
   int status;
   int skip_block;  // fault injection for tests: this CTA never arrives (-1: none)
   long long t;     // step counter of the batch
@@ -157,6 +160,79 @@ __global__ void __launch_bounds__(NT2) k_batch_persistent(const CaseDev* __restr
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t = t0 + nsteps;
 }
 
+// FP32DEV: per step a mu phase over all cases' mu tiles and a collision phase
+// over their collision tiles, each followed by the bounded device barrier
+template <int S, bool TAU1>
+__device__ void split_coll_item(const CaseDev& cd, int tile, long long t, unsigned char* smem) {
+  const int par = int(t & 1);
+  const int x0 = (tile % cd.ctiles_x) * T2X, y0 = (tile / cd.ctiles_x) * T2Y;
+  coll2d_tile<S, TAU1>(cd.kp, static_cast<const float*>(cd.f[par]), static_cast<float*>(cd.f[par ^ 1]),
+                       static_cast<const float*>(cd.rho[par]), cd.mu, static_cast<float*>(cd.rho[par ^ 1]), cd.bad, t,
+                       x0, y0, smem);
+}
+
+__device__ void split_item(const CaseDev& cd, int tile, long long t, int phase, unsigned char* smem) {
+  const int par = int(t & 1);
+  if (phase == 0) {
+    const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
+    const float* rin = static_cast<const float*>(cd.rho[par]);
+    switch (cd.scheme) {
+      case S_EFDS2: mu2d_tile<S_EFDS2>(cd.kp, rin, cd.mu, x0, y0, smem); break;
+      case S_EFDS4: mu2d_tile<S_EFDS4>(cd.kp, rin, cd.mu, x0, y0, smem); break;
+      case S_EFDS6: mu2d_tile<S_EFDS6>(cd.kp, rin, cd.mu, x0, y0, smem); break;
+      case S_E4: mu2d_tile<S_E4>(cd.kp, rin, cd.mu, x0, y0, smem); break;
+      case S_E8: mu2d_tile<S_E8>(cd.kp, rin, cd.mu, x0, y0, smem); break;
+      default: break;
+    }
+    return;
+  }
+  const bool tau1 = cd.kp.omega == 1.0;
+#define LBM_SPLIT_CASE(SS)                                              \
+  case SS:                                                              \
+    if (tau1) split_coll_item<SS, true>(cd, tile, t, smem);            \
+    else split_coll_item<SS, false>(cd, tile, t, smem);                \
+    break;
+  switch (cd.scheme) {
+    LBM_SPLIT_CASE(S_EFDS2)
+    LBM_SPLIT_CASE(S_EFDS4)
+    LBM_SPLIT_CASE(S_EFDS6)
+    LBM_SPLIT_CASE(S_E4)
+    LBM_SPLIT_CASE(S_E8)
+    default: break;
+  }
+#undef LBM_SPLIT_CASE
+}
+
+__global__ void __launch_bounds__(NT2S) k_batch_split(const CaseDev* __restrict__ cases,
+                                                      const Item* __restrict__ mitems, int nmu,
+                                                      const Item* __restrict__ citems, int ncoll, int nsteps,
+                                                      BatchCtl* ctl, unsigned long long timeout_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  const long long t0 = *((volatile long long*)&ctl->t);
+  for (int s = 0; s < nsteps; ++s) {
+    const long long t = t0 + s;
+    for (int phase = 0; phase < 2; ++phase) {
+      const Item* items = phase == 0 ? mitems : citems;
+      const int nitems = phase == 0 ? nmu : ncoll;
+      unsigned int* ctr = &ctl->work[phase * 2 + (s & 1)];
+      for (;;) {
+        if (threadIdx.x == 0) s_item = int(atomicAdd(ctr, 1u));
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const Item itm = items[it];
+        split_item(cases[itm.c], itm.tile, t, phase, smem);
+      }
+      // counters of the other step parity were last used a step ago: reset them
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[phase * 2 + ((s + 1) & 1)] = 0u;
+      if (!grid_barrier(ctl, timeout_ns)) return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t = t0 + nsteps;
+}
+
 // observation pass: one CTA per work item (not persistent)
 template <class P>
 __global__ void __launch_bounds__(NT2) k_batch_obs(const CaseDev* __restrict__ cases, const Item* __restrict__ items,
@@ -249,6 +325,11 @@ struct lbm_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   long long graph_steps = -1;
+  bool split = false;
+  Item* d_mitems = nullptr;
+  Item* d_citems = nullptr;
+  int nmu = 0, ncoll = 0, grid_split = 0;
+  size_t smem_split = 0;
   std::vector<std::pair<void*, size_t>> blocks;
 };
 
@@ -341,10 +422,31 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     cd.rho[1] = balloc(b, size_t(N) * fs);
     cd.snap = balloc(b, size_t(N) * fs);
     cd.bad = static_cast<unsigned long long*>(balloc(b, 8));
-    ok = cd.f[0] && cd.f[1] && cd.rho[0] && cd.rho[1] && cd.snap && cd.bad;
+    cd.mu = nullptr;
+    cd.mtiles_x = (q.nx + M2X - 1) / M2X;
+    cd.ctiles_x = (q.nx + T2X - 1) / T2X;
+    if (prec0 == LBM_FP32DEV && !mu0) cd.mu = static_cast<float*>(balloc(b, size_t(N) * 4));
+    ok = cd.f[0] && cd.f[1] && cd.rho[0] && cd.rho[1] && cd.snap && cd.bad && (cd.mu || prec0 != LBM_FP32DEV || mu0);
   }
   if (!ok) { lbm_batch_destroy(b); return LBM_ENOMEM; }
   b->nitems = int(items.size());
+  b->split = prec0 == LBM_FP32DEV && !mu0;
+  std::vector<Item> mitems, citems;
+  if (b->split) {
+    for (int k = 0; k < n; ++k) {
+      const int c = idx[k];
+      const CaseDev& cd = b->host_cases[c];
+      const int mt = cd.mtiles_x * ((cases[c].ny + M2Y - 1) / M2Y);
+      const int ct = cd.ctiles_x * ((cases[c].ny + T2Y - 1) / T2Y);
+      for (int tl = 0; tl < mt; ++tl) mitems.push_back({c, tl});
+      for (int tl = 0; tl < ct; ++tl) citems.push_back({c, tl});
+    }
+    b->nmu = int(mitems.size());
+    b->ncoll = int(citems.size());
+    b->d_mitems = static_cast<Item*>(balloc(b, sizeof(Item) * mitems.size()));
+    b->d_citems = static_cast<Item*>(balloc(b, sizeof(Item) * citems.size()));
+    if (!b->d_mitems || !b->d_citems) { lbm_batch_destroy(b); return LBM_ENOMEM; }
+  }
   b->d_cases = static_cast<CaseDev*>(balloc(b, sizeof(CaseDev) * n));
   b->d_items = static_cast<Item*>(balloc(b, sizeof(Item) * items.size()));
   b->ctl = static_cast<BatchCtl*>(balloc(b, sizeof(BatchCtl)));
@@ -356,6 +458,11 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
   cudaError_t e = cudaMemcpyAsync(b->d_cases, b->host_cases.data(), sizeof(CaseDev) * n, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && b->split) {
+    e = cudaMemcpyAsync(b->d_mitems, mitems.data(), sizeof(Item) * mitems.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_citems, citems.data(), sizeof(Item) * citems.size(), cudaMemcpyHostToDevice, b->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   // residency: CTAs per SM x SMs, all resident at once
   int dev = 0, sms = 0, per_sm = 0;
@@ -372,6 +479,19 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
   else { b->smem = batch_smem<PrecF32M64>(); setup(k_batch_persistent<PrecF32M64>, b->smem);
          cudaFuncSetAttribute(k_batch_obs<PrecF32M64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)); }
   b->grid = std::max(1, std::min(per_sm * sms, b->nitems));
+  if (b->split) {
+    size_t m = Split2DShape<S_EFDS2>::bytes;
+    m = std::max(m, Split2DShape<S_EFDS4>::bytes);
+    m = std::max(m, Split2DShape<S_EFDS6>::bytes);
+    m = std::max(m, Split2DShape<S_E4>::bytes);
+    m = std::max(m, Split2DShape<S_E8>::bytes);
+    b->smem_split = m;
+    int ps = 0;
+    cudaFuncSetAttribute(k_batch_split, cudaFuncAttributeMaxDynamicSharedMemorySize, int(m));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_batch_split, NT2S, m);
+    if (ps < 1) { lbm_batch_destroy(b); return LBM_ECUDA; }
+    b->grid_split = std::max(1, std::min(ps * sms, std::max(b->nmu, b->ncoll)));
+  }
   if (e != cudaSuccess || per_sm < 1 || cudaGetLastError() != cudaSuccess) { lbm_batch_destroy(b); return LBM_ECUDA; }
   *out = b;
   return LBM_OK;
@@ -442,6 +562,20 @@ extern "C" int lbm_batch_init_droplets(lbm_batch* b, const double* radius, doubl
 
 static cudaError_t launch_persistent(lbm_batch* b, int nsteps) {
   const unsigned long long timeout_ns = 1000000000ull;
+  if (b->split) {
+    cudaLaunchConfig_t cs{};
+    cs.gridDim = dim3(unsigned(b->grid_split));
+    cs.blockDim = dim3(NT2S);
+    cs.dynamicSmemBytes = b->smem_split;
+    cs.stream = b->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cs.attrs = at;
+    cs.numAttrs = 1;
+    return cudaLaunchKernelEx(&cs, k_batch_split, (const CaseDev*)b->d_cases, (const Item*)b->d_mitems, b->nmu,
+                              (const Item*)b->d_citems, b->ncoll, nsteps, b->ctl, timeout_ns);
+  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(unsigned(b->grid));
   cfg.blockDim = dim3(NT2);
@@ -547,7 +681,7 @@ extern "C" int lbm_batch_get_density(lbm_batch* b, int c, double* host) {
 extern "C" long long lbm_batch_get_step(const lbm_batch* b) { return b ? b->t : -1; }
 
 extern "C" int lbm_batch_inject_stall(lbm_batch* b, int cta) {
-  if (!b || cta < -1 || cta >= b->grid) return LBM_EINVAL;
+  if (!b || cta < -1 || cta >= (b->split ? b->grid_split : b->grid)) return LBM_EINVAL;
   cudaError_t e = cudaMemcpyAsync(&b->ctl->skip_block, &cta, sizeof(int), cudaMemcpyHostToDevice, b->stream);
   int zero = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&b->ctl->status, &zero, sizeof(int), cudaMemcpyHostToDevice, b->stream);
@@ -558,7 +692,7 @@ extern "C" int lbm_batch_inject_stall(lbm_batch* b, int cta) {
 extern "C" int lbm_batch_size(const lbm_batch* b, int* ncases, int* nitems, int* grid) {
   if (!b) return LBM_EINVAL;
   if (ncases) *ncases = b->n;
-  if (nitems) *nitems = b->nitems;
-  if (grid) *grid = b->grid;
+  if (nitems) *nitems = b->split ? b->nmu + b->ncoll : b->nitems;
+  if (grid) *grid = b->split ? b->grid_split : b->grid;
   return LBM_OK;
 }

@@ -1,6 +1,9 @@
 // Instantiations of the fused D2Q9 step for the explicit and isotropic schemes.
+#include <type_traits>
+
 #include "launch.cuh"
 #include "step2d.cuh"
+#include "step2d_split.cuh"
 
 namespace lbmd {
 
@@ -28,8 +31,36 @@ cudaError_t launch_mode(const Launch& c, int* nblocks) {
   return cudaGetLastError();
 }
 
+// FP32 deviation storage with FP32 mu: mu pass + row-per-warp collision pass
+template <int S, bool TAU1>
+cudaError_t launch_split2d(const Launch& c, int* nblocks) {
+  using Sh = Split2DShape<S>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_mu2d<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_coll2d<S, TAU1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 gm((c.kp.nx + M2X - 1) / M2X, (c.kp.ny + M2Y - 1) / M2Y);
+  k_mu2d<S><<<gm, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
+  dim3 gc((c.kp.nx + T2X - 1) / T2X, (c.kp.ny + T2Y - 1) / T2Y);
+  if (nblocks) *nblocks = int(gc.x * gc.y);
+  k_coll2d<S, TAU1><<<gc, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin),
+                                                       static_cast<float*>(c.fout), static_cast<const float*>(c.rin),
+                                                       static_cast<const float*>(c.mu), static_cast<float*>(c.rout),
+                                                       c.aux);
+  return cudaGetLastError();
+}
+
 template <int S, class P>
 cudaError_t launch(const Launch& c, int mode, int* nblocks) {
+  if constexpr (std::is_same<P, PrecF32>::value) {
+    if (mode == MODE_STEP && c.mu)
+      return c.kp.omega == 1.0 ? launch_split2d<S, true>(c, nblocks) : launch_split2d<S, false>(c, nblocks);
+  }
   if (mode == MODE_STEP) return launch_mode<S, P, MODE_STEP>(c, nblocks);
   if (mode == MODE_OBS) return launch_mode<S, P, MODE_OBS>(c, nblocks);
   return launch_mode<S, P, MODE_FIELDS>(c, nblocks);
@@ -45,6 +76,10 @@ StepFn pick(int prec) {
 
 long long step2d_obs_ctas(const KParams& kp) {
   return (long long)((kp.nx + TX2 - 1) / TX2) * ((kp.ny + TY2 - 1) / TY2);
+}
+
+bool split2d_scheme(int scheme, int prec) {
+  return prec == 1 && (scheme == S_EFDS2 || scheme == S_EFDS4 || scheme == S_EFDS6 || scheme == S_E4 || scheme == S_E8);
 }
 
 StepFn step2d_fn(int scheme, int prec) {

@@ -1,4 +1,6 @@
 // Instantiations of the fused 2.5D D3Q19 step for the explicit and isotropic schemes.
+#include <algorithm>
+#include <cstdint>
 #include <type_traits>
 
 #include "launch.cuh"
@@ -101,33 +103,58 @@ cudaError_t launch_fast(const Launch& c, int* nblocks) {
   return cudaGetLastError();
 }
 
-// mu pass + collision pass (line schemes, FP32DEV, FP32 mu)
-template <int S, bool TAU1>
-cudaError_t launch_split(const Launch& c, int* nblocks) {
+template <int S, bool TAU1, bool VEC>
+cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
   using Sh = CollShape<S>;
-  auto kc = k_coll3d<S, TAU1>;
+  auto kc = k_coll3d<S, TAU1, VEC>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (!c.mu) return cudaErrorInvalidValue;
-  const int zmu = 32;
-  dim3 gm((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + zmu - 1) / zmu);
-  k_mu3d<S><<<gm, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu), zmu);
-  if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
-  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sh::R);
-  dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + TYC - 1) / TYC, (c.kp.nz + zc - 1) / zc);
-  if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
   kc<<<grid, CNT, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
                                          static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
                                          static_cast<float*>(c.rout), c.aux, zc);
   return cudaGetLastError();
 }
 
+static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+
+// mu pass + collision pass (line schemes, FP32DEV, FP32 mu)
+template <int S, bool TAU1>
+cudaError_t launch_split(const Launch& c, int* nblocks) {
+  using Sh = CollShape<S>;
+  if (!c.mu) return cudaErrorInvalidValue;
+  dim3 gm((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
+  k_mu3d<S><<<gm, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
+  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sh::R);
+  dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + TYC - 1) / TYC, (c.kp.nz + zc - 1) / zc);
+  if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
+  // 16-byte copies need rows of whole chunks and aligned bases
+  const bool vec = c.kp.nx % 4 == 0 && aligned16(c.fin) && aligned16(c.rin) && aligned16(c.mu);
+  return vec ? launch_coll<S, TAU1, true>(c, grid, zc) : launch_coll<S, TAU1, false>(c, grid, zc);
+}
+
+// observation pass of the split path: mu field, then the node-parallel reduction
+template <int S>
+cudaError_t launch_obs_split(const Launch& c, int* nblocks) {
+  dim3 gm((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
+  k_mu3d<S><<<gm, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  // at most 8192 CTAs: the handle's partials buffer holds at least that many
+  const int nb = int(std::min<long long>(std::min<long long>((long long)c.kp.ny * c.kp.nz, 8LL * num_sms()), 8192LL));
+  if (nblocks) *nblocks = nb;
+  k_obs3d<S><<<nb, 256, 0, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<const float*>(c.rin),
+                                       static_cast<const float*>(c.mu), c.aux);
+  return cudaGetLastError();
+}
+
 template <int S, class P>
 cudaError_t launch(const Launch& c, int mode, int* nblocks) {
+  if constexpr (std::is_same<P, PrecF32>::value && !Sch<S>::ISO) {
+    if (mode == MODE_OBS && c.mu) return launch_obs_split<S>(c, nblocks);
+  }
   if constexpr (std::is_same<P, PrecF32>::value) {
     if (mode == MODE_STEP) {
       if constexpr (!Sch<S>::ISO)

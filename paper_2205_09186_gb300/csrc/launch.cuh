@@ -24,6 +24,7 @@ struct Launch {
 // the D3Q19 FP32DEV step of this scheme runs as mu pass + collision pass and
 // needs an N-float mu buffer in Launch::mu
 bool split3d_scheme(int scheme, int prec);
+bool split2d_scheme(int scheme, int prec);
 
 // z-chunk length for the pipelined D3Q19 kernel: balances the last wave of
 // CTAs against the per-chunk prologue (4R + 2 extra planes, of which only 2

@@ -405,9 +405,12 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
   h->d_obs = static_cast<double*>(dalloc(h, 64));
   // partials: one per CTA of the observation pass (upper bound over tilings used)
   h->n_partials = int((params->nx / 8 + 2) * (params->ny / 8 + 2) * (params->lattice == LBM_D2Q9 ? 1 : (params->nz / 8 + 2)));
+  // the node-parallel observation pass of the split D3Q19 path uses up to 8 CTAs per SM
+  if (h->n_partials < 8 * 1024) h->n_partials = 8 * 1024;
   h->d_partials = static_cast<double*>(dalloc(h, size_t(h->n_partials) * 4 * 8));
   bool ok = h->f[0] && h->f[1] && h->rho[0] && h->rho[1] && h->rho_snap && h->d_bad && h->d_obs && h->d_partials;
-  if (ok && h->D == 3 && !h->compact && split3d_scheme(params->scheme, h->prec)) {
+  if (ok && !h->compact &&
+      (h->D == 3 ? split3d_scheme(params->scheme, h->prec) : split2d_scheme(params->scheme, h->prec))) {
     h->mu = dalloc(h, size_t(h->N) * 4);
     ok = h->mu != nullptr;
   }

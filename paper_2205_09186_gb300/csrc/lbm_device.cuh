@@ -99,6 +99,15 @@ __device__ __forceinline__ T cs_mu(T rho, T RT, T b4, T two_a) {
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// periodic wrap of an index in [-n, inf): also for halo regions wider than a
+// small lattice (a 38-wide region on an 8-wide lattice reaches 4 periods out).
+// A loop, not i % n: the common case costs two compares, and a select form
+// lets the compiler evaluate the division for every index.
+__device__ __forceinline__ int wrapn(int i, int n) {
+  if (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
+}
 
 // ------------------------------------------------------------------ difference stencils
 // Line schemes (Eq. 18-20): derivative = sum_m g(m) (phi[+m] - phi[-m]);

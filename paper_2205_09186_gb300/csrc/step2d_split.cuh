@@ -1,0 +1,161 @@
+// D2Q9 FP32-deviation step as two passes (the 2D counterpart of
+// step3d_split.cuh):
+//
+//  mu2d_tile    mu = k^2 psi'(rho) - kappa lap rho (Eq. 16) for one 32 x 16
+//               tile (halo R staged in shared memory).
+//  coll2d_tile  grad mu, grad rho (Eq. 17-25) -> F (Eq. 12) -> BGK + EDM
+//               (Eq. 1, 6, 8) -> push streaming and the next density for a
+//               30 x 14 tile; its 32 x 16 tile-plus-ring region maps one warp
+//               to one row (512 threads, one collision per thread).
+//
+// Both are device functions so that the single-case kernels and the
+// persistent batch kernel share them.
+#pragma once
+#include "lbm_device.cuh"
+#include "step2d.cuh"
+
+namespace lbmd {
+
+constexpr int M2X = 32, M2Y = 16;           // mu tile
+constexpr int C2X = 32, C2Y = 16;           // collision region (tile + ring)
+constexpr int T2X = C2X - 2, T2Y = C2Y - 2; // 30 x 14 collision tile
+constexpr int NT2S = 512;                   // threads of both passes
+
+template <int S>
+struct Split2DShape {
+  static constexpr int R = Sch<S>::R;
+  static constexpr int MW = M2X + 2 * R, MH = M2Y + 2 * R;      // mu pass: density region
+  static constexpr int GW = C2X + 2 * R, GH = C2Y + 2 * R;      // collision: field region
+  static constexpr size_t mu_bytes = size_t(MW) * MH * 4;
+  static constexpr size_t off_mu = size_t(GW) * GH * 4;
+  static constexpr size_t off_f = (off_mu + size_t(GW) * GH * 4 + 15) / 16 * 16;
+  static constexpr size_t coll_bytes = off_f + size_t(9) * NT2S * 4;
+  static constexpr size_t bytes = coll_bytes > mu_bytes ? coll_bytes : mu_bytes;
+};
+
+template <int S>
+__device__ __forceinline__ void mu2d_tile(const KParams& p, const float* __restrict__ rin, float* __restrict__ mu,
+                                          int x0, int y0, unsigned char* smem) {
+  using Sh = Split2DShape<S>;
+  constexpr int R = Sh::R, MW = Sh::MW, MH = Sh::MH;
+  float* s = reinterpret_cast<float*>(smem);
+  const int nx = p.nx, ny = p.ny;
+  for (int idx = threadIdx.x; idx < MW * MH; idx += NT2S) {
+    const int ry = idx / MW, rx = idx - ry * MW;
+    s[idx] = rin[wrapn(y0 - R + ry, ny) * nx + wrapn(x0 - R + rx, nx)];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % M2X, ty = threadIdx.x / M2X;
+  if (x0 + tx < nx && y0 + ty < ny) {
+    const float RT = float(p.RT), b4 = float(p.b4), two_a = float(p.two_a), k2 = float(p.k2), kap = float(p.kappa);
+    const float rho = float(p.rho_ref) + s[(ty + R) * MW + tx + R];
+    const float eta = b4 * rho, om = 1.f - eta;
+    const float hs = __fdividef(eta * (8.f + eta * (-9.f + 3.f * eta)), om * om * om);
+    const float lap = lap2d<S, float>(s, MW, tx + R, ty + R);
+    mu[(y0 + ty) * nx + x0 + tx] = k2 * (RT * (__logf(rho) + hs) - two_a * rho) - kap * lap;
+  }
+  __syncthreads();
+}
+
+template <int S, bool TAU1>
+__device__ __forceinline__ void coll2d_tile(const KParams& p, const float* __restrict__ fin, float* __restrict__ fout,
+                                            const float* __restrict__ rin, const float* __restrict__ muf,
+                                            float* __restrict__ rout, unsigned long long* bad, long long t, int x0,
+                                            int y0, unsigned char* smem) {
+  using L = Lattice<0>;
+  using Sh = Split2DShape<S>;
+  constexpr int Q = 9, R = Sh::R, GW = Sh::GW, GH = Sh::GH;
+  float* s_ds = reinterpret_cast<float*>(smem);
+  float* s_mu = reinterpret_cast<float*>(smem + Sh::off_mu);
+  float* s_f = reinterpret_cast<float*>(smem + Sh::off_f);
+  const int nx = p.nx, ny = p.ny, N = int(p.n);
+  const int VW = min(T2X, nx - x0), VH = min(T2Y, ny - y0);
+  const int tid = threadIdx.x;
+  const int cy = tid / C2X, cx = tid - cy * C2X;
+  const int lx = cx - 1, ly = cy - 1;
+  const bool cnode = lx <= VW && ly <= VH;
+  const bool interior = lx >= 0 && lx < VW && ly >= 0 && ly < VH;
+  const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
+  // own populations first (latency overlaps the field staging)
+  float fv[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) fv[i] = cnode ? fin[i * N + gy * nx + gx] : 0.f;
+  for (int idx = tid; idx < GW * GH; idx += NT2S) {
+    const int ry = idx / GW, rx = idx - ry * GW;
+    if (rx < VW + 2 + 2 * R && ry < VH + 2 + 2 * R) {
+      const int g = wrapi(y0 - 1 - R + ry, ny) * nx + wrapi(x0 - 1 - R + rx, nx);
+      s_ds[idx] = rin[g];
+      s_mu[idx] = muf[g];
+    }
+  }
+  __syncthreads();
+  const float omega = float(p.omega), rref = float(p.rho_ref);
+  if (cnode) {
+    const int c = (cy + R) * GW + cx + R;
+    const float dsv = s_ds[c];
+    const float rc = rref + dsv;
+    float jx = 0.f, jy = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (L::ex(i) != 0) jx += float(L::ex(i)) * fv[i];
+      if (L::ey(i) != 0) jy += float(L::ey(i)) * fv[i];
+    }
+    const float irc = __fdividef(1.f, rc);
+    const float ux = jx * irc, uy = jy * irc;
+    float gmx, gmy, grx, gry;
+    grad2d<S, float>(s_mu, GW, cx + R, cy + R, gmx, gmy);
+    grad2d<S, float>(s_ds, GW, cx + R, cy + R, grx, gry);
+    const float Fx = -rc * gmx + grx * (1.f / 3.f), Fy = -rc * gmy + gry * (1.f / 3.f);
+    const float vx = ux + Fx * irc, vy = uy + Fy * irc;
+    if (interior && !(rc > 0.f)) atomicMin(bad, (unsigned long long)t);
+    const int dxp = (gx + 1 < nx) ? 1 : 1 - nx, dxm = (gx > 0) ? -1 : nx - 1;
+    const int dyp = (gy + 1 < ny) ? nx : nx - N, dym = (gy > 0) ? -nx : N - nx;
+    float* fo = fout + gy * nx + gx;
+    const float vv15 = 1.5f * (vx * vx + vy * vy), uu15 = 1.5f * (ux * ux + uy * uy);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float w = float(L::w(i));
+      const float ev = float(L::ex(i)) * vx + float(L::ey(i)) * vy;
+      const float Av = ev * (3.f + 4.5f * ev) - vv15;
+      float fs;
+      if constexpr (TAU1) {
+        fs = w * (dsv + rc * Av);
+      } else {
+        const float eu = float(L::ex(i)) * ux + float(L::ey(i)) * uy;
+        const float Au = eu * (3.f + 4.5f * eu) - uu15;
+        fs = (1.f - omega) * fv[i] + w * (omega * dsv + rc * (omega * Au + Av - Au));
+      }
+      s_f[i * NT2S + tid] = fs;
+      if (interior) {
+        const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) + (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0));
+        fo[i * N + d] = fs;
+      }
+    }
+  }
+  __syncthreads();
+  if (interior) {
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) acc += s_f[i * NT2S + tid - L::ey(i) * C2X - L::ex(i)];
+    rout[(y0 + ly) * nx + x0 + lx] = acc;
+    if (!(rref + acc > 0.f)) atomicMin(bad, (unsigned long long)(t + 1));
+  }
+  __syncthreads();
+}
+
+template <int S>
+__global__ void __launch_bounds__(NT2S) k_mu2d(const KParams p, const float* __restrict__ rin, float* __restrict__ mu) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  mu2d_tile<S>(p, rin, mu, blockIdx.x * M2X, blockIdx.y * M2Y, smem);
+}
+
+template <int S, bool TAU1>
+__global__ void __launch_bounds__(NT2S) k_coll2d(const KParams p, const float* __restrict__ fin,
+                                                 float* __restrict__ fout, const float* __restrict__ rin,
+                                                 const float* __restrict__ mu, float* __restrict__ rout,
+                                                 const StepAux aux) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  coll2d_tile<S, TAU1>(p, fin, fout, rin, mu, rout, aux.bad_step, aux.t, blockIdx.x * T2X, blockIdx.y * T2Y, smem);
+}
+
+}  // namespace lbmd

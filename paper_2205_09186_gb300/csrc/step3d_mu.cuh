@@ -1,0 +1,153 @@
+// The mu pass of the D3Q19 FP32-deviation step (mu = k^2 psi'(rho) - kappa
+// lap rho, Eq. 16, once per node) and the node-parallel observation pass that
+// reads the mu field.
+#pragma once
+#include "lbm_device.cuh"
+#include "step2d.cuh"
+#include "step3d.cuh"
+#include "step3d_fast.cuh"
+
+namespace lbmd {
+
+// ------------------------------------------------------------------ mu pass
+// One CTA: a 32 x 8 x 8 block of nodes.  The block and its stencil halo are
+// copied to shared memory in one asynchronous batch (every copy of the CTA in
+// flight at once: no per-plane round trip), then each thread walks its column
+// through the 8 planes with the z neighbours in a register queue.
+constexpr int MUX = 32, MUY = 8, MUZ = 8, MUT = MUX * MUY;
+
+// line schemes only (the isotropic 3D Laplacian needs diagonal neighbours)
+template <int S>
+__global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __restrict__ rin,
+                                              float* __restrict__ mu) {
+  static_assert(!Sch<S>::ISO, "line schemes only");
+  constexpr int R = Sch<S>::R;
+  constexpr int PW = MUX + 2 * R, PH = MUY + 2 * R, PD = MUZ + 2 * R;
+  static_assert(MUT / 32 < PH && PH + PD <= MUT, "row walk and offset tables");
+  __shared__ float blk[PD][PH][PW];
+  __shared__ int s_yo[PH], s_zo[PD];  // wrapped row and plane offsets of the block
+  const int nx = p.nx, ny = p.ny, nz = p.nz, NXY = nx * ny;
+  const int x0 = blockIdx.x * MUX, y0 = blockIdx.y * MUY, z0 = blockIdx.z * MUZ;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < PH) s_yo[threadIdx.x] = wrapn(y0 - R + int(threadIdx.x), ny) * nx;
+  else if (threadIdx.x < PH + PD) s_zo[threadIdx.x - PH] = wrapn(z0 - R + int(threadIdx.x) - PH, nz) * NXY;
+  // x sources of this lane (lanes < 2R also fill the two columns past 32)
+  const int xa = wrapn(x0 - R + lane, nx);
+  const int xb = wrapn(x0 - R + 32 + min(lane, 2 * R - 1), nx);
+  __syncthreads();
+  // rows warp, warp + 8, ...: (rz, ry) advanced incrementally (8 < PH)
+  int ry = warp, rz = 0;
+  float* dst = &blk[0][warp][lane];
+  for (int row = warp; row < PH * PD; row += MUT / 32) {
+    const float* src = rin + (s_zo[rz] + s_yo[ry]);
+    cpa4(dst, src + xa);
+    if (lane < 2 * R) cpa4(dst + 32, src + xb);
+    dst += (MUT / 32) * PW;
+    ry += MUT / 32;
+    if (ry >= PH) { ry -= PH; ++rz; }
+  }
+  cpa_commit();
+  cpa_wait_all();
+  __syncthreads();
+  const int tx = threadIdx.x % MUX, ty = threadIdx.x / MUX;
+  if (x0 + tx >= nx || y0 + ty >= ny) return;
+  const float RT = float(p.RT), b4 = float(p.b4), two_a = float(p.two_a), k2 = float(p.k2), kap = float(p.kappa);
+  const float rref = float(p.rho_ref);
+  const int cx = tx + R, cy = ty + R;
+  float q[2 * R + 1];  // q[R + d]: density deviation at plane z + d of this column
+#pragma unroll
+  for (int d = 0; d < 2 * R; ++d) q[d + 1] = blk[d][cy][cx];
+  const int zend = min(MUZ, nz - z0);
+  float* out = mu + z0 * NXY + (y0 + ty) * nx + x0 + tx;
+#pragma unroll
+  for (int dz = 0; dz < MUZ; ++dz) {
+#pragma unroll
+    for (int d = 0; d < 2 * R; ++d) q[d] = q[d + 1];
+    q[2 * R] = blk[dz + 2 * R][cy][cx];
+    if (dz < zend) {
+      const int pz = dz + R;
+      const float c = q[R];
+      float lap = float(3.0 * Sch<S>::l(0)) * c;
+#pragma unroll
+      for (int m = 1; m <= R; ++m)
+        lap += float(Sch<S>::l(m)) * ((blk[pz][cy][cx + m] + blk[pz][cy][cx - m]) +
+                                      (blk[pz][cy + m][cx] + blk[pz][cy - m][cx]) + (q[R + m] + q[R - m]));
+      const float rho = rref + c;
+      const float eta = b4 * rho, om = 1.f - eta;
+      const float hs = __fdividef(eta * (8.f + eta * (-9.f + 3.f * eta)), om * om * om);
+      out[dz * NXY] = k2 * (RT * (__logf(rho) + hs) - two_a * rho) - kap * lap;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ observation pass
+// max |v| (v = u + F/(2 rho)), max |u|, mass and max |rho - rho_snap| of the
+// current state from the populations, the density deviation and the mu field
+// (computed by k_mu3d); stencil neighbours are read through L1/L2.  One CTA
+// walks x-rows (grid-stride over the ny * nz rows, fixed grid); the node values
+// are FP32 like the step, the mass a compensated FP32 sum per thread, the CTA
+// partials FP64.
+template <int S>
+__global__ void __launch_bounds__(256) k_obs3d(const KParams p, const float* __restrict__ f,
+                                               const float* __restrict__ rin, const float* __restrict__ muf,
+                                               const StepAux aux) {
+  using L = Lattice<1>;
+  constexpr int R = Sch<S>::R;
+  const int nx = p.nx, ny = p.ny, nz = p.nz, N = int(p.n), NXY = nx * ny;
+  const float rref = float(p.rho_ref);
+  float o_vmax = 0.f, o_umax = 0.f, o_dmax = 0.f;
+  FSum o_dev;   // sum of the density deviations
+  int cnt = 0;  // nodes visited (mass = cnt * rho_ref + deviations)
+  const float* snap = static_cast<const float*>(aux.rho_snap);
+  bool bad = false;
+  for (int row = blockIdx.x; row < ny * nz; row += gridDim.x) {
+    const int z = row / ny, y = row - z * ny;
+    int ym[R], yp[R], zm[R], zp[R];
+#pragma unroll
+    for (int m = 1; m <= R; ++m) {
+      ym[m - 1] = (z * ny + wrapi(y - m, ny)) * nx;  // m <= 3 < 8 <= ny, nz: one period
+      yp[m - 1] = (z * ny + wrapi(y + m, ny)) * nx;
+      zm[m - 1] = (wrapi(z - m, nz) * ny + y) * nx;
+      zp[m - 1] = (wrapi(z + m, nz) * ny + y) * nx;
+    }
+    const int rowb = row * nx;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const int n = rowb + x;
+      float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+      for (int i = 0; i < 19; ++i) {
+        const float fi = f[i * N + n];
+        if (L::ex(i) != 0) jx += float(L::ex(i)) * fi;
+        if (L::ey(i) != 0) jy += float(L::ey(i)) * fi;
+        if (L::ez(i) != 0) jz += float(L::ez(i)) * fi;
+      }
+      const float dsv = rin[n];
+      const float rc = rref + dsv;
+      float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, gr0 = 0.f, gr1 = 0.f, gr2 = 0.f;
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const float g = float(Sch<S>::g(m));
+        const int xp = rowb + wrapi(x + m, nx), xm = rowb + wrapi(x - m, nx);
+        const int yq = yp[m - 1] + x, yr = ym[m - 1] + x, zq = zp[m - 1] + x, zr = zm[m - 1] + x;
+        gm0 += g * (muf[xp] - muf[xm]); gm1 += g * (muf[yq] - muf[yr]); gm2 += g * (muf[zq] - muf[zr]);
+        gr0 += g * (rin[xp] - rin[xm]); gr1 += g * (rin[yq] - rin[yr]); gr2 += g * (rin[zq] - rin[zr]);
+      }
+      const float irc = __fdividef(1.f, rc);
+      const float ux = jx * irc, uy = jy * irc, uz = jz * irc;
+      const float h = 0.5f * irc;
+      const float vx = ux + (-rc * gm0 + gr0 * (1.f / 3.f)) * h, vy = uy + (-rc * gm1 + gr1 * (1.f / 3.f)) * h,
+                  vz = uz + (-rc * gm2 + gr2 * (1.f / 3.f)) * h;
+      o_vmax = fmaxf(o_vmax, sqrtf(vx * vx + vy * vy + vz * vz));
+      o_umax = fmaxf(o_umax, sqrtf(ux * ux + uy * uy + uz * uz));
+      o_dev.add(dsv);
+      ++cnt;
+      o_dmax = fmaxf(o_dmax, fabsf(dsv - snap[n]));
+      bad |= !(rc > 0.f);
+    }
+  }
+  if (bad) atomicMin(aux.bad_step, (unsigned long long)aux.t);
+  block_obs_reduce<256>(double(o_vmax), double(o_umax), double(cnt) * p.rho_ref + o_dev.value(), double(o_dmax),
+                        aux.partials + 4 * blockIdx.x);
+}
+
+}  // namespace lbmd

@@ -1,8 +1,7 @@
 // D3Q19 FP32-deviation step as two passes per time step:
 //
 //  k_mu3d      mu = k^2 psi'(rho) - kappa lap rho (Eq. 16) for every node, once
-//              (a 2.5D stencil: x-y neighbours from a shared plane, z
-//              neighbours from a per-thread register queue).
+//              (step3d_mu.cuh).
 //  k_coll3d    grad mu, grad rho (Eq. 17-25) -> F (Eq. 12) -> BGK + EDM
 //              (Eq. 1, 6, 8) -> push streaming, plus the next density, for
 //              a 30 x 9 tile and its one-node ring marching through z.
@@ -19,92 +18,55 @@
 #include "lbm_device.cuh"
 #include "step3d.cuh"
 #include "step3d_fast.cuh"
+#include "step3d_mu.cuh"
 
 namespace lbmd {
-
-// ------------------------------------------------------------------ mu pass
-constexpr int MUX = 32, MUY = 8, MUT = MUX * MUY;
-
-// line schemes only (the isotropic 3D Laplacian needs diagonal neighbours in
-// the planes above and below, which the z queue does not hold)
-template <int S>
-__global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __restrict__ rin, float* __restrict__ mu,
-                                              const int zc) {
-  static_assert(!Sch<S>::ISO, "line schemes only");
-  constexpr int R = Sch<S>::R;
-  constexpr int PW = MUX + 2 * R, PH = MUY + 2 * R;
-  __shared__ float pl[2][PH][PW];
-  const int nx = p.nx, ny = p.ny, nz = p.nz, NXY = nx * ny;
-  const int x0 = blockIdx.x * MUX, y0 = blockIdx.y * MUY, z0 = blockIdx.z * zc;
-  const int z1 = min(z0 + zc, nz);
-  const int tx = threadIdx.x % MUX, ty = threadIdx.x / MUX;
-  const bool act = x0 + tx < nx && y0 + ty < ny;
-  const int gx = min(x0 + tx, nx - 1), gy = min(y0 + ty, ny - 1);
-  const float RT = float(p.RT), b4 = float(p.b4), two_a = float(p.two_a), k2 = float(p.k2), kap = float(p.kappa);
-  const float rref = float(p.rho_ref);
-  // z queue: q[R + d] = rho - rho_ref at (gx, gy, z + d)
-  float q[2 * R + 1];
-#pragma unroll
-  for (int d = -R; d <= R; ++d) q[d + R] = rin[pmod(z0 + d, nz) * NXY + gy * nx + gx];
-  auto load_plane = [&](int z, int b) {
-    const float* src = rin + pmod(z, nz) * NXY;
-    for (int idx = threadIdx.x; idx < PW * PH; idx += MUT) {
-      const int ry = idx / PW, rx = idx - ry * PW;
-      pl[b][ry][rx] = src[wrapi(y0 - R + ry, ny) * nx + wrapi(x0 - R + rx, nx)];
-    }
-  };
-  load_plane(z0, 0);
-  __syncthreads();
-  for (int z = z0; z < z1; ++z) {
-    const int b = (z - z0) & 1;
-    if (z + 1 < z1) load_plane(z + 1, b ^ 1);
-    const float next = rin[pmod(z + R + 1, nz) * NXY + gy * nx + gx];
-    if (act) {
-      const int cx = tx + R, cy = ty + R;
-      const float c = pl[b][cy][cx];
-      float lap = float(3.0 * Sch<S>::l(0)) * c;
-#pragma unroll
-      for (int m = 1; m <= R; ++m)
-        lap += float(Sch<S>::l(m)) * ((pl[b][cy][cx + m] + pl[b][cy][cx - m]) + (pl[b][cy + m][cx] + pl[b][cy - m][cx]) +
-                                      (q[R + m] + q[R - m]));
-      const float rho = rref + c;
-      const float eta = b4 * rho, om = 1.f - eta;
-      const float hs = __fdividef(eta * (8.f + eta * (-9.f + 3.f * eta)), om * om * om);
-      mu[z * NXY + gy * nx + gx] = k2 * (RT * (__logf(rho) + hs) - two_a * rho) - kap * lap;
-    }
-#pragma unroll
-    for (int d = 0; d < 2 * R; ++d) q[d] = q[d + 1];
-    q[2 * R] = next;
-    __syncthreads();
-  }
-}
 
 // ------------------------------------------------------------------ collision pass
 constexpr int CX = 32, CY = 11;     // collision region (tile + ring), one warp per row
 constexpr int TXC = CX - 2, TYC = CY - 2;  // 30 x 9 tile
 constexpr int CNT = CX * CY;        // 352 threads
+constexpr int FW = 36;              // staged population row: 32 nodes + up to 3 of alignment
 
+// Shared-memory rows start at a 16-byte-aligned global x (x of the region's
+// first node rounded down to a multiple of 4), so that with nx % 4 == 0 every
+// row is a whole number of 16-byte chunks that never straddle the periodic
+// seam; the region's first node then sits at column ox (field planes) or of
+// (populations), 0..3.  The scalar path (any nx) uses the same layout with
+// both offsets 0.
 template <int S>
 struct CollShape {
   static constexpr int R = Sch<S>::R;
   static constexpr int GW = CX + 2 * R, GH = CY + 2 * R;  // field region (ring + stencil halo)
+  static constexpr int GWV = (GW + 6) / 4 * 4;            // row stride: GW + 3 columns, whole chunks
   static constexpr int NS = 2 * R + 2;                    // ring of planes (one in flight)
-  static constexpr int plane = GW * GH;
-  static constexpr int NLD = (plane + CNT - 1) / CNT;
+  static constexpr int plane = GH * GWV;
+  static constexpr int FPL = CY * FW;                     // staged populations of one i
+  static constexpr int fbuf = 19 * FPL;
   static constexpr size_t off_mu = size_t(NS) * plane * 4;
   static constexpr size_t off_f = (off_mu + size_t(NS) * plane * 4 + 15) / 16 * 16;
-  static constexpr int fbuf = 19 * CNT;
   static constexpr size_t bytes = off_f + size_t(2) * fbuf * 4;
+  // 16-byte chunks per plane, and per thread
+  static constexpr int DCH = GH * (GWV / 4);              // of one field
+  static constexpr int KD = (2 * DCH + CNT - 1) / CNT;
+  static constexpr int FCH = 19 * CY * (FW / 4);
+  static constexpr int KF = (FCH + CNT - 1) / CNT;
 };
 
-template <int S, bool TAU1>
+__device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+// VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations)
+template <int S, bool TAU1, bool VEC>
 __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float* __restrict__ fin,
                                                     float* __restrict__ fout, const float* __restrict__ rin,
                                                     const float* __restrict__ muf, float* __restrict__ rout,
                                                     const StepAux aux, const int zc) {
   using L = Lattice<1>;
   using Sh = CollShape<S>;
-  constexpr int Q = 19, R = Sh::R, GW = Sh::GW, GH = Sh::GH, NS = Sh::NS;
+  constexpr int Q = 19, R = Sh::R, GWV = Sh::GWV, NS = Sh::NS, FPL = Sh::FPL;
   extern __shared__ __align__(16) unsigned char smem[];
   float* s_ds = reinterpret_cast<float*>(smem);
   float* s_mu = reinterpret_cast<float*>(smem + Sh::off_mu);
@@ -123,29 +85,73 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
   const float omega = float(p.omega), rref = float(p.rho_ref);
   const int pc_first = z0 - 1, pc_last = z1;
+  // first field / population column of the region in shared memory
+  const int ox = VEC ? (x0 - 1 - R) & 3 : 0;
+  const int of = VEC ? (x0 - 1) & 3 : 0;
 
-  // field planes q (density deviation and mu, region GW x GH) -> ring slot;
-  // populations of plane q - R (if collided) -> staging buffer of its parity
+  // VEC: the x-y part of the global offset of each of this thread's chunks
+  // (fixed for the whole z march; the shared offset of chunk c is 4 c)
+  int dofs[VEC ? Sh::KD : 1], fofs[VEC ? Sh::KF : 1];
+  if constexpr (VEC) {
+    const int xad = x0 - 1 - R - ox, xaf = x0 - 1 - of;  // aligned starts (may be negative)
+#pragma unroll
+    for (int k = 0; k < Sh::KD; ++k) {
+      const int c = tid + k * CNT, r = c < Sh::DCH ? c : c - Sh::DCH;
+      const int ry = r / (GWV / 4), j = r - ry * (GWV / 4);
+      dofs[k] = wrapn(y0 - 1 - R + ry, ny) * nx + wrapn(xad + 4 * j, nx);
+    }
+#pragma unroll
+    for (int k = 0; k < Sh::KF; ++k) {
+      const int c = tid + k * CNT, i = c / (CY * (FW / 4));  // population of chunk c
+      const int r = c - i * (CY * FW / 4), ry = r / (FW / 4), j = r - ry * (FW / 4);
+      fofs[k] = i * N + wrapn(y0 - 1 + ry, ny) * nx + wrapn(xaf + 4 * j, nx);
+    }
+  }
+
+  // field planes q (density deviation and mu) -> ring slot; populations of
+  // plane q - R (if collided) -> staging buffer of its parity
   auto issue = [&](int q, int slot) {
-    const int zo = pmod(q, nz) * NXY;
+    const int zo = wrapi(q, nz) * NXY;  // q in [z0 - 1 - R, z1 + R]: one period at most
     float* dd = s_ds + slot * Sh::plane;
     float* dm = s_mu + slot * Sh::plane;
-#pragma unroll
-    for (int k = 0; k < Sh::NLD; ++k) {
-      const int idx = tid + k * CNT;
-      const int ry = idx / GW, rx = idx - ry * GW;
-      if (idx < Sh::plane && rx < VW + 2 + 2 * R && ry < VH + 2 + 2 * R) {
-        const int g = zo + wrapi(y0 - 1 - R + ry, ny) * nx + wrapi(x0 - 1 - R + rx, nx);
-        cpa4(dd + idx, rin + g);
-        cpa4(dm + idx, muf + g);
-      }
-    }
     const int pc = q - R;
-    if (pc >= pc_first && pc <= pc_last && cnode) {
-      const float* fs = fin + pmod(pc, nz) * NXY + gy * nx + gx;
-      float* fd = s_f + (pc & 1) * Sh::fbuf + tid;
+    const bool fl = pc >= pc_first && pc <= pc_last;
+    const int zf = wrapi(pc, nz) * NXY;
+    float* fd = s_f + (pc & 1) * Sh::fbuf;
+    if constexpr (VEC) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) cpa4(fd + i * CNT, fs + i * N);
+      for (int k = 0; k < Sh::KD; ++k) {
+        const int c = tid + k * CNT;
+        if (c < 2 * Sh::DCH) {
+          if (c < Sh::DCH) cpa16(dd + 4 * c, rin + zo + dofs[k]);
+          else cpa16(dm + 4 * (c - Sh::DCH), muf + zo + dofs[k]);
+        }
+      }
+      if (fl) {
+#pragma unroll
+        for (int k = 0; k < Sh::KF; ++k) {
+          const int c = tid + k * CNT;
+          if (c < Sh::FCH) cpa16(fd + 4 * c, fin + zf + fofs[k]);
+        }
+      }
+    } else {
+      constexpr int GW = Sh::GW, NLD = (GW * Sh::GH + CNT - 1) / CNT;
+#pragma unroll
+      for (int k = 0; k < NLD; ++k) {
+        const int idx = tid + k * CNT;
+        const int ry = idx / GW, rx = idx - ry * GW;
+        if (idx < GW * Sh::GH && rx < VW + 2 + 2 * R && ry < VH + 2 + 2 * R) {
+          const int g = zo + wrapi(y0 - 1 - R + ry, ny) * nx + wrapi(x0 - 1 - R + rx, nx);
+          cpa4(dd + ry * GWV + rx, rin + g);
+          cpa4(dm + ry * GWV + rx, muf + g);
+        }
+      }
+      if (fl && cnode) {
+        const float* fs = fin + zf + gy * nx + gx;
+        float* fo = fd + cy * FW + cx;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) cpa4(fo + i * FPL, fs + i * N);
+      }
     }
     cpa_commit();
   };
@@ -160,6 +166,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
   issue(pc_first + R, slot);
   slot = ring(slot + 1, NS);
+  const int fme = cy * FW + of + cx;  // this node in a staged population plane
   for (int pc = pc_first; pc <= pc_last; ++pc) {
     cpa_wait_all();
     __syncthreads();
@@ -168,14 +175,15 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       slot = ring(slot + 1, NS);
     }
     float* fb = s_f + (pc & 1) * Sh::fbuf;
+    float own0 = 0.f, ownp = 0.f, ownm = 0.f;  // this node's populations with e_x = e_y = 0
     if (cnode) {
       int base[2 * R + 1];
 #pragma unroll
       for (int d = -R; d <= R; ++d) base[d + R] = ring(sc + d, NS) * Sh::plane;
       float fv[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fv[i] = fb[i * CNT + tid];
-      const int c = (cy + R) * GW + cx + R;
+      for (int i = 0; i < Q; ++i) fv[i] = fb[i * FPL + fme];
+      const int c = (cy + R) * GWV + ox + cx + R;
       const float dsv = s_ds[base[R] + c];
       const float rc = rref + dsv;
       float jx = 0.f, jy = 0.f, jz = 0.f;
@@ -188,15 +196,15 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       const float irc = __fdividef(1.f, rc);
       const float ux = jx * irc, uy = jy * irc, uz = jz * irc;
       float gmx, gmy, gmz, grx, gry, grz;
-      grad3d<S, float>(s_mu, base, GW, cx + R, cy + R, gmx, gmy, gmz);
-      grad3d<S, float>(s_ds, base, GW, cx + R, cy + R, grx, gry, grz);
+      grad3d<S, float>(s_mu, base, GWV, ox + cx + R, cy + R, gmx, gmy, gmz);
+      grad3d<S, float>(s_ds, base, GWV, ox + cx + R, cy + R, grx, gry, grz);
       const float Fx = -rc * gmx + grx * (1.f / 3.f), Fy = -rc * gmy + gry * (1.f / 3.f),
                   Fz = -rc * gmz + grz * (1.f / 3.f);
       const float vx = ux + Fx * irc, vy = uy + Fy * irc, vz = uz + Fz * irc;
       const bool push = interior && pc >= z0 && pc < z1;
       if (push && !(rc > 0.f)) atomicMin(aux.bad_step, (unsigned long long)aux.t);
       // target of population i = own node + per-axis deltas (periodic wrap folded in)
-      const int pz = pmod(pc, nz);
+      const int pz = wrapi(pc, nz);
       const int dxp = (gx + 1 < nx) ? 1 : 1 - nx, dxm = (gx > 0) ? -1 : nx - 1;
       const int dyp = (gy + 1 < ny) ? nx : nx - NXY, dym = (gy > 0) ? -nx : NXY - nx;
       const int dzp = (pz + 1 < nz) ? NXY : NXY - N, dzm = (pz > 0) ? -NXY : N - NXY;
@@ -205,35 +213,53 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       const float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
       const float wd0 = float(L::w(0)) * dsv, wd1 = float(L::w(1)) * dsv, wd2 = float(L::w(7)) * dsv;
       const float wr0 = float(L::w(0)) * rc, wr1 = float(L::w(1)) * rc, wr2 = float(L::w(7)) * rc;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
+      auto post = [&](const int i) {  // post-collision population i of this node
         const float wd = i == 0 ? wd0 : (i < 7 ? wd1 : wd2);
         const float wr = i == 0 ? wr0 : (i < 7 ? wr1 : wr2);
         const float ev = float(L::ex(i)) * vx + float(L::ey(i)) * vy + float(L::ez(i)) * vz;
         const float Av = ev * (3.f + 4.5f * ev) - vv15;
-        float fs;
         if constexpr (TAU1) {
-          fs = wd + wr * Av;
+          return wd + wr * Av;
         } else {
           const float eu = float(L::ex(i)) * ux + float(L::ey(i)) * uy + float(L::ez(i)) * uz;
           const float Au = eu * (3.f + 4.5f * eu) - uu15;
-          fs = (1.f - omega) * fv[i] + omega * wd + wr * (omega * Au + Av - Au);
+          return (1.f - omega) * fv[i] + omega * wd + wr * (omega * Au + Av - Au);
         }
-        fb[i * CNT + tid] = fs;
-        if (push) {
-          const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) + (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0)) +
-                        (L::ez(i) > 0 ? dzp : (L::ez(i) < 0 ? dzm : 0));
-          fo[i * N + d] = fs;
+      };
+      if (ly < 0 || ly == VH) {
+        // ring row (a whole warp): the neighbouring tile row gathers only the
+        // five populations moving towards it
+        const bool up = ly < 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          if (L::ey(i) != 0 && (L::ey(i) > 0) == up) fb[i * FPL + fme] = post(i);
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const float fs = post(i);
+          // populations that stay in this x-y column are gathered from registers
+          if (L::ex(i) == 0 && L::ey(i) == 0) {
+            if (L::ez(i) == 0) own0 = fs; else if (L::ez(i) > 0) ownp = fs; else ownm = fs;
+          } else {
+            fb[i * FPL + fme] = fs;
+          }
+          if (push) {
+            const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) +
+                          (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0)) +
+                          (L::ez(i) > 0 ? dzp : (L::ez(i) < 0 ? dzm : 0));
+            fo[i * N + d] = fs;
+          }
         }
       }
     }
     __syncthreads();
     // gather for the tile's own node of this thread
     if (interior) {
-      float s_m = 0.f, s_0 = 0.f, s_p = 0.f;
+      float s_m = ownm, s_0 = own0, s_p = ownp;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const float v = fb[i * CNT + tid - L::ey(i) * CX - L::ex(i)];
+        if (L::ex(i) == 0 && L::ey(i) == 0) continue;
+        const float v = fb[i * FPL + fme - L::ey(i) * FW - L::ex(i)];
         if (L::ez(i) < 0) s_m += v; else if (L::ez(i) == 0) s_0 += v; else s_p += v;
       }
       acc0 += s_m;

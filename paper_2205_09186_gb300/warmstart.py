@@ -6,11 +6,16 @@ density profile of each run is the target.  A small GELU network (4 inputs ->
 3 x 128 -> 64 outputs) is trained on the GPU by the library's own kernels
 (lbm_mlp_*), then predicts the initial profile of new droplets.  Warm and
 cold (tanh) starts are relaxed by the same solver to the same criterion; the
-cold-start result judges the warm start's final densities.
+cold-start result judges the warm start's final densities.  Droplets that
+evaporate (too small for their temperature) are left out of training and
+counted apart in the comparison.
 
 Network input: (T_r, ln k, R / 64, scheme id / 8).  Output: 64 samples of
 (rho - rho_g) / (rho_l - rho_g) (Maxwell densities) at r_j = max(0, R - 16) +
-j / 2, j = 0..63; the profile is held at its end values outside the window.
+j / 2, j = 0..63; the profile is held at its end values outside the window and
+shifted radially (plus a uniform remainder) so that it holds the same mass as
+the tanh start: both arms then relax towards the same equilibrium, which the
+cold start defines.
 """
 import math
 import time
@@ -68,6 +73,11 @@ def relax(sim, tol, max_steps, check_every=100):
     return steps, dev_ms * 1e-3, False, obs
 
 
+def survived(obs, g, l):
+    """A droplet is left at the centre (centre density above the Maxwell midpoint)."""
+    return obs["rho_center"] > 0.5 * (g + l)
+
+
 def make_sim(n, Tr, k, scheme="EFDS6", precision=L.LBM_FP32DEV):
     p = L.make_params(lattice=L.LBM_D3Q19, nx=n, ny=n, nz=n, Tr=Tr, k=k, kappa=0.1, scheme=scheme,
                       precision=precision)
@@ -85,11 +95,15 @@ def generate(cases, n=80, tol=1e-7, max_steps=20000, check_every=200):
             info.append(dict(c, steps=steps, converged=False))
             continue
         g, l = L.lbm_maxwell(p)
+        if not survived(obs, g, l):  # the droplet evaporated: no interface to learn
+            info.append(dict(c, steps=steps, converged=True, survived=False, device_s=dev_s))
+            sim.close()
+            continue
         rho = sim.lbm_get_density()
         prof = radial_profile(rho, (n // 2, n // 2, n // 2), window(c["R"]))
         X.append(features(c["Tr"], c["k"], c["R"], c.get("scheme", "EFDS6")))
         Y.append((prof - g) / (l - g))
-        info.append(dict(c, steps=steps, converged=True, device_s=dev_s))
+        info.append(dict(c, steps=steps, converged=True, survived=True, device_s=dev_s))
         sim.close()
     return np.array(X), np.array(Y), info
 
@@ -107,11 +121,61 @@ def train(X, Y, iters=3000, lr=1e-3, seed=0):
     return net, loss
 
 
-def predict(net, Tr, k, R, scheme, params):
+def lattice_radii(n):
+    """Distance of every node of an n^3 lattice to the centre node (n/2, n/2, n/2)."""
+    c = n // 2
+    x = np.arange(n) - c
+    return np.sqrt(x[:, None, None] ** 2 + x[None, :, None] ** 2 + x[None, None, :] ** 2)
+
+
+def tanh_mass(n, R, params, width=10.0):
+    """Mass of the Eq. 26 initial droplet on the n^3 lattice (Maxwell densities)."""
+    g, l = L.lbm_maxwell(params)
+    r = lattice_radii(n)
+    return float(np.sum(0.5 * (l + g) - 0.5 * (l - g) * np.tanh(2.0 * (r - R) / width)))
+
+
+MAX_REMAINDER = 0.05  # largest uniform mass remainder, as a fraction of the gas density
+
+
+def predict(net, Tr, k, R, scheme, params, n=None):
+    """Network profile (r, rho).  With n given, the profile is shifted radially so
+    that its mass on the n^3 lattice equals that of the tanh start it replaces:
+    the warm and cold starts then hold the same fluid and relax to the same state.
+    Returns None when the shift leaves a remainder above MAX_REMAINDER x rho_g."""
     y = net.lbm_mlp_forward(features(Tr, k, R, scheme)[None, :])[0].astype(np.float64)
     g, l = L.lbm_maxwell(params)
-    rho = g + (l - g) * y
-    return window(R), np.maximum(rho, 0.5 * g)
+    rho = np.maximum(g + (l - g) * y, 0.5 * g)
+    r = window(R)
+    if n is None:
+        return r, rho
+    rr = lattice_radii(n)
+    target = tanh_mass(n, R, params)
+
+    def placed(shift):
+        rs = r + shift
+        keep = rs >= 0
+        return rs[keep], rho[keep]
+
+    def mass(shift):
+        return float(np.sum(np.interp(rr, *placed(shift))))
+
+    lo, hi = -8.0, 8.0
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        if mass(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    shift = 0.5 * (lo + hi)
+    # what the shift cannot match (a profile that is nearly flat, or a shift
+    # beyond the search range) is spread uniformly: every node takes its value
+    # from the profile, so the masses are then equal
+    rs, vs = placed(shift)
+    rem = (target - mass(shift)) / rr.size
+    if abs(rem) > MAX_REMAINDER * g:
+        return None  # the network's profile cannot hold this mass: no warm start
+    return rs, vs + rem
 
 
 def compare(net, cases, n=80, tol=1e-7, max_steps=20000, check_every=200):
@@ -124,39 +188,54 @@ def compare(net, cases, n=80, tol=1e-7, max_steps=20000, check_every=200):
             if arm == "cold":
                 sim.lbm_init_droplet(c["R"])
             else:
-                r, rho = predict(net, c["Tr"], c["k"], c["R"], c.get("scheme", "EFDS6"), p)
-                sim.lbm_init_profile(r, rho)
+                prof = predict(net, c["Tr"], c["k"], c["R"], c.get("scheme", "EFDS6"), p, n=n)
+                out["fallback"] = prof is None
+                if prof is None:
+                    sim.lbm_init_droplet(c["R"])
+                else:
+                    sim.lbm_init_profile(*prof)
             steps, dev_s, ok, obs = relax(sim, tol, max_steps, check_every)
             out[arm] = dict(steps=steps, device_s=dev_s, converged=ok, rho_center=obs["rho_center"],
                             rho_corner=obs["rho_corner"], max_v=obs["max_v"])
             sim.close()
         out["case"] = c
-        rl = max(abs(out["cold"]["rho_center"]), 1e-30)
+        g, rl = L.lbm_maxwell(L.make_params(Tr=c["Tr"]))
+        out["survived"] = survived(out["cold"], g, rl)
         out["density_err"] = max(abs(out["warm"]["rho_center"] - out["cold"]["rho_center"]) / rl,
                                  abs(out["warm"]["rho_corner"] - out["cold"]["rho_corner"]) / rl)
         rows.append(out)
     return rows
 
 
-def sample_cases(n, seed, Tr=(0.6, 0.9), k=(0.15, 0.3), R=(10.0, 20.0), scheme="EFDS6"):
+def sample_cases(n, seed, Tr=(0.6, 0.85), k=(0.2, 0.35), R=(14.0, 22.0), scheme="EFDS6"):
     rng = np.random.default_rng(seed)
     return [dict(Tr=float(rng.uniform(*Tr)), k=float(math.exp(rng.uniform(math.log(k[0]), math.log(k[1])))),
                  R=float(rng.uniform(*R)), scheme=scheme) for _ in range(n)]
 
 
 def experiment(n_train=48, n_test=16, n=80, tol=1e-7, iters=4000, seed=2205):
+    """Generate, train, compare; the totals count the test cases where both arms
+    converged and the cold-start droplet survived (an evaporating droplet has
+    no profile to predict; those cases are counted separately)."""
     t0 = time.time()
     train_cases = sample_cases(n_train, seed)
     test_cases = sample_cases(n_test, seed + 1)
     X, Y, info = generate(train_cases, n=n, tol=tol)
     net, loss = train(X, Y, iters=iters)
     rows = compare(net, test_cases, n=n, tol=tol)
-    conv = [r for r in rows if r["warm"]["converged"] and r["cold"]["converged"]]
+    both = [r for r in rows if r["warm"]["converged"] and r["cold"]["converged"]]
+    conv = [r for r in both if r["survived"]]
     res = {"lattice": "D3Q19 %d^3, EFDS6, FP32DEV" % n, "tol_max_drho": tol, "train_cases": len(X),
-           "train_loss": loss, "test_cases": len(rows), "both_converged": len(conv),
+           "train_evaporated": sum(1 for i in info if i.get("survived") is False),
+           "train_loss": loss, "test_cases": len(rows), "both_converged": len(both),
+           "test_evaporated": len(both) - len(conv), "counted": len(conv),
+           "warm_fallbacks": sum(1 for r in rows if r["fallback"]),
+           "max_density_err_evaporated": max([r["density_err"] for r in both if not r["survived"]], default=None),
            "cold_steps": sum(r["cold"]["steps"] for r in conv), "warm_steps": sum(r["warm"]["steps"] for r in conv),
            "cold_device_s": sum(r["cold"]["device_s"] for r in conv),
            "warm_device_s": sum(r["warm"]["device_s"] for r in conv),
            "max_density_err_vs_cold": max([r["density_err"] for r in conv], default=None),
+           "warm_failed": sum(1 for r in rows if not r["warm"]["converged"]),
+           "cold_failed": sum(1 for r in rows if not r["cold"]["converged"]),
            "train_generation_device_s": sum(i.get("device_s", 0.0) for i in info), "wall_s": time.time() - t0}
     return res, rows

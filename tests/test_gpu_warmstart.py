@@ -22,12 +22,12 @@ def W():
 def test_warm_start_gain_and_agreement(W):
     L = W.L
     n = 48
-    train = [dict(Tr=tr, k=k, R=R, scheme="EFDS6") for tr in (0.75, 0.85) for k in (0.2, 0.3) for R in (9.0, 12.0)]
+    train = [dict(Tr=tr, k=k, R=R, scheme="EFDS6") for tr in (0.65, 0.75) for k in (0.25, 0.35) for R in (11.0, 14.0)]
     X, Y, info = W.generate(train, n=n, tol=1e-6, max_steps=6000, check_every=200)
     assert len(X) >= 6
     net, loss = W.train(X, Y, iters=1500, lr=2e-3)
     assert loss < 0.02
-    case = dict(Tr=0.8, k=0.25, R=10.5, scheme="EFDS6")
+    case = dict(Tr=0.7, k=0.3, R=12.5, scheme="EFDS6")
     # cold start: tanh profile; relax and take the converged profile
     sim, p = W.make_sim(n, case["Tr"], case["k"])
     sim.lbm_init_droplet(case["R"])
@@ -39,11 +39,14 @@ def test_warm_start_gain_and_agreement(W):
     assert ok_c
     # warm start from the network
     sim2, p2 = W.make_sim(n, case["Tr"], case["k"])
-    rr, rho = W.predict(net, case["Tr"], case["k"], case["R"], case["scheme"], p2)
+    rr, rho = W.predict(net, case["Tr"], case["k"], case["R"], case["scheme"], p2, n=n)
     sim2.lbm_init_profile(rr, rho)
     warm0 = W.radial_profile(sim2.lbm_get_density(), c, r)
     assert np.linalg.norm(warm0 - conv) < np.linalg.norm(cold0 - conv)
     steps_w, _, ok_w, obs_w = W.relax(sim2, 1e-6, 6000, 200)
     assert ok_w
-    assert abs(obs_w["rho_center"] - obs_c["rho_center"]) / obs_c["rho_center"] < 2e-3
-    assert abs(obs_w["rho_corner"] - obs_c["rho_corner"]) / obs_c["rho_center"] < 2e-3
+    # the droplet survives (centre is liquid) and both starts reach the same state
+    rl = L.lbm_maxwell(p)[1]
+    assert obs_c["rho_center"] > 0.5 * rl
+    assert abs(obs_w["rho_center"] - obs_c["rho_center"]) / rl < 2e-3
+    assert abs(obs_w["rho_corner"] - obs_c["rho_corner"]) / rl < 2e-3

@@ -42,11 +42,15 @@ def test_noalloc_matches_allocating_observables(L, lattice, shape, precision, sc
     ref = s.lbm_observables()
     d_f, d_rho = s.lbm_device_state()
     stream = torch.cuda.current_stream().cuda_stream
+    # FP64: the same kernels, so equal to rounding.  FP32 deviations: the handle
+    # evaluates D3Q19 observables from its mu field (separate FP32 pass), this
+    # entry point inside its tile kernel, so FP32 rounding differs.
+    tol = 1e-12 if precision == 0 else 2e-6
     for _ in range(2):  # two calls in a row share the fixed array
         rc, o = L.lbm_observables_noalloc(s.params, d_f, d_rho, step=20, stream=stream)
         assert rc == L.LBM_OK and o["status"] == 0 and o["step"] == 20
         for k in KEYS:
-            assert o[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-300), k
+            assert o[k] == pytest.approx(ref[k], rel=tol, abs=1e-300), k
     # max_drho against an earlier density held by the caller (here the same field)
     rc, o = L.lbm_observables_noalloc(s.params, d_f, d_rho, d_rho_prev=d_rho, steps_since_prev=5, step=20,
                                       stream=stream)
