@@ -283,18 +283,19 @@ def run_gpu(args):
     achieved = B_COLL * N / (coll_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
 
-    # end to end through the public API with host buffers: upload the initial
-    # density (H2D), step, read the observables every step (D2H), read back
-    # the final density (D2H)
-    rho0 = np.ascontiguousarray(sim.lbm_get_density())
+    # end to end through the public API with pinned host buffers: upload the
+    # initial density (H2D), step with the observables of every step read back
+    # (D2H; lbm_step_observe reports the state each step started from), read
+    # back the final density (D2H)
+    host_rho0 = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    host_rho0[:] = sim.lbm_get_density().reshape(-1)
     host_rho = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim.lbm_init_density(rho0)
+    sim.lbm_init_density(host_rho0)
     for _ in range(args.steps):
-        sim.lbm_step(1)
-        sim.lbm_observables()
-    host_rho[:] = sim.lbm_get_density().reshape(-1)
+        sim.lbm_step_observe(1)
+    sim.lbm_get_density(out=host_rho)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": N * args.steps * world / e2e_s / 1e6, "unit": UNIT,

@@ -177,6 +177,17 @@ int lbm_step_timed(lbm_handle* h, long long n, double* ms);
  * NaN density has been seen. */
 int lbm_observables(lbm_handle* h, lbm_obs* out);
 
+/* Advance n >= 1 time steps and return the observables of the state the last
+ * of them started from (step lbm_get_step() - 1 afterwards), as
+ * lbm_observables would have returned them before that step, within FP32
+ * rounding.  On the split D3Q19 FP32-deviation path (EFDS2/4/6) the last step
+ * computes them in its collision pass (u, F and rho are at hand there), so an
+ * observed step costs one step plus a small reduction instead of a step and a
+ * separate observation pass; elsewhere it observes, then steps.  Synchronises
+ * the stream.  Returns LBM_EUNSTABLE as lbm_observables does.  (A performance
+ * entry point; the paper's method has no counterpart.) */
+int lbm_step_observe(lbm_handle* h, long long n, lbm_obs* out);
+
 /* Copy the density field rho[N] (FP64) to host memory (synchronises). */
 int lbm_get_density(lbm_handle* h, double* host_rho);
 

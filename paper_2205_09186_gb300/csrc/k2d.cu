@@ -61,6 +61,7 @@ cudaError_t launch(const Launch& c, int mode, int* nblocks) {
     if (mode == MODE_STEP && c.mu)
       return c.kp.omega == 1.0 ? launch_split2d<S, true>(c, nblocks) : launch_split2d<S, false>(c, nblocks);
   }
+  if (mode == MODE_STEP_OBS) return cudaErrorNotSupported;
   if (mode == MODE_STEP) return launch_mode<S, P, MODE_STEP>(c, nblocks);
   if (mode == MODE_OBS) return launch_mode<S, P, MODE_OBS>(c, nblocks);
   return launch_mode<S, P, MODE_FIELDS>(c, nblocks);

@@ -103,10 +103,10 @@ cudaError_t launch_fast(const Launch& c, int* nblocks) {
   return cudaGetLastError();
 }
 
-template <int S, bool TAU1, bool VEC>
+template <int S, bool TAU1, bool VEC, bool OBS>
 cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
   using Sh = CollShape<S>;
-  auto kc = k_coll3d<S, TAU1, VEC>;
+  auto kc = k_coll3d<S, TAU1, VEC, OBS>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
@@ -115,26 +115,36 @@ cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
   }
   kc<<<grid, CNT, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
                                          static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
-                                         static_cast<float*>(c.rout), c.aux, zc);
+                                         static_cast<float*>(c.rout), c.aux, zc,
+                                         OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr);
   return cudaGetLastError();
 }
 
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
 
-// mu pass + collision pass (line schemes, FP32DEV, FP32 mu)
+// mu pass + collision pass (line schemes, FP32DEV, FP32 mu); with obs the
+// collision pass also reduces the observables of the state it advances
 template <int S, bool TAU1>
-cudaError_t launch_split(const Launch& c, int* nblocks) {
+cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   using Sh = CollShape<S>;
   if (!c.mu) return cudaErrorInvalidValue;
+  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sh::R);
+  dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + TYC - 1) / TYC, (c.kp.nz + zc - 1) / zc);
+  if (nblocks) {
+    // observation: the caller's partials buffer holds *nblocks entries
+    if (obs && (long long)grid.x * grid.y * grid.z > *nblocks) return cudaErrorNotSupported;
+    *nblocks = int(grid.x * grid.y * grid.z);
+  } else if (obs) {
+    return cudaErrorInvalidValue;
+  }
   dim3 gm((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
   k_mu3d<S><<<gm, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
   if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
-  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sh::R);
-  dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + TYC - 1) / TYC, (c.kp.nz + zc - 1) / zc);
-  if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
   // 16-byte copies need rows of whole chunks and aligned bases
   const bool vec = c.kp.nx % 4 == 0 && aligned16(c.fin) && aligned16(c.rin) && aligned16(c.mu);
-  return vec ? launch_coll<S, TAU1, true>(c, grid, zc) : launch_coll<S, TAU1, false>(c, grid, zc);
+  if (obs)
+    return vec ? launch_coll<S, TAU1, true, true>(c, grid, zc) : launch_coll<S, TAU1, false, true>(c, grid, zc);
+  return vec ? launch_coll<S, TAU1, true, false>(c, grid, zc) : launch_coll<S, TAU1, false, false>(c, grid, zc);
 }
 
 // observation pass of the split path: mu field, then the node-parallel reduction
@@ -156,12 +166,15 @@ cudaError_t launch(const Launch& c, int mode, int* nblocks) {
     if (mode == MODE_OBS && c.mu) return launch_obs_split<S>(c, nblocks);
   }
   if constexpr (std::is_same<P, PrecF32>::value) {
-    if (mode == MODE_STEP) {
+    if (mode == MODE_STEP || mode == MODE_STEP_OBS) {
+      const bool obs = mode == MODE_STEP_OBS;
       if constexpr (!Sch<S>::ISO)
-        return c.kp.omega == 1.0 ? launch_split<S, true>(c, nblocks) : launch_split<S, false>(c, nblocks);
+        return c.kp.omega == 1.0 ? launch_split<S, true>(c, nblocks, obs) : launch_split<S, false>(c, nblocks, obs);
+      if (obs) return cudaErrorNotSupported;
       return c.kp.omega == 1.0 ? launch_fast<S, true>(c, nblocks) : launch_fast<S, false>(c, nblocks);
     }
   }
+  if (mode == MODE_STEP_OBS) return cudaErrorNotSupported;
   if (mode == MODE_STEP) return launch_mode<S, P, MODE_STEP>(c, nblocks);
   if (mode == MODE_OBS) return launch_mode<S, P, MODE_OBS>(c, nblocks);
   return launch_mode<S, P, MODE_FIELDS>(c, nblocks);

@@ -677,6 +677,40 @@ extern "C" int lbm_step_timed(lbm_handle* h, long long n, double* ms) {
   return rc;
 }
 
+// reduce nb per-CTA partials, read the result (and the density at the centre
+// and corner nodes of rho_obs) back, fill out for the state of step t_obs
+static int finish_observables(lbm_handle* h, int nb, const void* rho_obs, long long t_obs, lbm_obs* out) {
+  if (nb > h->n_partials) return LBM_ECUDA;
+  const long long center =
+      (long long)(h->p.nz / 2) * h->p.nx * h->p.ny + (long long)(h->p.ny / 2) * h->p.nx + h->p.nx / 2;
+  if (h->p.precision == LBM_FP64)
+    k_obs_final<double><<<1, 256, 0, h->stream>>>(h->d_partials, nb, static_cast<const double*>(rho_obs), 0.0, center,
+                                                  h->d_bad, h->d_obs);
+  else
+    k_obs_final<float><<<1, 256, 0, h->stream>>>(h->d_partials, nb, static_cast<const float*>(rho_obs),
+                                                 h->kp.rho_ref, center, h->d_bad, h->d_obs);
+  double host[8];
+  if (cudaMemcpyAsync(host, h->d_obs, 64, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return LBM_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
+  unsigned long long bad;
+  std::memcpy(&bad, &host[6], 8);
+  out->max_v = host[0];
+  out->max_u = host[1];
+  out->mass = host[2];
+  out->max_drho = t_obs > h->t_snap ? host[3] / double(t_obs - h->t_snap) : 0.0;
+  out->rho_center = host[4];
+  out->rho_corner = host[5];
+  out->step = t_obs;
+  out->status = LBM_OK;
+  h->t_snap = t_obs;
+  if (bad != ULLONG_MAX) {
+    out->status = LBM_EUNSTABLE;
+    out->step = (long long)bad;
+    return LBM_EUNSTABLE;
+  }
+  return LBM_OK;
+}
+
 extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
   if (!h || !out) return LBM_EINVAL;
   std::memset(out, 0, sizeof(*out));
@@ -688,36 +722,37 @@ extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
                              : h->fn(c, MODE_OBS, &nb);
   if (e != cudaSuccess) return LBM_ECUDA;
   if (nb > h->n_partials) return LBM_ECUDA;
-  const long long center =
-      (long long)(h->p.nz / 2) * h->p.nx * h->p.ny + (long long)(h->p.ny / 2) * h->p.nx + h->p.nx / 2;
-  if (h->p.precision == LBM_FP64)
-    k_obs_final<double><<<1, 256, 0, h->stream>>>(h->d_partials, nb, static_cast<const double*>(h->rho[h->cur]), 0.0,
-                                                  center, h->d_bad, h->d_obs);
-  else
-    k_obs_final<float><<<1, 256, 0, h->stream>>>(h->d_partials, nb, static_cast<const float*>(h->rho[h->cur]),
-                                                 h->kp.rho_ref, center, h->d_bad, h->d_obs);
-  double host[8];
-  if (cudaMemcpyAsync(host, h->d_obs, 64, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return LBM_ECUDA;
+  // the snapshot for the next max |d rho / dt|, ordered after the reduction
   if (cudaMemcpyAsync(h->rho_snap, h->rho[h->cur], r_bytes(h), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return LBM_ECUDA;
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
-  unsigned long long bad;
-  std::memcpy(&bad, &host[6], 8);
-  out->max_v = host[0];
-  out->max_u = host[1];
-  out->mass = host[2];
-  out->max_drho = h->t > h->t_snap ? host[3] / double(h->t - h->t_snap) : 0.0;
-  out->rho_center = host[4];
-  out->rho_corner = host[5];
-  out->step = h->t;
-  out->status = LBM_OK;
-  h->t_snap = h->t;
-  if (bad != ULLONG_MAX) {
-    out->status = LBM_EUNSTABLE;
-    out->step = (long long)bad;
-    return LBM_EUNSTABLE;
+  return finish_observables(h, nb, h->rho[h->cur], h->t, out);
+}
+
+extern "C" int lbm_step_observe(lbm_handle* h, long long n, lbm_obs* out) {
+  if (!h || !out || n < 1) return LBM_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  int rc = lbm_step(h, n - 1);
+  if (rc != LBM_OK) return rc;
+  if (h->D == 3 && h->mu && !h->compact) {
+    // the last step reduces the observables of the state it advances and
+    // leaves that state's density in the snapshot
+    Launch c = make_launch(h, 1 - h->cur);
+    int nb = h->n_partials;  // capacity in, CTAs out
+    const cudaError_t e = h->fn(c, MODE_STEP_OBS, &nb);
+    if (e == cudaSuccess) {
+      const void* rho_obs = h->rho[h->cur];  // not overwritten before the next step
+      const long long t_obs = h->t;
+      h->cur = 1 - h->cur;
+      h->t += 1;
+      return finish_observables(h, nb, rho_obs, t_obs, out);
+    }
+    if (e != cudaErrorNotSupported) return LBM_ECUDA;
+    cudaGetLastError();  // nothing was launched: observe, then step
   }
-  return LBM_OK;
+  rc = lbm_observables(h, out);
+  if (rc != LBM_OK && rc != LBM_EUNSTABLE) return rc;
+  const int rs = lbm_step(h, 1);
+  return rs != LBM_OK ? rs : rc;
 }
 
 extern "C" int lbm_get_density(lbm_handle* h, double* host_rho) {

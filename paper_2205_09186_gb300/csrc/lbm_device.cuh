@@ -259,6 +259,36 @@ __device__ __forceinline__ T coll_one(int i, T d, T dr, T rho, T omega, T ux, T 
 
 // Error-free float summation (TwoSum accumulation) used for densities in
 // FP32DEV mode: returns s_hi + s_lo ~= exact sum of the terms.
+// asynchronous global -> shared copies (4 bytes, through L1) and their groups
+__device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// all but the most recent group complete
+__device__ __forceinline__ void cpa_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ int ring(int s, int n) { return s < 0 ? s + n : (s >= n ? s - n : s); }
+
+// e_i . (x, y, z) from the nonzero components of e_i only.  Under IEEE rules
+// 0 * x and 0 + x do not fold away (NaN, signed zero), so the plain dot product
+// costs three FMA-pipe instructions per population even for an axis direction;
+// with i a constant after unrolling this folds to at most two adds.
+template <class L>
+__device__ __forceinline__ float edot(int i, float x, float y, float z) {
+  const int a = L::ex(i), b = L::ey(i), c = L::ez(i);
+  const float X = a > 0 ? x : -x, Y = b > 0 ? y : -y, Z = c > 0 ? z : -z;
+  if (a != 0 && b != 0 && c != 0) return X + Y + Z;
+  if (a != 0 && b != 0) return X + Y;
+  if (a != 0 && c != 0) return X + Z;
+  if (b != 0 && c != 0) return Y + Z;
+  if (a != 0) return X;
+  if (b != 0) return Y;
+  if (c != 0) return Z;
+  return 0.f;
+}
+
 struct FSum {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float x) {

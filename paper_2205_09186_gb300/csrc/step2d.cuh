@@ -15,7 +15,9 @@
 
 namespace lbmd {
 
-enum { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2 };
+// MODE_STEP_OBS: one step that also reduces the observables of the state it
+// advances (split D3Q19 FP32DEV path only; other paths report not-supported)
+enum { MODE_STEP = 0, MODE_OBS = 1, MODE_FIELDS = 2, MODE_STEP_OBS = 3 };
 
 // fields written in MODE_FIELDS: F (component-major, D*N) and mu (N), FP64
 struct FieldOut {

@@ -33,18 +33,30 @@ struct Split2DShape {
   static constexpr size_t bytes = coll_bytes > mu_bytes ? coll_bytes : mu_bytes;
 };
 
+// Each pass is a load half (asynchronous copies into the tile's shared-memory
+// buffer; the caller commits and waits) and a compute half, so that the batch
+// kernel can copy its next tile while computing the current one.
+
 template <int S>
-__device__ __forceinline__ void mu2d_tile(const KParams& p, const float* __restrict__ rin, float* __restrict__ mu,
-                                          int x0, int y0, unsigned char* smem) {
+__device__ __forceinline__ void mu2d_load(const KParams& p, const float* __restrict__ rin, int x0, int y0,
+                                          unsigned char* smem) {
   using Sh = Split2DShape<S>;
   constexpr int R = Sh::R, MW = Sh::MW, MH = Sh::MH;
   float* s = reinterpret_cast<float*>(smem);
   const int nx = p.nx, ny = p.ny;
   for (int idx = threadIdx.x; idx < MW * MH; idx += NT2S) {
     const int ry = idx / MW, rx = idx - ry * MW;
-    s[idx] = rin[wrapn(y0 - R + ry, ny) * nx + wrapn(x0 - R + rx, nx)];
+    cpa4(s + idx, rin + wrapn(y0 - R + ry, ny) * nx + wrapn(x0 - R + rx, nx));
   }
-  __syncthreads();
+}
+
+template <int S>
+__device__ __forceinline__ void mu2d_compute(const KParams& p, float* __restrict__ mu, int x0, int y0,
+                                             const unsigned char* smem) {
+  using Sh = Split2DShape<S>;
+  constexpr int R = Sh::R, MW = Sh::MW;
+  const float* s = reinterpret_cast<const float*>(smem);
+  const int nx = p.nx, ny = p.ny;
   const int tx = threadIdx.x % M2X, ty = threadIdx.x / M2X;
   if (x0 + tx < nx && y0 + ty < ny) {
     const float RT = float(p.RT), b4 = float(p.b4), two_a = float(p.two_a), k2 = float(p.k2), kap = float(p.kappa);
@@ -54,15 +66,12 @@ __device__ __forceinline__ void mu2d_tile(const KParams& p, const float* __restr
     const float lap = lap2d<S, float>(s, MW, tx + R, ty + R);
     mu[(y0 + ty) * nx + x0 + tx] = k2 * (RT * (__logf(rho) + hs) - two_a * rho) - kap * lap;
   }
-  __syncthreads();
 }
 
-template <int S, bool TAU1>
-__device__ __forceinline__ void coll2d_tile(const KParams& p, const float* __restrict__ fin, float* __restrict__ fout,
-                                            const float* __restrict__ rin, const float* __restrict__ muf,
-                                            float* __restrict__ rout, unsigned long long* bad, long long t, int x0,
+template <int S>
+__device__ __forceinline__ void coll2d_load(const KParams& p, const float* __restrict__ fin,
+                                            const float* __restrict__ rin, const float* __restrict__ muf, int x0,
                                             int y0, unsigned char* smem) {
-  using L = Lattice<0>;
   using Sh = Split2DShape<S>;
   constexpr int Q = 9, R = Sh::R, GW = Sh::GW, GH = Sh::GH;
   float* s_ds = reinterpret_cast<float*>(smem);
@@ -72,25 +81,44 @@ __device__ __forceinline__ void coll2d_tile(const KParams& p, const float* __res
   const int VW = min(T2X, nx - x0), VH = min(T2Y, ny - y0);
   const int tid = threadIdx.x;
   const int cy = tid / C2X, cx = tid - cy * C2X;
-  const int lx = cx - 1, ly = cy - 1;
-  const bool cnode = lx <= VW && ly <= VH;
-  const bool interior = lx >= 0 && lx < VW && ly >= 0 && ly < VH;
-  const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
-  // own populations first (latency overlaps the field staging)
-  float fv[Q];
+  if (cx - 1 <= VW && cy - 1 <= VH) {  // collided node: stage its populations
+    const float* fs = fin + wrapi(y0 + cy - 1, ny) * nx + wrapi(x0 + cx - 1, nx);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) fv[i] = cnode ? fin[i * N + gy * nx + gx] : 0.f;
+    for (int i = 0; i < Q; ++i) cpa4(s_f + i * NT2S + tid, fs + i * N);
+  }
   for (int idx = tid; idx < GW * GH; idx += NT2S) {
     const int ry = idx / GW, rx = idx - ry * GW;
     if (rx < VW + 2 + 2 * R && ry < VH + 2 + 2 * R) {
       const int g = wrapi(y0 - 1 - R + ry, ny) * nx + wrapi(x0 - 1 - R + rx, nx);
-      s_ds[idx] = rin[g];
-      s_mu[idx] = muf[g];
+      cpa4(s_ds + idx, rin + g);
+      cpa4(s_mu + idx, muf + g);
     }
   }
-  __syncthreads();
+}
+
+template <int S, bool TAU1>
+__device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restrict__ fout, float* __restrict__ rout,
+                                               unsigned long long* bad, long long t, int x0, int y0,
+                                               unsigned char* smem) {
+  using L = Lattice<0>;
+  using Sh = Split2DShape<S>;
+  constexpr int Q = 9, R = Sh::R, GW = Sh::GW;
+  const float* s_ds = reinterpret_cast<const float*>(smem);
+  const float* s_mu = reinterpret_cast<const float*>(smem + Sh::off_mu);
+  float* s_f = reinterpret_cast<float*>(smem + Sh::off_f);
+  const int nx = p.nx, ny = p.ny, N = int(p.n);
+  const int VW = min(T2X, nx - x0), VH = min(T2Y, ny - y0);
+  const int tid = threadIdx.x;
+  const int cy = tid / C2X, cx = tid - cy * C2X;
+  const int lx = cx - 1, ly = cy - 1;
+  const bool cnode = lx <= VW && ly <= VH;
+  const bool interior = lx >= 0 && lx < VW && ly >= 0 && ly < VH;
+  const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
   const float omega = float(p.omega), rref = float(p.rho_ref);
   if (cnode) {
+    float fv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fv[i] = s_f[i * NT2S + tid];
     const int c = (cy + R) * GW + cx + R;
     const float dsv = s_ds[c];
     const float rc = rref + dsv;
@@ -115,14 +143,14 @@ __device__ __forceinline__ void coll2d_tile(const KParams& p, const float* __res
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const float w = float(L::w(i));
-      const float ev = float(L::ex(i)) * vx + float(L::ey(i)) * vy;
-      const float Av = ev * (3.f + 4.5f * ev) - vv15;
+      const float ev = edot<L>(i, vx, vy, 0.f);
+      const float Av = i == 0 ? -vv15 : ev * (3.f + 4.5f * ev) - vv15;
       float fs;
       if constexpr (TAU1) {
         fs = w * (dsv + rc * Av);
       } else {
-        const float eu = float(L::ex(i)) * ux + float(L::ey(i)) * uy;
-        const float Au = eu * (3.f + 4.5f * eu) - uu15;
+        const float eu = edot<L>(i, ux, uy, 0.f);
+        const float Au = i == 0 ? -uu15 : eu * (3.f + 4.5f * eu) - uu15;
         fs = (1.f - omega) * fv[i] + w * (omega * dsv + rc * (omega * Au + Av - Au));
       }
       s_f[i * NT2S + tid] = fs;
@@ -140,7 +168,29 @@ __device__ __forceinline__ void coll2d_tile(const KParams& p, const float* __res
     rout[(y0 + ly) * nx + x0 + lx] = acc;
     if (!(rref + acc > 0.f)) atomicMin(bad, (unsigned long long)(t + 1));
   }
+}
+
+// whole tiles (load, wait, compute) for the single-case kernels
+template <int S>
+__device__ __forceinline__ void mu2d_tile(const KParams& p, const float* __restrict__ rin, float* __restrict__ mu,
+                                          int x0, int y0, unsigned char* smem) {
+  mu2d_load<S>(p, rin, x0, y0, smem);
+  cpa_commit();
+  cpa_wait_all();
   __syncthreads();
+  mu2d_compute<S>(p, mu, x0, y0, smem);
+}
+
+template <int S, bool TAU1>
+__device__ __forceinline__ void coll2d_tile(const KParams& p, const float* __restrict__ fin, float* __restrict__ fout,
+                                            const float* __restrict__ rin, const float* __restrict__ muf,
+                                            float* __restrict__ rout, unsigned long long* bad, long long t, int x0,
+                                            int y0, unsigned char* smem) {
+  coll2d_load<S>(p, fin, rin, muf, x0, y0, smem);
+  cpa_commit();
+  cpa_wait_all();
+  __syncthreads();
+  coll2d_compute<S, TAU1>(p, fout, rout, bad, t, x0, y0, smem);
 }
 
 template <int S>

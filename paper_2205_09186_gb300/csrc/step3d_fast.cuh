@@ -49,14 +49,6 @@ struct FastShape {
   static constexpr size_t bytes = off_f + size_t(2) * fbuf * 4;
 };
 
-__device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ int ring(int s, int n) { return s < 0 ? s + n : (s >= n ? s - n : s); }
 
 template <int S, bool TAU1>
 __global__ void __launch_bounds__(FNT, 2) k_step3d_fast(const KParams p, const float* __restrict__ fin,
@@ -186,14 +178,14 @@ __global__ void __launch_bounds__(FNT, 2) k_step3d_fast(const KParams p, const f
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const float w = float(L::w(i));
-          const float ev = float(L::ex(i)) * vx + float(L::ey(i)) * vy + float(L::ez(i)) * vz;
-          const float Av = ev * (3.f + 4.5f * ev) - vv15;
+          const float ev = edot<L>(i, vx, vy, vz);
+          const float Av = i == 0 ? -vv15 : ev * (3.f + 4.5f * ev) - vv15;
           float fs;
           if constexpr (TAU1) {
             fs = w * (dsv + rc * Av);
           } else {
-            const float eu = float(L::ex(i)) * ux + float(L::ey(i)) * uy + float(L::ez(i)) * uz;
-            const float Au = eu * (3.f + 4.5f * eu) - uu15;
+            const float eu = edot<L>(i, ux, uy, uz);
+            const float Au = i == 0 ? -uu15 : eu * (3.f + 4.5f * eu) - uu15;
             fs = (1.f - omega) * fv[i] + w * (omega * dsv + rc * (omega * Au + Av - Au));
           }
           fb[i * FNC + tid] = fs;

@@ -58,12 +58,15 @@ __device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 
-// VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations)
-template <int S, bool TAU1, bool VEC>
+// VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations).
+// OBS: also reduce the observables of the state being advanced (max |v| with
+// v = u + F / (2 rho), max |u|, mass, max |rho - snap|) into aux.partials, one
+// set per CTA, and overwrite snap with this state's density deviation.
+template <int S, bool TAU1, bool VEC, bool OBS>
 __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float* __restrict__ fin,
                                                     float* __restrict__ fout, const float* __restrict__ rin,
                                                     const float* __restrict__ muf, float* __restrict__ rout,
-                                                    const StepAux aux, const int zc) {
+                                                    const StepAux aux, const int zc, float* __restrict__ snap) {
   using L = Lattice<1>;
   using Sh = CollShape<S>;
   constexpr int Q = 19, R = Sh::R, GWV = Sh::GWV, NS = Sh::NS, FPL = Sh::FPL;
@@ -167,6 +170,9 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   issue(pc_first + R, slot);
   slot = ring(slot + 1, NS);
   const int fme = cy * FW + of + cx;  // this node in a staged population plane
+  float o_v = 0.f, o_u = 0.f, o_d = 0.f;  // OBS: running maxima of this thread's nodes
+  FSum o_m;                                // OBS: sum of density deviations
+  int o_n = 0;                             // OBS: nodes counted
   for (int pc = pc_first; pc <= pc_last; ++pc) {
     cpa_wait_all();
     __syncthreads();
@@ -203,6 +209,18 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       const float vx = ux + Fx * irc, vy = uy + Fy * irc, vz = uz + Fz * irc;
       const bool push = interior && pc >= z0 && pc < z1;
       if (push && !(rc > 0.f)) atomicMin(aux.bad_step, (unsigned long long)aux.t);
+      if constexpr (OBS) {
+        if (push) {
+          const float hx = ux + 0.5f * Fx * irc, hy = uy + 0.5f * Fy * irc, hz = uz + 0.5f * Fz * irc;
+          o_v = fmaxf(o_v, sqrtf(hx * hx + hy * hy + hz * hz));
+          o_u = fmaxf(o_u, sqrtf(ux * ux + uy * uy + uz * uz));
+          const int n = wrapi(pc, nz) * NXY + gy * nx + gx;
+          o_d = fmaxf(o_d, fabsf(dsv - snap[n]));
+          snap[n] = dsv;
+          o_m.add(dsv);
+          ++o_n;
+        }
+      }
       // target of population i = own node + per-axis deltas (periodic wrap folded in)
       const int pz = wrapi(pc, nz);
       const int dxp = (gx + 1 < nx) ? 1 : 1 - nx, dxm = (gx > 0) ? -1 : nx - 1;
@@ -216,13 +234,13 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       auto post = [&](const int i) {  // post-collision population i of this node
         const float wd = i == 0 ? wd0 : (i < 7 ? wd1 : wd2);
         const float wr = i == 0 ? wr0 : (i < 7 ? wr1 : wr2);
-        const float ev = float(L::ex(i)) * vx + float(L::ey(i)) * vy + float(L::ez(i)) * vz;
-        const float Av = ev * (3.f + 4.5f * ev) - vv15;
+        const float ev = edot<L>(i, vx, vy, vz);
+        const float Av = i == 0 ? -vv15 : ev * (3.f + 4.5f * ev) - vv15;
         if constexpr (TAU1) {
           return wd + wr * Av;
         } else {
-          const float eu = float(L::ex(i)) * ux + float(L::ey(i)) * uy + float(L::ez(i)) * uz;
-          const float Au = eu * (3.f + 4.5f * eu) - uu15;
+          const float eu = edot<L>(i, ux, uy, uz);
+          const float Au = i == 0 ? -uu15 : eu * (3.f + 4.5f * eu) - uu15;
           return (1.f - omega) * fv[i] + omega * wd + wr * (omega * Au + Av - Au);
         }
       };
@@ -276,6 +294,9 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
     }
     sc = ring(sc + 1, NS);
   }
+  if constexpr (OBS)
+    block_obs_reduce<CNT>(double(o_v), double(o_u), double(o_n) * p.rho_ref + o_m.value(), double(o_d),
+                          aux.partials + 4 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }
 
 }  // namespace lbmd

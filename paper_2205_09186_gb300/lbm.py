@@ -61,6 +61,7 @@ SIGNATURES = {
     "lbm_step": (C.c_int, [_h, C.c_longlong]),
     "lbm_step_timed": (C.c_int, [_h, C.c_longlong, _dp]),
     "lbm_observables": (C.c_int, [_h, C.POINTER(lbm_obs)]),
+    "lbm_step_observe": (C.c_int, [_h, C.c_longlong, C.POINTER(lbm_obs)]),
     "lbm_get_density": (C.c_int, [_h, _dp]),
     "lbm_get_f": (C.c_int, [_h, _dp]),
     "lbm_get_force": (C.c_int, [_h, _dp, _dp]),
@@ -258,8 +259,20 @@ class Sim:
             check(rc, "lbm_observables")
         return o.as_dict()
 
-    def lbm_get_density(self):
-        out = np.empty(self.shape)
+    def lbm_step_observe(self, n=1, raise_unstable=False):
+        o = lbm_obs()
+        rc = lib().lbm_step_observe(self.h, n, C.byref(o))
+        if rc not in (LBM_OK, LBM_EUNSTABLE) or (raise_unstable and rc == LBM_EUNSTABLE):
+            check(rc, "lbm_step_observe")
+        return o.as_dict()
+
+    def lbm_get_density(self, out=None):
+        """Density field as FP64 host array; `out` (e.g. a pinned buffer of
+        self.shape or its size, C-contiguous float64) receives it in place."""
+        if out is None:
+            out = np.empty(self.shape)
+        elif out.dtype != np.float64 or out.size != int(np.prod(self.shape)) or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of the lattice size")
         check(lib().lbm_get_density(self.h, _ptr(out)), "lbm_get_density")
         return out
 

@@ -1,0 +1,98 @@
+"""lbm_step_observe: n steps whose last one also reports the observables of the
+state it started from.  On the split D3Q19 FP32-deviation path the collision
+pass computes them in passing; the result must match lbm_observables taken
+before that step (FP32 rounding apart) and the oracle's observables of the
+same state, and the stepped state must match plain stepping.  Elsewhere the
+call observes, then steps, and must equal doing exactly that."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("max_v", "max_u", "mass", "rho_center", "rho_corner", "max_drho")
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2205_09186_gb300 as pkg
+    pkg.build()
+    from paper_2205_09186_gb300 import lbm
+    return lbm
+
+
+def make(L, shape, **kw):
+    nx, ny, nz = shape
+    lat = L.LBM_D2Q9 if nz == 1 else L.LBM_D3Q19
+    args = dict(lattice=lat, nx=nx, ny=ny, nz=nz, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
+                precision=L.LBM_FP32DEV)
+    args.update(kw)
+    s = L.Sim(L.make_params(**args))
+    s.lbm_init_droplet(min(nx, ny) / 4.0)
+    s.lbm_observables()  # snapshot at t = 0 for max |d rho / dt|
+    return s
+
+
+def close(a, b, rel, keys=KEYS):
+    for k in keys:
+        assert a[k] == pytest.approx(b[k], rel=rel, abs=1e-12 * max(1.0, abs(b[k]))), k
+
+
+# nx % 4 == 0 takes the 16-byte copy variant of the collision pass, 42 the 4-byte one
+@pytest.mark.parametrize("shape,scheme", [((48, 40, 44), "EFDS6"), ((42, 36, 40), "EFDS4"), ((40, 40, 40), "EFDS2")])
+def test_fused_observation_matches_observe_then_step(L, shape, scheme):
+    a, b = make(L, shape, scheme=scheme), make(L, shape, scheme=scheme)
+    for n in (12, 5):  # two cycles: the second max |d rho / dt| uses the fused kernel's snapshot
+        a.lbm_step(n - 1)
+        oa = a.lbm_observables()
+        a.lbm_step(1)
+        ob = b.lbm_step_observe(n)
+        assert ob["status"] == 0 and ob["step"] == oa["step"] == b.lbm_get_step() - 1
+        close(ob, oa, 2e-6)
+    ra, rb = a.lbm_get_density(), b.lbm_get_density()
+    assert np.max(np.abs(ra - rb)) < 1e-6 * np.max(ra)
+    assert np.max(np.abs(a.lbm_get_f() - b.lbm_get_f())) < 1e-6 * np.max(np.abs(a.lbm_get_f()))
+
+
+def test_fused_observation_matches_oracle(L):
+    shape = (40, 36, 44)
+    b = make(L, shape)
+    o = O.Sim(lattice=O.D3Q19, nx=40, ny=36, nz=44, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6")
+    o.init_droplet(9.0)
+    o.observables()
+    ob = b.lbm_step_observe(16)
+    o.step(15)
+    oo = o.observables()
+    assert ob["step"] == oo["step"] == 15
+    # FP32 deviation storage against the FP64 oracle (the parity tolerance of the
+    # densities; velocities relative to their own scale)
+    rl = O.maxwell_tr(0.8)[1]
+    for k in ("rho_center", "rho_corner"):
+        assert abs(ob[k] - oo[k]) < 1e-5 * rl, k
+    assert ob["mass"] == pytest.approx(oo["mass"], rel=1e-6)
+    for k in ("max_v", "max_u"):
+        assert ob[k] == pytest.approx(oo[k], rel=2e-3, abs=1e-7), k
+
+
+@pytest.mark.parametrize("shape,kw", [((48, 40, 1), dict(precision=0)), ((48, 40, 1), dict()),
+                                      ((24, 24, 24), dict(scheme="OCFDS4")), ((24, 24, 24), dict(scheme="E4")),
+                                      ((24, 24, 24), dict(precision=0, scheme="EFDS4"))])
+def test_other_paths_observe_then_step(L, shape, kw):
+    a, b = make(L, shape, **kw), make(L, shape, **kw)
+    a.lbm_step(6)
+    oa = a.lbm_observables()
+    a.lbm_step(1)
+    ob = b.lbm_step_observe(7)
+    assert ob == oa
+    assert np.array_equal(a.lbm_get_density(), b.lbm_get_density())
+
+
+def test_step_observe_rejects_zero_steps(L):
+    s = make(L, (16, 16, 1))
+    with pytest.raises(L.LBMError) as e:
+        s.lbm_step_observe(0)
+    assert e.value.code == L.LBM_EINVAL
