@@ -161,36 +161,59 @@ __global__ void __launch_bounds__(NT2) k_batch_persistent(const CaseDev* __restr
 }
 
 // FP32DEV: per step a mu phase over all cases' mu tiles and a collision phase
-// over their collision tiles, each followed by the bounded device barrier
-template <int S, bool TAU1>
-__device__ void split_coll_item(const CaseDev& cd, int tile, long long t, unsigned char* smem) {
+// over their collision tiles, each followed by the bounded device barrier.
+// Within a phase a CTA works through its items in a two-stage pipeline: the
+// copies of the next item (and the fetch of the item after it) are in flight
+// while the current item is computed from the other shared-memory buffer.
+__device__ void split_load(const CaseDev& cd, int tile, long long t, int phase, unsigned char* buf) {
   const int par = int(t & 1);
-  const int x0 = (tile % cd.ctiles_x) * T2X, y0 = (tile / cd.ctiles_x) * T2Y;
-  coll2d_tile<S, TAU1>(cd.kp, static_cast<const float*>(cd.f[par]), static_cast<float*>(cd.f[par ^ 1]),
-                       static_cast<const float*>(cd.rho[par]), cd.mu, static_cast<float*>(cd.rho[par ^ 1]), cd.bad, t,
-                       x0, y0, smem);
-}
-
-__device__ void split_item(const CaseDev& cd, int tile, long long t, int phase, unsigned char* smem) {
-  const int par = int(t & 1);
+  const float* rin = static_cast<const float*>(cd.rho[par]);
   if (phase == 0) {
     const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
-    const float* rin = static_cast<const float*>(cd.rho[par]);
     switch (cd.scheme) {
-      case S_EFDS2: mu2d_tile<S_EFDS2>(cd.kp, rin, cd.mu, x0, y0, smem); break;
-      case S_EFDS4: mu2d_tile<S_EFDS4>(cd.kp, rin, cd.mu, x0, y0, smem); break;
-      case S_EFDS6: mu2d_tile<S_EFDS6>(cd.kp, rin, cd.mu, x0, y0, smem); break;
-      case S_E4: mu2d_tile<S_E4>(cd.kp, rin, cd.mu, x0, y0, smem); break;
-      case S_E8: mu2d_tile<S_E8>(cd.kp, rin, cd.mu, x0, y0, smem); break;
+      case S_EFDS2: mu2d_load<S_EFDS2>(cd.kp, rin, x0, y0, buf); break;
+      case S_EFDS4: mu2d_load<S_EFDS4>(cd.kp, rin, x0, y0, buf); break;
+      case S_EFDS6: mu2d_load<S_EFDS6>(cd.kp, rin, x0, y0, buf); break;
+      case S_E4: mu2d_load<S_E4>(cd.kp, rin, x0, y0, buf); break;
+      case S_E8: mu2d_load<S_E8>(cd.kp, rin, x0, y0, buf); break;
       default: break;
     }
     return;
   }
+  const int x0 = (tile % cd.ctiles_x) * T2X, y0 = (tile / cd.ctiles_x) * T2Y;
+  const float* fin = static_cast<const float*>(cd.f[par]);
+  switch (cd.scheme) {
+    case S_EFDS2: coll2d_load<S_EFDS2>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_EFDS4: coll2d_load<S_EFDS4>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_EFDS6: coll2d_load<S_EFDS6>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_E4: coll2d_load<S_E4>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_E8: coll2d_load<S_E8>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    default: break;
+  }
+}
+
+__device__ void split_compute(const CaseDev& cd, int tile, long long t, int phase, unsigned char* buf) {
+  const int par = int(t & 1);
+  if (phase == 0) {
+    const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
+    switch (cd.scheme) {
+      case S_EFDS2: mu2d_compute<S_EFDS2>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_EFDS4: mu2d_compute<S_EFDS4>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_EFDS6: mu2d_compute<S_EFDS6>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_E4: mu2d_compute<S_E4>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_E8: mu2d_compute<S_E8>(cd.kp, cd.mu, x0, y0, buf); break;
+      default: break;
+    }
+    return;
+  }
+  const int x0 = (tile % cd.ctiles_x) * T2X, y0 = (tile / cd.ctiles_x) * T2Y;
+  float* fout = static_cast<float*>(cd.f[par ^ 1]);
+  float* rout = static_cast<float*>(cd.rho[par ^ 1]);
   const bool tau1 = cd.kp.omega == 1.0;
-#define LBM_SPLIT_CASE(SS)                                              \
-  case SS:                                                              \
-    if (tau1) split_coll_item<SS, true>(cd, tile, t, smem);            \
-    else split_coll_item<SS, false>(cd, tile, t, smem);                \
+#define LBM_SPLIT_CASE(SS)                                                              \
+  case SS:                                                                              \
+    if (tau1) coll2d_compute<SS, true>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf);      \
+    else coll2d_compute<SS, false>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf);          \
     break;
   switch (cd.scheme) {
     LBM_SPLIT_CASE(S_EFDS2)
@@ -203,30 +226,51 @@ __device__ void split_item(const CaseDev& cd, int tile, long long t, int phase, 
 #undef LBM_SPLIT_CASE
 }
 
+// Items of a phase are dealt round-robin (CTA b takes items b, b + grid, ...):
+// they are tiles of nearly equal cost, so the static deal is balanced to one
+// item, and knowing the next items in advance lets the copies of the next
+// NBUF - 1 items be in flight while the current one is computed.
+// Dynamic shared memory: NBUF buffers of buf_bytes (a multiple of 16).
+constexpr int NBUF = 3;
+
 __global__ void __launch_bounds__(NT2S) k_batch_split(const CaseDev* __restrict__ cases,
                                                       const Item* __restrict__ mitems, int nmu,
                                                       const Item* __restrict__ citems, int ncoll, int nsteps,
-                                                      BatchCtl* ctl, unsigned long long timeout_ns) {
+                                                      BatchCtl* ctl, unsigned long long timeout_ns, int buf_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_item;
   const long long t0 = *((volatile long long*)&ctl->t);
+  const int G = int(gridDim.x);
   for (int s = 0; s < nsteps; ++s) {
     const long long t = t0 + s;
     for (int phase = 0; phase < 2; ++phase) {
       const Item* items = phase == 0 ? mitems : citems;
       const int nitems = phase == 0 ? nmu : ncoll;
-      unsigned int* ctr = &ctl->work[phase * 2 + (s & 1)];
-      for (;;) {
-        if (threadIdx.x == 0) s_item = int(atomicAdd(ctr, 1u));
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
-        if (it >= nitems) break;
-        const Item itm = items[it];
-        split_item(cases[itm.c], itm.tile, t, phase, smem);
+      // prologue: copies of the first NBUF - 1 items (one group each, empty past the end)
+#pragma unroll
+      for (int j = 0; j < NBUF - 1; ++j) {
+        const int it = int(blockIdx.x) + j * G;
+        if (it < nitems) {
+          const Item itm = items[it];
+          split_load(cases[itm.c], itm.tile, t, phase, smem + j * buf_bytes);
+        }
+        cpa_commit();
       }
-      // counters of the other step parity were last used a step ago: reset them
-      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[phase * 2 + ((s + 1) & 1)] = 0u;
+      int b = 0;
+      for (int it = int(blockIdx.x); it < nitems; it += G) {
+        __syncthreads();  // the buffer refilled below was last computed from one item ago
+        const int ahead = it + (NBUF - 1) * G;
+        if (ahead < nitems) {
+          const Item itm = items[ahead];
+          split_load(cases[itm.c], itm.tile, t, phase, smem + ring(b + NBUF - 1, NBUF) * buf_bytes);
+        }
+        cpa_commit();
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(NBUF - 1) : "memory");  // this item's copies landed
+        __syncthreads();
+        const Item itm = items[it];
+        split_compute(cases[itm.c], itm.tile, t, phase, smem + b * buf_bytes);
+        b = ring(b + 1, NBUF);
+      }
+      cpa_wait_all();
       if (!grid_barrier(ctl, timeout_ns)) return;
     }
   }
@@ -330,6 +374,7 @@ struct lbm_batch {
   Item* d_citems = nullptr;
   int nmu = 0, ncoll = 0, grid_split = 0;
   size_t smem_split = 0;
+  int buf_split = 0;  // bytes of one item buffer of the split kernel
   std::vector<std::pair<void*, size_t>> blocks;
 };
 
@@ -485,10 +530,11 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     m = std::max(m, Split2DShape<S_EFDS6>::bytes);
     m = std::max(m, Split2DShape<S_E4>::bytes);
     m = std::max(m, Split2DShape<S_E8>::bytes);
-    b->smem_split = m;
+    b->buf_split = int((m + 15) / 16 * 16);
+    b->smem_split = NBUF * size_t(b->buf_split);  // items in flight
     int ps = 0;
-    cudaFuncSetAttribute(k_batch_split, cudaFuncAttributeMaxDynamicSharedMemorySize, int(m));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_batch_split, NT2S, m);
+    cudaFuncSetAttribute(k_batch_split, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem_split));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_batch_split, NT2S, b->smem_split);
     if (ps < 1) { lbm_batch_destroy(b); return LBM_ECUDA; }
     b->grid_split = std::max(1, std::min(ps * sms, std::max(b->nmu, b->ncoll)));
   }
@@ -574,7 +620,7 @@ static cudaError_t launch_persistent(lbm_batch* b, int nsteps) {
     cs.attrs = at;
     cs.numAttrs = 1;
     return cudaLaunchKernelEx(&cs, k_batch_split, (const CaseDev*)b->d_cases, (const Item*)b->d_mitems, b->nmu,
-                              (const Item*)b->d_citems, b->ncoll, nsteps, b->ctl, timeout_ns);
+                              (const Item*)b->d_citems, b->ncoll, nsteps, b->ctl, timeout_ns, b->buf_split);
   }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(unsigned(b->grid));

@@ -170,9 +170,15 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   issue(pc_first + R, slot);
   slot = ring(slot + 1, NS);
   const int fme = cy * FW + of + cx;  // this node in a staged population plane
-  float o_v = 0.f, o_u = 0.f, o_d = 0.f;  // OBS: running maxima of this thread's nodes
-  FSum o_m;                                // OBS: sum of density deviations
-  int o_n = 0;                             // OBS: nodes counted
+  float o_v2 = 0.f, o_u2 = 0.f, o_d = 0.f;  // OBS: running maxima (|v|^2, |u|^2, |rho - snap|)
+  float o_m = 0.f;                           // OBS: sum of this thread's density deviations
+  int o_n = 0;                               // OBS: nodes counted
+  // OBS: the snapshot value of this thread's node in the next collided plane,
+  // loaded one plane ahead so that its latency hides behind a whole plane
+  const int snap_xy = gy * nx + gx;
+  float snap_next = 0.f;
+  if constexpr (OBS)
+    if (interior && z0 < z1) snap_next = snap[z0 * NXY + snap_xy];
   for (int pc = pc_first; pc <= pc_last; ++pc) {
     cpa_wait_all();
     __syncthreads();
@@ -212,12 +218,12 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       if constexpr (OBS) {
         if (push) {
           const float hx = ux + 0.5f * Fx * irc, hy = uy + 0.5f * Fy * irc, hz = uz + 0.5f * Fz * irc;
-          o_v = fmaxf(o_v, sqrtf(hx * hx + hy * hy + hz * hz));
-          o_u = fmaxf(o_u, sqrtf(ux * ux + uy * uy + uz * uz));
-          const int n = wrapi(pc, nz) * NXY + gy * nx + gx;
-          o_d = fmaxf(o_d, fabsf(dsv - snap[n]));
-          snap[n] = dsv;
-          o_m.add(dsv);
+          o_v2 = fmaxf(o_v2, hx * hx + hy * hy + hz * hz);
+          o_u2 = fmaxf(o_u2, ux * ux + uy * uy + uz * uz);
+          o_d = fmaxf(o_d, fabsf(dsv - snap_next));
+          snap[pc * NXY + snap_xy] = dsv;  // push planes lie in [z0, z1): no wrap
+          if (pc + 1 < z1) snap_next = snap[(pc + 1) * NXY + snap_xy];
+          o_m += dsv;  // at most one z-chunk of deviations per thread: FP32 suffices
           ++o_n;
         }
       }
@@ -252,20 +258,36 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
         for (int i = 0; i < Q; ++i)
           if (L::ey(i) != 0 && (L::ey(i) > 0) == up) fb[i * FPL + fme] = post(i);
       } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          const float fs = post(i);
+        auto keep = [&](const int i, const float fs) {
           // populations that stay in this x-y column are gathered from registers
           if (L::ex(i) == 0 && L::ey(i) == 0) {
             if (L::ez(i) == 0) own0 = fs; else if (L::ez(i) > 0) ownp = fs; else ownm = fs;
           } else {
             fb[i * FPL + fme] = fs;
           }
-          if (push) {
-            const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) +
-                          (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0)) +
-                          (L::ez(i) > 0 ? dzp : (L::ez(i) < 0 ? dzm : 0));
-            fo[i * N + d] = fs;
+        };
+        // Away from the periodic seams the target offset of population i is
+        // i N + e_x + e_y nx + e_z nx ny for every thread: a warp none of whose
+        // pushing nodes lies on a seam stores with these common offsets.
+        const bool seam = push && (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1 || pz == 0 || pz == nz - 1);
+        if (!__any_sync(__activemask(), seam)) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const float fs = post(i);
+            keep(i, fs);
+            if (push) fo[i * N + L::ex(i) + L::ey(i) * nx + L::ez(i) * NXY] = fs;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const float fs = post(i);
+            keep(i, fs);
+            if (push) {
+              const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) +
+                            (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0)) +
+                            (L::ez(i) > 0 ? dzp : (L::ez(i) < 0 ? dzm : 0));
+              fo[i * N + d] = fs;
+            }
           }
         }
       }
@@ -295,7 +317,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
     sc = ring(sc + 1, NS);
   }
   if constexpr (OBS)
-    block_obs_reduce<CNT>(double(o_v), double(o_u), double(o_n) * p.rho_ref + o_m.value(), double(o_d),
+    block_obs_reduce<CNT>(sqrt(double(o_v2)), sqrt(double(o_u2)), double(o_n) * p.rho_ref + double(o_m), double(o_d),
                           aux.partials + 4 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }
 
