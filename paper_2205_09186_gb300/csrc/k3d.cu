@@ -122,6 +122,26 @@ cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
 
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
 
+// the mu pass: the vector kernel when rows are whole 16-byte chunks
+template <int S>
+cudaError_t launch_mu(const Launch& c) {
+  if (c.kp.nx % 4 == 0 && aligned16(c.rin) && aligned16(c.mu)) {
+    using Sh = MuV4Shape<S>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_mu3d_v4<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    dim3 g((c.kp.nx + MVX - 1) / MVX, (c.kp.ny + MVY - 1) / MVY, (c.kp.nz + MVZ - 1) / MVZ);
+    k_mu3d_v4<S><<<g, MVT, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  } else {
+    dim3 g((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
+    k_mu3d<S><<<g, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  }
+  return cudaGetLastError();
+}
+
 // mu pass + collision pass (line schemes, FP32DEV, FP32 mu); with obs the
 // collision pass also reduces the observables of the state it advances
 template <int S, bool TAU1>
@@ -137,8 +157,8 @@ cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   } else if (obs) {
     return cudaErrorInvalidValue;
   }
-  dim3 gm((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
-  k_mu3d<S><<<gm, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  cudaError_t em = launch_mu<S>(c);
+  if (em != cudaSuccess) return em;
   if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
   // 16-byte copies need rows of whole chunks and aligned bases
   const bool vec = c.kp.nx % 4 == 0 && aligned16(c.fin) && aligned16(c.rin) && aligned16(c.mu);
@@ -150,8 +170,8 @@ cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
 // observation pass of the split path: mu field, then the node-parallel reduction
 template <int S>
 cudaError_t launch_obs_split(const Launch& c, int* nblocks) {
-  dim3 gm((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
-  k_mu3d<S><<<gm, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  cudaError_t em = launch_mu<S>(c);
+  if (em != cudaSuccess) return em;
   // at most 8192 CTAs: the handle's partials buffer holds at least that many
   const int nb = int(std::min<long long>(std::min<long long>((long long)c.kp.ny * c.kp.nz, 8LL * num_sms()), 8192LL));
   if (nblocks) *nblocks = nb;

@@ -264,6 +264,11 @@ __device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
+// 16 bytes, L2 only; both addresses 16-byte aligned
+__device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 // all but the most recent group complete

@@ -53,11 +53,6 @@ struct CollShape {
   static constexpr int KF = (FCH + CNT - 1) / CNT;
 };
 
-__device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-
 // VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations).
 // OBS: also reduce the observables of the state being advanced (max |v| with
 // v = u + F / (2 rho), max |u|, mass, max |rho - snap|) into aux.partials, one

@@ -90,6 +90,25 @@ def test_fp32dev_against_oracle(L, lattice, shape, scheme, mu_fp64):
     assert err < TOL32, err
 
 
+# nx % 4 == 0 takes the 16-byte (vector) mu and collision kernels, other nx the
+# 4-byte ones; 68 = 64 + 4 leaves a 4-wide vector block, 8^3 wraps every halo
+# several times around the lattice
+@pytest.mark.parametrize("shape", [(68, 40, 36), (42, 26, 20), (8, 8, 8), (12, 9, 10)])
+@pytest.mark.parametrize("scheme", ["EFDS2", "EFDS6"])
+def test_fp32dev_kernel_variants_against_oracle(L, shape, scheme):
+    nx, ny, nz = shape
+    kw = dict(nx=nx, ny=ny, nz=nz, Tr=0.9, k=0.3, kappa=0.1, scheme=scheme)
+    g, o = pair(L, 3, precision=L.LBM_FP32DEV, **kw)
+    rng = np.random.default_rng(nx * 1000 + ny * 10 + nz)
+    rho = 0.15 + 0.01 * rng.standard_normal((nz, ny, nx))
+    g.lbm_init_density(rho)
+    o.set_f(np.stack([w * rho for w in O.lattice(O.D3Q19)[1]]))
+    g.lbm_step(30)
+    assert o.step(30) == 0
+    err = np.max(np.abs(g.lbm_get_density() - o.density())) / 0.15
+    assert err < TOL32, err
+
+
 def test_observables_parity(L):
     kw = dict(nx=48, ny=40, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS4")
     g, o = pair(L, 2, **kw)
