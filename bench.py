@@ -307,7 +307,8 @@ def run_gpu(args):
         extra["batch2d"] = run_batch(L)
     if not args.no_warmstart:
         from paper_2205_09186_gb300 import warmstart as W
-        res, _ = W.experiment(n_train=32, n_test=12, n=80, tol=1e-7, iters=4000)
+        # the plain arm (FP64 storage, tanh start) on the first 4 test cases
+        res, _ = W.experiment(n_train=32, n_test=12, n=80, tol=1e-7, iters=4000, plain=4)
         res["device_s_ratio_cold_over_warm"] = (res["cold_device_s"] / res["warm_device_s"]
                                                 if res["warm_device_s"] else None)
         extra["warmstart"] = res

@@ -30,7 +30,8 @@ _ip = C.POINTER(C.c_int)
 class Params(C.Structure):
     _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("Tr", C.c_double),
-                ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double), ("scheme", C.c_int)]
+                ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double), ("scheme", C.c_int),
+                ("collision", C.c_int), ("mrt_s", C.c_double * 9)]
 
 
 class Obs(C.Structure):
@@ -64,6 +65,11 @@ def lib():
         L.or_lattice_q.argtypes = [C.c_int]
         L.or_lattice_e.argtypes = [C.c_int, _ip, _dp]
         L.or_feq.argtypes = [C.c_int, C.c_double, _dp, _dp]
+        L.or_mrt_matrix.argtypes = [_dp]
+        L.or_mrt_matrix.restype = None
+        L.or_mrt_inverse.argtypes = [_dp]
+        L.or_mrt_collide.argtypes = [_dp, _dp, _dp, _dp, _dp]
+        L.or_mrt_collide.restype = None
         L.or_edm.argtypes = [C.c_int, C.c_double, _dp, _dp, _dp]
         L.or_create.restype = C.c_void_p
         L.or_create.argtypes = [C.POINTER(Params)]
@@ -180,6 +186,33 @@ def lattice(lat):
     return e, w
 
 
+BGK, MRT = 0, 1
+
+
+def mrt_rates(tau):
+    """The relaxation rates the paper chooses (Eq. 5 and the text after it)."""
+    return [1.0, 1.64, 1.54, 1.0, 1.7, 1.0, 1.7, 1.0 / tau, 1.0 / tau]
+
+
+def mrt_matrix():
+    M = np.empty(81)
+    lib().or_mrt_matrix(_ptr(M))
+    return M.reshape(9, 9)
+
+
+def mrt_inverse():
+    M = np.empty(81)
+    if lib().or_mrt_inverse(_ptr(M)) != OK:
+        raise RuntimeError("singular")
+    return M.reshape(9, 9)
+
+
+def mrt_collide(f, feq_, Fi, s):
+    out = np.empty(9)
+    lib().or_mrt_collide(_ptr(_f64(f)), _ptr(_f64(feq_)), _ptr(_f64(Fi)), _ptr(_f64(s)), _ptr(out))
+    return out
+
+
 def feq(lat, rho, u):
     u = _f64(list(u) + [0.0] * (3 - len(u)))
     q = lib().or_lattice_q(lat)
@@ -202,8 +235,13 @@ class Sim:
     """One periodic droplet/slab simulation, plain FP64 (the paper's step)."""
 
     def __init__(self, lattice=D2Q9, nx=64, ny=64, nz=1, a=1.0, b=4.0, R=1.0, Tr=0.7, k=0.4,
-                 kappa=1.0, tau=1.0, scheme="EFDS2"):
-        self.p = Params(lattice, nx, ny, nz, a, b, R, Tr, k, kappa, tau, _scheme(scheme))
+                 kappa=1.0, tau=1.0, scheme="EFDS2", collision="BGK", mrt_s=None):
+        """collision "MRT" (D2Q9): rates s_1..s_9 of Eq. 5, by default the
+        paper's (1, 1.64, 1.54, 1, 1.7, 1, 1.7, 1/tau, 1/tau)."""
+        if mrt_s is None:
+            mrt_s = mrt_rates(tau)
+        self.p = Params(lattice, nx, ny, nz, a, b, R, Tr, k, kappa, tau, _scheme(scheme),
+                        {"BGK": BGK, "MRT": MRT}[collision], (C.c_double * 9)(*mrt_s))
         self.h = lib().or_create(C.byref(self.p))
         if not self.h:
             raise ValueError("invalid oracle parameters")

@@ -104,6 +104,8 @@ or_sim* or_create(const or_params* p) {
   if (p->scheme < 0 || p->scheme >= OR_NSCHEMES) return NULL;
   if (p->scheme == OR_E8 && p->lattice != OR_D2Q9) return NULL;
   if (!(p->tau > 0.5) || !(p->k > 0) || !(p->kappa >= 0) || !(p->Tr > 0)) return NULL;
+  if (p->collision != OR_BGK && p->collision != OR_MRT) return NULL;
+  if (p->collision == OR_MRT && p->lattice != OR_D2Q9) return NULL;
   double rc, Tc;
   if (or_cs_critical(p->a, p->b, p->R, &rc, &Tc) != OR_OK) return NULL;
   or_sim* s = (or_sim*)calloc(1, sizeof(or_sim));
@@ -326,11 +328,16 @@ int or_step(or_sim* s, long long nsteps) {
           double feq[19], Fi[19];
           or_feq(s->p.lattice, s->rho[c], u, feq);
           or_edm(s->p.lattice, s->rho[c], u, F, Fi);
+          double fc[19], post[19];
+          for (int i = 0; i < s->q; ++i) fc[i] = s->f[i * n + c];
+          if (s->p.collision == OR_MRT) {
+            or_mrt_collide(fc, feq, Fi, s->p.mrt_s, post);
+          } else {
+            for (int i = 0; i < s->q; ++i) post[i] = fc[i] - (fc[i] - feq[i]) / s->p.tau + Fi[i];
+          }
           for (int i = 0; i < s->q; ++i) {
-            double fi = s->f[i * n + c];
-            double post = fi - (fi - feq[i]) / s->p.tau + Fi[i];
             int xd = (x + e[i][0] + nx) % nx, yd = (y + e[i][1] + ny) % ny, zd = (z + e[i][2] + nz) % nz;
-            s->fn[i * n + node_index(s, xd, yd, zd)] = post;
+            s->fn[i * n + node_index(s, xd, yd, zd)] = post[i];
           }
         }
     double* tmp = s->f; s->f = s->fn; s->fn = tmp;
@@ -378,4 +385,65 @@ int or_observables(or_sim* s, or_obs* o) {
   memcpy(s->rho_snap, s->rho, sizeof(double) * n);
   s->t_snap = s->t;
   return OR_OK;
+}
+
+/* ---------------------------------------------------------------- MRT (D2Q9) */
+
+/* The matrix of Eq. 3 as printed; columns follow the velocity order of Eq. 2. */
+static const double MRT_M[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},         {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},     {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},      {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},      {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+void or_mrt_matrix(double M[81]) {
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) M[r * 9 + c] = MRT_M[r][c];
+}
+
+/* Gauss-Jordan elimination with partial pivoting on [M | I]. */
+int or_mrt_inverse(double Minv[81]) {
+  double a[9][18];
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 18; ++c) a[r][c] = c < 9 ? MRT_M[r][c] : (c - 9 == r ? 1.0 : 0.0);
+  for (int col = 0; col < 9; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 9; ++r)
+      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+    if (fabs(a[piv][col]) < 1e-12) return OR_EINVAL;
+    if (piv != col)
+      for (int c = 0; c < 18; ++c) {
+        double t = a[col][c]; a[col][c] = a[piv][c]; a[piv][c] = t;
+      }
+    double d = a[col][col];
+    for (int c = 0; c < 18; ++c) a[col][c] /= d;
+    for (int r = 0; r < 9; ++r) {
+      if (r == col) continue;
+      double m = a[r][col];
+      for (int c = 0; c < 18; ++c) a[r][c] -= m * a[col][c];
+    }
+  }
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) Minv[r * 9 + c] = a[r][c + 9];
+  return OR_OK;
+}
+
+void or_mrt_collide(const double* f, const double* feq, const double* Fi, const double s[9], double* post) {
+  double Minv[81];
+  or_mrt_inverse(Minv);
+  double dm[9];
+  for (int k = 0; k < 9; ++k) {
+    double m = 0.0, meq = 0.0;
+    for (int i = 0; i < 9; ++i) {
+      m += MRT_M[k][i] * f[i];
+      meq += MRT_M[k][i] * feq[i];
+    }
+    dm[k] = s[k] * (m - meq);
+  }
+  for (int i = 0; i < 9; ++i) {
+    double corr = 0.0;
+    for (int k = 0; k < 9; ++k) corr += Minv[i * 9 + k] * dm[k];
+    post[i] = f[i] - corr + Fi[i];
+  }
 }

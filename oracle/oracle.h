@@ -44,12 +44,18 @@ extern "C" {
 #define OR_ENOMEM -2
 #define OR_EUNSTABLE -4
 
+/* collision operators */
+#define OR_BGK 0 /* every MRT rate 1/tau: single relaxation (Sec. 2.1, after Eq. 5) */
+#define OR_MRT 1 /* Eq. 1 with M of Eq. 3 and S of Eq. 5 (D2Q9 only) */
+
 typedef struct {
   int lattice;          /* OR_D2Q9 or OR_D3Q19 */
   int nx, ny, nz;       /* nz = 1 for D2Q9; x fastest */
   double a, b, R, Tr;   /* Carnahan-Starling constants and reduced temperature */
   double k, kappa, tau; /* proportional coefficient (Eq. 16), kappa-hat, BGK tau */
   int scheme;           /* OR_EFDS2 .. OR_E8 */
+  int collision;        /* OR_BGK or OR_MRT */
+  double mrt_s[9];      /* OR_MRT: s_1 .. s_9 of Eq. 5 */
 } or_params;
 
 typedef struct {
@@ -81,6 +87,14 @@ int or_laplacian(int scheme, int dim, int nx, int ny, int nz, const double* phi,
 
 /* ---- the simulation ---- */
 or_sim* or_create(const or_params* p);
+
+/* MRT (Eq. 1, 3-5), D2Q9: the transformation matrix M of Eq. 3 (row-major,
+ * rows rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy; columns in the
+ * velocity order of Eq. 2) and its inverse by Gauss-Jordan elimination. */
+void or_mrt_matrix(double M[81]);
+int or_mrt_inverse(double Minv[81]);
+/* post-collision populations f* = f - M^-1 S (M f - M f_eq) + F_i (Eq. 1, 4) */
+void or_mrt_collide(const double* f, const double* feq, const double* Fi, const double s[9], double* post);
 void or_destroy(or_sim* s);
 int or_init_droplet(or_sim* s, const double center[3], double radius, double width, double rho_l, double rho_g);
 int or_init_slab(or_sim* s, int axis, double thickness, double width, double rho_l, double rho_g);

@@ -226,10 +226,12 @@ __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phas
 #undef LBM_SPLIT_CASE
 }
 
-// Items of a phase are dealt round-robin (CTA b takes items b, b + grid, ...):
-// they are tiles of nearly equal cost, so the static deal is balanced to one
-// item, and knowing the next items in advance lets the copies of the next
-// NBUF - 1 items be in flight while the current one is computed.
+// Items of a phase are dealt in contiguous runs (CTA b takes items
+// [n b / grid, n (b + 1) / grid)): they are tiles of nearly equal cost, so the
+// static deal is balanced to one item; consecutive items mostly belong to one
+// case, so its descriptor stays in L1 and neighbouring tiles share halos in L2;
+// and knowing the next items in advance lets the copies of the next NBUF - 1
+// items be in flight while the current one is computed.
 // Dynamic shared memory: NBUF buffers of buf_bytes (a multiple of 16).
 constexpr int NBUF = 3;
 
@@ -245,21 +247,22 @@ __global__ void __launch_bounds__(NT2S) k_batch_split(const CaseDev* __restrict_
     for (int phase = 0; phase < 2; ++phase) {
       const Item* items = phase == 0 ? mitems : citems;
       const int nitems = phase == 0 ? nmu : ncoll;
+      const int i0 = int((long long)nitems * blockIdx.x / G), i1 = int((long long)nitems * (blockIdx.x + 1) / G);
       // prologue: copies of the first NBUF - 1 items (one group each, empty past the end)
 #pragma unroll
       for (int j = 0; j < NBUF - 1; ++j) {
-        const int it = int(blockIdx.x) + j * G;
-        if (it < nitems) {
+        const int it = i0 + j;
+        if (it < i1) {
           const Item itm = items[it];
           split_load(cases[itm.c], itm.tile, t, phase, smem + j * buf_bytes);
         }
         cpa_commit();
       }
       int b = 0;
-      for (int it = int(blockIdx.x); it < nitems; it += G) {
+      for (int it = i0; it < i1; ++it) {
         __syncthreads();  // the buffer refilled below was last computed from one item ago
-        const int ahead = it + (NBUF - 1) * G;
-        if (ahead < nitems) {
+        const int ahead = it + NBUF - 1;
+        if (ahead < i1) {
           const Item itm = items[ahead];
           split_load(cases[itm.c], itm.tile, t, phase, smem + ring(b + NBUF - 1, NBUF) * buf_bytes);
         }

@@ -42,11 +42,17 @@ __device__ __forceinline__ void mu2d_load(const KParams& p, const float* __restr
                                           unsigned char* smem) {
   using Sh = Split2DShape<S>;
   constexpr int R = Sh::R, MW = Sh::MW, MH = Sh::MH;
+  static_assert(MW <= 64 && MW > 32, "two columns per lane");
   float* s = reinterpret_cast<float*>(smem);
   const int nx = p.nx, ny = p.ny;
-  for (int idx = threadIdx.x; idx < MW * MH; idx += NT2S) {
-    const int ry = idx / MW, rx = idx - ry * MW;
-    cpa4(s + idx, rin + wrapn(y0 - R + ry, ny) * nx + wrapn(x0 - R + rx, nx));
+  // warp w copies rows w, w + 16, ...; lane l columns l and 32 + l
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool two = lane + 32 < MW;
+  const int xa = wrapn(x0 - R + lane, nx), xb = two ? wrapn(x0 - R + 32 + lane, nx) : 0;
+  for (int ry = warp; ry < MH; ry += NT2S / 32) {
+    const float* src = rin + wrapn(y0 - R + ry, ny) * nx;
+    cpa4(s + ry * MW + lane, src + xa);
+    if (two) cpa4(s + ry * MW + 32 + lane, src + xb);
   }
 }
 
@@ -86,12 +92,23 @@ __device__ __forceinline__ void coll2d_load(const KParams& p, const float* __res
 #pragma unroll
     for (int i = 0; i < Q; ++i) cpa4(s_f + i * NT2S + tid, fs + i * N);
   }
-  for (int idx = tid; idx < GW * GH; idx += NT2S) {
-    const int ry = idx / GW, rx = idx - ry * GW;
-    if (rx < VW + 2 + 2 * R && ry < VH + 2 + 2 * R) {
-      const int g = wrapi(y0 - 1 - R + ry, ny) * nx + wrapi(x0 - 1 - R + rx, nx);
-      cpa4(s_ds + idx, rin + g);
-      cpa4(s_mu + idx, muf + g);
+  // fields: warp w copies rows w, w + 16, ...; lane l columns l and 32 + l
+  // (the region of a ragged tile only as far as its collided nodes reach)
+  static_assert(GW <= 64 && GW > 32, "two columns per lane");
+  const int lane = tid & 31, warp = tid >> 5;
+  const int xa = wrapi(x0 - 1 - R + lane, nx);
+  const bool two = lane + 32 < GW && lane + 32 < VW + 2 + 2 * R;
+  const int xb = two ? wrapi(x0 - 1 - R + 32 + lane, nx) : 0;
+  const bool one = lane < VW + 2 + 2 * R;
+  for (int ry = warp; ry < min(GH, VH + 2 + 2 * R); ry += NT2S / 32) {
+    const int g = wrapi(y0 - 1 - R + ry, ny) * nx;
+    if (one) {
+      cpa4(s_ds + ry * GW + lane, rin + g + xa);
+      cpa4(s_mu + ry * GW + lane, muf + g + xa);
+    }
+    if (two) {
+      cpa4(s_ds + ry * GW + 32 + lane, rin + g + xb);
+      cpa4(s_mu + ry * GW + 32 + lane, muf + g + xb);
     }
   }
 }

@@ -178,14 +178,17 @@ def predict(net, Tr, k, R, scheme, params, n=None):
     return rs, vs + rem
 
 
-def compare(net, cases, n=80, tol=1e-7, max_steps=20000, check_every=200):
-    """Warm (network profile) vs cold (Eq. 26 tanh) start on each case."""
+def compare(net, cases, n=80, tol=1e-7, max_steps=20000, check_every=200, plain=0):
+    """Warm (network profile) vs cold (Eq. 26 tanh) start on each case, both
+    with FP32 deviation storage; for the first `plain` cases also the plain
+    run: FP64 storage from the tanh start."""
     rows = []
-    for c in cases:
+    for ic, c in enumerate(cases):
         out = {}
-        for arm in ("cold", "warm"):
-            sim, p = make_sim(n, c["Tr"], c["k"], c.get("scheme", "EFDS6"))
-            if arm == "cold":
+        for arm in ("cold", "warm", "plain") if ic < plain else ("cold", "warm"):
+            prec = L.LBM_FP64 if arm == "plain" else L.LBM_FP32DEV
+            sim, p = make_sim(n, c["Tr"], c["k"], c.get("scheme", "EFDS6"), precision=prec)
+            if arm in ("cold", "plain"):
                 sim.lbm_init_droplet(c["R"])
             else:
                 prof = predict(net, c["Tr"], c["k"], c["R"], c.get("scheme", "EFDS6"), p, n=n)
@@ -213,7 +216,7 @@ def sample_cases(n, seed, Tr=(0.6, 0.85), k=(0.2, 0.35), R=(14.0, 22.0), scheme=
                  R=float(rng.uniform(*R)), scheme=scheme) for _ in range(n)]
 
 
-def experiment(n_train=48, n_test=16, n=80, tol=1e-7, iters=4000, seed=2205):
+def experiment(n_train=48, n_test=16, n=80, tol=1e-7, iters=4000, seed=2205, plain=0):
     """Generate, train, compare; the totals count the test cases where both arms
     converged and the cold-start droplet survived (an evaporating droplet has
     no profile to predict; those cases are counted separately)."""
@@ -222,7 +225,7 @@ def experiment(n_train=48, n_test=16, n=80, tol=1e-7, iters=4000, seed=2205):
     test_cases = sample_cases(n_test, seed + 1)
     X, Y, info = generate(train_cases, n=n, tol=tol)
     net, loss = train(X, Y, iters=iters)
-    rows = compare(net, test_cases, n=n, tol=tol)
+    rows = compare(net, test_cases, n=n, tol=tol, plain=plain)
     both = [r for r in rows if r["warm"]["converged"] and r["cold"]["converged"]]
     conv = [r for r in both if r["survived"]]
     res = {"lattice": "D3Q19 %d^3, EFDS6, FP32DEV" % n, "tol_max_drho": tol, "train_cases": len(X),
@@ -238,4 +241,19 @@ def experiment(n_train=48, n_test=16, n=80, tol=1e-7, iters=4000, seed=2205):
            "warm_failed": sum(1 for r in rows if not r["warm"]["converged"]),
            "cold_failed": sum(1 for r in rows if not r["cold"]["converged"]),
            "train_generation_device_s": sum(i.get("device_s", 0.0) for i in info), "wall_s": time.time() - t0}
+    if plain:
+        # the plain arm: FP64 storage, tanh start, one case at a time
+        both_p = [r for r in conv if "plain" in r and r["plain"]["converged"]]
+        res.update(plain_counted=len(both_p),
+                   plain_failed=sum(1 for r in rows if "plain" in r and not r["plain"]["converged"]),
+                   plain_steps=sum(r["plain"]["steps"] for r in both_p),
+                   plain_device_s=sum(r["plain"]["device_s"] for r in both_p),
+                   warm_device_s_same_cases=sum(r["warm"]["device_s"] for r in both_p),
+                   max_density_err_warm_vs_plain=max(
+                       [max(abs(r["warm"]["rho_center"] - r["plain"]["rho_center"]),
+                            abs(r["warm"]["rho_corner"] - r["plain"]["rho_corner"]))
+                        / L.lbm_maxwell(L.make_params(Tr=r["case"]["Tr"]))[1] for r in both_p], default=None))
+        res["device_s_ratio_plain_over_warm"] = (res["plain_device_s"] / res["warm_device_s_same_cases"]
+                                                 if res["warm_device_s_same_cases"] else None)
+    res["wall_s"] = time.time() - t0
     return res, rows
