@@ -204,6 +204,29 @@ def run_batch(L, steps=50, warmup=10):
             "stable_cases": stable, "work_items": nitems, "resident_ctas": grid, "status": rc}
 
 
+def run_2d(L, steps=200, warmup=20):
+    """D2Q9 512^2 droplet (r0 = 100, T_r = 0.8, k = 0.25, EFDS6, FP32 deviation
+    storage): BGK and the MRT operator of Eq. 1, 3-5; MLUPS and the roofline of
+    the collision pass (84 B per lattice update)."""
+    import torch
+    out = {"workload": "D2Q9 512^2 droplet r0=100, T_r 0.8, k 0.25, EFDS6, FP32DEV, tau 1"}
+    for col in ("BGK", "MRT"):
+        s = L.Sim(L.make_params(lattice=L.LBM_D2Q9, nx=512, ny=512, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
+                                precision=L.LBM_FP32DEV, collision=col))
+        s.lbm_init_droplet(100.0)
+        s.lbm_step(warmup)
+        torch.cuda.synchronize()
+        ms = s.lbm_step_timed(steps)
+        n = 512 * 512
+        coll_ms = ms[1] / steps
+        out[col.lower()] = {"mlups": n * steps / (ms[2] * 1e-3) / 1e6, "ms_per_step": ms[2] / steps,
+                            "coll_ms": coll_ms, "mu_ms": ms[0] / steps,
+                            "coll_frac": 84 * n / (coll_ms * 1e-3) / 1e9 / measured_peak()[0],
+                            "status": s.lbm_observables()["status"]}
+        s.close()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -305,6 +328,7 @@ def run_gpu(args):
     extra = {}
     if not args.no_batch:
         extra["batch2d"] = run_batch(L)
+        extra["d2q9_512"] = run_2d(L)
     if not args.no_warmstart:
         from paper_2205_09186_gb300 import warmstart as W
         # the plain arm (FP64 storage, tanh start) on the first 4 test cases

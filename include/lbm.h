@@ -62,6 +62,10 @@ extern "C" {
 #define LBM_E4 7     /* Eq. 25, fourth-order isotropic */
 #define LBM_E8 8     /* Eq. 25, eighth-order isotropic (D2Q9 only) */
 
+/* collision operator */
+#define LBM_BGK 0 /* single relaxation: the MRT operator with every rate 1/tau (Sec. 2.1, after Eq. 5) */
+#define LBM_MRT 1 /* Eq. 1 with M of Eq. 3 and S of Eq. 5 (D2Q9 only) */
+
 /* storage precision */
 #define LBM_FP64 0    /* populations, density and all arithmetic in FP64 */
 #define LBM_FP32DEV 1 /* populations stored in FP32 as f_i - w_i rho_ref, density as rho - rho_ref */
@@ -82,6 +86,11 @@ extern "C" {
  *            (slower on GB300, whose FP64 rate is a small fraction of FP32)
  *  rho_ref   FP32DEV only: reference density of the stored deviations;
  *            <= 0 selects the Maxwell gas density at Tr
+ *  collision LBM_BGK, or LBM_MRT (D2Q9; LBM_ENOTSUP on D3Q19)
+ *  mrt_s     LBM_MRT: the rates s_1..s_9 of Eq. 5 in the row order of Eq. 3
+ *            (rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy); all zero
+ *            selects the paper's (1, 1.64, 1.54, 1, 1.7, 1, 1.7, 1/tau, 1/tau).
+ *            The rates of the conserved moments (s_1, s_4, s_6) have no effect.
  */
 typedef struct {
   int lattice;
@@ -93,6 +102,8 @@ typedef struct {
   int precision;
   int mu_fp64;
   double rho_ref;
+  int collision;
+  double mrt_s[9];
 } lbm_params;
 
 /*

@@ -34,6 +34,7 @@ struct CaseDev {
   int tiles_x, tiles_y;
   int item_begin, item_end;      // observation / single-phase items
   int mtiles_x, ctiles_x;        // split path: mu tiles (32 x 16) and collision tiles (30 x 14) per row
+  Mrt mrt;                       // collision operator of the case
 };
 
 struct Item {
@@ -119,9 +120,9 @@ __device__ void run_item(const CaseDev& cd, int tile, long long t, unsigned char
 #define LBM_ITEM_CASE(S)                                                                                   \
   case S:                                                                                                  \
     if (mode == MODE_STEP)                                                                                 \
-      step2d_tile<S, P, TXB, TYB, MODE_STEP>(cd.kp, fin, fout, rin, rout, aux, fo, gi, x0, y0, smem, partial); \
+      step2d_tile<S, P, TXB, TYB, MODE_STEP>(cd.kp, fin, fout, rin, rout, aux, fo, gi, cd.mrt, x0, y0, smem, partial); \
     else                                                                                                   \
-      step2d_tile<S, P, TXB, TYB, MODE_OBS>(cd.kp, fin, fout, rin, rout, aux, fo, gi, x0, y0, smem, partial);  \
+      step2d_tile<S, P, TXB, TYB, MODE_OBS>(cd.kp, fin, fout, rin, rout, aux, fo, gi, cd.mrt, x0, y0, smem, partial); \
     break;
   switch (cd.scheme) {
     LBM_ITEM_CASE(S_EFDS2)
@@ -212,8 +213,8 @@ __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phas
   const bool tau1 = cd.kp.omega == 1.0;
 #define LBM_SPLIT_CASE(SS)                                                              \
   case SS:                                                                              \
-    if (tau1) coll2d_compute<SS, true>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf);      \
-    else coll2d_compute<SS, false>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf);          \
+    if (tau1) coll2d_compute<SS, true>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf, cd.mrt); \
+    else coll2d_compute<SS, false>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf, cd.mrt);     \
     break;
   switch (cd.scheme) {
     LBM_SPLIT_CASE(S_EFDS2)
@@ -235,7 +236,7 @@ __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phas
 // Dynamic shared memory: NBUF buffers of buf_bytes (a multiple of 16).
 constexpr int NBUF = 3;
 
-__global__ void __launch_bounds__(NT2S) k_batch_split(const CaseDev* __restrict__ cases,
+__global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restrict__ cases,
                                                       const Item* __restrict__ mitems, int nmu,
                                                       const Item* __restrict__ citems, int ncoll, int nsteps,
                                                       BatchCtl* ctl, unsigned long long timeout_ns, int buf_bytes) {
@@ -416,6 +417,7 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     if (!(q.scheme == LBM_EFDS2 || q.scheme == LBM_EFDS4 || q.scheme == LBM_EFDS6 || q.scheme == LBM_E4 ||
           q.scheme == LBM_E8))
       return LBM_ENOTSUP;
+    if (q.collision != LBM_BGK && q.collision != LBM_MRT) return LBM_EINVAL;
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_ENOMEM;
@@ -459,6 +461,7 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     cd.kp.k2 = q.k * q.k; cd.kp.kappa = q.kappa; cd.kp.omega = 1.0 / q.tau; cd.kp.rho_ref = rho_ref;
     b->p[c].rho_ref = rho_ref;
     cd.scheme = q.scheme;
+    cd.mrt = make_mrt(q.collision == LBM_MRT, q.mrt_s, q.tau);
     cd.tiles_x = (q.nx + TXB - 1) / TXB;
     cd.tiles_y = (q.ny + TYB - 1) / TYB;
     cd.item_begin = int(items.size());

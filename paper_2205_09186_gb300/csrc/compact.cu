@@ -201,7 +201,7 @@ cudaError_t launch_gf(const Launch& c, int D, int* nblocks) {
     dim3 grid((c.kp.nx + TXc - 1) / TXc, (c.kp.ny + TYc - 1) / TYc, 1);
     if (nblocks) *nblocks = int(grid.x * grid.y);
     k<<<grid, NT2, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), rin, rout,
-                                          c.aux, c.fo, c.gi);
+                                          c.aux, c.fo, c.gi, c.mrt);
   } else {
     using Sh = Step3DShape<S_CFDS4, P, TXc, TYc>;
     auto k = k_step3d<S_CFDS4, P, TXc, TYc, ZCc, MODE>;

@@ -27,7 +27,7 @@ cudaError_t launch_mode(const Launch& c, int* nblocks) {
   using Tr = typename P::Tr;
   k<<<grid, NT2, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout),
                                         static_cast<const Tr*>(c.rin), static_cast<Tr*>(c.rout),
-                                        c.aux, c.fo, c.gi);
+                                        c.aux, c.fo, c.gi, c.mrt);
   return cudaGetLastError();
 }
 
@@ -51,7 +51,7 @@ cudaError_t launch_split2d(const Launch& c, int* nblocks) {
   k_coll2d<S, TAU1><<<gc, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin),
                                                        static_cast<float*>(c.fout), static_cast<const float*>(c.rin),
                                                        static_cast<const float*>(c.mu), static_cast<float*>(c.rout),
-                                                       c.aux);
+                                                       c.aux, c.mrt);
   return cudaGetLastError();
 }
 

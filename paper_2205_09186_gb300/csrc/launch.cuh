@@ -18,6 +18,7 @@ struct Launch {
   cudaStream_t stream;
   int zc;       // z-chunk of the pipelined D3Q19 kernel; 0 = heuristic
   void* mu;     // N floats: mu field of the split D3Q19 FP32DEV path (else unused)
+  Mrt mrt;      // D2Q9 collision operator (on = 0: single relaxation)
   cudaEvent_t ev_mid;  // if set: recorded between the mu pass and the collision pass
 };
 

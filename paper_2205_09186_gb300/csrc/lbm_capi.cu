@@ -17,6 +17,7 @@ using namespace lbmd;
 
 struct lbm_handle {
   lbm_params p;
+  Mrt mrt{};  // D2Q9 collision operator
   int Q = 0, D = 0, prec = 0;
   long long N = 0;
   cudaStream_t stream = nullptr;
@@ -347,6 +348,8 @@ static int validate(const lbm_params* p) {
   if (p->scheme < LBM_EFDS2 || p->scheme > LBM_E8) return LBM_EINVAL;
   if (p->precision != LBM_FP64 && p->precision != LBM_FP32DEV) return LBM_EINVAL;
   if (p->scheme == LBM_E8 && p->lattice != LBM_D2Q9) return LBM_ENOTSUP;
+  if (p->collision != LBM_BGK && p->collision != LBM_MRT) return LBM_EINVAL;
+  if (p->collision == LBM_MRT && p->lattice != LBM_D2Q9) return LBM_ENOTSUP;
   return LBM_OK;
 }
 
@@ -383,6 +386,7 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
     }
   }
   h->prec = params->precision == LBM_FP64 ? 0 : (params->mu_fp64 ? 2 : 1);
+  h->mrt = make_mrt(params->collision == LBM_MRT, params->mrt_s, params->tau);
   h->compact = (params->scheme >= LBM_CFDS4 && params->scheme <= LBM_OCFDS4);
   h->kp.nx = params->nx; h->kp.ny = params->ny; h->kp.nz = params->nz; h->kp.n = h->N;
   h->kp.RT = params->R * T; h->kp.b4 = 0.25 * params->b; h->kp.two_a = 2.0 * params->a;
@@ -573,6 +577,7 @@ static Launch make_launch(lbm_handle* h, int out_buf) {
   c.stream = h->stream;
   c.zc = h->zc;
   c.mu = h->mu;
+  c.mrt = h->mrt;
   return c;
 }
 

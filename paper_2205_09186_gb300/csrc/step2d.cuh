@@ -12,6 +12,7 @@
 // are served by L2.
 #pragma once
 #include "lbm_device.cuh"
+#include "mrt.cuh"
 
 namespace lbmd {
 
@@ -73,7 +74,8 @@ template <int S, class P, int TX, int TY, int MODE>
 __device__ __forceinline__ void step2d_tile(const KParams& p, const typename P::Tf* __restrict__ fin,
                                             typename P::Tf* __restrict__ fout, const typename P::Tr* __restrict__ rin,
                                             typename P::Tr* __restrict__ rout, const StepAux& aux, const FieldOut& fo,
-                                            const GradIn& gi, const int x0, const int y0, unsigned char* smem,
+                                            const GradIn& gi, const Mrt& mrt, const int x0, const int y0,
+                                            unsigned char* smem,
                                             double* partial) {
   using Tf = typename P::Tf;
   using Tc = typename P::Tc;
@@ -163,9 +165,19 @@ __device__ __forceinline__ void step2d_tile(const KParams& p, const typename P::
         if (interior && !(rc > Tc(0))) atomicMin(aux.bad_step, (unsigned long long)aux.t);
         const Tc vx = ux + Fx / rc, vy = uy + Fy / rc;
         const Tc dr = P::DEV ? Tc(dsv) : rc;
+        Tc post[Q];
+        if (mrt.on) {
+          Tc fc[Q];
+#pragma unroll
+          for (int i = 0; i < Q; ++i) fc[i] = Tc(fv[i]);
+          mrt_post9<Tc>(fc, dr, rc, ux, uy, vx, vy, mrt, post);
+        } else {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) post[i] = coll_one<0, Tc>(i, Tc(fv[i]), dr, rc, omega, ux, uy, Tc(0), vx, vy, Tc(0));
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-          const Tc fs = coll_one<0, Tc>(i, Tc(fv[i]), dr, rc, omega, ux, uy, Tc(0), vx, vy, Tc(0));
+          const Tc fs = post[i];
           s_f[i * CH * CW + cy * CW + cx] = Tf(fs);
           if (interior) {
             const int tx = wrapi(gx + L::ex(i), nx), ty = wrapi(gy + L::ey(i), ny);
@@ -225,9 +237,9 @@ template <int S, class P, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(NT2) k_step2d(const KParams p, const typename P::Tf* __restrict__ fin,
                                                 typename P::Tf* __restrict__ fout, const typename P::Tr* __restrict__ rin,
                                                 typename P::Tr* __restrict__ rout, const StepAux aux, const FieldOut fo,
-                                                const GradIn gi) {
+                                                const GradIn gi, const Mrt mrt) {
   extern __shared__ __align__(16) unsigned char smem[];
-  step2d_tile<S, P, TX, TY, MODE>(p, fin, fout, rin, rout, aux, fo, gi, blockIdx.x * TX, blockIdx.y * TY, smem,
+  step2d_tile<S, P, TX, TY, MODE>(p, fin, fout, rin, rout, aux, fo, gi, mrt, blockIdx.x * TX, blockIdx.y * TY, smem,
                                   aux.partials + 4 * (blockIdx.y * gridDim.x + blockIdx.x));
 }
 

@@ -116,7 +116,7 @@ __device__ __forceinline__ void coll2d_load(const KParams& p, const float* __res
 template <int S, bool TAU1>
 __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restrict__ fout, float* __restrict__ rout,
                                                unsigned long long* bad, long long t, int x0, int y0,
-                                               unsigned char* smem) {
+                                               unsigned char* smem, const Mrt& mrt) {
   using L = Lattice<0>;
   using Sh = Split2DShape<S>;
   constexpr int Q = 9, R = Sh::R, GW = Sh::GW;
@@ -156,6 +156,18 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
     const int dxp = (gx + 1 < nx) ? 1 : 1 - nx, dxm = (gx > 0) ? -1 : nx - 1;
     const int dyp = (gy + 1 < ny) ? nx : nx - N, dym = (gy > 0) ? -nx : N - nx;
     float* fo = fout + gy * nx + gx;
+    if (mrt.on) {
+      float post[Q];
+      mrt_post9<float>(fv, dsv, rc, ux, uy, vx, vy, mrt, post);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        s_f[i * NT2S + tid] = post[i];
+        if (interior) {
+          const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) + (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0));
+          fo[i * N + d] = post[i];
+        }
+      }
+    } else {
     const float vv15 = 1.5f * (vx * vx + vy * vy), uu15 = 1.5f * (ux * ux + uy * uy);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -175,6 +187,7 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
         const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) + (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0));
         fo[i * N + d] = fs;
       }
+    }
     }
   }
   __syncthreads();
@@ -202,12 +215,12 @@ template <int S, bool TAU1>
 __device__ __forceinline__ void coll2d_tile(const KParams& p, const float* __restrict__ fin, float* __restrict__ fout,
                                             const float* __restrict__ rin, const float* __restrict__ muf,
                                             float* __restrict__ rout, unsigned long long* bad, long long t, int x0,
-                                            int y0, unsigned char* smem) {
+                                            int y0, unsigned char* smem, const Mrt& mrt) {
   coll2d_load<S>(p, fin, rin, muf, x0, y0, smem);
   cpa_commit();
   cpa_wait_all();
   __syncthreads();
-  coll2d_compute<S, TAU1>(p, fout, rout, bad, t, x0, y0, smem);
+  coll2d_compute<S, TAU1>(p, fout, rout, bad, t, x0, y0, smem, mrt);
 }
 
 template <int S>
@@ -220,9 +233,10 @@ template <int S, bool TAU1>
 __global__ void __launch_bounds__(NT2S) k_coll2d(const KParams p, const float* __restrict__ fin,
                                                  float* __restrict__ fout, const float* __restrict__ rin,
                                                  const float* __restrict__ mu, float* __restrict__ rout,
-                                                 const StepAux aux) {
+                                                 const StepAux aux, const Mrt mrt) {
   extern __shared__ __align__(16) unsigned char smem[];
-  coll2d_tile<S, TAU1>(p, fin, fout, rin, mu, rout, aux.bad_step, aux.t, blockIdx.x * T2X, blockIdx.y * T2Y, smem);
+  coll2d_tile<S, TAU1>(p, fin, fout, rin, mu, rout, aux.bad_step, aux.t, blockIdx.x * T2X, blockIdx.y * T2Y, smem,
+                       mrt);
 }
 
 }  // namespace lbmd

@@ -19,13 +19,15 @@ LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_EOS_CS = 0
 SCHEMES = {"EFDS2": 0, "EFDS4": 1, "EFDS6": 2, "CFDS4": 3, "CFDS6": 4, "CFDS8": 5, "OCFDS4": 6, "E4": 7, "E8": 8}
 LBM_FP64, LBM_FP32DEV = 0, 1
+LBM_BGK, LBM_MRT = 0, 1
 
 
 class lbm_params(C.Structure):
     _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("eos", C.c_int),
                 ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("Tr", C.c_double),
                 ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double),
-                ("scheme", C.c_int), ("precision", C.c_int), ("mu_fp64", C.c_int), ("rho_ref", C.c_double)]
+                ("scheme", C.c_int), ("precision", C.c_int), ("mu_fp64", C.c_int), ("rho_ref", C.c_double),
+                ("collision", C.c_int), ("mrt_s", C.c_double * 9)]
 
 
 class lbm_obs(C.Structure):
@@ -136,9 +138,13 @@ def _f64(a):
 
 
 def make_params(lattice=LBM_D2Q9, nx=64, ny=64, nz=1, a=1.0, b=4.0, R=1.0, Tr=0.7, k=0.25, kappa=0.1, tau=1.0,
-                scheme="EFDS2", precision=LBM_FP64, mu_fp64=0, rho_ref=0.0):
+                scheme="EFDS2", precision=LBM_FP64, mu_fp64=0, rho_ref=0.0, collision=LBM_BGK, mrt_s=None):
+    """collision: LBM_BGK / LBM_MRT or "BGK" / "MRT"; mrt_s None = the paper's rates."""
     s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
-    return lbm_params(lattice, nx, ny, nz, LBM_EOS_CS, a, b, R, Tr, k, kappa, tau, s, precision, int(mu_fp64), rho_ref)
+    col = {"BGK": LBM_BGK, "MRT": LBM_MRT}[collision] if isinstance(collision, str) else int(collision)
+    rates = (C.c_double * 9)(*(mrt_s if mrt_s is not None else [0.0] * 9))
+    return lbm_params(lattice, nx, ny, nz, LBM_EOS_CS, a, b, R, Tr, k, kappa, tau, s, precision, int(mu_fp64), rho_ref,
+                      col, rates)
 
 
 def lbm_observables_noalloc(params, d_f, d_rho, d_rho_prev=None, steps_since_prev=0, step=0, stream=None):
