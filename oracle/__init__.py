@@ -31,7 +31,7 @@ class Params(C.Structure):
     _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("Tr", C.c_double),
                 ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double), ("scheme", C.c_int),
-                ("collision", C.c_int), ("mrt_s", C.c_double * 9)]
+                ("collision", C.c_int), ("mrt_s", C.c_double * 9), ("eos", C.c_int), ("acentric", C.c_double)]
 
 
 class Obs(C.Structure):
@@ -65,6 +65,15 @@ def lib():
         L.or_lattice_q.argtypes = [C.c_int]
         L.or_lattice_e.argtypes = [C.c_int, _ip, _dp]
         L.or_feq.argtypes = [C.c_int, C.c_double, _dp, _dp]
+        L.or_eos_make.argtypes = [C.c_int] + [C.c_double] * 5 + [C.c_void_p]
+        L.or_eos_pressure.argtypes = [C.c_void_p, C.c_double]
+        L.or_eos_pressure.restype = C.c_double
+        L.or_eos_mu.argtypes = [C.c_void_p, C.c_double]
+        L.or_eos_mu.restype = C.c_double
+        L.or_eos_maxwell.argtypes = [C.c_void_p, _dp, _dp]
+        L.or_pr_alpha.argtypes = [C.c_double] * 3
+        L.or_pr_alpha.restype = C.c_double
+        L.or_pr_critical.argtypes = [C.c_double] * 3 + [_dp, _dp]
         L.or_mrt_matrix.argtypes = [_dp]
         L.or_mrt_matrix.restype = None
         L.or_mrt_inverse.argtypes = [_dp]
@@ -187,6 +196,46 @@ def lattice(lat):
 
 
 BGK, MRT = 0, 1
+EOS_CS, EOS_PR = 0, 1
+
+
+class Eos(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("T", C.c_double),
+                ("Tc", C.c_double), ("rho_c", C.c_double), ("alpha", C.c_double), ("rho_max", C.c_double)]
+
+
+def eos_make(kind, a, b, R, Tr, acentric=0.344):
+    """An equation of state (EOS_CS, or EOS_PR of Eq. 14-15) at T = Tr T_c."""
+    e = Eos()
+    if lib().or_eos_make(kind, a, b, R, Tr, acentric, C.byref(e)) != OK:
+        raise ValueError("invalid EOS parameters")
+    return e
+
+
+def eos_pressure(e, rho):
+    return lib().or_eos_pressure(C.byref(e), rho)
+
+
+def eos_mu(e, rho):
+    return lib().or_eos_mu(C.byref(e), rho)
+
+
+def eos_maxwell(e):
+    g, l = C.c_double(), C.c_double()
+    if lib().or_eos_maxwell(C.byref(e), C.byref(g), C.byref(l)) != OK:
+        raise ValueError("Maxwell construction failed")
+    return g.value, l.value
+
+
+def pr_alpha(T, Tc, acentric):
+    return lib().or_pr_alpha(T, Tc, acentric)
+
+
+def pr_critical(a, b, R):
+    rc, Tc = C.c_double(), C.c_double()
+    if lib().or_pr_critical(a, b, R, C.byref(rc), C.byref(Tc)) != OK:
+        raise ValueError
+    return rc.value, Tc.value
 
 
 def mrt_rates(tau):
@@ -235,13 +284,14 @@ class Sim:
     """One periodic droplet/slab simulation, plain FP64 (the paper's step)."""
 
     def __init__(self, lattice=D2Q9, nx=64, ny=64, nz=1, a=1.0, b=4.0, R=1.0, Tr=0.7, k=0.4,
-                 kappa=1.0, tau=1.0, scheme="EFDS2", collision="BGK", mrt_s=None):
+                 kappa=1.0, tau=1.0, scheme="EFDS2", collision="BGK", mrt_s=None, eos="CS", acentric=0.344):
         """collision "MRT" (D2Q9): rates s_1..s_9 of Eq. 5, by default the
         paper's (1, 1.64, 1.54, 1, 1.7, 1, 1.7, 1/tau, 1/tau)."""
         if mrt_s is None:
             mrt_s = mrt_rates(tau)
         self.p = Params(lattice, nx, ny, nz, a, b, R, Tr, k, kappa, tau, _scheme(scheme),
-                        {"BGK": BGK, "MRT": MRT}[collision], (C.c_double * 9)(*mrt_s))
+                        {"BGK": BGK, "MRT": MRT}[collision], (C.c_double * 9)(*mrt_s),
+                        {"CS": EOS_CS, "PR": EOS_PR}[eos], acentric)
         self.h = lib().or_create(C.byref(self.p))
         if not self.h:
             raise ValueError("invalid oracle parameters")

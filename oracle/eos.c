@@ -139,3 +139,132 @@ int or_maxwell(double a, double b, double R, double T, double* rho_g, double* rh
   if (!(r1 < 1e-9)) return OR_EINVAL;
   return OR_OK;
 }
+
+/* ---------------------------------------------------------------- Peng-Robinson */
+/*
+ * Eq. 14:  p0 = rho R T / (1 - b rho) - a alpha(T) rho^2 / (1 + 2 b rho - b^2 rho^2)
+ * Eq. 15:  mu = R T ln(rho / (1 - b rho)) - a alpha / (2 sqrt2 b) ln((sqrt2 - 1 + b rho) / (sqrt2 + 1 - b rho))
+ *               + R T / (1 - b rho) - a alpha rho / (1 + 2 b rho - b^2 rho^2)      (bulk part, kappa term apart)
+ * alpha(T) = [1 + (0.37464 + 1.54226 w - 0.26992 w^2)(1 - sqrt(T / T_c))]^2, w the acentric factor.
+ * The critical point is that of alpha = 1 (alpha(T_c) = 1).
+ */
+double or_pr_alpha(double T, double Tc, double w) {
+  double kap = 0.37464 + 1.54226 * w - 0.26992 * w * w;
+  double s = 1.0 + kap * (1.0 - sqrt(T / Tc));
+  return s * s;
+}
+
+double or_pr_pressure(double rho, double a, double b, double R, double T, double alpha) {
+  double br = b * rho;
+  return rho * R * T / (1.0 - br) - a * alpha * rho * rho / (1.0 + 2.0 * br - br * br);
+}
+
+double or_pr_mu(double rho, double a, double b, double R, double T, double alpha) {
+  double br = b * rho, s2 = sqrt(2.0);
+  return R * T * log(rho / (1.0 - br)) - a * alpha / (2.0 * s2 * b) * log((s2 - 1.0 + br) / (s2 + 1.0 - br)) +
+         R * T / (1.0 - br) - a * alpha * rho / (1.0 + 2.0 * br - br * br);
+}
+
+static double pr_dpdrho(double rho, double a, double b, double R, double T, double alpha) {
+  double br = b * rho, D = 1.0 + 2.0 * br - br * br;
+  return R * T / ((1.0 - br) * (1.0 - br)) - 2.0 * a * alpha * rho * (1.0 + br) / (D * D);
+}
+
+/* With x = b rho and h(x) = x^2 / (1 + 2x - x^2) the alpha = 1 pressure is
+ * p0 = (R T / b) x / (1 - x) - (a / b^2) h(x); p0' = p0'' = 0 give
+ * (1 - x) / 2 = h'(x) / h''(x), then R T_c = (a / b) (1 - x)^2 h'(x). */
+static void pr_h_derivs(double x, double* h1, double* h2) {
+  double D = 1.0 + 2.0 * x - x * x, D1 = 2.0 - 2.0 * x;
+  /* h' = 2x(1 + x) / D^2 (quotient rule, simplified) */
+  double n = 2.0 * x * (1.0 + x), n1 = 2.0 + 4.0 * x;
+  *h1 = n / (D * D);
+  *h2 = (n1 * D - 2.0 * n * D1) / (D * D * D);
+}
+
+int or_pr_critical(double a, double b, double R, double* rho_c, double* T_c) {
+  if (!(a > 0 && b > 0 && R > 0)) return OR_EINVAL;
+  double lo = 1e-6, hi = 0.9;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi), h1, h2;
+    pr_h_derivs(mid, &h1, &h2);
+    /* g(x) = (1 - x) h'' - 2 h': positive for small x, negative near x -> 1 */
+    if ((1.0 - mid) * h2 - 2.0 * h1 > 0) lo = mid; else hi = mid;
+  }
+  double x = 0.5 * (lo + hi), h1, h2;
+  pr_h_derivs(x, &h1, &h2);
+  *rho_c = x / b;
+  *T_c = (a / b) * (1.0 - x) * (1.0 - x) * h1 / R;
+  return OR_OK;
+}
+
+/* ---------------------------------------------------------------- EOS by kind */
+double or_eos_pressure(const or_eos* e, double rho) {
+  return e->kind == OR_EOS_PR ? or_pr_pressure(rho, e->a, e->b, e->R, e->T, e->alpha)
+                              : or_cs_pressure(rho, e->a, e->b, e->R, e->T);
+}
+
+double or_eos_mu(const or_eos* e, double rho) {
+  return e->kind == OR_EOS_PR ? or_pr_mu(rho, e->a, e->b, e->R, e->T, e->alpha)
+                              : or_cs_mu(rho, e->a, e->b, e->R, e->T);
+}
+
+static double eos_dpdrho(const or_eos* e, double rho) {
+  return e->kind == OR_EOS_PR ? pr_dpdrho(rho, e->a, e->b, e->R, e->T, e->alpha)
+                              : cs_dpdrho(rho, e->a, e->b, e->R, e->T);
+}
+
+int or_eos_critical(int kind, double a, double b, double R, double* rho_c, double* T_c) {
+  return kind == OR_EOS_PR ? or_pr_critical(a, b, R, rho_c, T_c) : or_cs_critical(a, b, R, rho_c, T_c);
+}
+
+int or_eos_make(int kind, double a, double b, double R, double Tr, double acentric, or_eos* e) {
+  double rc, Tc;
+  if (kind != OR_EOS_CS && kind != OR_EOS_PR) return OR_EINVAL;
+  if (or_eos_critical(kind, a, b, R, &rc, &Tc) != OR_OK) return OR_EINVAL;
+  e->kind = kind; e->a = a; e->b = b; e->R = R; e->T = Tr * Tc; e->Tc = Tc; e->rho_c = rc;
+  e->alpha = kind == OR_EOS_PR ? or_pr_alpha(e->T, Tc, acentric) : 1.0;
+  e->rho_max = kind == OR_EOS_PR ? 1.0 / b : 4.0 / b;
+  return OR_OK;
+}
+
+/* The same equal-pressure, equal-mu bisection as or_maxwell, for either EOS.
+ * At the PR critical point alpha = 1; below it alpha > 1 and the spinodals
+ * lie on either side of rho_c as for CS. */
+int or_eos_maxwell(const or_eos* e, double* rho_g, double* rho_l) {
+  if (!(e->T > 0 && e->T < e->Tc)) return OR_EINVAL;
+  double lo = -700.0, hi = log(e->rho_c);
+  for (int it = 0; it < 300; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (eos_dpdrho(e, exp(mid)) > 0) lo = mid; else hi = mid;
+  }
+  double sp_g = exp(lo);
+  lo = e->rho_c; hi = e->rho_max;
+  for (int it = 0; it < 300; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (eos_dpdrho(e, mid) < 0) lo = mid; else hi = mid;
+  }
+  double sp_l = hi;
+  double p_hi = or_eos_pressure(e, sp_g), p_lo = or_eos_pressure(e, sp_l);
+  double lp_hi = log(p_hi), lp_lo = (p_lo > 0) ? log(p_lo) : -700.0;
+  double rg = 0, rl = 0;
+  for (int it = 0; it < 300; ++it) {
+    double mid = 0.5 * (lp_lo + lp_hi), P = exp(mid);
+    double glo = -700.0, ghi = log(sp_g);
+    for (int k = 0; k < 300; ++k) {
+      double m = 0.5 * (glo + ghi);
+      if (or_eos_pressure(e, exp(m)) < P) glo = m; else ghi = m;
+    }
+    double llo = sp_l, lhi = e->rho_max;
+    for (int k = 0; k < 300; ++k) {
+      double m = 0.5 * (llo + lhi);
+      if (or_eos_pressure(e, m) < P) llo = m; else lhi = m;
+    }
+    rg = exp(0.5 * (glo + ghi));
+    rl = 0.5 * (llo + lhi);
+    if (or_eos_mu(e, rg) - or_eos_mu(e, rl) < 0) lp_lo = mid; else lp_hi = mid;
+  }
+  *rho_g = rg;
+  *rho_l = rl;
+  if (!(fabs(or_eos_mu(e, rg) - or_eos_mu(e, rl)) < 1e-9)) return OR_EINVAL;
+  return OR_OK;
+}

@@ -84,6 +84,7 @@ struct or_sim {
   int q, dim;
   long n;
   double T;
+  or_eos eos;                           /* the equation of state at T */
   double *f, *fn;                       /* f[i*n + node] */
   double *rho, *u, *F, *mu, *lap, *gmu, *grho;
   double* rho_snap;
@@ -106,14 +107,16 @@ or_sim* or_create(const or_params* p) {
   if (!(p->tau > 0.5) || !(p->k > 0) || !(p->kappa >= 0) || !(p->Tr > 0)) return NULL;
   if (p->collision != OR_BGK && p->collision != OR_MRT) return NULL;
   if (p->collision == OR_MRT && p->lattice != OR_D2Q9) return NULL;
-  double rc, Tc;
-  if (or_cs_critical(p->a, p->b, p->R, &rc, &Tc) != OR_OK) return NULL;
+  if (p->eos != OR_EOS_CS && p->eos != OR_EOS_PR) return NULL;
+  or_eos eos;
+  if (or_eos_make(p->eos, p->a, p->b, p->R, p->Tr, p->acentric, &eos) != OR_OK) return NULL;
   or_sim* s = (or_sim*)calloc(1, sizeof(or_sim));
   s->p = *p;
   s->q = or_lattice_q(p->lattice);
   s->dim = p->lattice == OR_D2Q9 ? 2 : 3;
   s->n = (long)p->nx * p->ny * p->nz;
-  s->T = p->Tr * Tc;
+  s->eos = eos;
+  s->T = eos.T;
   long n = s->n;
   s->f = (double*)calloc((size_t)s->q * n, sizeof(double));
   s->fn = (double*)calloc((size_t)s->q * n, sizeof(double));
@@ -157,7 +160,7 @@ static void init_from_rho(or_sim* s, const double* rho) {
 static int default_densities(or_sim* s, double* rho_l, double* rho_g) {
   if (*rho_l > 0 && *rho_g > 0) return OR_OK;
   double g, l;
-  int rc = or_maxwell(s->p.a, s->p.b, s->p.R, s->T, &g, &l);
+  int rc = or_eos_maxwell(&s->eos, &g, &l);
   if (rc != OR_OK) return rc;
   *rho_l = l;
   *rho_g = g;
@@ -276,7 +279,7 @@ static int macro_fields(or_sim* s) {
   int rc = or_laplacian(p->scheme, s->dim, p->nx, p->ny, p->nz, s->rho, s->lap);
   if (rc != OR_OK) return rc;
   for (long x = 0; x < n; ++x)
-    s->mu[x] = p->k * p->k * or_cs_mu(s->rho[x], p->a, p->b, p->R, s->T) - p->kappa * s->lap[x];
+    s->mu[x] = p->k * p->k * or_eos_mu(&s->eos, s->rho[x]) - p->kappa * s->lap[x];
   rc = or_gradient(p->scheme, s->dim, p->nx, p->ny, p->nz, s->mu, s->gmu);
   if (rc != OR_OK) return rc;
   rc = or_gradient(p->scheme, s->dim, p->nx, p->ny, p->nz, s->rho, s->grho);

@@ -56,6 +56,8 @@ typedef struct {
   int scheme;           /* OR_EFDS2 .. OR_E8 */
   int collision;        /* OR_BGK or OR_MRT */
   double mrt_s[9];      /* OR_MRT: s_1 .. s_9 of Eq. 5 */
+  int eos;              /* OR_EOS_CS or OR_EOS_PR */
+  double acentric;      /* OR_EOS_PR: acentric factor of alpha(T) (Eq. 15) */
 } or_params;
 
 typedef struct {
@@ -77,6 +79,25 @@ double or_cs_pressure(double rho, double a, double b, double R, double T);
 double or_cs_mu(double rho, double a, double b, double R, double T);
 int or_cs_critical(double a, double b, double R, double* rho_c, double* T_c);
 int or_maxwell(double a, double b, double R, double T, double* rho_g, double* rho_l);
+
+/* ---- Peng-Robinson EOS and chemical potential (Eq. 14-15) ---- */
+double or_pr_alpha(double T, double Tc, double acentric);
+double or_pr_pressure(double rho, double a, double b, double R, double T, double alpha);
+double or_pr_mu(double rho, double a, double b, double R, double T, double alpha);
+int or_pr_critical(double a, double b, double R, double* rho_c, double* T_c);
+
+/* ---- an EOS of either kind at one temperature ---- */
+#define OR_EOS_CS 0
+#define OR_EOS_PR 1
+typedef struct {
+  int kind;
+  double a, b, R, T, Tc, rho_c, alpha, rho_max;
+} or_eos;
+int or_eos_make(int kind, double a, double b, double R, double Tr, double acentric, or_eos* e);
+int or_eos_critical(int kind, double a, double b, double R, double* rho_c, double* T_c);
+double or_eos_pressure(const or_eos* e, double rho);
+double or_eos_mu(const or_eos* e, double rho);
+int or_eos_maxwell(const or_eos* e, double* rho_g, double* rho_l);
 
 /* ---- finite differences on periodic lattices (Sec. 2.3) ---- */
 void or_scheme_coeffs(int scheme, double* alpha, double* a, double* b, double* c);
