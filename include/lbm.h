@@ -50,6 +50,7 @@ extern "C" {
 #define LBM_D3Q19 1
 
 #define LBM_EOS_CS 0 /* Carnahan-Starling */
+#define LBM_EOS_PR 1 /* Peng-Robinson, Eq. 14 with the chemical potential of Eq. 15 */
 
 /* difference schemes (Sec. 2.3) */
 #define LBM_EFDS2 0  /* Eq. 18, second-order central */
@@ -74,9 +75,10 @@ extern "C" {
  * Simulation parameters.
  *  lattice   LBM_D2Q9 (nz must be 1) or LBM_D3Q19
  *  nx,ny,nz  periodic lattice size; each >= 8 (D2Q9: nx, ny >= 8)
- *  eos       LBM_EOS_CS
- *  a,b,R     CS constants: p0 = rho R T (1+eta+eta^2-eta^3)/(1-eta)^3 - a rho^2, eta = b rho/4
- *  Tr        reduced temperature T/T_c (T_c computed from a, b, R), 0 < Tr
+ *  eos       LBM_EOS_CS or LBM_EOS_PR
+ *  a,b,R     CS constants: p0 = rho R T (1+eta+eta^2-eta^3)/(1-eta)^3 - a rho^2, eta = b rho/4;
+ *            PR constants of Eq. 14 (the paper's: a = 2/49, b = 2/21, R = 1)
+ *  Tr        reduced temperature T/T_c (T_c computed from a, b, R), 0 < Tr (PR: Tr < 1)
  *  k         proportional coefficient of Eq. 16 (mu-hat = k^2 psi' - kappa lap rho)
  *  kappa     kappa-hat of Eq. 16
  *  tau       BGK relaxation time (> 0.5)
@@ -91,6 +93,8 @@ extern "C" {
  *            (rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy); all zero
  *            selects the paper's (1, 1.64, 1.54, 1, 1.7, 1, 1.7, 1/tau, 1/tau).
  *            The rates of the conserved moments (s_1, s_4, s_6) have no effect.
+ *  acentric  LBM_EOS_PR: the acentric factor omega of alpha(T) (Eq. 15; the
+ *            paper's water: 0.344)
  */
 typedef struct {
   int lattice;
@@ -104,6 +108,7 @@ typedef struct {
   double rho_ref;
   int collision;
   double mrt_s[9];
+  double acentric;
 } lbm_params;
 
 /*
@@ -236,6 +241,11 @@ int lbm_critical(double a, double b, double R, double* rho_c, double* T_c);
 /* Maxwell equal-area coexistence densities for params->(a, b, R, Tr):
  * equal chemical potential and pressure in both bulk phases. */
 int lbm_maxwell(const lbm_params* params, double* rho_g, double* rho_l);
+
+/* Critical density and temperature of the EOS that p selects (p0' = p0'' = 0;
+ * for Peng-Robinson with alpha = 1, which holds at T_c).  Host only.  (A
+ * companion of lbm_critical, which keeps its Carnahan-Starling signature.) */
+int lbm_eos_critical(const lbm_params* p, double* rho_c, double* T_c);
 
 /* Lattice size Q (9 or 19) of a lattice id, 0 if unknown. */
 int lbm_lattice_q(int lattice);

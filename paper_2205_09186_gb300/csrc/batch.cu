@@ -418,6 +418,7 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
           q.scheme == LBM_E8))
       return LBM_ENOTSUP;
     if (q.collision != LBM_BGK && q.collision != LBM_MRT) return LBM_EINVAL;
+    if (q.eos != LBM_EOS_CS && q.eos != LBM_EOS_PR) return LBM_EINVAL;
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_ENOMEM;
@@ -443,23 +444,9 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     const int c = idx[k];
     const lbm_params& q = cases[c];
     CaseDev& cd = b->host_cases[c];
-    double rc, Tc;
-    lbm_critical(q.a, q.b, q.R, &rc, &Tc);
-    const double T = q.Tr * Tc;
-    double rho_ref = 0.0;
-    if (q.precision == LBM_FP32DEV) {
-      rho_ref = q.rho_ref;
-      if (!(rho_ref > 0)) {
-        double g, l;
-        if (lbm_maxwell(&q, &g, &l) != LBM_OK) { ok = false; break; }
-        rho_ref = g;
-      }
-    }
-    const long long N = (long long)q.nx * q.ny;
-    cd.kp.nx = q.nx; cd.kp.ny = q.ny; cd.kp.nz = 1; cd.kp.n = N;
-    cd.kp.RT = q.R * T; cd.kp.b4 = 0.25 * q.b; cd.kp.two_a = 2.0 * q.a;
-    cd.kp.k2 = q.k * q.k; cd.kp.kappa = q.kappa; cd.kp.omega = 1.0 / q.tau; cd.kp.rho_ref = rho_ref;
-    b->p[c].rho_ref = rho_ref;
+    if (params_to_kp(&q, &cd.kp) != LBM_OK) { ok = false; break; }
+    const long long N = cd.kp.n;
+    b->p[c].rho_ref = cd.kp.rho_ref;
     cd.scheme = q.scheme;
     cd.mrt = make_mrt(q.collision == LBM_MRT, q.mrt_s, q.tau);
     cd.tiles_x = (q.nx + TXB - 1) / TXB;

@@ -81,7 +81,7 @@ __global__ void k_mu_field(KParams p, int D, bool dev, const Tr* __restrict__ rh
     lap += Tm(lc[m]) * s;
   }
   const Tm rfull = dev ? Tm(p.rho_ref) + Tm(rho[n]) : Tm(rho[n]);
-  mu[n] = Tm(p.k2) * cs_mu<Tm>(rfull, Tm(p.RT), Tm(p.b4), Tm(p.two_a)) - Tm(p.kappa) * lap;
+  mu[n] = Tm(p.k2) * eos_mu<Tm>(rfull, p) - Tm(p.kappa) * lap;
 }
 
 // Derivative along `axis` of lines of `in`, LPB lines per CTA held

@@ -1,6 +1,8 @@
 // Launch descriptors shared by the kernel translation units and the C ABI.
 #pragma once
 #include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
 #include "lbm_device.cuh"
 #include "step2d.cuh"
 
@@ -21,6 +23,12 @@ struct Launch {
   Mrt mrt;      // D2Q9 collision operator (on = 0: single relaxation)
   cudaEvent_t ev_mid;  // if set: recorded between the mu pass and the collision pass
 };
+
+// Kernel constants of a case: lattice size, the EOS at T = Tr T_c (either
+// kind), k^2, kappa-hat, 1/tau and the FP32DEV reference density (p->rho_ref,
+// or the Maxwell gas density when that is <= 0; 0 in FP64 mode).  Returns an
+// LBM_ status.
+int params_to_kp(const lbm_params* p, KParams* kp);
 
 // the D3Q19 FP32DEV step of this scheme runs as mu pass + collision pass and
 // needs an N-float mu buffer in Launch::mu

@@ -65,10 +65,6 @@ static size_t r_bytes(const lbm_handle* h) {
 // Carnahan-Starling: p0 = rho R T C0(eta) - a rho^2 with eta = b rho / 4 and
 // C0 = (1 + eta + eta^2 - eta^3)/(1 - eta)^3.  dp0/drho = R T C1(eta) - 2 a rho,
 // C1 = d(eta C0)/d eta = (1 + 4eta + 4eta^2 - 4eta^3 + eta^4)/(1 - eta)^4.
-static double cs_p(double rho, double a, double b, double R, double T) {
-  const double e = 0.25 * b * rho, q = 1.0 - e;
-  return rho * R * T * (1.0 + e * (1.0 + e * (1.0 - e))) / (q * q * q) - a * rho * rho;
-}
 static double cs_c1(double e) {
   const double q = 1.0 - e;
   return (1.0 + e * (4.0 + e * (4.0 + e * (-4.0 + e)))) / (q * q * q * q);
@@ -79,16 +75,67 @@ static double cs_c1p(double e) {  // d C1 / d eta
   const double dnum = 4.0 + e * (8.0 + e * (-12.0 + 4.0 * e));
   return dnum / (q * q * q * q) + 4.0 * num / (q * q * q * q * q);
 }
-static double cs_dp(double rho, double a, double b, double R, double T) {
-  return R * T * cs_c1(0.25 * b * rho) - 2.0 * a * rho;
-}
-static double cs_mub(double rho, double a, double b, double R, double T) {
-  const double e = 0.25 * b * rho, q = 1.0 - e;
-  return R * T * (std::log(rho) + e * (8.0 + e * (-9.0 + 3.0 * e)) / (q * q * q)) - 2.0 * a * rho;
-}
 
-extern "C" int lbm_critical(double a, double b, double R, double* rho_c, double* T_c) {
+// Peng-Robinson (Eq. 14-15) with x = b rho, D = 1 + 2x - x^2:
+//   p0 = rho R T / (1 - x) - a alpha rho^2 / D,   dp0/drho = R T / (1 - x)^2 - 2 a alpha rho (1 + x) / D^2.
+// Critical point (alpha = 1): with h(x) = x^2 / D, p0' = p0'' = 0 give
+// 2 h'(x) = (1 - x) h''(x) and R T_c = (a / b) (1 - x)^2 h'(x).
+static double pr_hp(double x) {  // h'
+  const double D = 1.0 + x * (2.0 - x);
+  return 2.0 * x * (1.0 + x) / (D * D);
+}
+static double pr_hpp(double x) {  // h''
+  const double D = 1.0 + x * (2.0 - x);
+  return (2.0 * (1.0 + 2.0 * x) * D - 8.0 * x * (1.0 + x) * (1.0 - x)) / (D * D * D);
+}
+static double pr_kappa(double w) { return 0.37464 + w * (1.54226 - 0.26992 * w); }
+
+namespace {
+struct HostEos {
+  int kind = LBM_EOS_CS;
+  double a = 0, b = 0, R = 0, T = 0, aa = 0;  // aa = a alpha(T) (PR)
+  double rc = 0, Tc = 0, rmax = 0;
+
+  double p(double rho) const {
+    if (kind == LBM_EOS_PR) {
+      const double x = b * rho;
+      return rho * R * T / (1.0 - x) - aa * rho * rho / (1.0 + x * (2.0 - x));
+    }
+    const double e = 0.25 * b * rho, q = 1.0 - e;
+    return rho * R * T * (1.0 + e * (1.0 + e * (1.0 - e))) / (q * q * q) - a * rho * rho;
+  }
+  double dp(double rho) const {
+    if (kind == LBM_EOS_PR) {
+      const double x = b * rho, D = 1.0 + x * (2.0 - x);
+      return R * T / ((1.0 - x) * (1.0 - x)) - 2.0 * aa * rho * (1.0 + x) / (D * D);
+    }
+    return R * T * cs_c1(0.25 * b * rho) - 2.0 * a * rho;
+  }
+  double mu(double rho) const {  // psi'(rho), additive constant dropped
+    if (kind == LBM_EOS_PR) {
+      const double x = b * rho, s2 = std::sqrt(2.0);
+      return R * T * (std::log(rho / (1.0 - x)) + 1.0 / (1.0 - x)) -
+             aa / (2.0 * s2 * b) * std::log((s2 - 1.0 + x) / (s2 + 1.0 - x)) - aa * rho / (1.0 + x * (2.0 - x));
+    }
+    const double e = 0.25 * b * rho, q = 1.0 - e;
+    return R * T * (std::log(rho) + e * (8.0 + e * (-9.0 + 3.0 * e)) / (q * q * q)) - 2.0 * a * rho;
+  }
+};
+
+int eos_critical(int kind, double a, double b, double R, double* rho_c, double* T_c) {
   if (!(a > 0 && b > 0 && R > 0) || !rho_c || !T_c) return LBM_EINVAL;
+  if (kind == LBM_EOS_PR) {
+    double lo = 1e-8, hi = 0.9;
+    for (int it = 0; it < 200; ++it) {
+      const double m = 0.5 * (lo + hi);
+      if ((1.0 - m) * pr_hpp(m) - 2.0 * pr_hp(m) > 0) lo = m; else hi = m;
+    }
+    const double x = 0.5 * (lo + hi);
+    *rho_c = x / b;
+    *T_c = (a / b) * (1.0 - x) * (1.0 - x) * pr_hp(x) / R;
+    return LBM_OK;
+  }
+  if (kind != LBM_EOS_CS) return LBM_EINVAL;
   // dp0/drho = 0 and d2p0/drho2 = 0  <=>  C1(eta) = eta C1'(eta);  R T_c = 8 a / (b C1'(eta_c))
   double lo = 1e-8, hi = 0.5;
   for (int it = 0; it < 200; ++it) {
@@ -101,48 +148,62 @@ extern "C" int lbm_critical(double a, double b, double R, double* rho_c, double*
   return LBM_OK;
 }
 
+int make_eos(const lbm_params* p, HostEos* e) {
+  if (!p || (p->eos != LBM_EOS_CS && p->eos != LBM_EOS_PR)) return LBM_EINVAL;
+  if (eos_critical(p->eos, p->a, p->b, p->R, &e->rc, &e->Tc) != LBM_OK) return LBM_EINVAL;
+  e->kind = p->eos; e->a = p->a; e->b = p->b; e->R = p->R; e->T = p->Tr * e->Tc;
+  if (p->eos == LBM_EOS_PR) {
+    const double s = 1.0 + pr_kappa(p->acentric) * (1.0 - std::sqrt(p->Tr));
+    e->aa = p->a * s * s;
+    e->rmax = 1.0 / p->b;
+  } else {
+    e->aa = p->a;
+    e->rmax = 4.0 / p->b;
+  }
+  return LBM_OK;
+}
+
 // Coexistence by bisection on the common chemical potential m: on the gas
-// branch (0, spinodal_g) and the liquid branch (spinodal_l, 4/b) mu is
+// branch (0, spinodal_g) and the liquid branch (spinodal_l, rho_max) mu is
 // increasing in rho, so each branch has one root of mu = m; by Gibbs-Duhem
 // (dp = rho dmu) p_gas(m) - p_liq(m) decreases with m, which brackets the
 // equal-pressure level.
-static int maxwell_T(double a, double b, double R, double T, double* rg, double* rl) {
-  double rc, Tc;
-  if (lbm_critical(a, b, R, &rc, &Tc) != LBM_OK) return LBM_EINVAL;
-  if (!(T > 0 && T < Tc)) return LBM_EINVAL;
+int maxwell_eos(const HostEos& E, double* rg, double* rl) {
+  const double rc = E.rc;
+  if (!(E.T > 0 && E.T < E.Tc)) return LBM_EINVAL;
   double lo = std::log(rc) - 800.0, hi = std::log(rc);  // ln rho on the gas side
   for (int it = 0; it < 400; ++it) {
     const double m = 0.5 * (lo + hi);
-    if (cs_dp(std::exp(m), a, b, R, T) > 0) lo = m; else hi = m;
+    if (E.dp(std::exp(m)) > 0) lo = m; else hi = m;
   }
   const double sg = std::exp(lo);
-  lo = rc; hi = 4.0 / b;
+  lo = rc; hi = E.rmax;
   for (int it = 0; it < 400; ++it) {
     const double m = 0.5 * (lo + hi);
-    if (cs_dp(m, a, b, R, T) < 0) lo = m; else hi = m;
+    if (E.dp(m) < 0) lo = m; else hi = m;
   }
   const double sl = hi;
   auto gas = [&](double m) {
     double l = std::log(rc) - 800.0, u = std::log(sg);
     for (int it = 0; it < 400; ++it) {
       const double c = 0.5 * (l + u);
-      if (cs_mub(std::exp(c), a, b, R, T) < m) l = c; else u = c;
+      if (E.mu(std::exp(c)) < m) l = c; else u = c;
     }
     return std::exp(0.5 * (l + u));
   };
   auto liq = [&](double m) {
-    double l = sl, u = 4.0 / b;
+    double l = sl, u = E.rmax;
     for (int it = 0; it < 400; ++it) {
       const double c = 0.5 * (l + u);
-      if (cs_mub(c, a, b, R, T) < m) l = c; else u = c;
+      if (E.mu(c) < m) l = c; else u = c;
     }
     return 0.5 * (l + u);
   };
-  double mlo = cs_mub(sl, a, b, R, T), mhi = cs_mub(sg, a, b, R, T);
+  double mlo = E.mu(sl), mhi = E.mu(sg);
   for (int it = 0; it < 200; ++it) {
     const double m = 0.5 * (mlo + mhi);
     const double g = gas(m), l = liq(m);
-    if (cs_p(g, a, b, R, T) - cs_p(l, a, b, R, T) > 0) mlo = m; else mhi = m;
+    if (E.p(g) - E.p(l) > 0) mlo = m; else mhi = m;
     if (mhi - mlo <= 1e-17 * std::fabs(m)) break;
   }
   const double m = 0.5 * (mlo + mhi);
@@ -150,12 +211,45 @@ static int maxwell_T(double a, double b, double R, double T, double* rg, double*
   *rl = liq(m);
   return LBM_OK;
 }
+}  // namespace
+
+int lbmd::params_to_kp(const lbm_params* p, KParams* kp) {
+  HostEos E;
+  if (make_eos(p, &E) != LBM_OK) return LBM_EINVAL;
+  *kp = KParams{};
+  kp->nx = p->nx; kp->ny = p->ny; kp->nz = p->nz;
+  kp->n = (long long)p->nx * p->ny * p->nz;
+  kp->RT = p->R * E.T; kp->b4 = 0.25 * p->b; kp->two_a = 2.0 * p->a;
+  kp->eos = p->eos == LBM_EOS_PR ? 1 : 0;
+  kp->aa = p->eos == LBM_EOS_PR ? E.aa : 0.0;
+  kp->c1 = p->eos == LBM_EOS_PR ? E.aa / (2.0 * std::sqrt(2.0) * p->b) : 0.0;
+  kp->k2 = p->k * p->k; kp->kappa = p->kappa; kp->omega = 1.0 / p->tau;
+  kp->rho_ref = 0.0;
+  if (p->precision == LBM_FP32DEV) {
+    kp->rho_ref = p->rho_ref;
+    if (!(kp->rho_ref > 0)) {
+      double g, l;
+      if (maxwell_eos(E, &g, &l) != LBM_OK) return LBM_EINVAL;
+      kp->rho_ref = g;
+    }
+  }
+  return LBM_OK;
+}
+
+extern "C" int lbm_critical(double a, double b, double R, double* rho_c, double* T_c) {
+  return eos_critical(LBM_EOS_CS, a, b, R, rho_c, T_c);
+}
+
+extern "C" int lbm_eos_critical(const lbm_params* p, double* rho_c, double* T_c) {
+  if (!p) return LBM_EINVAL;
+  return eos_critical(p->eos, p->a, p->b, p->R, rho_c, T_c);
+}
 
 extern "C" int lbm_maxwell(const lbm_params* p, double* rho_g, double* rho_l) {
   if (!p || !rho_g || !rho_l) return LBM_EINVAL;
-  double rc, Tc;
-  if (lbm_critical(p->a, p->b, p->R, &rc, &Tc) != LBM_OK) return LBM_EINVAL;
-  return maxwell_T(p->a, p->b, p->R, p->Tr * Tc, rho_g, rho_l);
+  HostEos E;
+  if (make_eos(p, &E) != LBM_OK) return LBM_EINVAL;
+  return maxwell_eos(E, rho_g, rho_l);
 }
 
 extern "C" int lbm_lattice_q(int lattice) { return lattice == LBM_D2Q9 ? 9 : (lattice == LBM_D3Q19 ? 19 : 0); }
@@ -342,7 +436,8 @@ static int validate(const lbm_params* p) {
   if (p->lattice == LBM_D2Q9 && p->nz != 1) return LBM_EINVAL;
   if (p->lattice == LBM_D3Q19 && p->nz < 8) return LBM_EINVAL;
   if ((long long)p->nx * p->ny * p->nz > (1LL << 31) / 19) return LBM_EINVAL;
-  if (p->eos != LBM_EOS_CS) return LBM_EINVAL;
+  if (p->eos != LBM_EOS_CS && p->eos != LBM_EOS_PR) return LBM_EINVAL;
+  if (p->eos == LBM_EOS_PR && !(p->Tr < 1.0 && p->acentric > -1.0)) return LBM_EINVAL;
   if (!(p->a > 0 && p->b > 0 && p->R > 0 && p->Tr > 0)) return LBM_EINVAL;
   if (!(p->k > 0) || !(p->kappa >= 0) || !(p->tau > 0.5)) return LBM_EINVAL;
   if (p->scheme < LBM_EFDS2 || p->scheme > LBM_E8) return LBM_EINVAL;
@@ -373,25 +468,11 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
     h->alloc.ctx = nullptr;
     h->own_alloc = true;
   }
-  double rc_, Tc;
-  lbm_critical(params->a, params->b, params->R, &rc_, &Tc);
-  const double T = params->Tr * Tc;
-  double rho_ref = 0.0;
-  if (params->precision == LBM_FP32DEV) {
-    rho_ref = params->rho_ref;
-    if (!(rho_ref > 0)) {
-      double rg, rl;
-      if (maxwell_T(params->a, params->b, params->R, T, &rg, &rl) != LBM_OK) { delete h; return LBM_EINVAL; }
-      rho_ref = rg;
-    }
-  }
+  if (params_to_kp(params, &h->kp) != LBM_OK) { delete h; return LBM_EINVAL; }
+  const double rho_ref = h->kp.rho_ref;
   h->prec = params->precision == LBM_FP64 ? 0 : (params->mu_fp64 ? 2 : 1);
   h->mrt = make_mrt(params->collision == LBM_MRT, params->mrt_s, params->tau);
   h->compact = (params->scheme >= LBM_CFDS4 && params->scheme <= LBM_OCFDS4);
-  h->kp.nx = params->nx; h->kp.ny = params->ny; h->kp.nz = params->nz; h->kp.n = h->N;
-  h->kp.RT = params->R * T; h->kp.b4 = 0.25 * params->b; h->kp.two_a = 2.0 * params->a;
-  h->kp.k2 = params->k * params->k; h->kp.kappa = params->kappa; h->kp.omega = 1.0 / params->tau;
-  h->kp.rho_ref = rho_ref;
   h->p.rho_ref = rho_ref;
   if (h->compact) {
     h->fn = nullptr;

@@ -76,6 +76,8 @@ struct KParams {
   double k2, kappa;       // k^2 and kappa-hat (Eq. 16)
   double omega;           // 1/tau
   double rho_ref;         // FP32DEV reference density (0 in FP64 mode)
+  int eos;                // 0: Carnahan-Starling, 1: Peng-Robinson (Eq. 14-15)
+  double aa, c1;          // Peng-Robinson: a alpha(T) and a alpha(T) / (2 sqrt2 b)
 };
 
 struct StepAux {
@@ -96,6 +98,47 @@ __device__ __forceinline__ T cs_mu(T rho, T RT, T b4, T two_a) {
   T om = T(1) - eta;
   T hs = eta * (T(8) + eta * (T(-9) + T(3) * eta)) / (om * om * om);
   return RT * (lg(rho) + hs) - two_a * rho;
+}
+
+// Bulk chemical potential of the Peng-Robinson fluid, Eq. 15 without the
+// kappa term: with x = b rho,
+//   R T [ln(rho / (1 - x)) + 1 / (1 - x)] - c1 ln((sqrt2 - 1 + x) / (sqrt2 + 1 - x)) - a alpha rho / (1 + 2x - x^2),
+// c1 = a alpha / (2 sqrt2 b).
+template <typename T>
+__device__ __forceinline__ T pr_mu(T rho, T RT, T b, T aa, T c1) {
+  const T x = b * rho, om = T(1) - x;
+  const T s2 = T(1.4142135623730950488);
+  return RT * (lg(rho / om) + T(1) / om) - c1 * lg((s2 - T(1) + x) / (s2 + T(1) - x)) -
+         aa * rho / (T(1) + x * (T(2) - x));
+}
+
+// psi'(rho) of the case's EOS (Eq. 10, 13-15), additive constant dropped
+template <typename T>
+__device__ __forceinline__ T eos_mu(T rho, const KParams& p) {
+  if (p.eos == 1) return pr_mu<T>(rho, T(p.RT), T(4.0 * p.b4), T(p.aa), T(p.c1));
+  return cs_mu<T>(rho, T(p.RT), T(p.b4), T(p.two_a));
+}
+
+// FP32 form with the hardware logarithm and division approximations, for the
+// FP32-deviation kernels; the constants converted once per thread
+struct EosF {
+  int eos;
+  float RT, b4, two_a, b, aa, c1;
+};
+__device__ __forceinline__ EosF eos_f(const KParams& p) {
+  return EosF{p.eos, float(p.RT), float(p.b4), float(p.two_a), float(4.0 * p.b4), float(p.aa), float(p.c1)};
+}
+__device__ __forceinline__ float eos_mu_f(float rho, const EosF& e) {
+  if (e.eos == 1) {
+    const float x = e.b * rho, om = 1.f - x;
+    const float iom = __fdividef(1.f, om);
+    return e.RT * (__logf(rho * iom) + iom) -
+           e.c1 * __logf(__fdividef(0.41421356f + x, 2.41421356f - x)) -
+           __fdividef(e.aa * rho, 1.f + x * (2.f - x));
+  }
+  const float eta = e.b4 * rho, om = 1.f - eta;
+  const float hs = __fdividef(eta * (8.f + eta * (-9.f + 3.f * eta)), om * om * om);
+  return e.RT * (__logf(rho) + hs) - e.two_a * rho;
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }

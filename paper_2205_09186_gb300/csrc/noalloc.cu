@@ -82,22 +82,8 @@ extern "C" int lbm_observables_noalloc(const lbm_params* p, const void* d_f, con
   StepFn fn = d3 ? step3d_fn(p->scheme, prec) : step2d_fn(p->scheme, prec);
   if (!fn) return LBM_ENOTSUP;
 
-  double rc, Tc;
-  if (lbm_critical(p->a, p->b, p->R, &rc, &Tc) != LBM_OK) return LBM_EINVAL;
-  KParams kp{};
-  kp.nx = p->nx; kp.ny = p->ny; kp.nz = p->nz;
-  kp.n = (long long)p->nx * p->ny * p->nz;
-  kp.RT = p->R * p->Tr * Tc; kp.b4 = 0.25 * p->b; kp.two_a = 2.0 * p->a;
-  kp.k2 = p->k * p->k; kp.kappa = p->kappa; kp.omega = 1.0 / p->tau;
-  kp.rho_ref = 0.0;
-  if (p->precision == LBM_FP32DEV) {
-    kp.rho_ref = p->rho_ref;
-    if (!(kp.rho_ref > 0)) {
-      double g, l;
-      if (lbm_maxwell(p, &g, &l) != LBM_OK) return LBM_EINVAL;
-      kp.rho_ref = g;
-    }
-  }
+  KParams kp;
+  if (params_to_kp(p, &kp) != LBM_OK) return LBM_EINVAL;
   const long long nctas = d3 ? step3d_obs_ctas(kp) : step2d_obs_ctas(kp);
   if (nctas > kMaxCtas) return LBM_ESCRATCH;
 

@@ -113,13 +113,13 @@ __device__ __forceinline__ void step2d_tile(const KParams& p, const typename P::
   // 2. mu = k^2 psi'(rho) - kappa lap(rho) on tile + halo R+1 (Eq. 16)
   if constexpr (!Sch<S>::GF) {
     const int mw = VW + 2 * R + 2, mh = VH + 2 * R + 2;
-    const Tm RT = Tm(p.RT), b4 = Tm(p.b4), two_a = Tm(p.two_a), k2 = Tm(p.k2), kap = Tm(p.kappa);
+    const Tm k2 = Tm(p.k2), kap = Tm(p.kappa);
     for (int idx = tid; idx < mw * mh; idx += NT2) {
       const int my = idx / mw, mx = idx - my * mw;
       const int sx = mx + (H - R - 1), sy = my + (H - R - 1);
       const Tm rho = P::DEV ? Tm(p.rho_ref) + Tm(s_ds[sy * RW + sx]) : Tm(s_ds[sy * RW + sx]);
       const Tm lap = lap2d<S, Tm>(s_ds, RW, sx, sy);
-      s_mu[my * MW + mx] = k2 * cs_mu<Tm>(rho, RT, b4, two_a) - kap * lap;
+      s_mu[my * MW + mx] = k2 * eos_mu<Tm>(rho, p) - kap * lap;
     }
   }
   __syncthreads();

@@ -65,12 +65,10 @@ __device__ __forceinline__ void mu2d_compute(const KParams& p, float* __restrict
   const int nx = p.nx, ny = p.ny;
   const int tx = threadIdx.x % M2X, ty = threadIdx.x / M2X;
   if (x0 + tx < nx && y0 + ty < ny) {
-    const float RT = float(p.RT), b4 = float(p.b4), two_a = float(p.two_a), k2 = float(p.k2), kap = float(p.kappa);
+    const float k2 = float(p.k2), kap = float(p.kappa);
     const float rho = float(p.rho_ref) + s[(ty + R) * MW + tx + R];
-    const float eta = b4 * rho, om = 1.f - eta;
-    const float hs = __fdividef(eta * (8.f + eta * (-9.f + 3.f * eta)), om * om * om);
     const float lap = lap2d<S, float>(s, MW, tx + R, ty + R);
-    mu[(y0 + ty) * nx + x0 + tx] = k2 * (RT * (__logf(rho) + hs) - two_a * rho) - kap * lap;
+    mu[(y0 + ty) * nx + x0 + tx] = k2 * eos_mu_f(rho, eos_f(p)) - kap * lap;
   }
 }
 

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
   const int VW = min(TX, nx - x0), VH = min(TY, ny - y0);
   const int tid = threadIdx.x;
   const int rw = VW + 2 * H, rh = VH + 2 * H, mw = VW + 2 * R + 2, mh = VH + 2 * R + 2, cw = VW + 2, ch = VH + 2;
-  const Tm RT = Tm(p.RT), b4 = Tm(p.b4), two_a = Tm(p.two_a), k2 = Tm(p.k2), kap = Tm(p.kappa);
+  const Tm k2 = Tm(p.k2), kap = Tm(p.kappa);
   const Tc omega = Tc(p.omega);
 
   // per-thread accumulators of the next density for target planes p-1, p, p+1
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NT3) k_step3d(const KParams p, const typename 
         const int mx = rx - (H - R - 1), my = ry - (H - R - 1);
         if constexpr (!Sch<S>::GF)
           if (mx >= 0 && mx < mw && my >= 0 && my < mh)
-            mup[my * MW + mx] = k2 * cs_mu<Tm>(P::DEV ? Tm(p.rho_ref) + Tm(v) : Tm(v), RT, b4, two_a);
+            mup[my * MW + mx] = k2 * eos_mu<Tm>(P::DEV ? Tm(p.rho_ref) + Tm(v) : Tm(v), p);
       }
     }
     __syncthreads();

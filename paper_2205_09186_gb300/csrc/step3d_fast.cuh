@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(FNT, 2) k_step3d_fast(const KParams p, const f
   const int ty = tid / FT, tx = tid - ty * FT;
   const bool gnode = tid < FT * FT && tx < VW && ty < VH;
 
-  const float RT = float(p.RT), b4 = float(p.b4), two_a = float(p.two_a), k2 = float(p.k2), kap = float(p.kappa);
+  const float k2 = float(p.k2), kap = float(p.kappa);
+  const EosF ef = eos_f(p);
   const float omega = float(p.omega), rref = float(p.rho_ref);
 
   const int pc_first = z0 - 1, pc_last = z1;
@@ -128,9 +129,7 @@ __global__ void __launch_bounds__(FNT, 2) k_step3d_fast(const KParams p, const f
         if (idx < MW * MW && mx < VW + 2 * R + 2 && my < VH + 2 * R + 2) {
           const int sx = mx + (H - R - 1), sy = my + (H - R - 1);
           const float rho = rref + s_ds[base[R] + sy * RW + sx];
-          const float eta = b4 * rho, om = 1.f - eta;
-          const float hs = __fdividef(eta * (8.f + eta * (-9.f + 3.f * eta)), om * om * om);
-          const float mub = RT * (__logf(rho) + hs) - two_a * rho;
+          const float mub = eos_mu_f(rho, ef);
           mup[idx] = k2 * mub - kap * lap3d<S, float>(s_ds, base, RW, sx, sy);
         }
       }

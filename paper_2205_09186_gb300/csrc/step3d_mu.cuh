@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __re
   __syncthreads();
   const int tx = threadIdx.x % MUX, ty = threadIdx.x / MUX;
   if (x0 + tx >= nx || y0 + ty >= ny) return;
-  const float RT = float(p.RT), b4 = float(p.b4), two_a = float(p.two_a), k2 = float(p.k2), kap = float(p.kappa);
+  const float k2 = float(p.k2), kap = float(p.kappa);
+  const EosF ef = eos_f(p);
   const float rref = float(p.rho_ref);
   const int cx = tx + R, cy = ty + R;
   float q[2 * R + 1];  // q[R + d]: density deviation at plane z + d of this column
@@ -72,10 +73,7 @@ __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __re
       for (int m = 1; m <= R; ++m)
         lap += float(Sch<S>::l(m)) * ((blk[pz][cy][cx + m] + blk[pz][cy][cx - m]) +
                                       (blk[pz][cy + m][cx] + blk[pz][cy - m][cx]) + (q[R + m] + q[R - m]));
-      const float rho = rref + c;
-      const float eta = b4 * rho, om = 1.f - eta;
-      const float hs = __fdividef(eta * (8.f + eta * (-9.f + 3.f * eta)), om * om * om);
-      out[dz * NXY] = k2 * (RT * (__logf(rho) + hs) - two_a * rho) - kap * lap;
+      out[dz * NXY] = k2 * eos_mu_f(rref + c, ef) - kap * lap;
     }
   }
 }
@@ -120,7 +118,8 @@ __global__ void __launch_bounds__(MVT) k_mu3d_v4(const KParams p, const float* _
   __syncthreads();
   const int tx = tid % (MVX / 4), ty = tid / (MVX / 4);
   if (x0 + 4 * tx >= nx || y0 + ty >= ny) return;  // nx % 4 == 0: all four nodes or none
-  const float RT = float(p.RT), b4 = float(p.b4), two_a = float(p.two_a), k2 = float(p.k2), kap = float(p.kappa);
+  const float k2 = float(p.k2), kap = float(p.kappa);
+  const EosF ef = eos_f(p);
   const float rref = float(p.rho_ref);
   const int cy = ty + R;
   auto at = [&](int rz, int ry, int j) { return blk4[(rz * PH + ry) * NCH + j]; };
@@ -155,10 +154,7 @@ __global__ void __launch_bounds__(MVT) k_mu3d_v4(const KParams p, const float* _
 #pragma unroll
         for (int m = 1; m <= R; ++m)
           lap[k] += float(Sch<S>::l(m)) * ((row[4 + k + m] + row[4 + k - m]) + yz[k][m - 1]);
-        const float rho = rref + cv;
-        const float eta = b4 * rho, om = 1.f - eta;
-        const float hs = __fdividef(eta * (8.f + eta * (-9.f + 3.f * eta)), om * om * om);
-        res[k] = k2 * (RT * (__logf(rho) + hs) - two_a * rho) - kap * lap[k];
+        res[k] = k2 * eos_mu_f(rref + cv, ef) - kap * lap[k];
       }
       *reinterpret_cast<float4*>(out + dz * NXY) = make_float4(res[0], res[1], res[2], res[3]);
     }

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOTSUP, LBM_ESCRATCH = (
     0, -1, -2, -3, -4, -5, -6, -7)
 LBM_D2Q9, LBM_D3Q19 = 0, 1
-LBM_EOS_CS = 0
+LBM_EOS_CS, LBM_EOS_PR = 0, 1
 SCHEMES = {"EFDS2": 0, "EFDS4": 1, "EFDS6": 2, "CFDS4": 3, "CFDS6": 4, "CFDS8": 5, "OCFDS4": 6, "E4": 7, "E8": 8}
 LBM_FP64, LBM_FP32DEV = 0, 1
 LBM_BGK, LBM_MRT = 0, 1
@@ -27,7 +27,7 @@ class lbm_params(C.Structure):
                 ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("Tr", C.c_double),
                 ("k", C.c_double), ("kappa", C.c_double), ("tau", C.c_double),
                 ("scheme", C.c_int), ("precision", C.c_int), ("mu_fp64", C.c_int), ("rho_ref", C.c_double),
-                ("collision", C.c_int), ("mrt_s", C.c_double * 9)]
+                ("collision", C.c_int), ("mrt_s", C.c_double * 9), ("acentric", C.c_double)]
 
 
 class lbm_obs(C.Structure):
@@ -71,6 +71,7 @@ SIGNATURES = {
     "lbm_device_state": (C.c_int, [_h, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "lbm_critical": (C.c_int, [C.c_double, C.c_double, C.c_double, _dp, _dp]),
     "lbm_maxwell": (C.c_int, [C.POINTER(lbm_params), _dp, _dp]),
+    "lbm_eos_critical": (C.c_int, [C.POINTER(lbm_params), _dp, _dp]),
     "lbm_lattice_q": (C.c_int, [C.c_int]),
     "lbm_set_zchunk": (C.c_int, [_h, C.c_int]),
     "lbm_autotune": (C.c_int, [_h, C.POINTER(C.c_int)]),
@@ -138,13 +139,16 @@ def _f64(a):
 
 
 def make_params(lattice=LBM_D2Q9, nx=64, ny=64, nz=1, a=1.0, b=4.0, R=1.0, Tr=0.7, k=0.25, kappa=0.1, tau=1.0,
-                scheme="EFDS2", precision=LBM_FP64, mu_fp64=0, rho_ref=0.0, collision=LBM_BGK, mrt_s=None):
-    """collision: LBM_BGK / LBM_MRT or "BGK" / "MRT"; mrt_s None = the paper's rates."""
+                scheme="EFDS2", precision=LBM_FP64, mu_fp64=0, rho_ref=0.0, collision=LBM_BGK, mrt_s=None,
+                eos=LBM_EOS_CS, acentric=0.344):
+    """collision: LBM_BGK / LBM_MRT or "BGK" / "MRT"; mrt_s None = the paper's rates;
+    eos: LBM_EOS_CS / LBM_EOS_PR or "CS" / "PR" (then a, b, R are the PR constants)."""
+    e = {"CS": LBM_EOS_CS, "PR": LBM_EOS_PR}[eos] if isinstance(eos, str) else int(eos)
     s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     col = {"BGK": LBM_BGK, "MRT": LBM_MRT}[collision] if isinstance(collision, str) else int(collision)
     rates = (C.c_double * 9)(*(mrt_s if mrt_s is not None else [0.0] * 9))
-    return lbm_params(lattice, nx, ny, nz, LBM_EOS_CS, a, b, R, Tr, k, kappa, tau, s, precision, int(mu_fp64), rho_ref,
-                      col, rates)
+    return lbm_params(lattice, nx, ny, nz, e, a, b, R, Tr, k, kappa, tau, s, precision, int(mu_fp64), rho_ref,
+                      col, rates, acentric)
 
 
 def lbm_observables_noalloc(params, d_f, d_rho, d_rho_prev=None, steps_since_prev=0, step=0, stream=None):
@@ -161,6 +165,12 @@ def lbm_observables_noalloc(params, d_f, d_rho, d_rho_prev=None, steps_since_pre
 def lbm_critical(a=1.0, b=4.0, R=1.0):
     rc, Tc = C.c_double(), C.c_double()
     check(lib().lbm_critical(a, b, R, C.byref(rc), C.byref(Tc)), "lbm_critical")
+    return rc.value, Tc.value
+
+
+def lbm_eos_critical(params):
+    rc, Tc = C.c_double(), C.c_double()
+    check(lib().lbm_eos_critical(C.byref(params), C.byref(rc), C.byref(Tc)), "lbm_eos_critical")
     return rc.value, Tc.value
 
 

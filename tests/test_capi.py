@@ -49,6 +49,15 @@ def test_host_only_entry_points(libpath):
         g, l = lbm.lbm_maxwell(lbm.make_params(Tr=tr))
         og, ol = O.maxwell_tr(tr)
         assert abs(g / og - 1) < 1e-9 and abs(l / ol - 1) < 1e-12
+    # Peng-Robinson (Eq. 14-15, the paper's a = 2/49, b = 2/21, acentric 0.344)
+    A, B = 2.0 / 49.0, 2.0 / 21.0
+    rc, Tc = lbm.lbm_eos_critical(lbm.make_params(eos="PR", a=A, b=B, Tr=0.7))
+    orc, oTc = O.pr_critical(A, B, 1.0)
+    assert abs(rc / orc - 1) < 1e-12 and abs(Tc / oTc - 1) < 1e-12
+    for tr in (0.9, 0.7, 0.5):
+        g, l = lbm.lbm_maxwell(lbm.make_params(eos="PR", a=A, b=B, Tr=tr))
+        og, ol = O.eos_maxwell(O.eos_make(O.EOS_PR, A, B, 1.0, tr, 0.344))
+        assert abs(g / og - 1) < 1e-9 and abs(l / ol - 1) < 1e-12
     assert lbm.lib().lbm_lattice_q(0) == 9 and lbm.lib().lbm_lattice_q(1) == 19
     assert lbm.lib().lbm_strerror(-4).decode().startswith("simulation unstable")
 
