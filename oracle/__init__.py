@@ -74,6 +74,7 @@ def lib():
         L.or_pr_alpha.argtypes = [C.c_double] * 3
         L.or_pr_alpha.restype = C.c_double
         L.or_pr_critical.argtypes = [C.c_double] * 3 + [_dp, _dp]
+        L.or_cubic_critical.argtypes = [C.c_int] + [C.c_double] * 3 + [_dp, _dp]
         L.or_mrt_matrix.argtypes = [_dp]
         L.or_mrt_matrix.restype = None
         L.or_mrt_inverse.argtypes = [_dp]
@@ -196,7 +197,7 @@ def lattice(lat):
 
 
 BGK, MRT = 0, 1
-EOS_CS, EOS_PR = 0, 1
+EOS_CS, EOS_PR, EOS_VDW, EOS_RKS = 0, 1, 2, 3
 
 
 class Eos(C.Structure):
@@ -229,6 +230,13 @@ def eos_maxwell(e):
 
 def pr_alpha(T, Tc, acentric):
     return lib().or_pr_alpha(T, Tc, acentric)
+
+
+def cubic_critical(kind, a, b, R):
+    rc, Tc = C.c_double(), C.c_double()
+    if lib().or_cubic_critical(kind, a, b, R, C.byref(rc), C.byref(Tc)) != OK:
+        raise ValueError
+    return rc.value, Tc.value
 
 
 def pr_critical(a, b, R):
@@ -291,7 +299,7 @@ class Sim:
             mrt_s = mrt_rates(tau)
         self.p = Params(lattice, nx, ny, nz, a, b, R, Tr, k, kappa, tau, _scheme(scheme),
                         {"BGK": BGK, "MRT": MRT}[collision], (C.c_double * 9)(*mrt_s),
-                        {"CS": EOS_CS, "PR": EOS_PR}[eos], acentric)
+                        {"CS": EOS_CS, "PR": EOS_PR, "VDW": EOS_VDW, "RKS": EOS_RKS}[eos], acentric)
         self.h = lib().or_create(C.byref(self.p))
         if not self.h:
             raise ValueError("invalid oracle parameters")

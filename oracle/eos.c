@@ -198,32 +198,58 @@ int or_pr_critical(double a, double b, double R, double* rho_c, double* T_c) {
 }
 
 /* ---------------------------------------------------------------- EOS by kind */
+static double vdw_dpdrho(double rho, double a, double b, double R, double T) {
+  double om = 1.0 - b * rho;
+  return R * T / (om * om) - 2.0 * a * rho;
+}
+static double rks_dpdrho(double rho, double a, double b, double R, double T, double alpha) {
+  double br = b * rho, om = 1.0 - br, q = 1.0 + br;
+  return R * T / (om * om) - a * alpha * rho * (2.0 + br) / (q * q);
+}
+
 double or_eos_pressure(const or_eos* e, double rho) {
-  return e->kind == OR_EOS_PR ? or_pr_pressure(rho, e->a, e->b, e->R, e->T, e->alpha)
-                              : or_cs_pressure(rho, e->a, e->b, e->R, e->T);
+  switch (e->kind) {
+    case OR_EOS_PR: return or_pr_pressure(rho, e->a, e->b, e->R, e->T, e->alpha);
+    case OR_EOS_VDW: return or_vdw_pressure(rho, e->a, e->b, e->R, e->T);
+    case OR_EOS_RKS: return or_rks_pressure(rho, e->a, e->b, e->R, e->T, e->alpha);
+    default: return or_cs_pressure(rho, e->a, e->b, e->R, e->T);
+  }
 }
 
 double or_eos_mu(const or_eos* e, double rho) {
-  return e->kind == OR_EOS_PR ? or_pr_mu(rho, e->a, e->b, e->R, e->T, e->alpha)
-                              : or_cs_mu(rho, e->a, e->b, e->R, e->T);
+  switch (e->kind) {
+    case OR_EOS_PR: return or_pr_mu(rho, e->a, e->b, e->R, e->T, e->alpha);
+    case OR_EOS_VDW: return or_vdw_mu(rho, e->a, e->b, e->R, e->T);
+    case OR_EOS_RKS: return or_rks_mu(rho, e->a, e->b, e->R, e->T, e->alpha);
+    default: return or_cs_mu(rho, e->a, e->b, e->R, e->T);
+  }
 }
 
 static double eos_dpdrho(const or_eos* e, double rho) {
-  return e->kind == OR_EOS_PR ? pr_dpdrho(rho, e->a, e->b, e->R, e->T, e->alpha)
-                              : cs_dpdrho(rho, e->a, e->b, e->R, e->T);
+  switch (e->kind) {
+    case OR_EOS_PR: return pr_dpdrho(rho, e->a, e->b, e->R, e->T, e->alpha);
+    case OR_EOS_VDW: return vdw_dpdrho(rho, e->a, e->b, e->R, e->T);
+    case OR_EOS_RKS: return rks_dpdrho(rho, e->a, e->b, e->R, e->T, e->alpha);
+    default: return cs_dpdrho(rho, e->a, e->b, e->R, e->T);
+  }
 }
 
 int or_eos_critical(int kind, double a, double b, double R, double* rho_c, double* T_c) {
-  return kind == OR_EOS_PR ? or_pr_critical(a, b, R, rho_c, T_c) : or_cs_critical(a, b, R, rho_c, T_c);
+  switch (kind) {
+    case OR_EOS_PR: return or_pr_critical(a, b, R, rho_c, T_c);
+    case OR_EOS_VDW: case OR_EOS_RKS: return or_cubic_critical(kind, a, b, R, rho_c, T_c);
+    default: return or_cs_critical(a, b, R, rho_c, T_c);
+  }
 }
 
 int or_eos_make(int kind, double a, double b, double R, double Tr, double acentric, or_eos* e) {
   double rc, Tc;
-  if (kind != OR_EOS_CS && kind != OR_EOS_PR) return OR_EINVAL;
+  if (kind < OR_EOS_CS || kind > OR_EOS_RKS) return OR_EINVAL;
   if (or_eos_critical(kind, a, b, R, &rc, &Tc) != OR_OK) return OR_EINVAL;
   e->kind = kind; e->a = a; e->b = b; e->R = R; e->T = Tr * Tc; e->Tc = Tc; e->rho_c = rc;
-  e->alpha = kind == OR_EOS_PR ? or_pr_alpha(e->T, Tc, acentric) : 1.0;
-  e->rho_max = kind == OR_EOS_PR ? 1.0 / b : 4.0 / b;
+  e->alpha = kind == OR_EOS_PR ? or_pr_alpha(e->T, Tc, acentric)
+             : kind == OR_EOS_RKS ? or_rks_alpha(e->T, Tc, acentric) : 1.0;
+  e->rho_max = kind == OR_EOS_CS ? 4.0 / b : 1.0 / b;
   return OR_OK;
 }
 
@@ -266,5 +292,61 @@ int or_eos_maxwell(const or_eos* e, double* rho_g, double* rho_l) {
   *rho_g = rg;
   *rho_l = rl;
   if (!(fabs(or_eos_mu(e, rg) - or_eos_mu(e, rl)) < 1e-9)) return OR_EINVAL;
+  return OR_OK;
+}
+
+/* ---------------------------------------------------------------- van der Waals, Redlich-Kwong-Soave */
+/*
+ * Not printed by the paper; their chemical potentials follow from Eq. 13 the
+ * way Eq. 15 does for PR (psi = rho (int p0 / rho^2 drho + C), mu = psi'):
+ *   VDW  p0 = rho R T / (1 - b rho) - a rho^2
+ *        mu = R T [ln(rho / (1 - b rho)) + 1 / (1 - b rho)] - 2 a rho
+ *   RKS  p0 = rho R T / (1 - b rho) - a alpha rho^2 / (1 + b rho)
+ *        mu = R T [ln(rho / (1 - b rho)) + 1 / (1 - b rho)] - (a alpha / b) ln(1 + b rho) - a alpha rho / (1 + b rho)
+ *        alpha(T) = [1 + (0.480 + 1.574 w - 0.176 w^2)(1 - sqrt(T / T_c))]^2
+ * Critical points (p0' = p0'' = 0; RKS with alpha = 1) by bisection on x = b rho.
+ */
+double or_vdw_pressure(double rho, double a, double b, double R, double T) {
+  return rho * R * T / (1.0 - b * rho) - a * rho * rho;
+}
+double or_vdw_mu(double rho, double a, double b, double R, double T) {
+  double om = 1.0 - b * rho;
+  return R * T * (log(rho / om) + 1.0 / om) - 2.0 * a * rho;
+}
+double or_rks_alpha(double T, double Tc, double w) {
+  double s = 1.0 + (0.480 + 1.574 * w - 0.176 * w * w) * (1.0 - sqrt(T / Tc));
+  return s * s;
+}
+double or_rks_pressure(double rho, double a, double b, double R, double T, double alpha) {
+  double br = b * rho;
+  return rho * R * T / (1.0 - br) - a * alpha * rho * rho / (1.0 + br);
+}
+double or_rks_mu(double rho, double a, double b, double R, double T, double alpha) {
+  double br = b * rho, om = 1.0 - br;
+  return R * T * (log(rho / om) + 1.0 / om) - a * alpha / b * log(1.0 + br) - a * alpha * rho / (1.0 + br);
+}
+
+/* critical x = b rho from the attractive term h(x) (p0 = (R T / b) x / (1 - x) - (a / b^2) h):
+ * 2 h'(x) = (1 - x) h''(x); R T_c = (a / b) (1 - x)^2 h'(x).  h = x^2 (VDW) or x^2 / (1 + x) (RKS). */
+static void attr_derivs(int kind, double x, double* h1, double* h2) {
+  if (kind == OR_EOS_VDW) { *h1 = 2.0 * x; *h2 = 2.0; return; }
+  /* x^2 / (1 + x): h' = (2x + x^2) / (1 + x)^2, h'' = 2 / (1 + x)^3 */
+  double q = 1.0 + x;
+  *h1 = (2.0 * x + x * x) / (q * q);
+  *h2 = 2.0 / (q * q * q);
+}
+
+int or_cubic_critical(int kind, double a, double b, double R, double* rho_c, double* T_c) {
+  if (!(a > 0 && b > 0 && R > 0)) return OR_EINVAL;
+  double lo = 1e-6, hi = 0.9;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi), h1, h2;
+    attr_derivs(kind, mid, &h1, &h2);
+    if ((1.0 - mid) * h2 - 2.0 * h1 > 0) lo = mid; else hi = mid;
+  }
+  double x = 0.5 * (lo + hi), h1, h2;
+  attr_derivs(kind, x, &h1, &h2);
+  *rho_c = x / b;
+  *T_c = (a / b) * (1.0 - x) * (1.0 - x) * h1 / R;
   return OR_OK;
 }

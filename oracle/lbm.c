@@ -107,7 +107,7 @@ or_sim* or_create(const or_params* p) {
   if (!(p->tau > 0.5) || !(p->k > 0) || !(p->kappa >= 0) || !(p->Tr > 0)) return NULL;
   if (p->collision != OR_BGK && p->collision != OR_MRT) return NULL;
   if (p->collision == OR_MRT && p->lattice != OR_D2Q9) return NULL;
-  if (p->eos != OR_EOS_CS && p->eos != OR_EOS_PR) return NULL;
+  if (p->eos < OR_EOS_CS || p->eos > OR_EOS_RKS) return NULL;
   or_eos eos;
   if (or_eos_make(p->eos, p->a, p->b, p->R, p->Tr, p->acentric, &eos) != OR_OK) return NULL;
   or_sim* s = (or_sim*)calloc(1, sizeof(or_sim));

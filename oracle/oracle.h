@@ -56,7 +56,7 @@ typedef struct {
   int scheme;           /* OR_EFDS2 .. OR_E8 */
   int collision;        /* OR_BGK or OR_MRT */
   double mrt_s[9];      /* OR_MRT: s_1 .. s_9 of Eq. 5 */
-  int eos;              /* OR_EOS_CS or OR_EOS_PR */
+  int eos;              /* OR_EOS_CS, OR_EOS_PR, OR_EOS_VDW or OR_EOS_RKS */
   double acentric;      /* OR_EOS_PR: acentric factor of alpha(T) (Eq. 15) */
 } or_params;
 
@@ -89,6 +89,14 @@ int or_pr_critical(double a, double b, double R, double* rho_c, double* T_c);
 /* ---- an EOS of either kind at one temperature ---- */
 #define OR_EOS_CS 0
 #define OR_EOS_PR 1
+#define OR_EOS_VDW 2 /* van der Waals, mu by Eq. 13 */
+#define OR_EOS_RKS 3 /* Redlich-Kwong-Soave, mu by Eq. 13 */
+double or_vdw_pressure(double rho, double a, double b, double R, double T);
+double or_vdw_mu(double rho, double a, double b, double R, double T);
+double or_rks_alpha(double T, double Tc, double acentric);
+double or_rks_pressure(double rho, double a, double b, double R, double T, double alpha);
+double or_rks_mu(double rho, double a, double b, double R, double T, double alpha);
+int or_cubic_critical(int kind, double a, double b, double R, double* rho_c, double* T_c);
 typedef struct {
   int kind;
   double a, b, R, T, Tc, rho_c, alpha, rho_max;
