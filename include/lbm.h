@@ -51,6 +51,8 @@ extern "C" {
 
 #define LBM_EOS_CS 0 /* Carnahan-Starling */
 #define LBM_EOS_PR 1 /* Peng-Robinson, Eq. 14 with the chemical potential of Eq. 15 */
+#define LBM_EOS_VDW 2 /* van der Waals, chemical potential by Eq. 13 */
+#define LBM_EOS_RKS 3 /* Redlich-Kwong-Soave, chemical potential by Eq. 13 */
 
 /* difference schemes (Sec. 2.3) */
 #define LBM_EFDS2 0  /* Eq. 18, second-order central */
@@ -75,10 +77,12 @@ extern "C" {
  * Simulation parameters.
  *  lattice   LBM_D2Q9 (nz must be 1) or LBM_D3Q19
  *  nx,ny,nz  periodic lattice size; each >= 8 (D2Q9: nx, ny >= 8)
- *  eos       LBM_EOS_CS or LBM_EOS_PR
+ *  eos       LBM_EOS_CS, LBM_EOS_PR, LBM_EOS_VDW or LBM_EOS_RKS (VDW: p0 = rho R T /
+ *            (1 - b rho) - a rho^2; RKS: p0 = rho R T / (1 - b rho) - a alpha(T) rho^2 /
+ *            (1 + b rho), alpha = [1 + (0.480 + 1.574 w - 0.176 w^2)(1 - sqrt(Tr))]^2)
  *  a,b,R     CS constants: p0 = rho R T (1+eta+eta^2-eta^3)/(1-eta)^3 - a rho^2, eta = b rho/4;
  *            PR constants of Eq. 14 (the paper's: a = 2/49, b = 2/21, R = 1)
- *  Tr        reduced temperature T/T_c (T_c computed from a, b, R), 0 < Tr (PR: Tr < 1)
+ *  Tr        reduced temperature T/T_c (T_c computed from a, b, R), 0 < Tr (PR, RKS: Tr < 1)
  *  k         proportional coefficient of Eq. 16 (mu-hat = k^2 psi' - kappa lap rho)
  *  kappa     kappa-hat of Eq. 16
  *  tau       BGK relaxation time (> 0.5)
@@ -93,8 +97,8 @@ extern "C" {
  *            (rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy); all zero
  *            selects the paper's (1, 1.64, 1.54, 1, 1.7, 1, 1.7, 1/tau, 1/tau).
  *            The rates of the conserved moments (s_1, s_4, s_6) have no effect.
- *  acentric  LBM_EOS_PR: the acentric factor omega of alpha(T) (Eq. 15; the
- *            paper's water: 0.344)
+ *  acentric  LBM_EOS_PR, LBM_EOS_RKS: the acentric factor w of alpha(T) (Eq. 15;
+ *            the paper's water: 0.344)
  */
 typedef struct {
   int lattice;

@@ -418,7 +418,7 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
           q.scheme == LBM_E8))
       return LBM_ENOTSUP;
     if (q.collision != LBM_BGK && q.collision != LBM_MRT) return LBM_EINVAL;
-    if (q.eos != LBM_EOS_CS && q.eos != LBM_EOS_PR) return LBM_EINVAL;
+    if (q.eos < LBM_EOS_CS || q.eos > LBM_EOS_RKS) return LBM_EINVAL;
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_ENOMEM;

@@ -89,6 +89,21 @@ static double pr_hpp(double x) {  // h''
   return (2.0 * (1.0 + 2.0 * x) * D - 8.0 * x * (1.0 + x) * (1.0 - x)) / (D * D * D);
 }
 static double pr_kappa(double w) { return 0.37464 + w * (1.54226 - 0.26992 * w); }
+static double rks_kappa(double w) { return 0.480 + w * (1.574 - 0.176 * w); }
+
+// van der Waals and Redlich-Kwong-Soave share the repulsive term; their
+// attractive terms h(x) = x^2 (VDW) and x^2 / (1 + x) (RKS) give the critical
+// point the same way as PR: 2 h'(x) = (1 - x) h''(x), R T_c = (a / b) (1 - x)^2 h'(x).
+static double cubic_hp(int kind, double x) {
+  if (kind == LBM_EOS_VDW) return 2.0 * x;
+  if (kind == LBM_EOS_RKS) return x * (2.0 + x) / ((1.0 + x) * (1.0 + x));
+  return pr_hp(x);
+}
+static double cubic_hpp(int kind, double x) {
+  if (kind == LBM_EOS_VDW) return 2.0;
+  if (kind == LBM_EOS_RKS) return 2.0 / ((1.0 + x) * (1.0 + x) * (1.0 + x));
+  return pr_hpp(x);
+}
 
 namespace {
 struct HostEos {
@@ -97,6 +112,10 @@ struct HostEos {
   double rc = 0, Tc = 0, rmax = 0;
 
   double p(double rho) const {
+    if (kind == LBM_EOS_VDW || kind == LBM_EOS_RKS) {
+      const double x = b * rho;
+      return rho * R * T / (1.0 - x) - aa * rho * rho / (kind == LBM_EOS_RKS ? 1.0 + x : 1.0);
+    }
     if (kind == LBM_EOS_PR) {
       const double x = b * rho;
       return rho * R * T / (1.0 - x) - aa * rho * rho / (1.0 + x * (2.0 - x));
@@ -105,6 +124,11 @@ struct HostEos {
     return rho * R * T * (1.0 + e * (1.0 + e * (1.0 - e))) / (q * q * q) - a * rho * rho;
   }
   double dp(double rho) const {
+    if (kind == LBM_EOS_VDW) return R * T / ((1.0 - b * rho) * (1.0 - b * rho)) - 2.0 * aa * rho;
+    if (kind == LBM_EOS_RKS) {
+      const double x = b * rho;
+      return R * T / ((1.0 - x) * (1.0 - x)) - aa * rho * (2.0 + x) / ((1.0 + x) * (1.0 + x));
+    }
     if (kind == LBM_EOS_PR) {
       const double x = b * rho, D = 1.0 + x * (2.0 - x);
       return R * T / ((1.0 - x) * (1.0 - x)) - 2.0 * aa * rho * (1.0 + x) / (D * D);
@@ -112,6 +136,11 @@ struct HostEos {
     return R * T * cs_c1(0.25 * b * rho) - 2.0 * a * rho;
   }
   double mu(double rho) const {  // psi'(rho), additive constant dropped
+    if (kind == LBM_EOS_VDW || kind == LBM_EOS_RKS) {
+      const double x = b * rho, rep = R * T * (std::log(rho / (1.0 - x)) + 1.0 / (1.0 - x));
+      if (kind == LBM_EOS_VDW) return rep - 2.0 * aa * rho;
+      return rep - aa / b * std::log(1.0 + x) - aa * rho / (1.0 + x);
+    }
     if (kind == LBM_EOS_PR) {
       const double x = b * rho, s2 = std::sqrt(2.0);
       return R * T * (std::log(rho / (1.0 - x)) + 1.0 / (1.0 - x)) -
@@ -124,15 +153,15 @@ struct HostEos {
 
 int eos_critical(int kind, double a, double b, double R, double* rho_c, double* T_c) {
   if (!(a > 0 && b > 0 && R > 0) || !rho_c || !T_c) return LBM_EINVAL;
-  if (kind == LBM_EOS_PR) {
+  if (kind == LBM_EOS_PR || kind == LBM_EOS_VDW || kind == LBM_EOS_RKS) {
     double lo = 1e-8, hi = 0.9;
     for (int it = 0; it < 200; ++it) {
       const double m = 0.5 * (lo + hi);
-      if ((1.0 - m) * pr_hpp(m) - 2.0 * pr_hp(m) > 0) lo = m; else hi = m;
+      if ((1.0 - m) * cubic_hpp(kind, m) - 2.0 * cubic_hp(kind, m) > 0) lo = m; else hi = m;
     }
     const double x = 0.5 * (lo + hi);
     *rho_c = x / b;
-    *T_c = (a / b) * (1.0 - x) * (1.0 - x) * pr_hp(x) / R;
+    *T_c = (a / b) * (1.0 - x) * (1.0 - x) * cubic_hp(kind, x) / R;
     return LBM_OK;
   }
   if (kind != LBM_EOS_CS) return LBM_EINVAL;
@@ -149,12 +178,16 @@ int eos_critical(int kind, double a, double b, double R, double* rho_c, double* 
 }
 
 int make_eos(const lbm_params* p, HostEos* e) {
-  if (!p || (p->eos != LBM_EOS_CS && p->eos != LBM_EOS_PR)) return LBM_EINVAL;
+  if (!p || p->eos < LBM_EOS_CS || p->eos > LBM_EOS_RKS) return LBM_EINVAL;
   if (eos_critical(p->eos, p->a, p->b, p->R, &e->rc, &e->Tc) != LBM_OK) return LBM_EINVAL;
   e->kind = p->eos; e->a = p->a; e->b = p->b; e->R = p->R; e->T = p->Tr * e->Tc;
-  if (p->eos == LBM_EOS_PR) {
-    const double s = 1.0 + pr_kappa(p->acentric) * (1.0 - std::sqrt(p->Tr));
+  if (p->eos == LBM_EOS_PR || p->eos == LBM_EOS_RKS) {
+    const double kap = p->eos == LBM_EOS_PR ? pr_kappa(p->acentric) : rks_kappa(p->acentric);
+    const double s = 1.0 + kap * (1.0 - std::sqrt(p->Tr));
     e->aa = p->a * s * s;
+    e->rmax = 1.0 / p->b;
+  } else if (p->eos == LBM_EOS_VDW) {
+    e->aa = p->a;
     e->rmax = 1.0 / p->b;
   } else {
     e->aa = p->a;
@@ -220,9 +253,9 @@ int lbmd::params_to_kp(const lbm_params* p, KParams* kp) {
   kp->nx = p->nx; kp->ny = p->ny; kp->nz = p->nz;
   kp->n = (long long)p->nx * p->ny * p->nz;
   kp->RT = p->R * E.T; kp->b4 = 0.25 * p->b; kp->two_a = 2.0 * p->a;
-  kp->eos = p->eos == LBM_EOS_PR ? 1 : 0;
-  kp->aa = p->eos == LBM_EOS_PR ? E.aa : 0.0;
-  kp->c1 = p->eos == LBM_EOS_PR ? E.aa / (2.0 * std::sqrt(2.0) * p->b) : 0.0;
+  kp->eos = p->eos;  // the device codes equal the LBM_EOS_ values
+  kp->aa = E.aa;
+  kp->c1 = p->eos == LBM_EOS_PR ? E.aa / (2.0 * std::sqrt(2.0) * p->b) : (p->eos == LBM_EOS_RKS ? E.aa / p->b : 0.0);
   kp->k2 = p->k * p->k; kp->kappa = p->kappa; kp->omega = 1.0 / p->tau;
   kp->rho_ref = 0.0;
   if (p->precision == LBM_FP32DEV) {
@@ -436,8 +469,8 @@ static int validate(const lbm_params* p) {
   if (p->lattice == LBM_D2Q9 && p->nz != 1) return LBM_EINVAL;
   if (p->lattice == LBM_D3Q19 && p->nz < 8) return LBM_EINVAL;
   if ((long long)p->nx * p->ny * p->nz > (1LL << 31) / 19) return LBM_EINVAL;
-  if (p->eos != LBM_EOS_CS && p->eos != LBM_EOS_PR) return LBM_EINVAL;
-  if (p->eos == LBM_EOS_PR && !(p->Tr < 1.0 && p->acentric > -1.0)) return LBM_EINVAL;
+  if (p->eos < LBM_EOS_CS || p->eos > LBM_EOS_RKS) return LBM_EINVAL;
+  if ((p->eos == LBM_EOS_PR || p->eos == LBM_EOS_RKS) && !(p->Tr < 1.0 && p->acentric > -1.0)) return LBM_EINVAL;
   if (!(p->a > 0 && p->b > 0 && p->R > 0 && p->Tr > 0)) return LBM_EINVAL;
   if (!(p->k > 0) || !(p->kappa >= 0) || !(p->tau > 0.5)) return LBM_EINVAL;
   if (p->scheme < LBM_EFDS2 || p->scheme > LBM_E8) return LBM_EINVAL;

@@ -76,8 +76,8 @@ struct KParams {
   double k2, kappa;       // k^2 and kappa-hat (Eq. 16)
   double omega;           // 1/tau
   double rho_ref;         // FP32DEV reference density (0 in FP64 mode)
-  int eos;                // 0: Carnahan-Starling, 1: Peng-Robinson (Eq. 14-15)
-  double aa, c1;          // Peng-Robinson: a alpha(T) and a alpha(T) / (2 sqrt2 b)
+  int eos;                // 0 Carnahan-Starling, 1 Peng-Robinson (Eq. 14-15), 2 van der Waals, 3 Redlich-Kwong-Soave
+  double aa, c1;          // PR: a alpha(T), a alpha(T) / (2 sqrt2 b); RKS: a alpha(T), a alpha(T) / b
 };
 
 struct StepAux {
@@ -112,10 +112,26 @@ __device__ __forceinline__ T pr_mu(T rho, T RT, T b, T aa, T c1) {
          aa * rho / (T(1) + x * (T(2) - x));
 }
 
+// van der Waals and Redlich-Kwong-Soave by Eq. 13: with x = b rho the
+// repulsive part is R T [ln(rho / (1 - x)) + 1 / (1 - x)]; the attractive part
+// is -2 a rho (VDW) or -(a alpha / b) ln(1 + x) - a alpha rho / (1 + x) (RKS).
+template <typename T>
+__device__ __forceinline__ T vdw_mu(T rho, T RT, T b, T two_a) {
+  const T om = T(1) - b * rho;
+  return RT * (lg(rho / om) + T(1) / om) - two_a * rho;
+}
+template <typename T>
+__device__ __forceinline__ T rks_mu(T rho, T RT, T b, T aa, T c1) {
+  const T x = b * rho, om = T(1) - x;
+  return RT * (lg(rho / om) + T(1) / om) - c1 * lg(T(1) + x) - aa * rho / (T(1) + x);
+}
+
 // psi'(rho) of the case's EOS (Eq. 10, 13-15), additive constant dropped
 template <typename T>
 __device__ __forceinline__ T eos_mu(T rho, const KParams& p) {
   if (p.eos == 1) return pr_mu<T>(rho, T(p.RT), T(4.0 * p.b4), T(p.aa), T(p.c1));
+  if (p.eos == 2) return vdw_mu<T>(rho, T(p.RT), T(4.0 * p.b4), T(p.two_a));
+  if (p.eos == 3) return rks_mu<T>(rho, T(p.RT), T(4.0 * p.b4), T(p.aa), T(p.c1));
   return cs_mu<T>(rho, T(p.RT), T(p.b4), T(p.two_a));
 }
 
@@ -129,6 +145,12 @@ __device__ __forceinline__ EosF eos_f(const KParams& p) {
   return EosF{p.eos, float(p.RT), float(p.b4), float(p.two_a), float(4.0 * p.b4), float(p.aa), float(p.c1)};
 }
 __device__ __forceinline__ float eos_mu_f(float rho, const EosF& e) {
+  if (e.eos >= 2) {
+    const float x = e.b * rho, iom = __fdividef(1.f, 1.f - x);
+    const float rep = e.RT * (__logf(rho * iom) + iom);
+    if (e.eos == 2) return rep - e.two_a * rho;
+    return rep - e.c1 * __logf(1.f + x) - __fdividef(e.aa * rho, 1.f + x);
+  }
   if (e.eos == 1) {
     const float x = e.b * rho, om = 1.f - x;
     const float iom = __fdividef(1.f, om);

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOTSUP, LBM_ESCRATCH = (
     0, -1, -2, -3, -4, -5, -6, -7)
 LBM_D2Q9, LBM_D3Q19 = 0, 1
-LBM_EOS_CS, LBM_EOS_PR = 0, 1
+LBM_EOS_CS, LBM_EOS_PR, LBM_EOS_VDW, LBM_EOS_RKS = 0, 1, 2, 3
+EOS = {"CS": LBM_EOS_CS, "PR": LBM_EOS_PR, "VDW": LBM_EOS_VDW, "RKS": LBM_EOS_RKS}
 SCHEMES = {"EFDS2": 0, "EFDS4": 1, "EFDS6": 2, "CFDS4": 3, "CFDS6": 4, "CFDS8": 5, "OCFDS4": 6, "E4": 7, "E8": 8}
 LBM_FP64, LBM_FP32DEV = 0, 1
 LBM_BGK, LBM_MRT = 0, 1
@@ -142,8 +143,8 @@ def make_params(lattice=LBM_D2Q9, nx=64, ny=64, nz=1, a=1.0, b=4.0, R=1.0, Tr=0.
                 scheme="EFDS2", precision=LBM_FP64, mu_fp64=0, rho_ref=0.0, collision=LBM_BGK, mrt_s=None,
                 eos=LBM_EOS_CS, acentric=0.344):
     """collision: LBM_BGK / LBM_MRT or "BGK" / "MRT"; mrt_s None = the paper's rates;
-    eos: LBM_EOS_CS / LBM_EOS_PR or "CS" / "PR" (then a, b, R are the PR constants)."""
-    e = {"CS": LBM_EOS_CS, "PR": LBM_EOS_PR}[eos] if isinstance(eos, str) else int(eos)
+    eos: LBM_EOS_* or "CS" / "PR" / "VDW" / "RKS" (a, b, R are that EOS's constants)."""
+    e = EOS[eos] if isinstance(eos, str) else int(eos)
     s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     col = {"BGK": LBM_BGK, "MRT": LBM_MRT}[collision] if isinstance(collision, str) else int(collision)
     rates = (C.c_double * 9)(*(mrt_s if mrt_s is not None else [0.0] * 9))

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -58,6 +59,11 @@ def test_host_only_entry_points(libpath):
         g, l = lbm.lbm_maxwell(lbm.make_params(eos="PR", a=A, b=B, Tr=tr))
         og, ol = O.eos_maxwell(O.eos_make(O.EOS_PR, A, B, 1.0, tr, 0.344))
         assert abs(g / og - 1) < 1e-9 and abs(l / ol - 1) < 1e-12
+    for name, kind, a in (("VDW", O.EOS_VDW, 9.0 / 49.0), ("RKS", O.EOS_RKS, 2.0 / 49.0)):
+        q = lbm.make_params(eos=name, a=a, b=B, Tr=0.7)
+        assert np.allclose(lbm.lbm_eos_critical(q), O.cubic_critical(kind, a, B, 1.0), rtol=1e-12, atol=0)
+        assert np.allclose(lbm.lbm_maxwell(q), O.eos_maxwell(O.eos_make(kind, a, B, 1.0, 0.7, 0.344)),
+                           rtol=1e-9, atol=0)
     assert lbm.lib().lbm_lattice_q(0) == 9 and lbm.lib().lbm_lattice_q(1) == 19
     assert lbm.lib().lbm_strerror(-4).decode().startswith("simulation unstable")
 

@@ -1,8 +1,10 @@
-"""GPU parity of the Peng-Robinson EOS path (Eq. 14-15; a = 2/49, b = 2/21,
-R = 1, acentric factor 0.344) against the oracle: FP64 to 1e-12 on D2Q9 and
-D3Q19, FP32 deviation storage to 1e-5 of rho_l on both split kernels (the
-16-byte and the 4-byte variants in 3D), and the batch against single cases.
-kappa-hat is 0.01: PR liquid densities are ~25 times the CS ones here."""
+"""GPU parity of the cubic equations of state against the oracle: Peng-Robinson
+(Eq. 14-15; a = 2/49, b = 2/21, R = 1, acentric factor 0.344) on every path --
+FP64 to 1e-12 on D2Q9 and D3Q19, FP32 deviation storage to 1e-5 of rho_l on
+both split kernels (the 16-byte and the 4-byte variants in 3D), the batch
+against single cases -- and van der Waals / Redlich-Kwong-Soave (chemical
+potential by Eq. 13) on FP64 and FP32 cases.  kappa-hat is 0.01: these liquid
+densities are ~25 times the CS ones here."""
 import numpy as np
 import pytest
 
@@ -74,3 +76,30 @@ def test_batch_pr_matches_single_cases(L):
         s.lbm_step(30)
         assert relerr(b.lbm_batch_get_density(i), s.lbm_get_density()) < 1e-6
     b.close()
+
+
+OTHER = {"VDW": dict(eos="VDW", a=9.0 / 49.0, b=2.0 / 21.0, R=1.0, Tr=0.8, k=0.2, kappa=0.01),
+         "RKS": dict(eos="RKS", a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, Tr=0.8, k=0.2, kappa=0.01)}
+
+
+@pytest.mark.parametrize("eos", ["VDW", "RKS"])
+@pytest.mark.parametrize("shape,scheme,precision", [((40, 24, 1), "EFDS4", 0), ((40, 24, 1), "OCFDS4", 0),
+                                                    ((24, 20, 28), "EFDS6", 0), ((48, 40, 44), "EFDS6", 1),
+                                                    ((42, 36, 30), "EFDS4", 1)])
+def test_vdw_rks_match_oracle(L, eos, shape, scheme, precision):
+    kw = OTHER[eos]
+    nx, ny, nz = shape
+    lat = L.LBM_D2Q9 if nz == 1 else L.LBM_D3Q19
+    g = L.Sim(L.make_params(lattice=lat, nx=nx, ny=ny, nz=nz, scheme=scheme, precision=precision, **kw))
+    o = O.Sim(lattice=O.D2Q9 if nz == 1 else O.D3Q19, nx=nx, ny=ny, nz=nz, scheme=scheme, acentric=0.344, **kw)
+    r = 7.0 if nx <= 40 else 10.0
+    g.lbm_init_droplet(r)
+    o.init_droplet(r)
+    g.lbm_step(40)
+    assert o.step(40) == 0
+    if precision == 0:
+        assert relerr(g.lbm_get_density(), o.density()) < 1e-12
+    else:
+        kind = O.EOS_VDW if eos == "VDW" else O.EOS_RKS
+        rl = O.eos_maxwell(O.eos_make(kind, kw["a"], kw["b"], 1.0, 0.8, 0.344))[1]
+        assert np.max(np.abs(g.lbm_get_density() - o.density())) / rl < 1e-5
