@@ -75,6 +75,7 @@ def lib():
         L.or_pr_alpha.restype = C.c_double
         L.or_pr_critical.argtypes = [C.c_double] * 3 + [_dp, _dp]
         L.or_cubic_critical.argtypes = [C.c_int] + [C.c_double] * 3 + [_dp, _dp]
+        L.or_flat_profile.argtypes = [C.c_void_p, C.c_int, C.c_double, _dp, _dp]
         L.or_mrt_matrix.argtypes = [_dp]
         L.or_mrt_matrix.restype = None
         L.or_mrt_inverse.argtypes = [_dp]
@@ -237,6 +238,16 @@ def cubic_critical(kind, a, b, R):
     if lib().or_cubic_critical(kind, a, b, R, C.byref(rc), C.byref(Tc)) != OK:
         raise ValueError
     return rc.value, Tc.value
+
+
+def flat_profile(n, y0, Tr, k, kappa, eos="CS", a=1.0, b=4.0, R=1.0, acentric=0.344):
+    """Equilibrium flat interface (Eq. 29): (rho, drho/dy) at nodes 0..n-1."""
+    p = Params(0, 8, 8, 1, a, b, R, Tr, k, kappa, 1.0, 0, 0, (C.c_double * 9)(),
+               {"CS": EOS_CS, "PR": EOS_PR, "VDW": EOS_VDW, "RKS": EOS_RKS}[eos], acentric)
+    rho, d = np.empty(n), np.empty(n)
+    if lib().or_flat_profile(C.byref(p), n, y0, _ptr(rho), _ptr(d)) != OK:
+        raise ValueError("invalid parameters")
+    return rho, d
 
 
 def pr_critical(a, b, R):

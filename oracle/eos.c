@@ -225,7 +225,7 @@ double or_eos_mu(const or_eos* e, double rho) {
   }
 }
 
-static double eos_dpdrho(const or_eos* e, double rho) {
+double or_eos_dpdrho(const or_eos* e, double rho) {
   switch (e->kind) {
     case OR_EOS_PR: return pr_dpdrho(rho, e->a, e->b, e->R, e->T, e->alpha);
     case OR_EOS_VDW: return vdw_dpdrho(rho, e->a, e->b, e->R, e->T);
@@ -261,13 +261,13 @@ int or_eos_maxwell(const or_eos* e, double* rho_g, double* rho_l) {
   double lo = -700.0, hi = log(e->rho_c);
   for (int it = 0; it < 300; ++it) {
     double mid = 0.5 * (lo + hi);
-    if (eos_dpdrho(e, exp(mid)) > 0) lo = mid; else hi = mid;
+    if (or_eos_dpdrho(e, exp(mid)) > 0) lo = mid; else hi = mid;
   }
   double sp_g = exp(lo);
   lo = e->rho_c; hi = e->rho_max;
   for (int it = 0; it < 300; ++it) {
     double mid = 0.5 * (lo + hi);
-    if (eos_dpdrho(e, mid) < 0) lo = mid; else hi = mid;
+    if (or_eos_dpdrho(e, mid) < 0) lo = mid; else hi = mid;
   }
   double sp_l = hi;
   double p_hi = or_eos_pressure(e, sp_g), p_lo = or_eos_pressure(e, sp_l);
@@ -348,5 +348,98 @@ int or_cubic_critical(int kind, double a, double b, double R, double* rho_c, dou
   attr_derivs(kind, x, &h1, &h2);
   *rho_c = x / b;
   *T_c = (a / b) * (1.0 - x) * (1.0 - x) * h1 / R;
+  return OR_OK;
+}
+
+/* ---------------------------------------------------------------- flat interface (Eq. 29) */
+/*
+ * A flat liquid-vapour interface in equilibrium (Eq. 29, with rho(-inf) =
+ * rho_g, rho(+inf) = rho_l) has a uniform chemical potential in mesh units
+ * (Eq. 16):  k^2 psi'(rho) - kappa rho'' = mu_0 = k^2 psi'(rho_g).
+ * Multiplying by rho' and integrating from the gas side,
+ *     (kappa / 2) rho'^2 = k^2 W(rho),
+ *     W(rho) = psi(rho) - psi(rho_g) - psi'(rho_g) (rho - rho_g),
+ * and with psi = rho psi' - p0 (Eq. 10),
+ *     W(rho) = rho (psi'(rho) - psi'(rho_g)) - (p0(rho) - p0(rho_g)).
+ * So rho' = k sqrt(2 W / kappa) and y(rho) = int_{rho_m}^{rho} dr / rho'(r),
+ * rho_m = (rho_g + rho_l) / 2 at y = y0.  The integral is taken in the logit
+ * variable s, rho = rho_g + (rho_l - rho_g) / (1 + e^-s), where dy/ds stays
+ * finite, with 3-point Gauss-Legendre on a table of steps 0.01 over |s| <= 14;
+ * the node values by bisection on the table and Newton within a step.
+ * Beyond the table (rho within 1e-6 of a bulk value, where W is a difference
+ * of nearly equal terms) the profile follows the linearised equation
+ * kappa d'' = k^2 psi''(rho_b) d, psi'' = p0' / rho: exponential tails.
+ */
+#define FLAT_S 14.0
+#define FLAT_H 0.01
+#define FLAT_M 2800 /* 2 FLAT_S / FLAT_H */
+
+typedef struct {
+  const or_eos* e;
+  double g, l, mug, pg, k, kappa;
+} flat_ctx;
+
+static double flat_rho(const flat_ctx* c, double s) { return c->g + (c->l - c->g) / (1.0 + exp(-s)); }
+
+static double flat_drho(const flat_ctx* c, double rho) {
+  double W = rho * (or_eos_mu(c->e, rho) - c->mug) - (or_eos_pressure(c->e, rho) - c->pg);
+  if (W < 0) W = 0;
+  return c->k * sqrt(2.0 * W / c->kappa);
+}
+
+static double flat_dyds(const flat_ctx* c, double s) {
+  double sig = 1.0 / (1.0 + exp(-s));
+  double drds = (c->l - c->g) * sig * (1.0 - sig);
+  return drds / flat_drho(c, flat_rho(c, s));
+}
+
+/* int_a^b dy/ds ds, 3-point Gauss-Legendre */
+static double flat_gl3(const flat_ctx* c, double a, double b) {
+  const double x = sqrt(0.6), m = 0.5 * (a + b), h = 0.5 * (b - a);
+  return h * (5.0 / 9.0 * flat_dyds(c, m - h * x) + 8.0 / 9.0 * flat_dyds(c, m) + 5.0 / 9.0 * flat_dyds(c, m + h * x));
+}
+
+int or_flat_profile(const or_params* p, int n, double y0, double* rho, double* drho) {
+  if (!p || n < 1 || !rho || !(p->k > 0) || !(p->kappa > 0)) return OR_EINVAL;
+  or_eos e;
+  if (or_eos_make(p->eos, p->a, p->b, p->R, p->Tr, p->acentric, &e) != OR_OK) return OR_EINVAL;
+  double g, l;
+  if (or_eos_maxwell(&e, &g, &l) != OR_OK) return OR_EINVAL;
+  flat_ctx c = {&e, g, l, or_eos_mu(&e, g), or_eos_pressure(&e, g), p->k, p->kappa};
+  static double Y[FLAT_M + 1]; /* y(s_i) - y0, s_i = -FLAT_S + i FLAT_H; y(0) = 0 at i = FLAT_M / 2 */
+  const int mid = FLAT_M / 2;
+  Y[mid] = 0.0;
+  for (int i = mid + 1; i <= FLAT_M; ++i)
+    Y[i] = Y[i - 1] + flat_gl3(&c, -FLAT_S + (i - 1) * FLAT_H, -FLAT_S + i * FLAT_H);
+  for (int i = mid - 1; i >= 0; --i) Y[i] = Y[i + 1] - flat_gl3(&c, -FLAT_S + i * FLAT_H, -FLAT_S + (i + 1) * FLAT_H);
+  /* tail rates from the linearised equation */
+  const double lam_g = p->k * sqrt(or_eos_dpdrho(&e, g) / g / p->kappa);
+  const double lam_l = p->k * sqrt(or_eos_dpdrho(&e, l) / l / p->kappa);
+  for (int j = 0; j < n; ++j) {
+    const double t = (double)j - y0;
+    double r, d;
+    if (t <= Y[0]) {
+      const double d0 = flat_rho(&c, -FLAT_S) - g;
+      r = g + d0 * exp(lam_g * (t - Y[0]));
+      d = lam_g * (r - g);
+    } else if (t >= Y[FLAT_M]) {
+      const double d0 = l - flat_rho(&c, FLAT_S);
+      r = l - d0 * exp(-lam_l * (t - Y[FLAT_M]));
+      d = lam_l * (l - r);
+    } else {
+      int lo = 0, hi = FLAT_M;
+      while (hi - lo > 1) {
+        const int m = (lo + hi) / 2;
+        if (Y[m] <= t) lo = m; else hi = m;
+      }
+      const double sa = -FLAT_S + lo * FLAT_H;
+      double s = sa + FLAT_H * (t - Y[lo]) / (Y[hi] - Y[lo]);
+      for (int it = 0; it < 6; ++it) s -= (Y[lo] + flat_gl3(&c, sa, s) - t) / flat_dyds(&c, s);
+      r = flat_rho(&c, s);
+      d = flat_drho(&c, r);
+    }
+    rho[j] = r;
+    if (drho) drho[j] = d;
+  }
   return OR_OK;
 }

@@ -105,7 +105,13 @@ int or_eos_make(int kind, double a, double b, double R, double Tr, double acentr
 int or_eos_critical(int kind, double a, double b, double R, double* rho_c, double* T_c);
 double or_eos_pressure(const or_eos* e, double rho);
 double or_eos_mu(const or_eos* e, double rho);
+double or_eos_dpdrho(const or_eos* e, double rho);
 int or_eos_maxwell(const or_eos* e, double* rho_g, double* rho_l);
+
+/* Equilibrium flat interface (Eq. 29) along one axis: rho and its analytic
+ * derivative at nodes j = 0..n-1, gas for j < y0 and liquid beyond, rho(y0) =
+ * (rho_g + rho_l) / 2, for the EOS, T_r, k and kappa-hat of p. */
+int or_flat_profile(const or_params* p, int n, double y0, double* rho, double* drho);
 
 /* ---- finite differences on periodic lattices (Sec. 2.3) ---- */
 void or_scheme_coeffs(int scheme, double* alpha, double* a, double* b, double* c);
