@@ -65,6 +65,8 @@ def lib():
         L.or_lattice_q.argtypes = [C.c_int]
         L.or_lattice_e.argtypes = [C.c_int, _ip, _dp]
         L.or_feq.argtypes = [C.c_int, C.c_double, _dp, _dp]
+        L.or_set_solid.argtypes = [C.c_void_p, C.c_void_p, C.c_double]
+        L.or_solid_layers.argtypes = [C.c_void_p, C.c_void_p]
         L.or_eos_make.argtypes = [C.c_int] + [C.c_double] * 5 + [C.c_void_p]
         L.or_eos_pressure.argtypes = [C.c_void_p, C.c_double]
         L.or_eos_pressure.restype = C.c_double
@@ -332,6 +334,18 @@ class Sim:
     def _check(self, rc):
         if rc not in (OK,):
             raise RuntimeError("oracle call failed: %d" % rc)
+
+    def set_solid(self, mask, mu_w):
+        """Wall nodes (Appendix A): mask of the lattice shape, wall chemical potential."""
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+        assert m.size == self.n
+        if lib().or_set_solid(self.h, m.ctypes.data_as(C.c_void_p), mu_w) != OK:
+            raise ValueError("walls need an explicit scheme (EFDS2/4/6) and a fluid node")
+
+    def solid_layers(self):
+        out = np.zeros(self.n, dtype=np.int32)
+        lib().or_solid_layers(self.h, out.ctypes.data_as(C.c_void_p))
+        return out.reshape(self.shape)
 
     def init_droplet(self, radius, width=10.0, center=None, rho_l=0.0, rho_g=0.0):
         c = _f64(center) if center is not None else None

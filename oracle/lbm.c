@@ -86,6 +86,9 @@ struct or_sim {
   double T;
   or_eos eos;                           /* the equation of state at T */
   double *f, *fn;                       /* f[i*n + node] */
+  unsigned char* solid;                 /* wall nodes (Appendix A), NULL: none */
+  int* layer;                           /* 0 fluid, 1..3 wall layers, 4 deeper wall */
+  double mu_w;                          /* chemical potential assigned to wall nodes */
   double *rho, *u, *F, *mu, *lap, *gmu, *grho;
   double* rho_snap;
   long long t, t_snap;
@@ -140,6 +143,7 @@ void or_destroy(or_sim* s) {
   if (!s) return;
   free(s->f); free(s->fn); free(s->rho); free(s->u); free(s->F);
   free(s->mu); free(s->lap); free(s->gmu); free(s->grho); free(s->rho_snap);
+  free(s->solid); free(s->layer);
   free(s);
 }
 
@@ -258,12 +262,104 @@ int or_get_f(const or_sim* s, double* f) {
   return OR_OK;
 }
 
+/* index of the velocity opposite to e_i */
+static int opposite(const or_sim* s, int i) {
+  const int(*e)[3] = lat_e(s->p.lattice);
+  for (int j = 0; j < s->q; ++j)
+    if (e[j][0] == -e[i][0] && e[j][1] == -e[i][1] && e[j][2] == -e[i][2]) return j;
+  return i;
+}
+
+/*
+ * Wall nodes (Appendix A).  Layer 1: wall nodes with a fluid neighbour along
+ * some lattice velocity; layer L: not in an earlier layer, with a neighbour in
+ * layer L - 1 (up to 3 layers: the reach of the sixth-order stencil).  Each
+ * step the densities of layers 1, 2, 3 are, in that order, the w_i-weighted
+ * average of the neighbours in the layer before (Eq. A.1: the switching
+ * function selects those neighbours), and every wall node carries the chemical
+ * potential mu_w.  Deeper wall nodes take the fluid's mean density (no
+ * stencil of a fluid node reaches them).
+ */
+int or_set_solid(or_sim* s, const unsigned char* mask, double mu_w) {
+  if (!s || !mask) return OR_EINVAL;
+  if (s->p.scheme != OR_EFDS2 && s->p.scheme != OR_EFDS4 && s->p.scheme != OR_EFDS6) return OR_EINVAL;
+  long n = s->n;
+  if (!s->solid) {
+    s->solid = (unsigned char*)calloc(n, 1);
+    s->layer = (int*)calloc(n, sizeof(int));
+  }
+  const int(*e)[3] = lat_e(s->p.lattice);
+  int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+  long nfluid = 0;
+  for (long x = 0; x < n; ++x) {
+    s->solid[x] = mask[x] ? 1 : 0;
+    s->layer[x] = mask[x] ? 4 : 0;
+    nfluid += !mask[x];
+  }
+  if (nfluid == 0) return OR_EINVAL;
+  for (int L = 1; L <= 3; ++L) {
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          long c = node_index(s, x, y, z);
+          if (s->layer[c] != 4) continue;
+          for (int i = 1; i < s->q; ++i) {
+            long t = node_index(s, (x + e[i][0] + nx) % nx, (y + e[i][1] + ny) % ny, (z + e[i][2] + nz) % nz);
+            if (s->layer[t] == L - 1) { s->layer[c] = -L; break; }
+          }
+        }
+    /* marks of this pass become layer L only after it, so that a node does
+     * not join layer L through a neighbour marked in the same pass */
+    for (long x = 0; x < n; ++x)
+      if (s->layer[x] < 0) s->layer[x] = -s->layer[x];
+  }
+  s->mu_w = mu_w;
+  return OR_OK;
+}
+
+int or_solid_layers(const or_sim* s, int* layer) {
+  if (!s || !layer) return OR_EINVAL;
+  for (long x = 0; x < s->n; ++x) layer[x] = s->layer ? s->layer[x] : 0;
+  return OR_OK;
+}
+
+static void wall_densities(or_sim* s) {
+  const int(*e)[3] = lat_e(s->p.lattice);
+  const double* w = lat_w(s->p.lattice);
+  int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+  long n = s->n;
+  double mean = 0;
+  long nf = 0;
+  for (long x = 0; x < n; ++x)
+    if (!s->solid[x]) { mean += s->rho[x]; ++nf; }
+  mean /= (double)nf;
+  for (int L = 1; L <= 3; ++L)
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          long c = node_index(s, x, y, z);
+          if (s->layer[c] != L) continue;
+          double num = 0, den = 0;
+          for (int i = 1; i < s->q; ++i) {
+            long t = node_index(s, (x + e[i][0] + nx) % nx, (y + e[i][1] + ny) % ny, (z + e[i][2] + nz) % nz);
+            if (s->layer[t] == L - 1) { num += w[i] * s->rho[t]; den += w[i]; }
+          }
+          s->rho[c] = num / den;
+        }
+  for (long x = 0; x < n; ++x)
+    if (s->solid[x] && s->layer[x] == 4) s->rho[x] = mean;
+}
+
 /* steps 1-4 for the current state: rho, u, mu, grad mu, grad rho, F */
 static int macro_fields(or_sim* s) {
   const int(*e)[3] = lat_e(s->p.lattice);
   long n = s->n;
   int ok = 1;
   for (long x = 0; x < n; ++x) {
+    if (s->solid && s->solid[x]) {
+      for (int d = 0; d < 3; ++d) s->u[d * n + x] = 0.0;
+      continue;
+    }
     double r = 0, j[3] = {0, 0, 0};
     for (int i = 0; i < s->q; ++i) {
       double fi = s->f[i * n + x];
@@ -275,18 +371,20 @@ static int macro_fields(or_sim* s) {
     if (!(r > 0) || !isfinite(r)) ok = 0;
   }
   if (!ok) return OR_EUNSTABLE;
+  if (s->solid) wall_densities(s);
   const or_params* p = &s->p;
   int rc = or_laplacian(p->scheme, s->dim, p->nx, p->ny, p->nz, s->rho, s->lap);
   if (rc != OR_OK) return rc;
   for (long x = 0; x < n; ++x)
-    s->mu[x] = p->k * p->k * or_eos_mu(&s->eos, s->rho[x]) - p->kappa * s->lap[x];
+    s->mu[x] = (s->solid && s->solid[x]) ? s->mu_w
+                                         : p->k * p->k * or_eos_mu(&s->eos, s->rho[x]) - p->kappa * s->lap[x];
   rc = or_gradient(p->scheme, s->dim, p->nx, p->ny, p->nz, s->mu, s->gmu);
   if (rc != OR_OK) return rc;
   rc = or_gradient(p->scheme, s->dim, p->nx, p->ny, p->nz, s->rho, s->grho);
   if (rc != OR_OK) return rc;
   for (int d = 0; d < 3; ++d)
     for (long x = 0; x < n; ++x)
-      s->F[d * n + x] = (d < s->dim) ? -s->rho[x] * s->gmu[d * n + x] + s->grho[d * n + x] / 3.0 : 0.0;
+      s->F[d * n + x] = (d < s->dim && !(s->solid && s->solid[x])) ? -s->rho[x] * s->gmu[d * n + x] + s->grho[d * n + x] / 3.0 : 0.0;
   return OR_OK;
 }
 
@@ -331,6 +429,7 @@ int or_step(or_sim* s, long long nsteps) {
           double feq[19], Fi[19];
           or_feq(s->p.lattice, s->rho[c], u, feq);
           or_edm(s->p.lattice, s->rho[c], u, F, Fi);
+          if (s->solid && s->solid[c]) continue; /* wall nodes do not collide */
           double fc[19], post[19];
           for (int i = 0; i < s->q; ++i) fc[i] = s->f[i * n + c];
           if (s->p.collision == OR_MRT) {
@@ -340,7 +439,11 @@ int or_step(or_sim* s, long long nsteps) {
           }
           for (int i = 0; i < s->q; ++i) {
             int xd = (x + e[i][0] + nx) % nx, yd = (y + e[i][1] + ny) % ny, zd = (z + e[i][2] + nz) % nz;
-            s->fn[i * n + node_index(s, xd, yd, zd)] = post[i];
+            long t = node_index(s, xd, yd, zd);
+            if (s->solid && s->solid[t])
+              s->fn[opposite(s, i) * n + c] = post[i]; /* halfway bounce-back off a wall */
+            else
+              s->fn[i * n + t] = post[i];
           }
         }
     double* tmp = s->f; s->f = s->fn; s->fn = tmp;
@@ -365,6 +468,7 @@ int or_observables(or_sim* s, or_obs* o) {
   long n = s->n;
   double max_v = 0, max_u = 0, mass = 0, max_dr = 0;
   for (long x = 0; x < n; ++x) {
+    if (s->solid && s->solid[x]) continue; /* fluid nodes only */
     double r = s->rho[x], uu = 0, vv = 0;
     for (int d = 0; d < 3; ++d) {
       double ud = s->u[d * n + x];

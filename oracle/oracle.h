@@ -131,6 +131,14 @@ int or_mrt_inverse(double Minv[81]);
 /* post-collision populations f* = f - M^-1 S (M f - M f_eq) + F_i (Eq. 1, 4) */
 void or_mrt_collide(const double* f, const double* feq, const double* Fi, const double s[9], double* post);
 void or_destroy(or_sim* s);
+
+/* Walls (Appendix A; explicit schemes EFDS2/4/6): mask[N] nonzero marks a wall
+ * node.  Wall nodes do not collide; populations reaching them bounce back
+ * (halfway) to the opposite direction at the fluid node; their densities are
+ * the Eq. A.1 averages over the previous layer, layer by layer, and their
+ * chemical potential is mu_w.  Observables cover fluid nodes only. */
+int or_set_solid(or_sim* s, const unsigned char* mask, double mu_w);
+int or_solid_layers(const or_sim* s, int* layer /* N */);
 int or_init_droplet(or_sim* s, const double center[3], double radius, double width, double rho_l, double rho_g);
 int or_init_slab(or_sim* s, int axis, double thickness, double width, double rho_l, double rho_g);
 int or_init_profile(or_sim* s, const double center[3], const double* r, const double* rho, int n);
