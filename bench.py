@@ -207,7 +207,8 @@ def run_batch(L, steps=50, warmup=10):
 def run_2d(L, steps=200, warmup=20):
     """D2Q9 512^2 droplet (r0 = 100, T_r = 0.8, k = 0.25, EFDS6, FP32 deviation
     storage): BGK and the MRT operator of Eq. 1, 3-5; MLUPS and the roofline of
-    the collision pass (84 B per lattice update)."""
+    the collision pass (84 B per lattice update); the same droplet on a wall."""
+    import numpy as np
     import torch
     out = {"workload": "D2Q9 512^2 droplet r0=100, T_r 0.8, k 0.25, EFDS6, FP32DEV, tau 1"}
     for col in ("BGK", "MRT"):
@@ -224,6 +225,22 @@ def run_2d(L, steps=200, warmup=20):
                             "coll_frac": 84 * n / (coll_ms * 1e-3) / 1e9 / measured_peak()[0],
                             "status": s.lbm_observables()["status"]}
         s.close()
+    # the same droplet sitting on a flat wall of 8 rows (Appendix A), wall
+    # chemical potential 0.005 below saturation; node-parallel wall step
+    p = L.make_params(lattice=L.LBM_D2Q9, nx=512, ny=512, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
+                      precision=L.LBM_FP32DEV)
+    s = L.Sim(p)
+    s.lbm_init_droplet(100.0, center=[256.0, 8.0 + 80.0, 0.0])
+    mask = np.zeros((512, 512), np.uint8)
+    mask[:8] = 1
+    s.lbm_set_solid(mask, L.lbm_bulk_mu(p, L.lbm_maxwell(p)[0]) - 0.005)
+    s.lbm_step(warmup)
+    torch.cuda.synchronize()
+    ms = s.lbm_step_timed(steps)
+    n = 512 * 512
+    out["walls"] = {"mlups": n * steps / (ms[2] * 1e-3) / 1e6, "ms_per_step": ms[2] / steps,
+                    "status": s.lbm_observables()["status"]}
+    s.close()
     return out
 
 

@@ -182,6 +182,23 @@ int lbm_init_density(lbm_handle* h, const double* host_rho);
  * Resets the step counter. */
 int lbm_set_f(lbm_handle* h, const double* host_f);
 
+/* Chemical-potential wall boundary (Appendix A).  mask[N] (node order x
+ * fastest, then y, then z): nonzero marks a wall node.  Wall nodes reached by
+ * a fluid stencil are layered by their link distance to the fluid (layers
+ * 1..3); every step their densities are set, layer by layer, to the
+ * w_i-weighted average of the neighbours in the layer before (Eq. A.1), all
+ * wall nodes carry the chemical potential mu_w in the force of Eq. 12, fluid
+ * populations streaming into a wall return reversed to their node (halfway
+ * bounce-back), and wall nodes neither collide nor count in the observables.
+ * The wall step runs as node-parallel passes (several launches per step) on
+ * the explicit schemes LBM_EFDS2/4/6 only: other schemes -> LBM_ENOTSUP.
+ * mask NULL removes the walls.  The populations of wall nodes are undefined;
+ * after lbm_step the density field holds the Eq. A.1 wall densities of the
+ * state.  The mask is copied (host memory, read only); synchronises the
+ * stream.  Errors: LBM_EINVAL (no fluid node, mu_w not finite), LBM_ENOTSUP,
+ * LBM_ENOMEM, LBM_ECUDA. */
+int lbm_set_solid(lbm_handle* h, const unsigned char* mask, double mu_w);
+
 /* Advance n >= 0 time steps; asynchronous on the handle's stream. */
 int lbm_step(lbm_handle* h, long long n);
 
@@ -246,10 +263,35 @@ int lbm_critical(double a, double b, double R, double* rho_c, double* T_c);
  * equal chemical potential and pressure in both bulk phases. */
 int lbm_maxwell(const lbm_params* params, double* rho_g, double* rho_l);
 
+/* Bulk chemical potential k^2 psi'(rho) of the EOS that p selects at
+ * T = Tr T_c, with the additive constant the step's mu (Eq. 16) uses: the mu
+ * of a uniform fluid of density rho.  For choosing the wall chemical
+ * potential of lbm_set_solid relative to the saturation value
+ * lbm_bulk_mu(p, rho_g) (Appendix A).  Host only.  Errors: LBM_EINVAL (rho
+ * outside (0, the EOS's packing limit), bad parameters). */
+int lbm_bulk_mu(const lbm_params* p, double rho, double* mu);
+
 /* Critical density and temperature of the EOS that p selects (p0' = p0'' = 0;
  * for Peng-Robinson with alpha = 1, which holds at T_c).  Host only.  (A
  * companion of lbm_critical, which keeps its Carnahan-Starling signature.) */
 int lbm_eos_critical(const lbm_params* p, double* rho_c, double* T_c);
+
+/* Equilibrium flat interface (Eq. 29) along one axis for the EOS, T_r, k and
+ * kappa-hat of p: rho[n] and, if drho is not NULL, drho/dy[n] at nodes
+ * j = 0..n-1 (lattice units), gas for j < y0, liquid beyond, rho(y0) =
+ * (rho_g + rho_l) / 2.  Uniform mu-hat (Eq. 16) gives the first integral
+ * (kappa-hat / 2) rho'^2 = k^2 [rho (psi'(rho) - psi'(rho_g)) - (p0(rho) - p0(rho_g))],
+ * integrated numerically (~1e-10).  The analytic reference of Sec. 3.1 (Fig. 3);
+ * host only; fill a slab with it through lbm_init_density. */
+int lbm_flat_profile(const lbm_params* p, int n, double y0, double* rho, double* drho);
+
+/* Force-direction error of Sec. 3.2 (Eq. 30) on the current state: for nodes
+ * with |F| >= frac max|F| (F of Eq. 12), the angle between F and the line
+ * from center (NULL: the lattice centre node) through the node, atan2(|F x r|,
+ * |F . r|) in radians (Eq. 30's atan gives the direction modulo pi; this is
+ * its absolute value, in any dimension).  out[0] = max angle, out[1] =
+ * |F|-weighted mean angle, out[2] = number of nodes.  Synchronises. */
+int lbm_force_angle(lbm_handle* h, const double center[3], double frac, double out[3]);
 
 /* Lattice size Q (9 or 19) of a lattice id, 0 if unknown. */
 int lbm_lattice_q(int lattice);

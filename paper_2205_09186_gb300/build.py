@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
-SOURCES = ["lbm_capi.cu", "k2d.cu", "k3d.cu", "compact.cu", "batch.cu", "mlp.cu", "noalloc.cu"]
+SOURCES = ["lbm_capi.cu", "k2d.cu", "k3d.cu", "compact.cu", "batch.cu", "mlp.cu", "noalloc.cu", "walls.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -8,9 +8,12 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <algorithm>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "launch.cuh"
+#include "walls.cuh"
 #include "compact.cuh"
 
 using namespace lbmd;
@@ -38,6 +41,9 @@ struct lbm_handle {
   bool compact = false;
   int zc = 0;  // z-chunk of the pipelined D3Q19 kernel (0 = heuristic)
   void* mu = nullptr;  // mu field of the split D3Q19 FP32DEV path
+  signed char* layer = nullptr;  // wall layers (Appendix A): 0 fluid, 1..3, 4 deeper; null: no walls
+  void* wmu = nullptr;           // mu field of the wall step (N values of the precision's mu type)
+  double mu_w = 0.0;             // wall chemical potential
 };
 
 // ------------------------------------------------------------------ allocation
@@ -285,6 +291,16 @@ extern "C" int lbm_maxwell(const lbm_params* p, double* rho_g, double* rho_l) {
   return maxwell_eos(E, rho_g, rho_l);
 }
 
+extern "C" int lbm_bulk_mu(const lbm_params* p, double rho, double* mu) {
+  if (!p || !mu || !(rho > 0)) return LBM_EINVAL;
+  HostEos E;
+  if (make_eos(p, &E) != LBM_OK) return LBM_EINVAL;
+  if (E.kind != LBM_EOS_CS && !(E.b * rho < 1.0)) return LBM_EINVAL;
+  if (E.kind == LBM_EOS_CS && !(0.25 * E.b * rho < 1.0)) return LBM_EINVAL;
+  *mu = p->k * p->k * E.mu(rho);
+  return LBM_OK;
+}
+
 extern "C" int lbm_lattice_q(int lattice) { return lattice == LBM_D2Q9 ? 9 : (lattice == LBM_D3Q19 ? 19 : 0); }
 
 extern "C" const char* lbm_strerror(int code) {
@@ -458,6 +474,8 @@ extern "C" void lbm_destroy(lbm_handle* h) {
   dfree(h, h->d_partials, size_t(h->n_partials) * 4 * 8);
   dfree(h, h->d_obs, 64);
   dfree(h, h->mu, size_t(h->N) * 4);
+  dfree(h, h->layer, size_t(h->N));
+  dfree(h, h->wmu, size_t(h->N) * 8);
   compact_free(h->cb, [&](void* p, size_t b) { dfree(h, p, b); });
   delete h;
 }
@@ -695,8 +713,18 @@ static Launch make_launch(lbm_handle* h, int out_buf) {
   return c;
 }
 
+// one pass of the handle's step: walls, compact line schemes or the fused kernels
+static cudaError_t run_pass(lbm_handle* h, const Launch& c, int mode, int* nb) {
+  if (h->layer) {
+    WallLaunch w{c, h->layer, h->mu_w, h->wmu};
+    return wall_step(w, h->D == 2 ? 0 : 1, h->p.scheme, h->prec, mode, nb);
+  }
+  if (h->compact) return compact_step(h->cb, c, h->D, h->p.scheme, h->prec, mode, nb);
+  return h->fn(c, mode, nb);
+}
+
 static bool tunable(const lbm_handle* h) {
-  return h->D == 3 && h->prec == 1 && !h->compact &&
+  return h->D == 3 && h->prec == 1 && !h->compact && !h->layer &&
          (h->p.scheme == LBM_EFDS2 || h->p.scheme == LBM_EFDS4 || h->p.scheme == LBM_EFDS6 || h->p.scheme == LBM_E4);
 }
 
@@ -741,15 +769,13 @@ extern "C" int lbm_step(lbm_handle* h, long long n) {
   if (!h || n < 0) return LBM_EINVAL;
   for (long long s = 0; s < n; ++s) {
     Launch c = make_launch(h, 1 - h->cur);
-    cudaError_t e;
-    if (h->compact)
-      e = compact_step(h->cb, c, h->D, h->p.scheme, h->prec, MODE_STEP, nullptr);
-    else
-      e = h->fn(c, MODE_STEP, nullptr);
-    if (e != cudaSuccess) return LBM_ECUDA;
+    if (run_pass(h, c, MODE_STEP, nullptr) != cudaSuccess) return LBM_ECUDA;
     h->cur = 1 - h->cur;
     h->t += 1;
   }
+  // wall densities of the state left behind (the next step refreshes them anyway)
+  if (h->layer && n > 0 && run_pass(h, make_launch(h, h->cur), MODE_WALL_FILL, nullptr) != cudaSuccess)
+    return LBM_ECUDA;
   return LBM_OK;
 }
 
@@ -758,7 +784,7 @@ extern "C" long long lbm_get_step(const lbm_handle* h) { return h ? h->t : -1; }
 extern "C" int lbm_step_timed(lbm_handle* h, long long n, double* ms) {
   if (!h || n < 0 || n > 100000 || !ms) return LBM_EINVAL;
   ms[0] = ms[1] = ms[2] = 0.0;
-  const bool split = h->mu != nullptr;
+  const bool split = h->mu != nullptr && !h->layer;
   // three events per step, recorded back to back; one synchronisation at the end
   const size_t ne = size_t(3 * n);
   cudaEvent_t* e = new (std::nothrow) cudaEvent_t[ne > 0 ? ne : 1];
@@ -771,8 +797,7 @@ extern "C" int lbm_step_timed(lbm_handle* h, long long n, double* ms) {
     Launch c = make_launch(h, 1 - h->cur);
     c.ev_mid = split ? e[3 * s + 1] : nullptr;
     cudaEventRecord(e[3 * s], h->stream);
-    cudaError_t err = h->compact ? compact_step(h->cb, c, h->D, h->p.scheme, h->prec, MODE_STEP, nullptr)
-                                 : h->fn(c, MODE_STEP, nullptr);
+    cudaError_t err = run_pass(h, c, MODE_STEP, nullptr);
     cudaEventRecord(e[3 * s + 2], h->stream);
     if (err != cudaSuccess) rc = LBM_ECUDA;
     h->cur = 1 - h->cur;
@@ -837,8 +862,7 @@ extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
   c.fout = nullptr;
   c.rout = nullptr;
   int nb = 0;
-  cudaError_t e = h->compact ? compact_step(h->cb, c, h->D, h->p.scheme, h->prec, MODE_OBS, &nb)
-                             : h->fn(c, MODE_OBS, &nb);
+  cudaError_t e = run_pass(h, c, MODE_OBS, &nb);
   if (e != cudaSuccess) return LBM_ECUDA;
   if (nb > h->n_partials) return LBM_ECUDA;
   // the snapshot for the next max |d rho / dt|, ordered after the reduction
@@ -852,7 +876,7 @@ extern "C" int lbm_step_observe(lbm_handle* h, long long n, lbm_obs* out) {
   std::memset(out, 0, sizeof(*out));
   int rc = lbm_step(h, n - 1);
   if (rc != LBM_OK) return rc;
-  if (h->D == 3 && h->mu && !h->compact) {
+  if (h->D == 3 && h->mu && !h->compact && !h->layer) {
     // the last step reduces the observables of the state it advances and
     // leaves that state's density in the snapshot
     Launch c = make_launch(h, 1 - h->cur);
@@ -919,8 +943,7 @@ extern "C" int lbm_get_force(lbm_handle* h, double* host_F, double* host_mu) {
   c.rout = nullptr;
   c.fo.F = tmp;
   c.fo.mu = tmp + size_t(h->D) * h->N;
-  cudaError_t e = h->compact ? compact_step(h->cb, c, h->D, h->p.scheme, h->prec, MODE_FIELDS, nullptr)
-                             : h->fn(c, MODE_FIELDS, nullptr);
+  cudaError_t e = run_pass(h, c, MODE_FIELDS, nullptr);
   int rc = ck(e);
   if (rc == LBM_OK && host_F) rc = ck(cudaMemcpyAsync(host_F, tmp, size_t(h->D) * h->N * 8, cudaMemcpyDeviceToHost, h->stream));
   if (rc == LBM_OK && host_mu) rc = ck(cudaMemcpyAsync(host_mu, c.fo.mu, size_t(h->N) * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -933,5 +956,238 @@ extern "C" int lbm_device_state(lbm_handle* h, void** f, void** rho) {
   if (!h) return LBM_EINVAL;
   if (f) *f = h->f[h->cur];
   if (rho) *rho = h->rho[h->cur];
+  return LBM_OK;
+}
+
+// ------------------------------------------------------------------ walls (Appendix A)
+// Wall layers by breadth-first search over the lattice links from the fluid:
+// a wall node's layer is its link distance to the nearest fluid node (periodic
+// lattice), capped at 4.
+extern "C" int lbm_set_solid(lbm_handle* h, const unsigned char* mask, double mu_w) {
+  if (!h) return LBM_EINVAL;
+  const long long N = h->N;
+  if (!mask) {
+    cudaStreamSynchronize(h->stream);
+    dfree(h, h->layer, size_t(N));
+    dfree(h, h->wmu, size_t(N) * 8);
+    h->layer = nullptr;
+    h->wmu = nullptr;
+    return LBM_OK;
+  }
+  if (!std::isfinite(mu_w)) return LBM_EINVAL;
+  if (h->compact || (h->p.scheme != LBM_EFDS2 && h->p.scheme != LBM_EFDS4 && h->p.scheme != LBM_EFDS6))
+    return LBM_ENOTSUP;
+  const int nx = h->p.nx, ny = h->p.ny, nz = h->D == 3 ? h->p.nz : 1;
+  int ex[19], ey[19], ez[19];
+  for (int i = 0; i < h->Q; ++i) {
+    ex[i] = h->D == 2 ? Lattice<0>::ex(i) : Lattice<1>::ex(i);
+    ey[i] = h->D == 2 ? Lattice<0>::ey(i) : Lattice<1>::ey(i);
+    ez[i] = h->D == 2 ? 0 : Lattice<1>::ez(i);
+  }
+  std::vector<signed char> lay(size_t(N), -1);
+  std::vector<long long> front, next;
+  for (long long n = 0; n < N; ++n)
+    if (!mask[n]) {
+      lay[size_t(n)] = 0;
+      front.push_back(n);
+    }
+  if (front.empty()) return LBM_EINVAL;
+  for (int d = 1; d <= 3 && !front.empty(); ++d) {
+    next.clear();
+    for (const long long n : front) {
+      const int x = int(n % nx), y = int((n / nx) % ny), z = int(n / ((long long)nx * ny));
+      for (int i = 1; i < h->Q; ++i) {
+        const int tx = (x + ex[i] + nx) % nx, ty = (y + ey[i] + ny) % ny, tz = (z + ez[i] + nz) % nz;
+        const long long t = ((long long)tz * ny + ty) * nx + tx;
+        if (lay[size_t(t)] < 0) {
+          lay[size_t(t)] = static_cast<signed char>(d);
+          next.push_back(t);
+        }
+      }
+    }
+    front.swap(next);
+  }
+  for (auto& v : lay)
+    if (v < 0) v = 4;
+  if (!h->layer) {
+    h->layer = static_cast<signed char*>(dalloc(h, size_t(N)));
+    h->wmu = dalloc(h, size_t(N) * 8);
+    if (!h->layer || !h->wmu) {
+      dfree(h, h->layer, size_t(N));
+      dfree(h, h->wmu, size_t(N) * 8);
+      h->layer = nullptr;
+      h->wmu = nullptr;
+      return LBM_ENOMEM;
+    }
+  }
+  int rc = ck(cudaMemcpyAsync(h->layer, lay.data(), size_t(N), cudaMemcpyHostToDevice, h->stream));
+  if (rc == LBM_OK) rc = ck(cudaStreamSynchronize(h->stream));
+  h->mu_w = mu_w;
+  return rc;
+}
+
+// ------------------------------------------------------------------ Sec. 3.1-3.2 diagnostics
+// Flat interface (Eq. 29): uniform mu-hat (Eq. 16) gives the first integral
+// (kappa / 2) rho'^2 = k^2 W(rho), W = rho (mu_b(rho) - mu_b(rho_g)) - (p0(rho) -
+// p0(rho_g)).  Position as a function of density, y(rho) = int dr / rho', is
+// integrated in t = atanh(2 (rho - rho_m) / (rho_l - rho_g)) (finite dy/dt)
+// with composite 4-point Gauss-Legendre on a uniform t grid; node densities
+// by bracketing on the grid and Newton steps.  Outside |t| <= 8 (densities
+// within ~1e-7 of a bulk value) the linearised equation's exponential tails.
+extern "C" int lbm_flat_profile(const lbm_params* p, int n, double y0, double* rho, double* drho) {
+  if (!p || n < 1 || !rho || !(p->k > 0) || !(p->kappa > 0)) return LBM_EINVAL;
+  HostEos E;
+  if (make_eos(p, &E) != LBM_OK) return LBM_EINVAL;
+  double g, l;
+  if (maxwell_eos(E, &g, &l) != LBM_OK) return LBM_EINVAL;
+  const double mug = E.mu(g), pg = E.p(g), rm = 0.5 * (g + l), hw = 0.5 * (l - g);
+  const double k = p->k, kap = p->kappa;
+  auto slope = [&](double r) {
+    const double W = r * (E.mu(r) - mug) - (E.p(r) - pg);
+    return W > 0 ? k * std::sqrt(2.0 * W / kap) : 0.0;
+  };
+  auto dens = [&](double t) { return rm + hw * std::tanh(t); };
+  auto dydt = [&](double t) {
+    const double c = std::cosh(t);
+    return hw / (c * c) / slope(dens(t));
+  };
+  const double gx[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
+  const double gw[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
+  auto integ = [&](double a, double b) {
+    const double m = 0.5 * (a + b), h = 0.5 * (b - a);
+    double s = 0;
+    for (int q = 0; q < 4; ++q) s += gw[q] * dydt(m + h * gx[q]);
+    return h * s;
+  };
+  const double TMAX = 8.0, DT = 0.005;
+  const int M = int(2 * TMAX / DT + 0.5);
+  std::vector<double> Y(M + 1);
+  Y[M / 2] = 0.0;
+  for (int i = M / 2 + 1; i <= M; ++i) Y[i] = Y[i - 1] + integ(-TMAX + (i - 1) * DT, -TMAX + i * DT);
+  for (int i = M / 2 - 1; i >= 0; --i) Y[i] = Y[i + 1] - integ(-TMAX + i * DT, -TMAX + (i + 1) * DT);
+  const double lg_ = k * std::sqrt(E.dp(g) / g / kap), ll_ = k * std::sqrt(E.dp(l) / l / kap);
+  for (int j = 0; j < n; ++j) {
+    const double y = double(j) - y0;
+    double r, d;
+    if (y <= Y[0]) {
+      r = g + (dens(-TMAX) - g) * std::exp(lg_ * (y - Y[0]));
+      d = lg_ * (r - g);
+    } else if (y >= Y[M]) {
+      r = l - (l - dens(TMAX)) * std::exp(-ll_ * (y - Y[M]));
+      d = ll_ * (l - r);
+    } else {
+      const int i = int(std::upper_bound(Y.begin(), Y.end(), y) - Y.begin()) - 1;
+      const double ta = -TMAX + i * DT;
+      double t = ta + DT * (y - Y[i]) / (Y[i + 1] - Y[i]);
+      for (int it = 0; it < 5; ++it) t -= (Y[i] + integ(ta, t) - y) / dydt(t);
+      r = dens(t);
+      d = slope(r);
+    }
+    rho[j] = r;
+    if (drho) drho[j] = d;
+  }
+  return LBM_OK;
+}
+
+namespace {
+// Eq. 30 generalised to any dimension: the angle between the force and the
+// radial line through the droplet centre, atan2(|F x r|, |F . r|) (atan in
+// Eq. 30 defines the direction modulo pi; the atan2 form keeps small angles
+// accurate, where acos of a ratio near 1 would not); nodes with |F| >= frac max |F|.
+// Pass 1: per-CTA max |F|^2.  Pass 2: per-CTA max angle, sum of |F| angle, sum of |F|, count.
+__global__ void k_fmax(const double* F, int D, long long N, double* part) {
+  __shared__ double red[256];
+  double m = 0;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int d = 0; d < D; ++d) s += F[d * N + n] * F[d * N + n];
+    m = fmax(m, s);
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_fangle(const double* F, int D, int nx, int ny, long long N, double cx, double cy, double cz,
+                         const double* fmax_part, int nparts, double frac, double* part) {
+  __shared__ double red[4][256];
+  __shared__ double s_thr;
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int i = 0; i < nparts; ++i) m = fmax(m, fmax_part[i]);
+    s_thr = frac * frac * m;  // on |F|^2
+  }
+  __syncthreads();
+  double amax = 0, wsum = 0, fsum = 0, cnt = 0;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    const double x = double(n % nx) - cx, y = double((n / nx) % ny) - cy;
+    const double z = D == 3 ? double(n / ((long long)nx * ny)) - cz : 0.0;
+    const double r2 = x * x + y * y + z * z;
+    const double fx = F[n], fy = F[N + n], fz = D == 3 ? F[2 * N + n] : 0.0;
+    const double f2 = fx * fx + fy * fy + fz * fz, fr = fx * x + fy * y + fz * z;
+    const double c0 = fy * z - fz * y, c1 = fz * x - fx * z, c2 = fx * y - fy * x;
+    if (r2 > 0 && f2 > 0 && f2 >= s_thr) {
+      const double a = atan2(sqrt(c0 * c0 + c1 * c1 + c2 * c2), fabs(fr)), fm = sqrt(f2);
+      amax = fmax(amax, a);
+      wsum += fm * a;
+      fsum += fm;
+      cnt += 1;
+    }
+  }
+  red[0][threadIdx.x] = amax; red[1][threadIdx.x] = wsum; red[2][threadIdx.x] = fsum; red[3][threadIdx.x] = cnt;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + s]);
+      for (int q = 1; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 4; ++q) part[4 * blockIdx.x + q] = red[q][0];
+}
+}  // namespace
+
+extern "C" int lbm_force_angle(lbm_handle* h, const double center[3], double frac, double out[3]) {
+  if (!h || !out || !(frac >= 0 && frac <= 1)) return LBM_EINVAL;
+  const int nb = 512;
+  const size_t fbytes = size_t(h->D + 1) * h->N * 8, pbytes = size_t(nb) * 5 * 8;
+  double* tmp = static_cast<double*>(dalloc(h, fbytes + pbytes));
+  if (!tmp) return LBM_ENOMEM;
+  double* fpart = tmp + size_t(h->D + 1) * h->N;
+  double* apart = fpart + nb;
+  Launch c = make_launch(h, h->cur);
+  c.fout = nullptr;
+  c.rout = nullptr;
+  c.fo.F = tmp;
+  c.fo.mu = tmp + size_t(h->D) * h->N;
+  cudaError_t e = run_pass(h, c, MODE_FIELDS, nullptr);
+  int rc = ck(e);
+  const double cx = center ? center[0] : double(h->p.nx / 2), cy = center ? center[1] : double(h->p.ny / 2);
+  const double cz = center ? center[2] : double(h->p.nz / 2);
+  if (rc == LBM_OK) {
+    k_fmax<<<nb, 256, 0, h->stream>>>(tmp, h->D, h->N, fpart);
+    k_fangle<<<nb, 256, 0, h->stream>>>(tmp, h->D, h->p.nx, h->p.ny, h->N, cx, cy, cz, fpart, nb, frac, apart);
+    rc = ck(cudaGetLastError());
+  }
+  std::vector<double> host(size_t(nb) * 4);
+  if (rc == LBM_OK) rc = ck(cudaMemcpyAsync(host.data(), apart, host.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  cudaStreamSynchronize(h->stream);
+  dfree(h, tmp, fbytes + pbytes);
+  if (rc != LBM_OK) return rc;
+  double amax = 0, wsum = 0, fsum = 0, cnt = 0;
+  for (int b = 0; b < nb; ++b) {
+    amax = std::max(amax, host[4 * b]);
+    wsum += host[4 * b + 1];
+    fsum += host[4 * b + 2];
+    cnt += host[4 * b + 3];
+  }
+  out[0] = amax;
+  out[1] = fsum > 0 ? wsum / fsum : 0.0;
+  out[2] = cnt;
   return LBM_OK;
 }

@@ -73,6 +73,10 @@ SIGNATURES = {
     "lbm_critical": (C.c_int, [C.c_double, C.c_double, C.c_double, _dp, _dp]),
     "lbm_maxwell": (C.c_int, [C.POINTER(lbm_params), _dp, _dp]),
     "lbm_eos_critical": (C.c_int, [C.POINTER(lbm_params), _dp, _dp]),
+    "lbm_flat_profile": (C.c_int, [C.POINTER(lbm_params), C.c_int, C.c_double, _dp, _dp]),
+    "lbm_force_angle": (C.c_int, [_h, _dp, C.c_double, _dp]),
+    "lbm_set_solid": (C.c_int, [_h, C.POINTER(C.c_ubyte), C.c_double]),
+    "lbm_bulk_mu": (C.c_int, [C.POINTER(lbm_params), C.c_double, _dp]),
     "lbm_lattice_q": (C.c_int, [C.c_int]),
     "lbm_set_zchunk": (C.c_int, [_h, C.c_int]),
     "lbm_autotune": (C.c_int, [_h, C.POINTER(C.c_int)]),
@@ -152,6 +156,13 @@ def make_params(lattice=LBM_D2Q9, nx=64, ny=64, nz=1, a=1.0, b=4.0, R=1.0, Tr=0.
                       col, rates, acentric)
 
 
+def lbm_bulk_mu(params, rho):
+    """k^2 psi'(rho): the chemical potential of a uniform fluid of density rho."""
+    out = C.c_double()
+    check(lib().lbm_bulk_mu(C.byref(params), float(rho), C.byref(out)), "lbm_bulk_mu")
+    return out.value
+
+
 def lbm_observables_noalloc(params, d_f, d_rho, d_rho_prev=None, steps_since_prev=0, step=0, stream=None):
     """Observables of a caller-held device state; the library allocates nothing.
     Returns (status code, observables dict)."""
@@ -173,6 +184,13 @@ def lbm_eos_critical(params):
     rc, Tc = C.c_double(), C.c_double()
     check(lib().lbm_eos_critical(C.byref(params), C.byref(rc), C.byref(Tc)), "lbm_eos_critical")
     return rc.value, Tc.value
+
+
+def lbm_flat_profile(params, n, y0):
+    """(rho, drho/dy) of the equilibrium flat interface at nodes 0..n-1."""
+    rho, d = np.empty(n), np.empty(n)
+    check(lib().lbm_flat_profile(C.byref(params), n, y0, _ptr(rho), _ptr(d)), "lbm_flat_profile")
+    return rho, d
 
 
 def lbm_maxwell(params):
@@ -282,6 +300,24 @@ class Sim:
         if rc not in (LBM_OK, LBM_EUNSTABLE) or (raise_unstable and rc == LBM_EUNSTABLE):
             check(rc, "lbm_step_observe")
         return o.as_dict()
+
+    def lbm_force_angle(self, frac=0.1, center=None):
+        """(max angle, |F|-weighted mean angle, nodes) of Eq. 30 on the current state."""
+        out = np.zeros(3)
+        c = _f64(center) if center is not None else None
+        check(lib().lbm_force_angle(self.h, _ptr(c) if c is not None else None, frac, _ptr(out)), "lbm_force_angle")
+        return out[0], out[1], int(out[2])
+
+    def lbm_set_solid(self, mask, mu_w=0.0):
+        """Wall nodes (Appendix A) where `mask` (lattice shape) is nonzero,
+        with wall chemical potential mu_w; mask None removes the walls."""
+        if mask is None:
+            check(lib().lbm_set_solid(self.h, None, 0.0), "lbm_set_solid")
+            return
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        if m.size != int(np.prod(self.shape)):
+            raise ValueError("mask must have the lattice's size")
+        check(lib().lbm_set_solid(self.h, m.ctypes.data_as(C.POINTER(C.c_ubyte)), float(mu_w)), "lbm_set_solid")
 
     def lbm_get_density(self, out=None):
         """Density field as FP64 host array; `out` (e.g. a pinned buffer of

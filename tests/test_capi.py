@@ -74,3 +74,36 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(lbm, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(ImportError):
         lbm.lib()
+
+
+def test_flat_profile_matches_oracle(libpath):
+    # the library's analytic flat interface (Eq. 29) against the oracle's, two
+    # independent quadratures of the same first integral; CS and PR
+    import numpy as np
+    from paper_2205_09186_gb300 import lbm
+    import oracle as O
+    for kw, okw in ((dict(Tr=0.6, k=0.4, kappa=0.1), dict()),
+                    (dict(eos="PR", a=2.0 / 49.0, b=2.0 / 21.0, Tr=0.7, k=0.2, kappa=0.01),
+                     dict(eos="PR", a=2.0 / 49.0, b=2.0 / 21.0))):
+        r, d = lbm.lbm_flat_profile(lbm.make_params(**kw), 96, 47.5)
+        ro, do = O.flat_profile(96, 47.5, kw["Tr"], kw["k"], kw["kappa"], **okw)
+        assert np.max(np.abs(r - ro)) < 1e-8 * np.max(ro)
+        assert np.max(np.abs(d - do)) < 5e-8 * np.max(do)
+
+
+def test_bulk_mu_matches_oracle(libpath):
+    # k^2 psi'(rho) of the library's host EOS against the oracle's, for each EOS
+    from paper_2205_09186_gb300 import lbm
+    import oracle as O
+    k = 0.3
+    cases = [("CS", O.EOS_CS, 1.0, 4.0, (0.01, 0.1, 0.5)),
+             ("PR", O.EOS_PR, 2.0 / 49.0, 2.0 / 21.0, (0.05, 1.0, 6.0)),
+             ("VDW", O.EOS_VDW, 9.0 / 49.0, 2.0 / 21.0, (0.05, 1.0, 6.0)),
+             ("RKS", O.EOS_RKS, 2.0 / 49.0, 2.0 / 21.0, (0.05, 1.0, 6.0))]
+    for name, kind, a, b, rhos in cases:
+        p = lbm.make_params(eos=name, a=a, b=b, Tr=0.8, k=k)
+        e = O.eos_make(kind, a, b, 1.0, 0.8, 0.344)
+        for rho in rhos:
+            assert lbm.lbm_bulk_mu(p, rho) == pytest.approx(k * k * O.eos_mu(e, rho), rel=1e-12, abs=1e-14)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_bulk_mu(lbm.make_params(), -1.0)
