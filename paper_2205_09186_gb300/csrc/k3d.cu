@@ -126,15 +126,15 @@ static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 
 template <int S>
 cudaError_t launch_mu(const Launch& c) {
   if (c.kp.nx % 4 == 0 && aligned16(c.rin) && aligned16(c.mu)) {
-    using Sh = MuV4Shape<S>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_mu3d_v4<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    dim3 g((c.kp.nx + MVX - 1) / MVX, (c.kp.ny + MVY - 1) / MVY, (c.kp.nz + MVZ - 1) / MVZ);
-    k_mu3d_v4<S><<<g, MVT, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+    // z chunks: enough CTAs for several waves, at least 8 planes per chunk
+    const int gx = (c.kp.nx + MZX - 1) / MZX, gy = (c.kp.ny + MZY - 1) / MZY;
+    const long long want = 8LL * num_sms();
+    const int nzc = int(std::max<long long>(1, std::min<long long>((want + gx * gy - 1) / (gx * gy),
+                                                                    (c.kp.nz + 7) / 8)));
+    const int zc = (c.kp.nz + nzc - 1) / nzc;
+    dim3 g(gx, gy, (c.kp.nz + zc - 1) / zc);
+    k_mu3d_zm<S><<<g, MZT, MuZShape<S>::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin),
+                                                           static_cast<float*>(c.mu), zc);
   } else {
     dim3 g((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
     k_mu3d<S><<<g, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));

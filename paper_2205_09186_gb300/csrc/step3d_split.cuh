@@ -53,6 +53,30 @@ struct CollShape {
   static constexpr int KF = (FCH + CNT - 1) / CNT;
 };
 
+// grad mu and grad rho of a line scheme together: the two fields' terms of a
+// stencil offset packed in one float2 (x: mu, y: density deviation), each
+// offset pair costing two packed FMAs, d = p - q (as -1 q + p, one rounding)
+// and acc += g d, instead of four scalar instructions.
+template <int S>
+__device__ __forceinline__ void grad3d_pair(const float* smu, const float* sds, const int* base, int W, int cx, int cy,
+                                            float2& gx, float2& gy, float2& gz) {
+  constexpr int R = Sch<S>::R;
+  const float2 m1 = make_float2(-1.f, -1.f);
+  float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+  const int c = cy * W + cx;
+  auto pr = [&](int o) { return make_float2(smu[o], sds[o]); };
+#pragma unroll
+  for (int m = 1; m <= R; ++m) {
+    const float2 g = make_float2(float(Sch<S>::g(m)), float(Sch<S>::g(m)));
+    ax = __ffma2_rn(g, __ffma2_rn(m1, pr(base[R] + c - m), pr(base[R] + c + m)), ax);
+    ay = __ffma2_rn(g, __ffma2_rn(m1, pr(base[R] + c - m * W), pr(base[R] + c + m * W)), ay);
+    az = __ffma2_rn(g, __ffma2_rn(m1, pr(base[R - m] + c), pr(base[R + m] + c)), az);
+  }
+  gx = ax;
+  gy = ay;
+  gz = az;
+}
+
 // VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations).
 // OBS: also reduce the observables of the state being advanced (max |v| with
 // v = u + F / (2 rho), max |u|, mass, max |rho - snap|) into aux.partials, one
@@ -193,18 +217,21 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       const int c = (cy + R) * GWV + ox + cx + R;
       const float dsv = s_ds[base[R] + c];
       const float rc = rref + dsv;
+      // momentum from the differences of opposite populations (e_{i+1} = -e_i
+      // for odd i): nine subtractions, then each component sums five of them
       float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (L::ex(i) != 0) jx += float(L::ex(i)) * fv[i];
-        if (L::ey(i) != 0) jy += float(L::ey(i)) * fv[i];
-        if (L::ez(i) != 0) jz += float(L::ez(i)) * fv[i];
+      for (int i = 1; i < Q; i += 2) {
+        const float d = fv[i] - fv[i + 1];
+        if (L::ex(i) != 0) jx = L::ex(i) > 0 ? jx + d : jx - d;
+        if (L::ey(i) != 0) jy = L::ey(i) > 0 ? jy + d : jy - d;
+        if (L::ez(i) != 0) jz = L::ez(i) > 0 ? jz + d : jz - d;
       }
       const float irc = __fdividef(1.f, rc);
       const float ux = jx * irc, uy = jy * irc, uz = jz * irc;
-      float gmx, gmy, gmz, grx, gry, grz;
-      grad3d<S, float>(s_mu, base, GWV, ox + cx + R, cy + R, gmx, gmy, gmz);
-      grad3d<S, float>(s_ds, base, GWV, ox + cx + R, cy + R, grx, gry, grz);
+      float2 g2x, g2y, g2z;
+      grad3d_pair<S>(s_mu, s_ds, base, GWV, ox + cx + R, cy + R, g2x, g2y, g2z);
+      const float gmx = g2x.x, gmy = g2y.x, gmz = g2z.x, grx = g2x.y, gry = g2y.y, grz = g2z.y;
       const float Fx = -rc * gmx + grx * (1.f / 3.f), Fy = -rc * gmy + gry * (1.f / 3.f),
                   Fz = -rc * gmz + grz * (1.f / 3.f);
       const float vx = ux + Fx * irc, vy = uy + Fy * irc, vz = uz + Fz * irc;
@@ -264,18 +291,39 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
         // Away from the periodic seams the target offset of population i is
         // i N + e_x + e_y nx + e_z nx ny for every thread: a warp none of whose
         // pushing nodes lies on a seam stores with these common offsets.
+        // all 19 post-collision values first; at tau = 1 the pairs (i, i + 1)
+        // of opposite velocities (e_{i+1} = -e_i for odd i) share e_i . v and
+        // are evaluated two at a time by packed FMAs
+        float pst[Q];
+        if constexpr (TAU1) {
+          pst[0] = post(0);
+#pragma unroll
+          for (int i = 1; i < Q; i += 2) {
+            const float ev = edot<L>(i, vx, vy, vz);
+            const float wd = i < 7 ? wd1 : wd2, wr = i < 7 ? wr1 : wr2;
+            const float2 E = make_float2(ev, ev);
+            const float2 T = __ffma2_rn(make_float2(4.5f, 4.5f), E, make_float2(3.f, -3.f));
+            const float2 A = __ffma2_rn(E, T, make_float2(-vv15, -vv15));
+            const float2 P = __ffma2_rn(make_float2(wr, wr), A, make_float2(wd, wd));
+            pst[i] = P.x;
+            pst[i + 1] = P.y;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) pst[i] = post(i);
+        }
         const bool seam = push && (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1 || pz == 0 || pz == nz - 1);
         if (!__any_sync(__activemask(), seam)) {
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
-            const float fs = post(i);
+            const float fs = pst[i];
             keep(i, fs);
             if (push) fo[i * N + L::ex(i) + L::ey(i) * nx + L::ez(i) * NXY] = fs;
           }
         } else {
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
-            const float fs = post(i);
+            const float fs = pst[i];
             keep(i, fs);
             if (push) {
               const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) +
