@@ -28,43 +28,43 @@ constexpr int TXC = CX - 2, TYC = CY - 2;  // 30 x 9 tile
 constexpr int CNT = CX * CY;        // 352 threads
 constexpr int FW = 36;              // staged population row: 32 nodes + up to 3 of alignment
 
-// Shared-memory rows start at a 16-byte-aligned global x (x of the region's
-// first node rounded down to a multiple of 4), so that with nx % 4 == 0 every
-// row is a whole number of 16-byte chunks that never straddle the periodic
-// seam; the region's first node then sits at column ox (field planes) or of
-// (populations), 0..3.  The scalar path (any nx) uses the same layout with
-// both offsets 0.
+// Field planes: the density deviation and mu of a node side by side (one
+// float2, x = deviation, y = mu), copied in by two 4-byte copies per node, so
+// that every stencil offset of the two gradients is one 8-byte shared load.
+// Staged populations: rows start at a 16-byte-aligned global x (x of the
+// region's first node rounded down to a multiple of 4), so that with
+// nx % 4 == 0 every row is a whole number of 16-byte chunks that never
+// straddle the periodic seam; the region's first node then sits at column of
+// (0..3).  The scalar path (any nx) uses the same layout with of = 0.
 template <int S>
 struct CollShape {
   static constexpr int R = Sch<S>::R;
   static constexpr int GW = CX + 2 * R, GH = CY + 2 * R;  // field region (ring + stencil halo)
-  static constexpr int GWV = (GW + 6) / 4 * 4;            // row stride: GW + 3 columns, whole chunks
   static constexpr int NS = 2 * R + 2;                    // ring of planes (one in flight)
-  static constexpr int plane = GH * GWV;
+  static constexpr int plane = GH * GW;                   // float2 per field plane
   static constexpr int FPL = CY * FW;                     // staged populations of one i
   static constexpr int fbuf = 19 * FPL;
-  static constexpr size_t off_mu = size_t(NS) * plane * 4;
-  static constexpr size_t off_f = (off_mu + size_t(NS) * plane * 4 + 15) / 16 * 16;
+  static constexpr size_t off_f = (size_t(NS) * plane * 8 + 15) / 16 * 16;
   static constexpr size_t bytes = off_f + size_t(2) * fbuf * 4;
-  // 16-byte chunks per plane, and per thread
-  static constexpr int DCH = GH * (GWV / 4);              // of one field
-  static constexpr int KD = (2 * DCH + CNT - 1) / CNT;
+  // field nodes per plane, and per thread; 16-byte population chunks, and per thread
+  static constexpr int DE = plane;
+  static constexpr int KD = (DE + CNT - 1) / CNT;
   static constexpr int FCH = 19 * CY * (FW / 4);
   static constexpr int KF = (FCH + CNT - 1) / CNT;
 };
 
-// grad mu and grad rho of a line scheme together: the two fields' terms of a
-// stencil offset packed in one float2 (x: mu, y: density deviation), each
-// offset pair costing two packed FMAs, d = p - q (as -1 q + p, one rounding)
-// and acc += g d, instead of four scalar instructions.
+// grad rho and grad mu of a line scheme together from the interleaved field
+// planes (x: density deviation, y: mu): one 8-byte load per stencil value and
+// two packed FMAs per offset pair, d = p - q (as -1 q + p, one rounding) and
+// acc += g d, instead of four scalar instructions.
 template <int S>
-__device__ __forceinline__ void grad3d_pair(const float* smu, const float* sds, const int* base, int W, int cx, int cy,
+__device__ __forceinline__ void grad3d_pair(const float2* sdm, const int* base, int W, int cx, int cy,
                                             float2& gx, float2& gy, float2& gz) {
   constexpr int R = Sch<S>::R;
   const float2 m1 = make_float2(-1.f, -1.f);
   float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
   const int c = cy * W + cx;
-  auto pr = [&](int o) { return make_float2(smu[o], sds[o]); };
+  auto pr = [&](int o) { return sdm[o]; };
 #pragma unroll
   for (int m = 1; m <= R; ++m) {
     const float2 g = make_float2(float(Sch<S>::g(m)), float(Sch<S>::g(m)));
@@ -88,10 +88,9 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
                                                     const StepAux aux, const int zc, float* __restrict__ snap) {
   using L = Lattice<1>;
   using Sh = CollShape<S>;
-  constexpr int Q = 19, R = Sh::R, GWV = Sh::GWV, NS = Sh::NS, FPL = Sh::FPL;
+  constexpr int Q = 19, R = Sh::R, GW = Sh::GW, NS = Sh::NS, FPL = Sh::FPL;
   extern __shared__ __align__(16) unsigned char smem[];
-  float* s_ds = reinterpret_cast<float*>(smem);
-  float* s_mu = reinterpret_cast<float*>(smem + Sh::off_mu);
+  float2* s_dm = reinterpret_cast<float2*>(smem);
   float* s_f = reinterpret_cast<float*>(smem + Sh::off_f);
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -107,21 +106,21 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
   const float omega = float(p.omega), rref = float(p.rho_ref);
   const int pc_first = z0 - 1, pc_last = z1;
-  // first field / population column of the region in shared memory
-  const int ox = VEC ? (x0 - 1 - R) & 3 : 0;
+  // first population column of the region in shared memory
   const int of = VEC ? (x0 - 1) & 3 : 0;
 
-  // VEC: the x-y part of the global offset of each of this thread's chunks
-  // (fixed for the whole z march; the shared offset of chunk c is 4 c)
-  int dofs[VEC ? Sh::KD : 1], fofs[VEC ? Sh::KF : 1];
-  if constexpr (VEC) {
-    const int xad = x0 - 1 - R - ox, xaf = x0 - 1 - of;  // aligned starts (may be negative)
+  // the x-y part of the global offset of each of this thread's field nodes
+  // (fixed for the whole z march; the shared offset of node e is e) and, VEC,
+  // of its population chunks (shared offset of chunk c: 4 c)
+  int dofs[Sh::KD], fofs[VEC ? Sh::KF : 1];
 #pragma unroll
-    for (int k = 0; k < Sh::KD; ++k) {
-      const int c = tid + k * CNT, r = c < Sh::DCH ? c : c - Sh::DCH;
-      const int ry = r / (GWV / 4), j = r - ry * (GWV / 4);
-      dofs[k] = wrapn(y0 - 1 - R + ry, ny) * nx + wrapn(xad + 4 * j, nx);
-    }
+  for (int k = 0; k < Sh::KD; ++k) {
+    const int e = tid + k * CNT;
+    const int ry = e / GW, rx = e - ry * GW;
+    dofs[k] = e < Sh::DE ? wrapn(y0 - 1 - R + ry, ny) * nx + wrapn(x0 - 1 - R + rx, nx) : 0;
+  }
+  if constexpr (VEC) {
+    const int xaf = x0 - 1 - of;  // aligned start (may be negative)
 #pragma unroll
     for (int k = 0; k < Sh::KF; ++k) {
       const int c = tid + k * CNT, i = c / (CY * (FW / 4));  // population of chunk c
@@ -134,21 +133,20 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   // plane q - R (if collided) -> staging buffer of its parity
   auto issue = [&](int q, int slot) {
     const int zo = wrapi(q, nz) * NXY;  // q in [z0 - 1 - R, z1 + R]: one period at most
-    float* dd = s_ds + slot * Sh::plane;
-    float* dm = s_mu + slot * Sh::plane;
+    float2* dd = s_dm + slot * Sh::plane;
     const int pc = q - R;
     const bool fl = pc >= pc_first && pc <= pc_last;
     const int zf = wrapi(pc, nz) * NXY;
     float* fd = s_f + (pc & 1) * Sh::fbuf;
-    if constexpr (VEC) {
 #pragma unroll
-      for (int k = 0; k < Sh::KD; ++k) {
-        const int c = tid + k * CNT;
-        if (c < 2 * Sh::DCH) {
-          if (c < Sh::DCH) cpa16(dd + 4 * c, rin + zo + dofs[k]);
-          else cpa16(dm + 4 * (c - Sh::DCH), muf + zo + dofs[k]);
-        }
+    for (int k = 0; k < Sh::KD; ++k) {
+      const int e = tid + k * CNT;
+      if (e < Sh::DE) {
+        cpa4(&dd[e].x, rin + zo + dofs[k]);
+        cpa4(&dd[e].y, muf + zo + dofs[k]);
       }
+    }
+    if constexpr (VEC) {
       if (fl) {
 #pragma unroll
         for (int k = 0; k < Sh::KF; ++k) {
@@ -157,17 +155,6 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
         }
       }
     } else {
-      constexpr int GW = Sh::GW, NLD = (GW * Sh::GH + CNT - 1) / CNT;
-#pragma unroll
-      for (int k = 0; k < NLD; ++k) {
-        const int idx = tid + k * CNT;
-        const int ry = idx / GW, rx = idx - ry * GW;
-        if (idx < GW * Sh::GH && rx < VW + 2 + 2 * R && ry < VH + 2 + 2 * R) {
-          const int g = zo + wrapi(y0 - 1 - R + ry, ny) * nx + wrapi(x0 - 1 - R + rx, nx);
-          cpa4(dd + ry * GWV + rx, rin + g);
-          cpa4(dm + ry * GWV + rx, muf + g);
-        }
-      }
       if (fl && cnode) {
         const float* fs = fin + zf + gy * nx + gx;
         float* fo = fd + cy * FW + cx;
@@ -214,8 +201,8 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       float fv[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) fv[i] = fb[i * FPL + fme];
-      const int c = (cy + R) * GWV + ox + cx + R;
-      const float dsv = s_ds[base[R] + c];
+      const int c = (cy + R) * GW + cx + R;
+      const float dsv = s_dm[base[R] + c].x;
       const float rc = rref + dsv;
       // momentum from the differences of opposite populations (e_{i+1} = -e_i
       // for odd i): nine subtractions, then each component sums five of them
@@ -230,8 +217,8 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       const float irc = __fdividef(1.f, rc);
       const float ux = jx * irc, uy = jy * irc, uz = jz * irc;
       float2 g2x, g2y, g2z;
-      grad3d_pair<S>(s_mu, s_ds, base, GWV, ox + cx + R, cy + R, g2x, g2y, g2z);
-      const float gmx = g2x.x, gmy = g2y.x, gmz = g2z.x, grx = g2x.y, gry = g2y.y, grz = g2z.y;
+      grad3d_pair<S>(s_dm, base, GW, cx + R, cy + R, g2x, g2y, g2z);
+      const float grx = g2x.x, gry = g2y.x, grz = g2z.x, gmx = g2x.y, gmy = g2y.y, gmz = g2z.y;
       const float Fx = -rc * gmx + grx * (1.f / 3.f), Fy = -rc * gmy + gry * (1.f / 3.f),
                   Fz = -rc * gmz + grz * (1.f / 3.f);
       const float vx = ux + Fx * irc, vy = uy + Fy * irc, vz = uz + Fz * irc;

@@ -170,3 +170,21 @@ def test_bulk_mu_is_the_mu_of_a_uniform_fluid(L, eos, a, b, kap, rho):
     _, mu = s.lbm_get_force()
     want = L.lbm_bulk_mu(p, rho)
     assert np.max(np.abs(mu - want)) <= 1e-13 * abs(want) + 1e-15
+
+
+@pytest.mark.parametrize("lattice,shape,scheme,precision,tol,steps",
+                         [(2, (29, 37), "EFDS4", 0, 1e-12, 60), (3, (11, 13, 17), "EFDS6", 0, 1e-12, 30),
+                          (3, (11, 13, 17), "EFDS6", 1, 1e-5, 30)])
+def test_scattered_obstacles_on_ragged_lattices(L, lattice, shape, scheme, precision, tol, steps):
+    # isolated wall nodes and small clusters (seed 7, ~6-8% of the nodes),
+    # lattice sizes that fill no tile or warp evenly
+    rng = np.random.default_rng(7)
+    mask = (rng.random(shape) < (0.08 if lattice == 2 else 0.06)).astype(np.uint8)
+    g, o = pair(L, lattice, shape, scheme, precision=precision)
+    c = [shape[-1] // 2, shape[-2] // 2, shape[0] // 2 if lattice == 3 else 0]
+    r = 7.0 if lattice == 2 else 4.0
+    g.lbm_init_droplet(r, center=[float(v) for v in c])
+    o.init_droplet(r, center=[float(v) for v in c])
+    g.lbm_set_solid(mask, mu_sat())
+    o.set_solid(mask, mu_sat())
+    compare(g, o, mask, tol, steps)
