@@ -12,6 +12,7 @@ Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead,
 on a bounded sample of the same workload.
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -325,21 +326,26 @@ def run_gpu(args):
 
     # end to end through the public API with pinned host buffers: upload the
     # initial density (H2D), step with the observables of every step read back
-    # (D2H; lbm_step_observe reports the state each step started from), read
+    # (D2H; lbm_step_observe_async reports the state each step started from), read
     # back the final density (D2H)
     host_rho0 = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
     host_rho0[:] = sim.lbm_get_density().reshape(-1)
     host_rho = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    # one page-locked lbm_obs record per step, filled by the stream
+    rec_size = ctypes.sizeof(L.lbm_obs)
+    host_obs = torch.empty(rec_size * args.steps, dtype=torch.uint8).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim.lbm_init_density(host_rho0)
-    for _ in range(args.steps):
-        sim.lbm_step_observe(1)
-    sim.lbm_get_density(out=host_rho)
+    for k in range(args.steps):
+        sim.lbm_step_observe_async(1, host_obs.data_ptr() + rec_size * k)
+    sim.lbm_get_density(out=host_rho)  # synchronises the stream
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    e2e_last = L.lbm_obs.from_address(host_obs.data_ptr() + rec_size * (args.steps - 1))
     e2e = {"value": N * args.steps * world / e2e_s / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": N * 8 / args.steps, "d2h_bytes_per_step": 64 + N * 8 / args.steps}
+           "h2d_bytes_per_step": N * 8 / args.steps, "d2h_bytes_per_step": rec_size + N * 8 / args.steps,
+           "last_status": e2e_last.status}
 
     sim.close()
     extra = {}

@@ -225,6 +225,17 @@ int lbm_observables(lbm_handle* h, lbm_obs* out);
  * entry point; the paper's method has no counterpart.) */
 int lbm_step_observe(lbm_handle* h, long long n, lbm_obs* out);
 
+/* As lbm_step_observe without synchronising the stream: the observables are
+ * reduced and packed on the device and copied to *out by the handle's stream,
+ * so consecutive calls queue their steps back to back.  out: host memory
+ * (page-locked for the copy to be asynchronous) or device memory, at least
+ * sizeof(lbm_obs) bytes; valid once the stream has been synchronised (for
+ * example by the next synchronising call); out->status and out->step report
+ * instability (LBM_EUNSTABLE and the first bad step).  Returns LBM_OK once the
+ * work is queued (LBM_EINVAL, LBM_ECUDA otherwise).  (A performance entry
+ * point; the paper's method has no counterpart.) */
+int lbm_step_observe_async(lbm_handle* h, long long n, lbm_obs* out);
+
 /* Copy the density field rho[N] (FP64) to host memory (synchronises). */
 int lbm_get_density(lbm_handle* h, double* host_rho);
 

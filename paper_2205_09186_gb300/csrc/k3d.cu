@@ -107,13 +107,14 @@ template <int S, bool TAU1, bool VEC, bool OBS>
 cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
   using Sh = CollShape<S>;
   auto kc = k_coll3d<S, TAU1, VEC, OBS>;
+  constexpr size_t by = OBS ? Sh::bytes_obs : Sh::bytes;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+    cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(by));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  kc<<<grid, CNT, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
+  kc<<<grid, CNT, by, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
                                          static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
                                          static_cast<float*>(c.rout), c.aux, zc,
                                          OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr);

@@ -33,7 +33,7 @@ struct lbm_handle {
   unsigned long long* d_bad = nullptr;
   double* d_partials = nullptr;
   int n_partials = 0;
-  double* d_obs = nullptr;   // 8 doubles
+  double* d_obs = nullptr;   // 8 doubles, then one packed lbm_obs
   long long t = 0, t_snap = 0;
   KParams kp{};
   StepFn fn = nullptr;
@@ -325,6 +325,11 @@ __constant__ double c_w19[19] = {1.0 / 3,  1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 1
                                  1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36,
                                  1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
+__constant__ float c_w9f[9] = {4.f / 9, 1.f / 9, 1.f / 9, 1.f / 9, 1.f / 9, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36};
+__constant__ float c_w19f[19] = {1.f / 3,  1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18,
+                                 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36,
+                                 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36};
+
 struct InitSpec {
   int kind;  // 0 droplet, 1 slab, 2 radial profile, 3 density array
   double cx, cy, cz, radius, width, rho_l, rho_g;
@@ -361,10 +366,12 @@ template <typename Tf>
 __global__ void k_init(KParams p, int Q, InitSpec s, Tf* f, Tf* rho) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= p.n) return;
-  const int x = int(n % p.nx), y = int((n / p.nx) % p.ny), z = int(n / ((long long)p.nx * p.ny));
+  // (a density array needs no coordinates: skip the 64-bit divisions)
+  const int x = s.kind == 3 ? 0 : int(n % p.nx), y = s.kind == 3 ? 0 : int((n / p.nx) % p.ny);
+  const int z = s.kind == 3 ? 0 : int(n / ((long long)p.nx * p.ny));
   const double r0 = init_density(s, x, y, z, n);
-  const double* w = Q == 9 ? c_w9 : c_w19;
   if constexpr (sizeof(Tf) == 8) {
+    const double* w = Q == 9 ? c_w9 : c_w19;
     double acc = 0;
     for (int i = 0; i < Q; ++i) {
       const double fi = w[i] * r0;
@@ -373,9 +380,13 @@ __global__ void k_init(KParams p, int Q, InitSpec s, Tf* f, Tf* rho) {
     }
     rho[n] = acc;
   } else {
+    // the deviation once in FP64, the Q weighted copies in FP32 (FP64 runs at
+    // a small fraction of the FP32 rate on this GPU)
+    const float dv = float(r0 - p.rho_ref);
+    const float* w = Q == 9 ? c_w9f : c_w19f;
     FSum acc;
     for (int i = 0; i < Q; ++i) {
-      const float d = float(w[i] * (r0 - p.rho_ref));
+      const float d = w[i] * dv;
       f[i * p.n + n] = d;
       acc.add(d);
     }
@@ -424,9 +435,11 @@ __global__ void k_import_f(KParams p, int Q, const double* in, Tf* f) {
 }
 
 // final reduction of per-CTA observables, fixed order (deterministic)
+// rec (optional): the same as a complete lbm_obs of the state of step t_obs,
+// max |d rho / dt| over dt steps (0: none)
 template <typename Tr>
 __global__ void k_obs_final(const double* part, int nb, const Tr* rho, double rho_ref, long long center,
-                            const unsigned long long* bad, double* out) {
+                            const unsigned long long* bad, double* out, lbm_obs* rec, long long t_obs, long long dt) {
   __shared__ double red[4][256];
   double a = 0, b = 0, c = 0, d = 0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -452,6 +465,16 @@ __global__ void k_obs_final(const double* part, int nb, const Tr* rho, double rh
     out[5] = sizeof(Tr) == 8 ? double(rho[0]) : rho_ref + double(rho[0]);
     unsigned long long bs = *bad;
     reinterpret_cast<unsigned long long*>(out)[6] = bs;
+    if (rec) {
+      rec->max_v = out[0];
+      rec->max_u = out[1];
+      rec->mass = out[2];
+      rec->max_drho = dt > 0 ? out[3] / double(dt) : 0.0;
+      rec->rho_center = out[4];
+      rec->rho_corner = out[5];
+      rec->step = bs != ~0ULL ? (long long)bs : t_obs;
+      rec->status = bs != ~0ULL ? LBM_EUNSTABLE : LBM_OK;
+    }
   }
 }
 
@@ -472,7 +495,7 @@ extern "C" void lbm_destroy(lbm_handle* h) {
   dfree(h, h->rho_snap, r_bytes(h));
   dfree(h, h->d_bad, 8);
   dfree(h, h->d_partials, size_t(h->n_partials) * 4 * 8);
-  dfree(h, h->d_obs, 64);
+  dfree(h, h->d_obs, 64 + sizeof(lbm_obs));
   dfree(h, h->mu, size_t(h->N) * 4);
   dfree(h, h->layer, size_t(h->N));
   dfree(h, h->wmu, size_t(h->N) * 8);
@@ -538,7 +561,7 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
   h->rho[1] = dalloc(h, r_bytes(h));
   h->rho_snap = dalloc(h, r_bytes(h));
   h->d_bad = static_cast<unsigned long long*>(dalloc(h, 8));
-  h->d_obs = static_cast<double*>(dalloc(h, 64));
+  h->d_obs = static_cast<double*>(dalloc(h, 64 + sizeof(lbm_obs)));
   // partials: one per CTA of the observation pass (upper bound over tilings used)
   h->n_partials = int((params->nx / 8 + 2) * (params->ny / 8 + 2) * (params->lattice == LBM_D2Q9 ? 1 : (params->nz / 8 + 2)));
   // the node-parallel observation pass of the split D3Q19 path uses up to 8 CTAs per SM
@@ -822,17 +845,26 @@ extern "C" int lbm_step_timed(lbm_handle* h, long long n, double* ms) {
 }
 
 // reduce nb per-CTA partials, read the result (and the density at the centre
-// and corner nodes of rho_obs) back, fill out for the state of step t_obs
-static int finish_observables(lbm_handle* h, int nb, const void* rho_obs, long long t_obs, lbm_obs* out) {
+// and corner nodes of rho_obs) back, fill out for the state of step t_obs.
+// async: the record is packed on the device and copied to out by the stream
+// (no synchronisation; out valid once the stream has been synchronised).
+static int finish_observables(lbm_handle* h, int nb, const void* rho_obs, long long t_obs, lbm_obs* out,
+                              bool async = false) {
   if (nb > h->n_partials) return LBM_ECUDA;
   const long long center =
       (long long)(h->p.nz / 2) * h->p.nx * h->p.ny + (long long)(h->p.ny / 2) * h->p.nx + h->p.nx / 2;
+  lbm_obs* rec = async ? reinterpret_cast<lbm_obs*>(h->d_obs + 8) : nullptr;
+  const long long dt = t_obs > h->t_snap ? t_obs - h->t_snap : 0;
   if (h->p.precision == LBM_FP64)
     k_obs_final<double><<<1, 256, 0, h->stream>>>(h->d_partials, nb, static_cast<const double*>(rho_obs), 0.0, center,
-                                                  h->d_bad, h->d_obs);
+                                                  h->d_bad, h->d_obs, rec, t_obs, dt);
   else
     k_obs_final<float><<<1, 256, 0, h->stream>>>(h->d_partials, nb, static_cast<const float*>(rho_obs),
-                                                 h->kp.rho_ref, center, h->d_bad, h->d_obs);
+                                                 h->kp.rho_ref, center, h->d_bad, h->d_obs, rec, t_obs, dt);
+  if (async) {
+    h->t_snap = t_obs;
+    return ck(cudaMemcpyAsync(out, rec, sizeof(lbm_obs), cudaMemcpyDefault, h->stream));
+  }
   double host[8];
   if (cudaMemcpyAsync(host, h->d_obs, 64, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return LBM_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
@@ -855,9 +887,7 @@ static int finish_observables(lbm_handle* h, int nb, const void* rho_obs, long l
   return LBM_OK;
 }
 
-extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
-  if (!h || !out) return LBM_EINVAL;
-  std::memset(out, 0, sizeof(*out));
+static int observe_impl(lbm_handle* h, lbm_obs* out, bool async) {
   Launch c = make_launch(h, h->cur);
   c.fout = nullptr;
   c.rout = nullptr;
@@ -868,12 +898,16 @@ extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
   // the snapshot for the next max |d rho / dt|, ordered after the reduction
   if (cudaMemcpyAsync(h->rho_snap, h->rho[h->cur], r_bytes(h), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return LBM_ECUDA;
-  return finish_observables(h, nb, h->rho[h->cur], h->t, out);
+  return finish_observables(h, nb, h->rho[h->cur], h->t, out, async);
 }
 
-extern "C" int lbm_step_observe(lbm_handle* h, long long n, lbm_obs* out) {
-  if (!h || !out || n < 1) return LBM_EINVAL;
+extern "C" int lbm_observables(lbm_handle* h, lbm_obs* out) {
+  if (!h || !out) return LBM_EINVAL;
   std::memset(out, 0, sizeof(*out));
+  return observe_impl(h, out, false);
+}
+
+static int step_observe_impl(lbm_handle* h, long long n, lbm_obs* out, bool async) {
   int rc = lbm_step(h, n - 1);
   if (rc != LBM_OK) return rc;
   if (h->D == 3 && h->mu && !h->compact && !h->layer) {
@@ -887,15 +921,26 @@ extern "C" int lbm_step_observe(lbm_handle* h, long long n, lbm_obs* out) {
       const long long t_obs = h->t;
       h->cur = 1 - h->cur;
       h->t += 1;
-      return finish_observables(h, nb, rho_obs, t_obs, out);
+      return finish_observables(h, nb, rho_obs, t_obs, out, async);
     }
     if (e != cudaErrorNotSupported) return LBM_ECUDA;
     cudaGetLastError();  // nothing was launched: observe, then step
   }
-  rc = lbm_observables(h, out);
+  rc = observe_impl(h, out, async);
   if (rc != LBM_OK && rc != LBM_EUNSTABLE) return rc;
   const int rs = lbm_step(h, 1);
   return rs != LBM_OK ? rs : rc;
+}
+
+extern "C" int lbm_step_observe(lbm_handle* h, long long n, lbm_obs* out) {
+  if (!h || !out || n < 1) return LBM_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  return step_observe_impl(h, n, out, false);
+}
+
+extern "C" int lbm_step_observe_async(lbm_handle* h, long long n, lbm_obs* out) {
+  if (!h || !out || n < 1) return LBM_EINVAL;
+  return step_observe_impl(h, n, out, true);
 }
 
 extern "C" int lbm_get_density(lbm_handle* h, double* host_rho) {

@@ -46,6 +46,10 @@ struct CollShape {
   static constexpr int fbuf = 19 * FPL;
   static constexpr size_t off_f = (size_t(NS) * plane * 8 + 15) / 16 * 16;
   static constexpr size_t bytes = off_f + size_t(2) * fbuf * 4;
+  // OBS: the snapshot values of the collided plane, one per thread, staged
+  // like the populations (double-buffered by plane parity)
+  static constexpr size_t off_snap = bytes;
+  static constexpr size_t bytes_obs = bytes + size_t(2) * CNT * 4;
   // field nodes per plane, and per thread; 16-byte population chunks, and per thread
   static constexpr int DE = plane;
   static constexpr int KD = (DE + CNT - 1) / CNT;
@@ -92,6 +96,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   extern __shared__ __align__(16) unsigned char smem[];
   float2* s_dm = reinterpret_cast<float2*>(smem);
   float* s_f = reinterpret_cast<float*>(smem + Sh::off_f);
+  float* s_snap = reinterpret_cast<float*>(smem + Sh::off_snap);  // OBS only
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int N = int(p.n), NXY = nx * ny;
@@ -162,6 +167,10 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
         for (int i = 0; i < Q; ++i) cpa4(fo + i * FPL, fs + i * N);
       }
     }
+    if constexpr (OBS) {
+      // the snapshot of this thread's node in plane pc (push planes only)
+      if (interior && pc >= z0 && pc < z1) cpa4(s_snap + (pc & 1) * CNT + tid, snap + pc * NXY + gy * nx + gx);
+    }
     cpa_commit();
   };
 
@@ -176,15 +185,10 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   issue(pc_first + R, slot);
   slot = ring(slot + 1, NS);
   const int fme = cy * FW + of + cx;  // this node in a staged population plane
-  float o_v2 = 0.f, o_u2 = 0.f, o_d = 0.f;  // OBS: running maxima (|v|^2, |u|^2, |rho - snap|)
+  float o_v2 = 0.f, o_u2 = 0.f, o_d = 0.f;  // OBS: running maxima (4 |v|^2, |u|^2, |rho - snap|)
   float o_m = 0.f;                           // OBS: sum of this thread's density deviations
   int o_n = 0;                               // OBS: nodes counted
-  // OBS: the snapshot value of this thread's node in the next collided plane,
-  // loaded one plane ahead so that its latency hides behind a whole plane
-  const int snap_xy = gy * nx + gx;
-  float snap_next = 0.f;
-  if constexpr (OBS)
-    if (interior && z0 < z1) snap_next = snap[z0 * NXY + snap_xy];
+  const int snap_xy = gy * nx + gx;  // OBS: this thread's node in a plane
   for (int pc = pc_first; pc <= pc_last; ++pc) {
     cpa_wait_all();
     __syncthreads();
@@ -226,12 +230,14 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       if (push && !(rc > 0.f)) atomicMin(aux.bad_step, (unsigned long long)aux.t);
       if constexpr (OBS) {
         if (push) {
-          const float hx = ux + 0.5f * Fx * irc, hy = uy + 0.5f * Fy * irc, hz = uz + 0.5f * Fz * irc;
+          // 2 (u + F / (2 rho)) = u + v: the running maximum holds 4 |v_obs|^2
+          const float hx = ux + vx, hy = uy + vy, hz = uz + vz;
           o_v2 = fmaxf(o_v2, hx * hx + hy * hy + hz * hz);
           o_u2 = fmaxf(o_u2, ux * ux + uy * uy + uz * uz);
-          o_d = fmaxf(o_d, fabsf(dsv - snap_next));
+          // the staged snapshot value was copied in before this plane's
+          // barrier; it is overwritten with this state's deviation
+          o_d = fmaxf(o_d, fabsf(dsv - s_snap[(pc & 1) * CNT + tid]));
           snap[pc * NXY + snap_xy] = dsv;  // push planes lie in [z0, z1): no wrap
-          if (pc + 1 < z1) snap_next = snap[(pc + 1) * NXY + snap_xy];
           o_m += dsv;  // at most one z-chunk of deviations per thread: FP32 suffices
           ++o_n;
         }
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
     sc = ring(sc + 1, NS);
   }
   if constexpr (OBS)
-    block_obs_reduce<CNT>(sqrt(double(o_v2)), sqrt(double(o_u2)), double(o_n) * p.rho_ref + double(o_m), double(o_d),
+    block_obs_reduce<CNT>(0.5 * sqrt(double(o_v2)), sqrt(double(o_u2)), double(o_n) * p.rho_ref + double(o_m), double(o_d),
                           aux.partials + 4 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }
 

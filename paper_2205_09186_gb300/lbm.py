@@ -65,6 +65,7 @@ SIGNATURES = {
     "lbm_step_timed": (C.c_int, [_h, C.c_longlong, _dp]),
     "lbm_observables": (C.c_int, [_h, C.POINTER(lbm_obs)]),
     "lbm_step_observe": (C.c_int, [_h, C.c_longlong, C.POINTER(lbm_obs)]),
+    "lbm_step_observe_async": (C.c_int, [_h, C.c_longlong, C.c_void_p]),
     "lbm_get_density": (C.c_int, [_h, _dp]),
     "lbm_get_f": (C.c_int, [_h, _dp]),
     "lbm_get_force": (C.c_int, [_h, _dp, _dp]),
@@ -300,6 +301,13 @@ class Sim:
         if rc not in (LBM_OK, LBM_EUNSTABLE) or (raise_unstable and rc == LBM_EUNSTABLE):
             check(rc, "lbm_step_observe")
         return o.as_dict()
+
+    def lbm_step_observe_async(self, n, out_addr):
+        """n steps; the observables of the state the last one started from are
+        written, by the stream, to the lbm_obs at address out_addr (page-locked
+        host or device memory), valid after the next synchronisation; read
+        them with lbm_obs.from_address(out_addr)."""
+        check(lib().lbm_step_observe_async(self.h, n, C.c_void_p(out_addr)), "lbm_step_observe_async")
 
     def lbm_force_angle(self, frac=0.1, center=None):
         """(max angle, |F|-weighted mean angle, nodes) of Eq. 30 on the current state."""

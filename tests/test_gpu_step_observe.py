@@ -46,13 +46,21 @@ def close(a, b, rel, keys=KEYS):
 @pytest.mark.parametrize("shape,scheme", [((48, 40, 44), "EFDS6"), ((42, 36, 40), "EFDS4"), ((40, 40, 40), "EFDS2")])
 def test_fused_observation_matches_observe_then_step(L, shape, scheme):
     a, b = make(L, shape, scheme=scheme), make(L, shape, scheme=scheme)
+    t_prev = 0
     for n in (12, 5):  # two cycles: the second max |d rho / dt| uses the fused kernel's snapshot
         a.lbm_step(n - 1)
         oa = a.lbm_observables()
         a.lbm_step(1)
         ob = b.lbm_step_observe(n)
         assert ob["status"] == 0 and ob["step"] == oa["step"] == b.lbm_get_step() - 1
-        close(ob, oa, 2e-6)
+        close(ob, oa, 2e-6, keys=[k for k in KEYS if k != "max_drho"])
+        # after the first cycle the two states differ by the FP32 rounding of the
+        # observing step (bounded below by 1e-6 of max rho): max |d rho / dt|, a
+        # difference of two such states, agrees to that bound over dt, not to a
+        # relative tolerance of its own small value
+        dt = ob["step"] - t_prev
+        assert abs(ob["max_drho"] - oa["max_drho"]) <= 1e-6 * oa["rho_center"] / dt
+        t_prev = ob["step"]
     ra, rb = a.lbm_get_density(), b.lbm_get_density()
     assert np.max(np.abs(ra - rb)) < 1e-6 * np.max(ra)
     assert np.max(np.abs(a.lbm_get_f() - b.lbm_get_f())) < 1e-6 * np.max(np.abs(a.lbm_get_f()))
@@ -96,3 +104,25 @@ def test_step_observe_rejects_zero_steps(L):
     with pytest.raises(L.LBMError) as e:
         s.lbm_step_observe(0)
     assert e.value.code == L.LBM_EINVAL
+
+
+@pytest.mark.parametrize("shape,kw", [((48, 40, 44), dict()), ((48, 40, 1), dict()), ((24, 24, 24), dict(scheme="E4")),
+                                      ((48, 40, 1), dict(precision=0))])
+def test_async_observation_equals_the_synchronous_one(L, shape, kw):
+    # the same kernels in the same order: bit-identical records, written by the
+    # stream into page-locked host memory and into device memory
+    import ctypes
+    import torch
+    a, b = make(L, shape, **kw), make(L, shape, **kw)
+    size = ctypes.sizeof(L.lbm_obs)
+    host = torch.empty(3 * size, dtype=torch.uint8).pin_memory()
+    dev = torch.empty(size, dtype=torch.uint8, device="cuda")
+    sync = [a.lbm_step_observe(n) for n in (9, 1, 4)]
+    for k, n in enumerate((9, 1)):
+        b.lbm_step_observe_async(n, host.data_ptr() + k * size)
+    b.lbm_step_observe_async(4, dev.data_ptr())
+    torch.cuda.synchronize()
+    host[2 * size:] = dev.cpu()
+    recs = [L.lbm_obs.from_address(host.data_ptr() + k * size).as_dict() for k in range(3)]
+    assert recs == sync
+    assert np.array_equal(a.lbm_get_density(), b.lbm_get_density())
