@@ -176,11 +176,12 @@ def batch_cases(n=512, seed=2205):
     return out
 
 
-def run_batch(L, steps=50, warmup=10):
-    """512 D2Q9 droplets of uneven sizes in one persistent graph-captured launch
-    per lbm_batch_step (FP32 deviation storage); returns MLUPS and case counts."""
+def run_batch(L, steps=50, warmup=10, ncases=512):
+    """ncases (512) D2Q9 droplets of uneven sizes in one persistent graph-captured
+    launch per lbm_batch_step (FP32 deviation storage); returns MLUPS and case
+    counts."""
     import torch
-    cases = batch_cases()
+    cases = batch_cases(ncases)
     params = [L.make_params(lattice=L.LBM_D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1,
                             scheme=c["scheme"], precision=L.LBM_FP32DEV) for c in cases]
     b = L.Batch(params)
@@ -199,7 +200,7 @@ def run_batch(L, steps=50, warmup=10):
     stable = sum(1 for o in obs if o["status"] == 0)
     ncases, nitems, grid = b.lbm_batch_size()
     b.close()
-    return {"workload": "512 D2Q9 droplets, sizes U{64..512}^2 (seed 2205), FP32DEV, one persistent launch",
+    return {"workload": "%d D2Q9 droplets, sizes U{64..512}^2 (seed 2205), FP32DEV, one persistent launch" % ncases,
             "nodes": nodes, "steps": steps, "ms": ms, "mlups": nodes * steps / (ms * 1e-3) / 1e6,
             "hbm_frac": nodes * steps * (9 * 4 * 2 + 4 * 2) / (ms * 1e-3) / 1e9 / measured_peak()[0],
             "stable_cases": stable, "work_items": nitems, "resident_ctas": grid, "status": rc}
@@ -350,7 +351,7 @@ def run_gpu(args):
     sim.close()
     extra = {}
     if not args.no_batch:
-        extra["batch2d"] = run_batch(L)
+        extra["batch2d"] = run_batch(L, steps=args.batch_steps, ncases=args.batch_cases)
         extra["d2q9_512"] = run_2d(L)
     if not args.no_warmstart:
         from paper_2205_09186_gb300 import warmstart as W
@@ -400,6 +401,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D sweep measurement")
+    ap.add_argument("--batch-cases", type=int, default=512, help="cases of the batched 2D sweep (small: profiling)")
+    ap.add_argument("--batch-steps", type=int, default=50, help="steps per timed launch of the batched 2D sweep")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start experiment")
     ap.add_argument("--zchunk", type=int, default=0, help="fix the z-chunk instead of autotuning (profiling runs)")
     ap.add_argument("--size", type=int, default=256,

@@ -233,8 +233,9 @@ __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phas
 // case, so its descriptor stays in L1 and neighbouring tiles share halos in L2;
 // and knowing the next items in advance lets the copies of the next NBUF - 1
 // items be in flight while the current one is computed.
-// Dynamic shared memory: NBUF buffers of buf_bytes (a multiple of 16).
-constexpr int NBUF = 3;
+// Dynamic shared memory: NBUF buffers of buf_bytes (a multiple of 16); two
+// 30 x 30 tiles' buffers (~48 KB each) keep two CTAs resident per SM.
+constexpr int NBUF = 2;
 
 __global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restrict__ cases,
                                                       const Item* __restrict__ mitems, int nmu,

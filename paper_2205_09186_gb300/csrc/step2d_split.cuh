@@ -1,12 +1,15 @@
 // D2Q9 FP32-deviation step as two passes (the 2D counterpart of
 // step3d_split.cuh):
 //
-//  mu2d_tile    mu = k^2 psi'(rho) - kappa lap rho (Eq. 16) for one 32 x 16
+//  mu2d_tile    mu = k^2 psi'(rho) - kappa lap rho (Eq. 16) for one 32 x 32
 //               tile (halo R staged in shared memory).
 //  coll2d_tile  grad mu, grad rho (Eq. 17-25) -> F (Eq. 12) -> BGK + EDM
 //               (Eq. 1, 6, 8) -> push streaming and the next density for a
-//               30 x 14 tile; its 32 x 16 tile-plus-ring region maps one warp
-//               to one row (512 threads, one collision per thread).
+//               30 x 30 tile; its 32 x 32 tile-plus-ring region maps one warp
+//               to two rows, w and w + 16 (512 threads, two collisions per
+//               thread: the per-tile staging, barriers and bookkeeping are
+//               shared by twice the nodes of a 30 x 14 tile, and the ring is
+//               6% of the region's rows instead of 12%).
 //
 // Both are device functions so that the single-case kernels and the
 // persistent batch kernel share them.
@@ -16,10 +19,12 @@
 
 namespace lbmd {
 
-constexpr int M2X = 32, M2Y = 16;           // mu tile
-constexpr int C2X = 32, C2Y = 16;           // collision region (tile + ring)
-constexpr int T2X = C2X - 2, T2Y = C2Y - 2; // 30 x 14 collision tile
 constexpr int NT2S = 512;                   // threads of both passes
+constexpr int RPT = 2;                      // rows per thread
+constexpr int M2X = 32, M2Y = 16 * RPT;     // mu tile
+constexpr int C2X = 32, C2Y = 16 * RPT;     // collision region (tile + ring)
+constexpr int T2X = C2X - 2, T2Y = C2Y - 2; // 30 x 30 collision tile
+constexpr int C2N = C2X * C2Y;              // nodes of the collision region
 
 template <int S>
 struct Split2DShape {
@@ -29,7 +34,7 @@ struct Split2DShape {
   static constexpr size_t mu_bytes = size_t(MW) * MH * 4;
   static constexpr size_t off_mu = size_t(GW) * GH * 4;
   static constexpr size_t off_f = (off_mu + size_t(GW) * GH * 4 + 15) / 16 * 16;
-  static constexpr size_t coll_bytes = off_f + size_t(9) * NT2S * 4;
+  static constexpr size_t coll_bytes = off_f + size_t(9) * C2N * 4;
   static constexpr size_t bytes = coll_bytes > mu_bytes ? coll_bytes : mu_bytes;
 };
 
@@ -63,12 +68,16 @@ __device__ __forceinline__ void mu2d_compute(const KParams& p, float* __restrict
   constexpr int R = Sh::R, MW = Sh::MW;
   const float* s = reinterpret_cast<const float*>(smem);
   const int nx = p.nx, ny = p.ny;
-  const int tx = threadIdx.x % M2X, ty = threadIdx.x / M2X;
-  if (x0 + tx < nx && y0 + ty < ny) {
-    const float k2 = float(p.k2), kap = float(p.kappa);
-    const float rho = float(p.rho_ref) + s[(ty + R) * MW + tx + R];
-    const float lap = lap2d<S, float>(s, MW, tx + R, ty + R);
-    mu[(y0 + ty) * nx + x0 + tx] = k2 * eos_mu_f(rho, eos_f(p)) - kap * lap;
+  const int tx = threadIdx.x % M2X;
+  const float k2 = float(p.k2), kap = float(p.kappa);
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int ty = threadIdx.x / M2X + r * (NT2S / M2X);
+    if (x0 + tx < nx && y0 + ty < ny) {
+      const float rho = float(p.rho_ref) + s[(ty + R) * MW + tx + R];
+      const float lap = lap2d<S, float>(s, MW, tx + R, ty + R);
+      mu[(y0 + ty) * nx + x0 + tx] = k2 * eos_mu_f(rho, eos_f(p)) - kap * lap;
+    }
   }
 }
 
@@ -84,11 +93,15 @@ __device__ __forceinline__ void coll2d_load(const KParams& p, const float* __res
   const int nx = p.nx, ny = p.ny, N = int(p.n);
   const int VW = min(T2X, nx - x0), VH = min(T2Y, ny - y0);
   const int tid = threadIdx.x;
-  const int cy = tid / C2X, cx = tid - cy * C2X;
-  if (cx - 1 <= VW && cy - 1 <= VH) {  // collided node: stage its populations
-    const float* fs = fin + wrapi(y0 + cy - 1, ny) * nx + wrapi(x0 + cx - 1, nx);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) cpa4(s_f + i * NT2S + tid, fs + i * N);
+  for (int r = 0; r < RPT; ++r) {
+    const int node = tid + r * NT2S;  // region rows w and w + 16 of warp w
+    const int cy = node / C2X, cx = node - cy * C2X;
+    if (cx - 1 <= VW && cy - 1 <= VH) {  // collided node: stage its populations
+      const float* fs = fin + wrapi(y0 + cy - 1, ny) * nx + wrapi(x0 + cx - 1, nx);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) cpa4(s_f + i * C2N + node, fs + i * N);
+    }
   }
   // fields: warp w copies rows w, w + 16, ...; lane l columns l and 32 + l
   // (the region of a ragged tile only as far as its collided nodes reach)
@@ -123,17 +136,18 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
   float* s_f = reinterpret_cast<float*>(smem + Sh::off_f);
   const int nx = p.nx, ny = p.ny, N = int(p.n);
   const int VW = min(T2X, nx - x0), VH = min(T2Y, ny - y0);
-  const int tid = threadIdx.x;
-  const int cy = tid / C2X, cx = tid - cy * C2X;
-  const int lx = cx - 1, ly = cy - 1;
-  const bool cnode = lx <= VW && ly <= VH;
-  const bool interior = lx >= 0 && lx < VW && ly >= 0 && ly < VH;
-  const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
   const float omega = float(p.omega), rref = float(p.rho_ref);
-  if (cnode) {
+#pragma unroll 1
+  for (int r = 0; r < RPT; ++r) {
+    const int node = threadIdx.x + r * NT2S;  // region rows w and w + 16 of warp w
+    const int cy = node / C2X, cx = node - cy * C2X;
+    const int lx = cx - 1, ly = cy - 1;
+    if (!(lx <= VW && ly <= VH)) continue;  // not a collided node
+    const bool interior = lx >= 0 && lx < VW && ly >= 0 && ly < VH;
+    const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
     float fv[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fv[i] = s_f[i * NT2S + tid];
+    for (int i = 0; i < Q; ++i) fv[i] = s_f[i * C2N + node];
     const int c = (cy + R) * GW + cx + R;
     const float dsv = s_ds[c];
     const float rc = rref + dsv;
@@ -159,42 +173,48 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
       mrt_post9<float>(fv, dsv, rc, ux, uy, vx, vy, mrt, post);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        s_f[i * NT2S + tid] = post[i];
+        s_f[i * C2N + node] = post[i];
         if (interior) {
           const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) + (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0));
           fo[i * N + d] = post[i];
         }
       }
     } else {
-    const float vv15 = 1.5f * (vx * vx + vy * vy), uu15 = 1.5f * (ux * ux + uy * uy);
+      const float vv15 = 1.5f * (vx * vx + vy * vy), uu15 = 1.5f * (ux * ux + uy * uy);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float w = float(L::w(i));
-      const float ev = edot<L>(i, vx, vy, 0.f);
-      const float Av = i == 0 ? -vv15 : ev * (3.f + 4.5f * ev) - vv15;
-      float fs;
-      if constexpr (TAU1) {
-        fs = w * (dsv + rc * Av);
-      } else {
-        const float eu = edot<L>(i, ux, uy, 0.f);
-        const float Au = i == 0 ? -uu15 : eu * (3.f + 4.5f * eu) - uu15;
-        fs = (1.f - omega) * fv[i] + w * (omega * dsv + rc * (omega * Au + Av - Au));
+      for (int i = 0; i < Q; ++i) {
+        const float w = float(L::w(i));
+        const float ev = edot<L>(i, vx, vy, 0.f);
+        const float Av = i == 0 ? -vv15 : ev * (3.f + 4.5f * ev) - vv15;
+        float fs;
+        if constexpr (TAU1) {
+          fs = w * (dsv + rc * Av);
+        } else {
+          const float eu = edot<L>(i, ux, uy, 0.f);
+          const float Au = i == 0 ? -uu15 : eu * (3.f + 4.5f * eu) - uu15;
+          fs = (1.f - omega) * fv[i] + w * (omega * dsv + rc * (omega * Au + Av - Au));
+        }
+        s_f[i * C2N + node] = fs;
+        if (interior) {
+          const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) + (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0));
+          fo[i * N + d] = fs;
+        }
       }
-      s_f[i * NT2S + tid] = fs;
-      if (interior) {
-        const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) + (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0));
-        fo[i * N + d] = fs;
-      }
-    }
     }
   }
   __syncthreads();
-  if (interior) {
-    float acc = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) acc += s_f[i * NT2S + tid - L::ey(i) * C2X - L::ex(i)];
-    rout[(y0 + ly) * nx + x0 + lx] = acc;
-    if (!(rref + acc > 0.f)) atomicMin(bad, (unsigned long long)(t + 1));
+  for (int r = 0; r < RPT; ++r) {
+    const int node = threadIdx.x + r * NT2S;
+    const int cy = node / C2X, cx = node - cy * C2X;
+    const int lx = cx - 1, ly = cy - 1;
+    if (lx >= 0 && lx < VW && ly >= 0 && ly < VH) {
+      float acc = 0.f;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) acc += s_f[i * C2N + node - L::ey(i) * C2X - L::ex(i)];
+      rout[(y0 + ly) * nx + x0 + lx] = acc;
+      if (!(rref + acc > 0.f)) atomicMin(bad, (unsigned long long)(t + 1));
+    }
   }
 }
 
