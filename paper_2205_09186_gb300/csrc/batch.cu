@@ -262,15 +262,17 @@ __global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restri
       }
       int b = 0;
       for (int it = i0; it < i1; ++it) {
-        __syncthreads();  // the buffer refilled below was last computed from one item ago
+        // this item's copies (the oldest group) have landed, and every thread
+        // is past the computation of the item before: one barrier covers both
+        // the data and the reuse of that item's buffer
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(NBUF - 2) : "memory");
+        __syncthreads();
         const int ahead = it + NBUF - 1;
         if (ahead < i1) {
           const Item itm = items[ahead];
           split_load(cases[itm.c], itm.tile, t, phase, smem + ring(b + NBUF - 1, NBUF) * buf_bytes);
         }
         cpa_commit();
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(NBUF - 1) : "memory");  // this item's copies landed
-        __syncthreads();
         const Item itm = items[it];
         split_compute(cases[itm.c], itm.tile, t, phase, smem + b * buf_bytes);
         b = ring(b + 1, NBUF);
