@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <type_traits>
 
+#include <cudaTypedefs.h>
+
 #include "launch.cuh"
 #include "step3d.cuh"
 #include "step3d_fast.cuh"
@@ -108,6 +110,11 @@ cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
   using Sh = CollShape<S>;
   auto kc = k_coll3d<S, TAU1, VEC, OBS>;
   constexpr size_t by = OBS ? Sh::bytes_obs : Sh::bytes;
+  CUtensorMap tm{};
+  if constexpr (VEC) {
+    if (!c.tmap) return cudaErrorInvalidValue;
+    tm = *static_cast<const CUtensorMap*>(c.tmap);
+  }
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(by));
@@ -117,11 +124,12 @@ cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
   kc<<<grid, CNT, by, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
                                          static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
                                          static_cast<float*>(c.rout), c.aux, zc,
-                                         OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr);
+                                         OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr, tm);
   return cudaGetLastError();
 }
 
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+
 
 // the mu pass: the vector kernel when rows are whole 16-byte chunks
 template <int S>
@@ -162,7 +170,7 @@ cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   if (em != cudaSuccess) return em;
   if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
   // 16-byte copies need rows of whole chunks and aligned bases
-  const bool vec = c.kp.nx % 4 == 0 && aligned16(c.fin) && aligned16(c.rin) && aligned16(c.mu);
+  const bool vec = c.kp.nx % 4 == 0 && aligned16(c.fin) && aligned16(c.rin) && aligned16(c.mu) && c.tmap;
   if (obs)
     return vec ? launch_coll<S, TAU1, true, true>(c, grid, zc) : launch_coll<S, TAU1, false, true>(c, grid, zc);
   return vec ? launch_coll<S, TAU1, true, false>(c, grid, zc) : launch_coll<S, TAU1, false, false>(c, grid, zc);
@@ -211,6 +219,26 @@ StepFn pick(int prec) {
 
 long long step3d_obs_ctas(const KParams& kp) {
   return (long long)((kp.nx + TX3 - 1) / TX3) * ((kp.ny + TY3 - 1) / TY3) * ((kp.nz + ZC3 - 1) / ZC3);
+}
+
+bool make_coll3d_tmap(const void* f, const KParams& kp, void* out) {
+  if (kp.nx % 4 != 0 || (reinterpret_cast<uintptr_t>(f) & 15) != 0) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[4] = {cuuint64_t(kp.nx), cuuint64_t(kp.ny), cuuint64_t(kp.nz), 19};
+  const cuuint64_t strides[3] = {cuuint64_t(kp.nx) * 4, cuuint64_t(kp.nx) * kp.ny * 4, cuuint64_t(kp.n) * 4};
+  const cuuint32_t box[4] = {cuuint32_t(FW), cuuint32_t(CY), 1, 19};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(f), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 StepFn step3d_fn(int scheme, int prec) {

@@ -22,6 +22,7 @@ struct Launch {
   void* mu;     // N floats: mu field of the split D3Q19 FP32DEV path (else unused)
   Mrt mrt;      // D2Q9 collision operator (on = 0: single relaxation)
   cudaEvent_t ev_mid;  // if set: recorded between the mu pass and the collision pass
+  const void* tmap;    // D3Q19 FP32DEV: tensor map (CUtensorMap) of the populations fin, or null
 };
 
 // Kernel constants of a case: lattice size, the EOS at T = Tr T_c (either
@@ -47,6 +48,12 @@ using StepFn = cudaError_t (*)(const Launch&, int mode, int* nblocks);
 // precision index: 0 = FP64, 1 = FP32DEV with FP32 mu, 2 = FP32DEV with FP64 mu
 StepFn step2d_fn(int scheme, int prec);
 StepFn step3d_fn(int scheme, int prec);
+
+// Tensor map of a D3Q19 FP32-deviation population array f[19][nz][ny][nx]
+// for the collision pass's tensor copies, written to out (a CUtensorMap, 128
+// bytes, 64-byte aligned).  False when the lattice or the pointer does not
+// allow one (nx % 4 != 0, unaligned base) or the driver refuses it.
+bool make_coll3d_tmap(const void* f, const KParams& kp, void* out);
 
 // number of CTAs (hence partial results) of the observation pass
 long long step2d_obs_ctas(const KParams& kp);

@@ -44,6 +44,8 @@ struct lbm_handle {
   signed char* layer = nullptr;  // wall layers (Appendix A): 0 fluid, 1..3, 4 deeper; null: no walls
   void* wmu = nullptr;           // mu field of the wall step (N values of the precision's mu type)
   double mu_w = 0.0;             // wall chemical potential
+  alignas(64) unsigned char tmap[2][128];  // D3Q19 FP32DEV: tensor maps (CUtensorMap) of f[0], f[1]
+  bool has_tmap = false;
 };
 
 // ------------------------------------------------------------------ allocation
@@ -572,6 +574,9 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
       (h->D == 3 ? split3d_scheme(params->scheme, h->prec) : split2d_scheme(params->scheme, h->prec))) {
     h->mu = dalloc(h, size_t(h->N) * 4);
     ok = h->mu != nullptr;
+    // tensor maps of both population buffers for the collision pass's copies
+    if (ok && h->D == 3)
+      h->has_tmap = make_coll3d_tmap(h->f[0], h->kp, h->tmap[0]) && make_coll3d_tmap(h->f[1], h->kp, h->tmap[1]);
   }
   if (ok && h->compact) {
     rc = compact_alloc(h->cb, h->kp, h->D, params->scheme, h->prec, [&](size_t b) { return dalloc(h, b); });
@@ -733,6 +738,7 @@ static Launch make_launch(lbm_handle* h, int out_buf) {
   c.zc = h->zc;
   c.mu = h->mu;
   c.mrt = h->mrt;
+  c.tmap = h->has_tmap ? h->tmap[h->cur] : nullptr;
   return c;
 }
 

@@ -15,6 +15,8 @@
 // collision region, so the stencil reads of a warp are contiguous (free of
 // bank conflicts).
 #pragma once
+#include <cuda.h>  // CUtensorMap
+
 #include "lbm_device.cuh"
 #include "step3d.cuh"
 #include "step3d_fast.cuh"
@@ -35,7 +37,11 @@ constexpr int FW = 36;              // staged population row: 32 nodes + up to 3
 // region's first node rounded down to a multiple of 4), so that with
 // nx % 4 == 0 every row is a whole number of 16-byte chunks that never
 // straddle the periodic seam; the region's first node then sits at column of
-// (0..3).  The scalar path (any nx) uses the same layout with of = 0.
+// (0..3).  The scalar path (any nx) uses the same layout with of = 0.  With
+// VEC a CTA whose population region lies inside the lattice (no periodic
+// seam) stages it with one tensor copy (TMA) per plane: a 36 x 11 x 1 x 19 box
+// of the populations viewed as a 4-D tensor (x, y, z, i) lands in exactly this
+// layout; the buffers are 1 KB aligned for it.
 template <int S>
 struct CollShape {
   static constexpr int R = Sch<S>::R;
@@ -43,8 +49,9 @@ struct CollShape {
   static constexpr int NS = 2 * R + 2;                    // ring of planes (one in flight)
   static constexpr int plane = GH * GW;                   // float2 per field plane
   static constexpr int FPL = CY * FW;                     // staged populations of one i
-  static constexpr int fbuf = 19 * FPL;
-  static constexpr size_t off_f = (size_t(NS) * plane * 8 + 15) / 16 * 16;
+  static constexpr int fbuf = (19 * FPL + 255) / 256 * 256;  // buffer stride (floats), 1 KB multiple
+  static constexpr unsigned box_bytes = 19u * FPL * 4u;       // one tensor copy
+  static constexpr size_t off_f = (size_t(NS) * plane * 8 + 1023) / 1024 * 1024;
   static constexpr size_t bytes = off_f + size_t(2) * fbuf * 4;
   // OBS: the snapshot values of the collided plane, one per thread, staged
   // like the populations (double-buffered by plane parity)
@@ -81,7 +88,26 @@ __device__ __forceinline__ void grad3d_pair(const float2* sdm, const int* base, 
   gz = az;
 }
 
-// VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations).
+// mbarrier helpers of the tensor-copy staging.  Waits are bounded: after about
+// a second of polling the wait gives up (the caller records an error) instead
+// of hanging the GPU.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations),
+// and tensor copies of the populations for CTAs away from the periodic seams
+// (tmf: the populations as a 4-D tensor (nx, ny, nz, 19), box (FW, CY, 1, 19)).
 // OBS: also reduce the observables of the state being advanced (max |v| with
 // v = u + F / (2 rho), max |u|, mass, max |rho - snap|) into aux.partials, one
 // set per CTA, and overwrite snap with this state's density deviation.
@@ -89,11 +115,14 @@ template <int S, bool TAU1, bool VEC, bool OBS>
 __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float* __restrict__ fin,
                                                     float* __restrict__ fout, const float* __restrict__ rin,
                                                     const float* __restrict__ muf, float* __restrict__ rout,
-                                                    const StepAux aux, const int zc, float* __restrict__ snap) {
+                                                    const StepAux aux, const int zc, float* __restrict__ snap,
+                                                    const __grid_constant__ CUtensorMap tmf) {
   using L = Lattice<1>;
   using Sh = CollShape<S>;
   constexpr int Q = 19, R = Sh::R, GW = Sh::GW, NS = Sh::NS, FPL = Sh::FPL;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_c3[];  // (own name: other kernels align theirs to 16)
+  unsigned char* smem = smem_c3;
+  __shared__ __align__(8) unsigned long long s_bar[2];  // tensor copies: one mbarrier per buffer
   float2* s_dm = reinterpret_cast<float2*>(smem);
   float* s_f = reinterpret_cast<float*>(smem + Sh::off_f);
   float* s_snap = reinterpret_cast<float*>(smem + Sh::off_snap);  // OBS only
@@ -113,6 +142,19 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   const int pc_first = z0 - 1, pc_last = z1;
   // first population column of the region in shared memory
   const int of = VEC ? (x0 - 1) & 3 : 0;
+  // tensor copies when the population region (36 columns from the aligned
+  // start, 11 rows) needs no periodic wrap
+  // (and the staging buffers 128-byte aligned, as tensor copies require)
+  const bool tcta = VEC && x0 - 1 - of >= 0 && x0 - 1 - of + FW <= nx && y0 - 1 >= 0 && y0 - 1 + CY <= ny &&
+                    (smem_u32(s_f) & 127u) == 0 && ((Sh::fbuf * 4) & 127) == 0;
+  if (tcta && tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned bar_phase = 0;  // bit b: parity of the next completion of s_bar[b]
+  bool tma_lost = false;   // a wait ran out: later waits are skipped (the step is already marked bad)
 
   // the x-y part of the global offset of each of this thread's field nodes
   // (fixed for the whole z march; the shared offset of node e is e) and, VEC,
@@ -152,7 +194,22 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       }
     }
     if constexpr (VEC) {
-      if (fl) {
+      if (fl && tcta) {
+        if (tid == 0) {
+          // the buffer's previous contents were read and written through the
+          // generic proxy before the barrier that precedes this call
+          const unsigned bar = smem_u32(&s_bar[pc & 1]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(Sh::box_bytes)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(fd)),
+              "l"(reinterpret_cast<unsigned long long>(&tmf)), "r"(x0 - 1 - of), "r"(y0 - 1), "r"(wrapi(pc, nz)),
+              "r"(0), "r"(bar)
+              : "memory");
+        }
+      } else if (fl) {
 #pragma unroll
         for (int k = 0; k < Sh::KF; ++k) {
           const int c = tid + k * CNT;
@@ -191,6 +248,19 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   const int snap_xy = gy * nx + gx;  // OBS: this thread's node in a plane
   for (int pc = pc_first; pc <= pc_last; ++pc) {
     cpa_wait_all();
+    if (tcta) {
+      // this plane's tensor copy has landed (bounded wait; on time-out the
+      // step is marked bad and the march goes on with whatever arrived)
+      const int b = pc & 1;
+      if (!tma_lost && !mbar_wait_bounded(smem_u32(&s_bar[b]), (bar_phase >> b) & 1u)) {
+        atomicMin(aux.bad_step, 0ull);
+        tma_lost = true;
+      }
+      bar_phase ^= 1u << b;
+      // this thread's generic accesses to the other buffer (the previous
+      // plane) precede the tensor copy issued into it after the barrier
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     __syncthreads();
     if (pc < pc_last) {
       issue(pc + R + 1, slot);
