@@ -3,6 +3,8 @@
 // the resulting gradient fields.
 #include <cmath>
 
+#include <type_traits>
+
 #include "compact.cuh"
 #include "step2d.cuh"
 #include "step3d.cuh"
@@ -84,20 +86,28 @@ __global__ void k_mu_field(KParams p, int D, bool dev, const Tr* __restrict__ rh
   mu[n] = Tm(p.k2) * eos_mu<Tm>(rfull, p) - Tm(p.kappa) * lap;
 }
 
-// Derivative along `axis` of lines of `in`, LPB lines per CTA held
-// in shared memory; explicit right side of Eq. 21 then PCR levels.
+// Derivative along `axis` of lines of `in`: LPB lines per CTA (a power of
+// two, 1..16) held in shared memory, line j owned by warp j % 8.  A warp forms
+// the explicit right side of Eq. 21 for its lines and runs the PCR levels on
+// them with only warp-level synchronisation (element i of a line on lane
+// i % 32); CTA barriers separate the copies in and out only where the global
+// layout differs from the warp ownership (lines along y and z are copied
+// across x, 32-byte runs of LPB consecutive lines, for coalescing).
+constexpr int LT = 256;  // threads of a line CTA: 8 warps
+
 template <typename Tin, typename T>
-__global__ void k_lines(int axis, int nx, int ny, int nz, const Tin* __restrict__ in, double ref, T* __restrict__ out,
-                        const LineCoef lc, int LPB) {
+__global__ void __launch_bounds__(LT) k_lines(int axis, int nx, int ny, int nz, const Tin* __restrict__ in,
+                                              T* __restrict__ out, const LineCoef lc, int LPB, int lpb_shift) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = axis == 0 ? nx : (axis == 1 ? ny : nz);
   const int LP = L + 1;
   T* A = reinterpret_cast<T*>(smem);
   T* B = A + LPB * LP;
   const long long NXY = (long long)nx * ny;
-  // line j of this CTA: base offset and element stride
   const long long stride = axis == 0 ? 1 : (axis == 1 ? nx : NXY);
-  const int groups_x = (nx + LPB - 1) / LPB;  // for y/z lines: groups of LPB consecutive x
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int groups_x = (nx + LPB - 1) >> lpb_shift;  // y/z lines: groups of LPB consecutive x
+  // global offset of the first element of line j of this CTA (ok: the line exists)
   auto line_base = [&](int j, bool& ok) -> long long {
     if (axis == 0) {
       const long long row = (long long)blockIdx.x * LPB + j;  // (y, z) row
@@ -109,57 +119,75 @@ __global__ void k_lines(int axis, int nx, int ny, int nz, const Tin* __restrict_
     ok = gx < nx;
     return axis == 1 ? r * NXY + gx : r * nx + gx;
   };
-  const int tot = LPB * L;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    int j, i;
-    if (axis == 0) { j = idx / L; i = idx - j * L; } else { i = idx / LPB; j = idx - i * LPB; }
+  if (axis == 0) {
+    for (int j = warp; j < LPB; j += LT / 32) {
+      bool ok;
+      const long long b = line_base(j, ok);
+      for (int i = lane; i < L; i += 32) A[j * LP + i] = ok ? T(in[b + i]) : T(0);
+    }
+    __syncwarp();
+  } else {
+    // thread t copies line t % LPB at positions t / LPB + k LT / LPB
+    const int j = threadIdx.x & (LPB - 1), i0 = threadIdx.x >> lpb_shift, di = LT >> lpb_shift;
     bool ok;
     const long long b = line_base(j, ok);
-    A[j * LP + i] = ok ? T(in[b + i * stride]) : T(0);
+    for (int i = i0; i < L; i += di) A[j * LP + i] = ok ? T(in[b + i * stride]) : T(0);
+    __syncthreads();
   }
-  __syncthreads();
-  // explicit side: a (f[i+1]-f[i-1])/2 + b (f[i+2]-f[i-2])/4 + c (f[i+3]-f[i-3])/6
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int j = idx / L, i = idx - j * L;
+  const T A1 = T(lc.A1), A2 = T(lc.A2), A3 = T(lc.A3);
+  for (int j = warp; j < LPB; j += LT / 32) {
+    // explicit side: a (f[i+1]-f[i-1])/2 + b (f[i+2]-f[i-2])/4 + c (f[i+3]-f[i-3])/6
     const T* f = A + j * LP;
-    const int p1 = i + 1 >= L ? i + 1 - L : i + 1, m1 = i - 1 < 0 ? i - 1 + L : i - 1;
-    T r = T(lc.A1) * (f[p1] - f[m1]);
-    if (lc.A2 != 0.0) r += T(lc.A2) * (f[lmod(i + 2, L)] - f[lmod(i - 2, L)]);
-    if (lc.A3 != 0.0) r += T(lc.A3) * (f[lmod(i + 3, L)] - f[lmod(i - 3, L)]);
-    B[j * LP + i] = r;
+    for (int i = lane; i < L; i += 32) {
+      auto at = [&](int k) { return f[k < 0 ? k + L : (k >= L ? k - L : k)]; };
+      T r = A1 * (at(i + 1) - at(i - 1));
+      if (lc.A2 != 0.0) r += A2 * (at(i + 2) - at(i - 2));
+      if (lc.A3 != 0.0) r += A3 * (at(i + 3) - at(i - 3));
+      B[j * LP + i] = r;
+    }
   }
-  __syncthreads();
+  __syncwarp();
   T* cur = B;
   T* nxt = A;
   int s = 1 % L;
   for (int k = 0; k < lc.nlev; ++k) {
     const T al = T(lc.alpha[k]), iv = T(lc.inv[k]);
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      const int j = idx / L, i = idx - j * L;
+    for (int j = warp; j < LPB; j += LT / 32) {
       const T* d = cur + j * LP;
-      int ip = i + s; if (ip >= L) ip -= L;
-      int im = i - s; if (im < 0) im += L;
-      nxt[j * LP + i] = (d[i] - al * (d[im] + d[ip])) * iv;
+      for (int i = lane; i < L; i += 32) {
+        int ip = i + s; if (ip >= L) ip -= L;
+        int im = i - s; if (im < 0) im += L;
+        nxt[j * LP + i] = (d[i] - al * (d[im] + d[ip])) * iv;
+      }
     }
-    __syncthreads();
+    __syncwarp();
     T* t = cur; cur = nxt; nxt = t;
-    s = (2 * s) % L;
+    s = 2 * s; if (s >= L) s -= L;
   }
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    int j, i;
-    if (axis == 0) { j = idx / L; i = idx - j * L; } else { i = idx / LPB; j = idx - i * LPB; }
+  if (axis == 0) {
+    for (int j = warp; j < LPB; j += LT / 32) {
+      bool ok;
+      const long long b = line_base(j, ok);
+      if (ok)
+        for (int i = lane; i < L; i += 32) out[b + i] = cur[j * LP + i];
+    }
+  } else {
+    __syncthreads();
+    const int j = threadIdx.x & (LPB - 1), i0 = threadIdx.x >> lpb_shift, di = LT >> lpb_shift;
     bool ok;
     const long long b = line_base(j, ok);
-    if (ok) out[b + i * stride] = cur[j * LP + i];
+    if (ok)
+      for (int i = i0; i < L; i += di) out[b + i * stride] = cur[j * LP + i];
   }
 }
 
 template <typename Tin, typename T>
 cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T* out, const LineCoef& lc,
                       cudaStream_t st) {
+  (void)ref;
   const int L = axis == 0 ? kp.nx : (axis == 1 ? kp.ny : kp.nz);
-  int LPB = 16;
-  while (LPB > 1 && size_t(2) * LPB * (L + 1) * sizeof(T) > 200 * 1024) LPB /= 2;
+  int LPB = 16, sh = 4;
+  while (LPB > 1 && size_t(2) * LPB * (L + 1) * sizeof(T) > 200 * 1024) { LPB /= 2; --sh; }
   const size_t smem = size_t(2) * LPB * (L + 1) * sizeof(T);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
   static int set_bytes = 0;
@@ -168,16 +196,14 @@ cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T*
     if (e != cudaSuccess) return e;
     set_bytes = 220 * 1024;
   }
-  long long nlines;
   unsigned grid;
   if (axis == 0) {
-    nlines = (long long)kp.ny * kp.nz;
-    grid = unsigned((nlines + LPB - 1) / LPB);
+    grid = unsigned(((long long)kp.ny * kp.nz + LPB - 1) / LPB);
   } else {
     const int gx = (kp.nx + LPB - 1) / LPB;
     grid = unsigned((long long)gx * (axis == 1 ? kp.nz : kp.ny));
   }
-  k_lines<Tin, T><<<grid, 256, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, in, ref, out, lc, LPB);
+  k_lines<Tin, T><<<grid, LT, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, in, out, lc, LPB, sh);
   return cudaGetLastError();
 }
 
@@ -229,10 +255,18 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   const int bs = 256;
   const unsigned g = unsigned((kp.n + bs - 1) / bs);
   Tm* mu = static_cast<Tm*>(cb.mu);
-  if (cb.lap_order == 4) k_mu_field<Tm, Tr, 4><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
-  else if (cb.lap_order == 6) k_mu_field<Tm, Tr, 6><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
-  else k_mu_field<Tm, Tr, 8><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (std::is_same<P, PrecF32>::value && D == 3 && (cb.lap_order == 4 || cb.lap_order == 6)) {
+    // FP32 mu in 3D: the z-marching mu pass of the split path
+    Launch cm = c;
+    cm.mu = mu;
+    e = mu3d_pass(cm, cb.lap_order);
+  } else {
+    if (cb.lap_order == 4) k_mu_field<Tm, Tr, 4><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
+    else if (cb.lap_order == 6) k_mu_field<Tm, Tr, 6><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
+    else k_mu_field<Tm, Tr, 8><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   Tm* gmu = static_cast<Tm*>(cb.gmu);
   Tc* grho = static_cast<Tc*>(cb.grho);
@@ -245,6 +279,10 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   c.gi.gmu = gmu;
   c.gi.grho = grho;
   c.gi.mu = mu;
+  if (std::is_same<P, PrecF32>::value && D == 3 && mode == MODE_STEP) {
+    e = coll3d_gf_step(c, nblocks);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (mode == MODE_STEP) return launch_gf<P, MODE_STEP>(c, D, nblocks);
   if (mode == MODE_OBS) return launch_gf<P, MODE_OBS>(c, D, nblocks);
   return launch_gf<P, MODE_FIELDS>(c, D, nblocks);

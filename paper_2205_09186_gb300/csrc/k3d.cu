@@ -124,7 +124,8 @@ cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
   kc<<<grid, CNT, by, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
                                          static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
                                          static_cast<float*>(c.rout), c.aux, zc,
-                                         OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr, tm);
+                                         OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr, tm,
+                                         static_cast<const float*>(c.gi.gmu), static_cast<const float*>(c.gi.grho));
   return cudaGetLastError();
 }
 
@@ -239,6 +240,22 @@ bool make_coll3d_tmap(const void* f, const KParams& kp, void* out) {
   return encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(f), dims, strides,
                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t coll3d_gf_step(const Launch& c, int* nblocks) {
+  if (c.kp.nx % 4 != 0 || !aligned16(c.fin) || !aligned16(c.rin) || !c.tmap || !c.gi.gmu || !c.gi.grho)
+    return cudaErrorNotSupported;
+  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, 0);
+  dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + TYC - 1) / TYC, (c.kp.nz + zc - 1) / zc);
+  if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
+  return c.kp.omega == 1.0 ? launch_coll<S_CFDS4, true, true, false>(c, grid, zc)
+                           : launch_coll<S_CFDS4, false, true, false>(c, grid, zc);
+}
+
+cudaError_t mu3d_pass(const Launch& c, int order) {
+  if (order == 4) return launch_mu<S_EFDS4>(c);
+  if (order == 6) return launch_mu<S_EFDS6>(c);
+  return cudaErrorNotSupported;
 }
 
 StepFn step3d_fn(int scheme, int prec) {

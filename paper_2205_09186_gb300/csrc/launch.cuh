@@ -55,6 +55,17 @@ StepFn step3d_fn(int scheme, int prec);
 // allow one (nx % 4 != 0, unaligned base) or the driver refuses it.
 bool make_coll3d_tmap(const void* f, const KParams& kp, void* out);
 
+// D3Q19 FP32 mu field (Eq. 16) with the explicit central Laplacian of the
+// given order (4 or 6) from c.rin into c.mu (N floats): the mu pass of the
+// split path, shared with the compact schemes.
+cudaError_t mu3d_pass(const Launch& c, int order);
+
+// D3Q19 FP32DEV collision pass of the compact schemes on the tiled z-marching
+// kernel, the derivatives read from c.gi (gmu, grho: 3 x N floats each);
+// cudaErrorNotSupported (nothing launched) when the lattice or the buffers do
+// not allow the vector variant.
+cudaError_t coll3d_gf_step(const Launch& c, int* nblocks);
+
 // number of CTAs (hence partial results) of the observation pass
 long long step2d_obs_ctas(const KParams& kp);
 long long step3d_obs_ctas(const KParams& kp);

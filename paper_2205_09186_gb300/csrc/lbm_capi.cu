@@ -574,10 +574,11 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
       (h->D == 3 ? split3d_scheme(params->scheme, h->prec) : split2d_scheme(params->scheme, h->prec))) {
     h->mu = dalloc(h, size_t(h->N) * 4);
     ok = h->mu != nullptr;
-    // tensor maps of both population buffers for the collision pass's copies
-    if (ok && h->D == 3)
-      h->has_tmap = make_coll3d_tmap(h->f[0], h->kp, h->tmap[0]) && make_coll3d_tmap(h->f[1], h->kp, h->tmap[1]);
   }
+  // tensor maps of both population buffers for the D3Q19 FP32DEV collision
+  // pass's copies (split explicit schemes and compact schemes)
+  if (ok && h->D == 3 && h->prec == 1)
+    h->has_tmap = make_coll3d_tmap(h->f[0], h->kp, h->tmap[0]) && make_coll3d_tmap(h->f[1], h->kp, h->tmap[1]);
   if (ok && h->compact) {
     rc = compact_alloc(h->cb, h->kp, h->D, params->scheme, h->prec, [&](size_t b) { return dalloc(h, b); });
     if (rc != LBM_OK) ok = false;

@@ -51,7 +51,11 @@ struct CollShape {
   static constexpr int FPL = CY * FW;                     // staged populations of one i
   static constexpr int fbuf = (19 * FPL + 255) / 256 * 256;  // buffer stride (floats), 1 KB multiple
   static constexpr unsigned box_bytes = 19u * FPL * 4u;       // one tensor copy
-  static constexpr size_t off_f = (size_t(NS) * plane * 8 + 1023) / 1024 * 1024;
+  // compact schemes (GF): per collided node the density deviation and the six
+  // derivative values (grad mu, grad rho) of its own plane, double-buffered
+  static constexpr int NG = 7;
+  static constexpr size_t fields_bytes = Sch<S>::GF ? size_t(2) * NG * CNT * 4 : size_t(NS) * plane * 8;
+  static constexpr size_t off_f = (fields_bytes + 1023) / 1024 * 1024;
   static constexpr size_t bytes = off_f + size_t(2) * fbuf * 4;
   // OBS: the snapshot values of the collided plane, one per thread, staged
   // like the populations (double-buffered by plane parity)
@@ -105,6 +109,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
   return false;
 }
 
+// S a compact scheme (GF): the derivatives come from the fields gmu and grho
+// (component-major, N each) of the line solves; no stencil halo.
 // VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations),
 // and tensor copies of the populations for CTAs away from the periodic seams
 // (tmf: the populations as a 4-D tensor (nx, ny, nz, 19), box (FW, CY, 1, 19)).
@@ -116,14 +122,17 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
                                                     float* __restrict__ fout, const float* __restrict__ rin,
                                                     const float* __restrict__ muf, float* __restrict__ rout,
                                                     const StepAux aux, const int zc, float* __restrict__ snap,
-                                                    const __grid_constant__ CUtensorMap tmf) {
+                                                    const __grid_constant__ CUtensorMap tmf,
+                                                    const float* __restrict__ gmu, const float* __restrict__ grho) {
   using L = Lattice<1>;
   using Sh = CollShape<S>;
   constexpr int Q = 19, R = Sh::R, GW = Sh::GW, NS = Sh::NS, FPL = Sh::FPL;
   extern __shared__ __align__(1024) unsigned char smem_c3[];  // (own name: other kernels align theirs to 16)
   unsigned char* smem = smem_c3;
   __shared__ __align__(8) unsigned long long s_bar[2];  // tensor copies: one mbarrier per buffer
+  constexpr bool GF = Sch<S>::GF;
   float2* s_dm = reinterpret_cast<float2*>(smem);
+  float* s_g = reinterpret_cast<float*>(smem);  // GF: [2][NG][CNT]
   float* s_f = reinterpret_cast<float*>(smem + Sh::off_f);
   float* s_snap = reinterpret_cast<float*>(smem + Sh::off_snap);  // OBS only
 
@@ -185,12 +194,26 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
     const bool fl = pc >= pc_first && pc <= pc_last;
     const int zf = wrapi(pc, nz) * NXY;
     float* fd = s_f + (pc & 1) * Sh::fbuf;
+    if constexpr (GF) {
+      // this node's deviation and derivatives in plane pc (R = 0: q = pc)
+      if (fl && cnode) {
+        float* gd = s_g + (pc & 1) * Sh::NG * CNT + tid;
+        const int o = zf + gy * nx + gx;
+        cpa4(gd, rin + o);
 #pragma unroll
-    for (int k = 0; k < Sh::KD; ++k) {
-      const int e = tid + k * CNT;
-      if (e < Sh::DE) {
-        cpa4(&dd[e].x, rin + zo + dofs[k]);
-        cpa4(&dd[e].y, muf + zo + dofs[k]);
+        for (int a = 0; a < 3; ++a) {
+          cpa4(gd + (1 + a) * CNT, gmu + a * N + o);
+          cpa4(gd + (4 + a) * CNT, grho + a * N + o);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < Sh::KD; ++k) {
+        const int e = tid + k * CNT;
+        if (e < Sh::DE) {
+          cpa4(&dd[e].x, rin + zo + dofs[k]);
+          cpa4(&dd[e].y, muf + zo + dofs[k]);
+        }
       }
     }
     if constexpr (VEC) {
@@ -276,7 +299,8 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
 #pragma unroll
       for (int i = 0; i < Q; ++i) fv[i] = fb[i * FPL + fme];
       const int c = (cy + R) * GW + cx + R;
-      const float dsv = s_dm[base[R] + c].x;
+      const float* gq = s_g + (pc & 1) * Sh::NG * CNT + tid;  // GF
+      const float dsv = GF ? gq[0] : s_dm[base[R] + c].x;
       const float rc = rref + dsv;
       // momentum from the differences of opposite populations (e_{i+1} = -e_i
       // for odd i): nine subtractions, then each component sums five of them
@@ -291,7 +315,13 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       const float irc = __fdividef(1.f, rc);
       const float ux = jx * irc, uy = jy * irc, uz = jz * irc;
       float2 g2x, g2y, g2z;
-      grad3d_pair<S>(s_dm, base, GW, cx + R, cy + R, g2x, g2y, g2z);
+      if constexpr (GF) {
+        g2x = make_float2(gq[4 * CNT], gq[1 * CNT]);
+        g2y = make_float2(gq[5 * CNT], gq[2 * CNT]);
+        g2z = make_float2(gq[6 * CNT], gq[3 * CNT]);
+      } else {
+        grad3d_pair<S>(s_dm, base, GW, cx + R, cy + R, g2x, g2y, g2z);
+      }
       const float grx = g2x.x, gry = g2y.x, grz = g2z.x, gmx = g2x.y, gmy = g2y.y, gmz = g2z.y;
       const float Fx = -rc * gmx + grx * (1.f / 3.f), Fy = -rc * gmy + gry * (1.f / 3.f),
                   Fz = -rc * gmz + grz * (1.f / 3.f);

@@ -226,3 +226,23 @@ def test_zchunk_and_autotune_do_not_change_results(L):
         outs.append(g.lbm_get_f())
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+
+
+# compact schemes in 3D with FP32 deviation storage: z-marching mu pass (orders
+# 4 and 6; the node-parallel one for CFDS8), line solves, and the tiled
+# collision pass reading the derivative fields (64: tensor-copy and 16-byte
+# variants by tile; 42: the 4-byte variant everywhere)
+@pytest.mark.parametrize("shape", [(64, 40, 36), (42, 26, 20)])
+@pytest.mark.parametrize("scheme", ["OCFDS4", "CFDS6", "CFDS8"])
+def test_fp32dev_compact_3d_against_oracle(L, shape, scheme):
+    nx, ny, nz = shape
+    kw = dict(nx=nx, ny=ny, nz=nz, Tr=0.9, k=0.3, kappa=0.1, scheme=scheme)
+    g, o = pair(L, 3, precision=L.LBM_FP32DEV, **kw)
+    rng = np.random.default_rng(nx * 1000 + ny * 10 + nz)
+    rho = 0.15 + 0.01 * rng.standard_normal((nz, ny, nx))
+    g.lbm_init_density(rho)
+    o.set_f(np.stack([w * rho for w in O.lattice(O.D3Q19)[1]]))
+    g.lbm_step(30)
+    assert o.step(30) == 0
+    err = np.max(np.abs(g.lbm_get_density() - o.density())) / 0.15
+    assert err < TOL32, err
