@@ -40,7 +40,9 @@ extern "C" {
 #define LBM_EINVAL -1     /* invalid argument or parameter combination */
 #define LBM_ENOMEM -2     /* the allocator returned NULL */
 #define LBM_ECUDA -3      /* a CUDA runtime call failed */
-#define LBM_EUNSTABLE -4  /* a density became non-positive or NaN; see lbm_obs.step */
+#define LBM_EUNSTABLE -4  /* a density became non-positive or NaN; see lbm_obs.step
+                           (step 0 is also recorded when a tensor-copy wait of the
+                           D3Q19 FP32DEV collision pass runs out, after ~1 s) */
 #define LBM_ETIMEOUT -5   /* a bounded device-side wait gave up */
 #define LBM_ENOTSUP -6    /* combination not provided (e.g. E8 on D3Q19) */
 #define LBM_ESCRATCH -7   /* larger than the fixed scratch of lbm_observables_noalloc */

@@ -87,12 +87,12 @@ __global__ void k_mu_field(KParams p, int D, bool dev, const Tr* __restrict__ rh
 }
 
 // Derivative along `axis` of lines of `in`: LPB lines per CTA (a power of
-// two, 1..16) held in shared memory, line j owned by warp j % 8.  A warp forms
+// two, 1..32) held in shared memory, line j owned by warp j % 8.  A warp forms
 // the explicit right side of Eq. 21 for its lines and runs the PCR levels on
 // them with only warp-level synchronisation (element i of a line on lane
 // i % 32); CTA barriers separate the copies in and out only where the global
 // layout differs from the warp ownership (lines along y and z are copied
-// across x, 32-byte runs of LPB consecutive lines, for coalescing).
+// across x, runs of LPB consecutive lines, for coalescing).
 constexpr int LT = 256;  // threads of a line CTA: 8 warps
 
 template <typename Tin, typename T>
@@ -186,7 +186,7 @@ cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T*
                       cudaStream_t st) {
   (void)ref;
   const int L = axis == 0 ? kp.nx : (axis == 1 ? kp.ny : kp.nz);
-  int LPB = 16, sh = 4;
+  int LPB = 32, sh = 5;
   while (LPB > 1 && size_t(2) * LPB * (L + 1) * sizeof(T) > 200 * 1024) { LPB /= 2; --sh; }
   const size_t smem = size_t(2) * LPB * (L + 1) * sizeof(T);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
@@ -203,7 +203,15 @@ cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T*
     const int gx = (kp.nx + LPB - 1) / LPB;
     grid = unsigned((long long)gx * (axis == 1 ? kp.nz : kp.ny));
   }
-  k_lines<Tin, T><<<grid, LT, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, in, out, lc, LPB, sh);
+  // FP32 lines: a level whose |alpha| is below 2^-30 moves no value by more
+  // than 2^-29 of itself, far below the float rounding: stop before it
+  LineCoef lf = lc;
+  if (sizeof(T) == 4) {
+    int k = 0;
+    while (k < lc.nlev && std::fabs(lc.alpha[k]) > 9.3e-10) ++k;
+    lf.nlev = k;
+  }
+  k_lines<Tin, T><<<grid, LT, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, in, out, lf, LPB, sh);
   return cudaGetLastError();
 }
 
