@@ -1,6 +1,8 @@
 // Instantiations of the fused D2Q9 step for the explicit and isotropic schemes.
 #include <type_traits>
 
+#include <cstdint>
+
 #include "launch.cuh"
 #include "step2d.cuh"
 #include "step2d_split.cuh"
@@ -43,8 +45,29 @@ cudaError_t launch_split2d(const Launch& c, int* nblocks) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 gm((c.kp.nx + M2X - 1) / M2X, (c.kp.ny + M2Y - 1) / M2Y);
-  k_mu2d<S><<<gm, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  if constexpr (!Sch<S>::ISO) {
+    if (c.kp.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(c.rin) & 15) == 0 && (reinterpret_cast<uintptr_t>(c.mu) & 15) == 0) {
+      // rows per thread: about four CTAs of 8 warps per SM, 2..32 rows
+      const int gx = (c.kp.nx + 63) / 64;
+      static int sms = 0;
+      if (!sms) {
+        int d = 0;
+        cudaGetDevice(&d);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms < 1) sms = 1;
+      }
+      const int want_gy = (4 * sms + gx - 1) / gx;
+      int rpt = (c.kp.ny + 16 * want_gy - 1) / (16 * want_gy);
+      rpt = rpt < 2 ? 2 : (rpt > 32 ? 32 : rpt);
+      dim3 gm(gx, (c.kp.ny + 16 * rpt - 1) / (16 * rpt));
+      k_mu2d_ym<S><<<gm, YMT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu), rpt);
+    } else {
+      dim3 gm((c.kp.nx + M2X - 1) / M2X, (c.kp.ny + M2Y - 1) / M2Y);
+      k_mu2d<S><<<gm, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+    }
+  } else {
+    dim3 gm((c.kp.nx + M2X - 1) / M2X, (c.kp.ny + M2Y - 1) / M2Y);
+    k_mu2d<S><<<gm, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+  }
   if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
   dim3 gc((c.kp.nx + T2X - 1) / T2X, (c.kp.ny + T2Y - 1) / T2Y);
   if (nblocks) *nblocks = int(gc.x * gc.y);

@@ -218,6 +218,77 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
   }
 }
 
+// y-marching vector mu pass (line schemes EFDS2/4/6, nx % 4 == 0, 16-byte
+// aligned fields): thread (tx, ty) of a 256-thread CTA owns four x-adjacent
+// nodes (one float4, x = 64 blockIdx.x + 4 tx) through rpt consecutive rows.
+// Its y neighbours sit in a register queue fed one row ahead by 16-byte loads;
+// its x neighbours are the neighbouring lanes' centre chunks (shuffles within
+// the 16-lane group that marches the same rows); a group's edge lanes load the
+// chunk beyond it themselves.  No shared memory, no CTA barrier.
+constexpr int YMT = 256;
+
+template <int S>
+__global__ void __launch_bounds__(YMT) k_mu2d_ym(const KParams p, const float* __restrict__ rin,
+                                                 float* __restrict__ mu, const int rpt) {
+  static_assert(!Sch<S>::ISO && Sch<S>::R <= 4, "line schemes, stencil within one chunk on each side");
+  constexpr int R = Sch<S>::R;
+  const int nx = p.nx, ny = p.ny;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int x = blockIdx.x * 64 + 4 * tx;
+  const int ya = (blockIdx.y * (YMT / 16) + ty) * rpt;
+  if (ya >= ny) return;  // the whole 16-lane group (same ty)
+  const int yb = min(ya + rpt, ny);
+  const unsigned gmask = 0xffffu << (16 * (ty & 1));  // this group's lanes
+  const bool own = x < nx;
+  const bool need_lo = tx == 0, need_hi = tx == 15 || x + 4 >= nx;
+  auto ld = [&](int xx, int yy) {
+    return __ldg(reinterpret_cast<const float4*>(rin + wrapn(yy, ny) * nx + wrapn(xx, nx)));
+  };
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 q[2 * R + 1];
+#pragma unroll
+  for (int d = 1; d <= 2 * R; ++d) q[d] = own ? ld(x, ya - R - 1 + d) : z4;
+  float4 pre = own ? ld(x, ya + R) : z4;
+  float4 elo_n = own && need_lo ? ld(x - 4, ya) : z4, ehi_n = own && need_hi ? ld(x + 4, ya) : z4;
+  const float k2 = float(p.k2), kap = float(p.kappa), rref = float(p.rho_ref);
+  const EosF ef = eos_f(p);
+  for (int y = ya; y < yb; ++y) {
+#pragma unroll
+    for (int d = 0; d < 2 * R; ++d) q[d] = q[d + 1];
+    q[2 * R] = pre;
+    const float4 elo = elo_n, ehi = ehi_n;
+    if (own && y + 1 < yb) {
+      pre = ld(x, y + R + 1);
+      if (need_lo) elo_n = ld(x - 4, y + 1);
+      if (need_hi) ehi_n = ld(x + 4, y + 1);
+    }
+    const float4 c4 = q[R];
+    float4 lo, hi;
+    lo.x = __shfl_up_sync(gmask, c4.x, 1, 16); lo.y = __shfl_up_sync(gmask, c4.y, 1, 16);
+    lo.z = __shfl_up_sync(gmask, c4.z, 1, 16); lo.w = __shfl_up_sync(gmask, c4.w, 1, 16);
+    hi.x = __shfl_down_sync(gmask, c4.x, 1, 16); hi.y = __shfl_down_sync(gmask, c4.y, 1, 16);
+    hi.z = __shfl_down_sync(gmask, c4.z, 1, 16); hi.w = __shfl_down_sync(gmask, c4.w, 1, 16);
+    if (need_lo) lo = elo;
+    if (need_hi) hi = ehi;
+    if (!own) continue;
+    const float row[12] = {lo.x, lo.y, lo.z, lo.w, c4.x, c4.y, c4.z, c4.w, hi.x, hi.y, hi.z, hi.w};
+    float res[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float cv = row[4 + k];
+      float lap = float(2.0 * Sch<S>::l(0)) * cv;
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const float4 e = q[R + m], f = q[R - m];
+        const float ym = k == 0 ? e.x + f.x : (k == 1 ? e.y + f.y : (k == 2 ? e.z + f.z : e.w + f.w));
+        lap += float(Sch<S>::l(m)) * ((row[4 + k + m] + row[4 + k - m]) + ym);
+      }
+      res[k] = k2 * eos_mu_f(rref + cv, ef) - kap * lap;
+    }
+    *reinterpret_cast<float4*>(mu + y * nx + x) = make_float4(res[0], res[1], res[2], res[3]);
+  }
+}
+
 // whole tiles (load, wait, compute) for the single-case kernels
 template <int S>
 __device__ __forceinline__ void mu2d_tile(const KParams& p, const float* __restrict__ rin, float* __restrict__ mu,

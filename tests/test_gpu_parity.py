@@ -246,3 +246,22 @@ def test_fp32dev_compact_3d_against_oracle(L, shape, scheme):
     assert o.step(30) == 0
     err = np.max(np.abs(g.lbm_get_density() - o.density())) / 0.15
     assert err < TOL32, err
+
+
+# D2Q9 FP32 deviation storage: nx % 4 == 0 takes the y-marching vector mu pass
+# (68: a 4-node chunk past one 64-wide group; 40: a partial group; 8: every
+# stencil wraps the lattice), 42 the tiled one
+@pytest.mark.parametrize("shape", [(68, 37), (40, 24), (8, 8), (42, 26)])
+@pytest.mark.parametrize("scheme", ["EFDS2", "EFDS4", "EFDS6"])
+def test_fp32dev_2d_mu_variants_against_oracle(L, shape, scheme):
+    nx, ny = shape
+    kw = dict(nx=nx, ny=ny, Tr=0.9, k=0.3, kappa=0.1, scheme=scheme)
+    g, o = pair(L, 2, precision=L.LBM_FP32DEV, **kw)
+    rng = np.random.default_rng(nx * 100 + ny)
+    rho = 0.15 + 0.01 * rng.standard_normal((ny, nx))
+    g.lbm_init_density(rho)
+    o.set_f(np.stack([w * rho for w in O.lattice(O.D2Q9)[1]]))
+    g.lbm_step(40)
+    assert o.step(40) == 0
+    err = np.max(np.abs(g.lbm_get_density() - o.density())) / 0.15
+    assert err < TOL32, err
