@@ -193,6 +193,20 @@ __device__ void split_load(const CaseDev& cd, int tile, long long t, int phase, 
   }
 }
 
+__device__ void mu_direct(const CaseDev& cd, int tile, long long t) {
+  const int par = int(t & 1);
+  const float* rin = static_cast<const float*>(cd.rho[par]);
+  const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
+  switch (cd.scheme) {
+    case S_EFDS2: mu2d_direct<S_EFDS2>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_EFDS4: mu2d_direct<S_EFDS4>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_EFDS6: mu2d_direct<S_EFDS6>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_E4: mu2d_direct<S_E4>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_E8: mu2d_direct<S_E8>(cd.kp, rin, cd.mu, x0, y0); break;
+    default: break;
+  }
+}
+
 __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phase, unsigned char* buf) {
   const int par = int(t & 1);
   if (phase == 0) {
@@ -250,6 +264,16 @@ __global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restri
       const Item* items = phase == 0 ? mitems : citems;
       const int nitems = phase == 0 ? nmu : ncoll;
       const int i0 = int((long long)nitems * blockIdx.x / G), i1 = int((long long)nitems * (blockIdx.x + 1) / G);
+      if (phase == 0) {
+        // mu items: every thread reads its stencils through the read-only
+        // cache; no staging, no CTA barrier
+        for (int it = i0; it < i1; ++it) {
+          const Item itm = items[it];
+          mu_direct(cases[itm.c], itm.tile, t);
+        }
+        if (!grid_barrier(ctl, timeout_ns)) return;
+        continue;
+      }
       // prologue: copies of the first NBUF - 1 items (one group each, empty past the end)
 #pragma unroll
       for (int j = 0; j < NBUF - 1; ++j) {

@@ -218,6 +218,47 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
   }
 }
 
+// mu of one 32 x 32 tile straight from global memory (read-only cache): each
+// thread its two nodes (rows w and w + 16 of warp w), every stencil value a
+// cached load.  No shared memory and no barrier, so that the persistent batch
+// kernel deals mu items without CTA synchronisation.
+template <int S>
+__device__ __forceinline__ void mu2d_direct(const KParams& p, const float* __restrict__ rin, float* __restrict__ mu,
+                                            int x0, int y0) {
+  using Sc = Sch<S>;
+  constexpr int R = Sc::R;
+  const int nx = p.nx, ny = p.ny;
+  const int gx = x0 + int(threadIdx.x) % M2X;
+  if (gx >= nx) return;
+  int xo[2 * R + 1];  // wrapped x of the stencil columns
+#pragma unroll
+  for (int d = -R; d <= R; ++d) xo[d + R] = wrapi(gx + d, nx);
+  const float k2 = float(p.k2), kap = float(p.kappa), rref = float(p.rho_ref);
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int gy = y0 + int(threadIdx.x) / M2X + r * (NT2S / M2X);
+    if (gy >= ny) break;
+    auto at = [&](int dx, int dy) { return __ldg(rin + wrapi(gy + dy, ny) * nx + xo[dx + R]); };
+    const float c = at(0, 0);
+    float lap;
+    if constexpr (Sc::ISO) {
+      lap = 0.f;
+#pragma unroll
+      for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+        for (int dx = -R; dx <= R; ++dx) {
+          const double w = Sc::w2d(dx, dy);
+          if (w != 0.0) lap += float(2.0 * w) * (at(dx, dy) - c);
+        }
+    } else {
+      lap = float(2.0 * Sc::l(0)) * c;
+#pragma unroll
+      for (int m = 1; m <= R; ++m) lap += float(Sc::l(m)) * ((at(m, 0) + at(-m, 0)) + (at(0, m) + at(0, -m)));
+    }
+    mu[gy * nx + gx] = k2 * eos_mu_f(rref + c, eos_f(p)) - kap * lap;
+  }
+}
+
 // y-marching vector mu pass (line schemes EFDS2/4/6, nx % 4 == 0, 16-byte
 // aligned fields): thread (tx, ty) of a 256-thread CTA owns four x-adjacent
 // nodes (one float4, x = 64 blockIdx.x + 4 tx) through rpt consecutive rows.
