@@ -265,8 +265,8 @@ __global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restri
       const int nitems = phase == 0 ? nmu : ncoll;
       const int i0 = int((long long)nitems * blockIdx.x / G), i1 = int((long long)nitems * (blockIdx.x + 1) / G);
       if (phase == 0) {
-        // mu items: every thread reads its stencils through the read-only
-        // cache; no staging, no CTA barrier
+        // mu items: every thread reads its stencils with cached global loads;
+        // no staging, no CTA barrier
         for (int it = i0; it < i1; ++it) {
           const Item itm = items[it];
           mu_direct(cases[itm.c], itm.tile, t);

@@ -218,13 +218,15 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
   }
 }
 
-// mu of one 32 x 32 tile straight from global memory (read-only cache): each
-// thread its two nodes (rows w and w + 16 of warp w), every stencil value a
-// cached load.  No shared memory and no barrier, so that the persistent batch
-// kernel deals mu items without CTA synchronisation.
+// mu of one 32 x 32 tile straight from global memory: each thread its two
+// nodes (rows w and w + 16 of warp w), every stencil value an L1-cached load.
+// No shared memory and no barrier, so that the persistent batch kernel deals
+// mu items without CTA synchronisation.  The inputs are written earlier in the
+// same persistent launch (by other CTAs, before a device-wide barrier with
+// acquire semantics), so they are read with ordinary coherent loads, never
+// through the non-coherent read-only path (no __ldg, no __restrict__).
 template <int S>
-__device__ __forceinline__ void mu2d_direct(const KParams& p, const float* __restrict__ rin, float* __restrict__ mu,
-                                            int x0, int y0) {
+__device__ __forceinline__ void mu2d_direct(const KParams& p, const float* rin, float* mu, int x0, int y0) {
   using Sc = Sch<S>;
   constexpr int R = Sc::R;
   const int nx = p.nx, ny = p.ny;
@@ -238,7 +240,7 @@ __device__ __forceinline__ void mu2d_direct(const KParams& p, const float* __res
   for (int r = 0; r < RPT; ++r) {
     const int gy = y0 + int(threadIdx.x) / M2X + r * (NT2S / M2X);
     if (gy >= ny) break;
-    auto at = [&](int dx, int dy) { return __ldg(rin + wrapi(gy + dy, ny) * nx + xo[dx + R]); };
+    auto at = [&](int dx, int dy) { return (*(rin + wrapi(gy + dy, ny) * nx + xo[dx + R])); };
     const float c = at(0, 0);
     float lap;
     if constexpr (Sc::ISO) {
