@@ -71,8 +71,11 @@ __device__ __forceinline__ void block_obs_reduce(double vmax, double umax, doubl
 // One TX x TY tile of the fused step (all threads of the CTA take part).
 // partial: where MODE_OBS writes this tile's 4 partial observables.
 template <int S, class P, int TX, int TY, int MODE>
-__device__ __forceinline__ void step2d_tile(const KParams& p, const typename P::Tf* __restrict__ fin,
-                                            typename P::Tf* __restrict__ fout, const typename P::Tr* __restrict__ rin,
+// (fin and rin without __restrict__: the persistent batch kernel calls this on
+// buffers it rewrites every step, so their reads must stay coherent loads,
+// never the non-coherent read-only path)
+__device__ __forceinline__ void step2d_tile(const KParams& p, const typename P::Tf* fin,
+                                            typename P::Tf* __restrict__ fout, const typename P::Tr* rin,
                                             typename P::Tr* __restrict__ rout, const StepAux& aux, const FieldOut& fo,
                                             const GradIn& gi, const Mrt& mrt, const int x0, const int y0,
                                             unsigned char* smem,
