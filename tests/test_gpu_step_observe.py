@@ -107,13 +107,22 @@ def test_step_observe_rejects_zero_steps(L):
 
 
 @pytest.mark.parametrize("shape,kw", [((48, 40, 44), dict()), ((48, 40, 1), dict()), ((24, 24, 24), dict(scheme="E4")),
-                                      ((48, 40, 1), dict(precision=0))])
+                                      ((48, 40, 1), dict(precision=0)), ((32, 24, 28), dict(scheme="OCFDS4")),
+                                      ((48, 40, 1), dict(scheme="EFDS4", walls=True))])
 def test_async_observation_equals_the_synchronous_one(L, shape, kw):
     # the same kernels in the same order: bit-identical records, written by the
     # stream into page-locked host memory and into device memory
     import ctypes
     import torch
+    kw = dict(kw)
+    walls = kw.pop("walls", False)
     a, b = make(L, shape, **kw), make(L, shape, **kw)
+    if walls:  # a flat wall of 4 rows (Appendix A) on both handles
+        mask = np.zeros((shape[1], shape[0]), np.uint8)
+        mask[:4] = 1
+        mu_w = L.lbm_bulk_mu(a.params, L.lbm_maxwell(a.params)[0])  # saturation
+        for s in (a, b):
+            s.lbm_set_solid(mask, mu_w)
     size = ctypes.sizeof(L.lbm_obs)
     host = torch.empty(3 * size, dtype=torch.uint8).pin_memory()
     dev = torch.empty(size, dtype=torch.uint8, device="cuda")
