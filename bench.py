@@ -185,6 +185,7 @@ def run_batch(L, steps=50, warmup=10, ncases=512):
     params = [L.make_params(lattice=L.LBM_D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1,
                             scheme=c["scheme"], precision=L.LBM_FP32DEV) for c in cases]
     b = L.Batch(params)
+    rows = b.lbm_batch_autotune(steps=5)  # tile shape by timing (advances the state: initialise after)
     b.lbm_batch_init_droplets([c["r"] for c in cases])
     nodes = sum(c["nx"] * c["ny"] for c in cases)
     b.lbm_batch_step(warmup)
@@ -203,7 +204,8 @@ def run_batch(L, steps=50, warmup=10, ncases=512):
     return {"workload": "%d D2Q9 droplets, sizes U{64..512}^2 (seed 2205), FP32DEV, one persistent launch" % ncases,
             "nodes": nodes, "steps": steps, "ms": ms, "mlups": nodes * steps / (ms * 1e-3) / 1e6,
             "hbm_frac": nodes * steps * (9 * 4 * 2 + 4 * 2) / (ms * 1e-3) / 1e9 / measured_peak()[0],
-            "stable_cases": stable, "work_items": nitems, "resident_ctas": grid, "status": rc}
+            "stable_cases": stable, "work_items": nitems, "resident_ctas": grid, "tile_rows_per_thread": rows,
+            "status": rc}
 
 
 def run_2d(L, steps=200, warmup=20):

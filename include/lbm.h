@@ -385,6 +385,18 @@ int lbm_batch_size(const lbm_batch* b, int* ncases, int* nitems, int* grid);
  * -1 clears the injection and the error status. */
 int lbm_batch_inject_stall(lbm_batch* b, int cta);
 
+/* Tile shape of the FP32-deviation batch kernel: collision tiles of
+ * 30 x (16 rows - 2) and mu tiles of 32 x 16 rows, rows = 16 x (rows per
+ * thread), rows per thread 1, 2 (default) or 4.  lbm_batch_set_tiles fixes
+ * it; lbm_batch_autotune times `steps` steps of every shape that has a
+ * resident launch configuration (after one captured warm-up launch each) and
+ * keeps the fastest, reported in *rows_out.  The tuning steps run on the
+ * batch's state, which they advance: initialise after tuning.  The shapes
+ * give identical results (same arithmetic per node).  Errors: LBM_EINVAL,
+ * LBM_ENOTSUP (not an FP32-deviation batch), LBM_ECUDA. */
+int lbm_batch_set_tiles(lbm_batch* b, int rows_per_thread);
+int lbm_batch_autotune(lbm_batch* b, int steps, int* rows_out);
+
 /* ================================================================ warm start
  * A small fully connected network (FP32; GELU hidden layers, linear output)
  * that maps droplet parameters to an initial radial density profile, trained

@@ -166,17 +166,19 @@ __global__ void __launch_bounds__(NT2) k_batch_persistent(const CaseDev* __restr
 // Within a phase a CTA works through its items in a two-stage pipeline: the
 // copies of the next item (and the fetch of the item after it) are in flight
 // while the current item is computed from the other shared-memory buffer.
+template <int RPT>
 __device__ void split_load(const CaseDev& cd, int tile, long long t, int phase, unsigned char* buf) {
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, T2Y = Tile2<RPT>::T2Y;
   const int par = int(t & 1);
   const float* rin = static_cast<const float*>(cd.rho[par]);
   if (phase == 0) {
     const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
     switch (cd.scheme) {
-      case S_EFDS2: mu2d_load<S_EFDS2>(cd.kp, rin, x0, y0, buf); break;
-      case S_EFDS4: mu2d_load<S_EFDS4>(cd.kp, rin, x0, y0, buf); break;
-      case S_EFDS6: mu2d_load<S_EFDS6>(cd.kp, rin, x0, y0, buf); break;
-      case S_E4: mu2d_load<S_E4>(cd.kp, rin, x0, y0, buf); break;
-      case S_E8: mu2d_load<S_E8>(cd.kp, rin, x0, y0, buf); break;
+      case S_EFDS2: mu2d_load<S_EFDS2, RPT>(cd.kp, rin, x0, y0, buf); break;
+      case S_EFDS4: mu2d_load<S_EFDS4, RPT>(cd.kp, rin, x0, y0, buf); break;
+      case S_EFDS6: mu2d_load<S_EFDS6, RPT>(cd.kp, rin, x0, y0, buf); break;
+      case S_E4: mu2d_load<S_E4, RPT>(cd.kp, rin, x0, y0, buf); break;
+      case S_E8: mu2d_load<S_E8, RPT>(cd.kp, rin, x0, y0, buf); break;
       default: break;
     }
     return;
@@ -184,39 +186,43 @@ __device__ void split_load(const CaseDev& cd, int tile, long long t, int phase, 
   const int x0 = (tile % cd.ctiles_x) * T2X, y0 = (tile / cd.ctiles_x) * T2Y;
   const float* fin = static_cast<const float*>(cd.f[par]);
   switch (cd.scheme) {
-    case S_EFDS2: coll2d_load<S_EFDS2>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
-    case S_EFDS4: coll2d_load<S_EFDS4>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
-    case S_EFDS6: coll2d_load<S_EFDS6>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
-    case S_E4: coll2d_load<S_E4>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
-    case S_E8: coll2d_load<S_E8>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_EFDS2: coll2d_load<S_EFDS2, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_EFDS4: coll2d_load<S_EFDS4, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_EFDS6: coll2d_load<S_EFDS6, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_E4: coll2d_load<S_E4, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
+    case S_E8: coll2d_load<S_E8, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
     default: break;
   }
 }
 
+template <int RPT>
 __device__ void mu_direct(const CaseDev& cd, int tile, long long t) {
+  constexpr int M2Y = Tile2<RPT>::M2Y;
   const int par = int(t & 1);
   const float* rin = static_cast<const float*>(cd.rho[par]);
   const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
   switch (cd.scheme) {
-    case S_EFDS2: mu2d_direct<S_EFDS2>(cd.kp, rin, cd.mu, x0, y0); break;
-    case S_EFDS4: mu2d_direct<S_EFDS4>(cd.kp, rin, cd.mu, x0, y0); break;
-    case S_EFDS6: mu2d_direct<S_EFDS6>(cd.kp, rin, cd.mu, x0, y0); break;
-    case S_E4: mu2d_direct<S_E4>(cd.kp, rin, cd.mu, x0, y0); break;
-    case S_E8: mu2d_direct<S_E8>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_EFDS2: mu2d_direct<S_EFDS2, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_EFDS4: mu2d_direct<S_EFDS4, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_EFDS6: mu2d_direct<S_EFDS6, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_E4: mu2d_direct<S_E4, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_E8: mu2d_direct<S_E8, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
     default: break;
   }
 }
 
+template <int RPT>
 __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phase, unsigned char* buf) {
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, T2Y = Tile2<RPT>::T2Y;
   const int par = int(t & 1);
   if (phase == 0) {
     const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
     switch (cd.scheme) {
-      case S_EFDS2: mu2d_compute<S_EFDS2>(cd.kp, cd.mu, x0, y0, buf); break;
-      case S_EFDS4: mu2d_compute<S_EFDS4>(cd.kp, cd.mu, x0, y0, buf); break;
-      case S_EFDS6: mu2d_compute<S_EFDS6>(cd.kp, cd.mu, x0, y0, buf); break;
-      case S_E4: mu2d_compute<S_E4>(cd.kp, cd.mu, x0, y0, buf); break;
-      case S_E8: mu2d_compute<S_E8>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_EFDS2: mu2d_compute<S_EFDS2, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_EFDS4: mu2d_compute<S_EFDS4, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_EFDS6: mu2d_compute<S_EFDS6, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_E4: mu2d_compute<S_E4, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
+      case S_E8: mu2d_compute<S_E8, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
       default: break;
     }
     return;
@@ -227,8 +233,8 @@ __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phas
   const bool tau1 = cd.kp.omega == 1.0;
 #define LBM_SPLIT_CASE(SS)                                                              \
   case SS:                                                                              \
-    if (tau1) coll2d_compute<SS, true>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf, cd.mrt); \
-    else coll2d_compute<SS, false>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf, cd.mrt);     \
+    if (tau1) coll2d_compute<SS, true, RPT>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf, cd.mrt); \
+    else coll2d_compute<SS, false, RPT>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf, cd.mrt);     \
     break;
   switch (cd.scheme) {
     LBM_SPLIT_CASE(S_EFDS2)
@@ -251,7 +257,8 @@ __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phas
 // 30 x 30 tiles' buffers (~48 KB each) keep two CTAs resident per SM.
 constexpr int NBUF = 2;
 
-__global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restrict__ cases,
+template <int RPT>  // rows per thread of the tiles (1, 2, 4)
+__global__ void __launch_bounds__(NT2S, RPT >= 4 ? 1 : 2) k_batch_split(const CaseDev* __restrict__ cases,
                                                       const Item* __restrict__ mitems, int nmu,
                                                       const Item* __restrict__ citems, int ncoll, int nsteps,
                                                       BatchCtl* ctl, unsigned long long timeout_ns, int buf_bytes) {
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restri
         // no staging, no CTA barrier
         for (int it = i0; it < i1; ++it) {
           const Item itm = items[it];
-          mu_direct(cases[itm.c], itm.tile, t);
+          mu_direct<RPT>(cases[itm.c], itm.tile, t);
         }
         if (!grid_barrier(ctl, timeout_ns)) return;
         continue;
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restri
         const int it = i0 + j;
         if (it < i1) {
           const Item itm = items[it];
-          split_load(cases[itm.c], itm.tile, t, phase, smem + j * buf_bytes);
+          split_load<RPT>(cases[itm.c], itm.tile, t, phase, smem + j * buf_bytes);
         }
         cpa_commit();
       }
@@ -294,11 +301,11 @@ __global__ void __launch_bounds__(NT2S, 2) k_batch_split(const CaseDev* __restri
         const int ahead = it + NBUF - 1;
         if (ahead < i1) {
           const Item itm = items[ahead];
-          split_load(cases[itm.c], itm.tile, t, phase, smem + ring(b + NBUF - 1, NBUF) * buf_bytes);
+          split_load<RPT>(cases[itm.c], itm.tile, t, phase, smem + ring(b + NBUF - 1, NBUF) * buf_bytes);
         }
         cpa_commit();
         const Item itm = items[it];
-        split_compute(cases[itm.c], itm.tile, t, phase, smem + b * buf_bytes);
+        split_compute<RPT>(cases[itm.c], itm.tile, t, phase, smem + b * buf_bytes);
         b = ring(b + 1, NBUF);
       }
       cpa_wait_all();
@@ -406,6 +413,9 @@ struct lbm_batch {
   int nmu = 0, ncoll = 0, grid_split = 0;
   size_t smem_split = 0;
   int buf_split = 0;  // bytes of one item buffer of the split kernel
+  int rpt = 0;        // split kernel: tile rows per thread (1, 2, 4)
+  int item_cap = 0;   // capacity of d_mitems and of d_citems
+  std::vector<int> case_order;  // split path: cases in work-list order
   std::vector<std::pair<void*, size_t>> blocks;
 };
 
@@ -427,6 +437,58 @@ extern "C" void lbm_batch_destroy(lbm_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto& blk : b->blocks) b->alloc.free(blk.first, blk.second, b->alloc.ctx);
   delete b;
+}
+
+template <int RPT>
+static int setup_split_t(lbm_batch* b) {
+  constexpr int M2Y = Tile2<RPT>::M2Y, T2Y = Tile2<RPT>::T2Y;
+  std::vector<Item> mitems, citems;
+  for (const int c : b->case_order) {
+    const CaseDev& cd = b->host_cases[c];
+    const int ny = b->p[c].ny;
+    const int mt = cd.mtiles_x * ((ny + M2Y - 1) / M2Y);
+    const int ct = cd.ctiles_x * ((ny + T2Y - 1) / T2Y);
+    for (int tl = 0; tl < mt; ++tl) mitems.push_back({c, tl});
+    for (int tl = 0; tl < ct; ++tl) citems.push_back({c, tl});
+  }
+  if (int(mitems.size()) > b->item_cap || int(citems.size()) > b->item_cap) return LBM_ECUDA;
+  cudaError_t e = cudaMemcpyAsync(b->d_mitems, mitems.data(), sizeof(Item) * mitems.size(), cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_citems, citems.data(), sizeof(Item) * citems.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return LBM_ECUDA;
+  size_t m = Split2DShape<S_EFDS2, RPT>::bytes;
+  m = std::max(m, Split2DShape<S_EFDS4, RPT>::bytes);
+  m = std::max(m, Split2DShape<S_EFDS6, RPT>::bytes);
+  m = std::max(m, Split2DShape<S_E4, RPT>::bytes);
+  m = std::max(m, Split2DShape<S_E8, RPT>::bytes);
+  const int buf = int((m + 15) / 16 * 16);
+  const size_t smem = NBUF * size_t(buf);  // items in flight
+  int dev = 0, sms = 0, ps = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaFuncSetAttribute(k_batch_split<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_batch_split<RPT>, NT2S, smem) != cudaSuccess || ps < 1)
+    return LBM_ENOTSUP;
+  b->nmu = int(mitems.size());
+  b->ncoll = int(citems.size());
+  b->buf_split = buf;
+  b->smem_split = smem;
+  b->grid_split = std::max(1, std::min(ps * sms, std::max(b->nmu, b->ncoll)));
+  b->rpt = RPT;
+  // the captured launch depends on the shape: capture again at the next step
+  if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  b->graph_steps = -1;
+  return LBM_OK;
+}
+
+static int setup_split(lbm_batch* b, int rpt) {
+  if (rpt == 1) return setup_split_t<1>(b);
+  if (rpt == 2) return setup_split_t<2>(b);
+  if (rpt == 4) return setup_split_t<4>(b);
+  return LBM_EINVAL;
 }
 
 extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, const lbm_allocator* alloc,
@@ -496,20 +558,20 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
   if (!ok) { lbm_batch_destroy(b); return LBM_ENOMEM; }
   b->nitems = int(items.size());
   b->split = prec0 == LBM_FP32DEV && !mu0;
-  std::vector<Item> mitems, citems;
   if (b->split) {
+    // work lists are rebuilt per tile shape; the shortest tiles (one row per
+    // thread) give the longest lists
+    b->case_order.assign(idx.begin(), idx.end());
+    long long cap = 0;
     for (int k = 0; k < n; ++k) {
       const int c = idx[k];
       const CaseDev& cd = b->host_cases[c];
-      const int mt = cd.mtiles_x * ((cases[c].ny + M2Y - 1) / M2Y);
-      const int ct = cd.ctiles_x * ((cases[c].ny + T2Y - 1) / T2Y);
-      for (int tl = 0; tl < mt; ++tl) mitems.push_back({c, tl});
-      for (int tl = 0; tl < ct; ++tl) citems.push_back({c, tl});
+      cap += (long long)std::max(cd.mtiles_x * ((cases[c].ny + Tile2<1>::M2Y - 1) / Tile2<1>::M2Y),
+                                 cd.ctiles_x * ((cases[c].ny + Tile2<1>::T2Y - 1) / Tile2<1>::T2Y));
     }
-    b->nmu = int(mitems.size());
-    b->ncoll = int(citems.size());
-    b->d_mitems = static_cast<Item*>(balloc(b, sizeof(Item) * mitems.size()));
-    b->d_citems = static_cast<Item*>(balloc(b, sizeof(Item) * citems.size()));
+    b->item_cap = int(cap);
+    b->d_mitems = static_cast<Item*>(balloc(b, sizeof(Item) * cap));
+    b->d_citems = static_cast<Item*>(balloc(b, sizeof(Item) * cap));
     if (!b->d_mitems || !b->d_citems) { lbm_batch_destroy(b); return LBM_ENOMEM; }
   }
   b->d_cases = static_cast<CaseDev*>(balloc(b, sizeof(CaseDev) * n));
@@ -523,11 +585,6 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
   cudaError_t e = cudaMemcpyAsync(b->d_cases, b->host_cases.data(), sizeof(CaseDev) * n, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess && b->split) {
-    e = cudaMemcpyAsync(b->d_mitems, mitems.data(), sizeof(Item) * mitems.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(b->d_citems, citems.data(), sizeof(Item) * citems.size(), cudaMemcpyHostToDevice, b->stream);
-  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   // residency: CTAs per SM x SMs, all resident at once
   int dev = 0, sms = 0, per_sm = 0;
@@ -544,19 +601,9 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
   else { b->smem = batch_smem<PrecF32M64>(); setup(k_batch_persistent<PrecF32M64>, b->smem);
          cudaFuncSetAttribute(k_batch_obs<PrecF32M64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)); }
   b->grid = std::max(1, std::min(per_sm * sms, b->nitems));
-  if (b->split) {
-    size_t m = Split2DShape<S_EFDS2>::bytes;
-    m = std::max(m, Split2DShape<S_EFDS4>::bytes);
-    m = std::max(m, Split2DShape<S_EFDS6>::bytes);
-    m = std::max(m, Split2DShape<S_E4>::bytes);
-    m = std::max(m, Split2DShape<S_E8>::bytes);
-    b->buf_split = int((m + 15) / 16 * 16);
-    b->smem_split = NBUF * size_t(b->buf_split);  // items in flight
-    int ps = 0;
-    cudaFuncSetAttribute(k_batch_split, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem_split));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_batch_split, NT2S, b->smem_split);
-    if (ps < 1) { lbm_batch_destroy(b); return LBM_ECUDA; }
-    b->grid_split = std::max(1, std::min(ps * sms, std::max(b->nmu, b->ncoll)));
+  if (b->split && e == cudaSuccess && setup_split(b, RPT_DEFAULT) != LBM_OK) {
+    lbm_batch_destroy(b);
+    return LBM_ECUDA;
   }
   if (e != cudaSuccess || per_sm < 1 || cudaGetLastError() != cudaSuccess) { lbm_batch_destroy(b); return LBM_ECUDA; }
   *out = b;
@@ -639,7 +686,8 @@ static cudaError_t launch_persistent(lbm_batch* b, int nsteps) {
     at[0].val.cooperative = 1;
     cs.attrs = at;
     cs.numAttrs = 1;
-    return cudaLaunchKernelEx(&cs, k_batch_split, (const CaseDev*)b->d_cases, (const Item*)b->d_mitems, b->nmu,
+    auto kern = b->rpt == 1 ? k_batch_split<1> : (b->rpt == 4 ? k_batch_split<4> : k_batch_split<2>);
+    return cudaLaunchKernelEx(&cs, kern, (const CaseDev*)b->d_cases, (const Item*)b->d_mitems, b->nmu,
                               (const Item*)b->d_citems, b->ncoll, nsteps, b->ctl, timeout_ns, b->buf_split);
   }
   cudaLaunchConfig_t cfg{};
@@ -689,6 +737,41 @@ extern "C" int lbm_batch_step(lbm_batch* b, long long n) {
   }
   if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) return LBM_ECUDA;
   b->t += n;
+  return LBM_OK;
+}
+
+extern "C" int lbm_batch_set_tiles(lbm_batch* b, int rows) {
+  if (!b || (rows != 1 && rows != 2 && rows != 4)) return LBM_EINVAL;
+  if (!b->split) return LBM_ENOTSUP;
+  return setup_split(b, rows);
+}
+
+extern "C" int lbm_batch_autotune(lbm_batch* b, int steps, int* rows_out) {
+  if (!b || steps < 1 || steps > 100000) return LBM_EINVAL;
+  if (rows_out) *rows_out = b->rpt;
+  if (!b->split) return LBM_OK;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LBM_ECUDA; }
+  int best = 0, rc = LBM_OK;
+  float best_ms = 1e30f;
+  for (const int r : {1, 2, 4}) {
+    if (setup_split(b, r) != LBM_OK) continue;  // shape without a resident configuration
+    if ((rc = lbm_batch_step(b, steps)) != LBM_OK) break;  // capture and warm up
+    cudaEventRecord(e0, b->stream);
+    if ((rc = lbm_batch_step(b, steps)) != LBM_OK) break;
+    cudaEventRecord(e1, b->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LBM_ECUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = r; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LBM_OK) return rc;
+  if (best == 0) return LBM_ECUDA;
+  if ((rc = setup_split(b, best)) != LBM_OK) return rc;
+  if (rows_out) *rows_out = best;
   return LBM_OK;
 }
 

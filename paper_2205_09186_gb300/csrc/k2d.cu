@@ -33,15 +33,17 @@ cudaError_t launch_mode(const Launch& c, int* nblocks) {
   return cudaGetLastError();
 }
 
-// FP32 deviation storage with FP32 mu: mu pass + row-per-warp collision pass
-template <int S, bool TAU1>
-cudaError_t launch_split2d(const Launch& c, int* nblocks) {
-  using Sh = Split2DShape<S>;
+// FP32 deviation storage with FP32 mu: mu pass + row-per-warp collision pass,
+// tiles of RPT rows per thread
+template <int S, bool TAU1, int RPT>
+cudaError_t launch_split2d_t(const Launch& c, int* nblocks) {
+  using Sh = Split2DShape<S, RPT>;
+  constexpr int M2Y = Tile2<RPT>::M2Y, T2Y = Tile2<RPT>::T2Y;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mu2d<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+    cudaError_t e = cudaFuncSetAttribute(k_mu2d<S, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_coll2d<S, TAU1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
+      e = cudaFuncSetAttribute(k_coll2d<S, TAU1, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -56,26 +58,36 @@ cudaError_t launch_split2d(const Launch& c, int* nblocks) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms < 1) sms = 1;
       }
       const int want_gy = (4 * sms + gx - 1) / gx;
-      int rpt = (c.kp.ny + 16 * want_gy - 1) / (16 * want_gy);
-      rpt = rpt < 2 ? 2 : (rpt > 32 ? 32 : rpt);
-      dim3 gm(gx, (c.kp.ny + 16 * rpt - 1) / (16 * rpt));
-      k_mu2d_ym<S><<<gm, YMT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu), rpt);
+      int rows = (c.kp.ny + 16 * want_gy - 1) / (16 * want_gy);
+      rows = rows < 2 ? 2 : (rows > 32 ? 32 : rows);
+      dim3 gm(gx, (c.kp.ny + 16 * rows - 1) / (16 * rows));
+      k_mu2d_ym<S><<<gm, YMT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu), rows);
     } else {
       dim3 gm((c.kp.nx + M2X - 1) / M2X, (c.kp.ny + M2Y - 1) / M2Y);
-      k_mu2d<S><<<gm, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+      k_mu2d<S, RPT><<<gm, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin),
+                                                        static_cast<float*>(c.mu));
     }
   } else {
     dim3 gm((c.kp.nx + M2X - 1) / M2X, (c.kp.ny + M2Y - 1) / M2Y);
-    k_mu2d<S><<<gm, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+    k_mu2d<S, RPT><<<gm, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin),
+                                                      static_cast<float*>(c.mu));
   }
   if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
   dim3 gc((c.kp.nx + T2X - 1) / T2X, (c.kp.ny + T2Y - 1) / T2Y);
   if (nblocks) *nblocks = int(gc.x * gc.y);
-  k_coll2d<S, TAU1><<<gc, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin),
+  k_coll2d<S, TAU1, RPT><<<gc, NT2S, Sh::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.fin),
                                                        static_cast<float*>(c.fout), static_cast<const float*>(c.rin),
                                                        static_cast<const float*>(c.mu), static_cast<float*>(c.rout),
                                                        c.aux, c.mrt);
   return cudaGetLastError();
+}
+
+// tile rows per thread of the handle (Launch::rpt2d: 1, 2 or 4; 0 = default)
+template <int S, bool TAU1>
+cudaError_t launch_split2d(const Launch& c, int* nblocks) {
+  if (c.rpt2d == 1) return launch_split2d_t<S, TAU1, 1>(c, nblocks);
+  if (c.rpt2d == 4) return launch_split2d_t<S, TAU1, 4>(c, nblocks);
+  return launch_split2d_t<S, TAU1, 2>(c, nblocks);
 }
 
 template <int S, class P>

@@ -23,6 +23,7 @@ struct Launch {
   Mrt mrt;      // D2Q9 collision operator (on = 0: single relaxation)
   cudaEvent_t ev_mid;  // if set: recorded between the mu pass and the collision pass
   const void* tmap;    // D3Q19 FP32DEV: tensor map (CUtensorMap) of the populations fin, or null
+  int rpt2d;           // D2Q9 FP32DEV split tiles: rows per thread (1, 2, 4; 0 = default 2)
 };
 
 // Kernel constants of a case: lattice size, the EOS at T = Tr T_c (either

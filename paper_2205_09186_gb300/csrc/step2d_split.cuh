@@ -20,14 +20,19 @@
 namespace lbmd {
 
 constexpr int NT2S = 512;                   // threads of both passes
-constexpr int RPT = 2;                      // rows per thread
-constexpr int M2X = 32, M2Y = 16 * RPT;     // mu tile
-constexpr int C2X = 32, C2Y = 16 * RPT;     // collision region (tile + ring)
-constexpr int T2X = C2X - 2, T2Y = C2Y - 2; // 30 x 30 collision tile
-constexpr int C2N = C2X * C2Y;              // nodes of the collision region
+constexpr int M2X = 32, C2X = 32;           // mu tile and collision region width
+constexpr int T2X = C2X - 2;                // collision tile width
+// Tile heights by rows per thread RPT (1, 2 or 4; 2 unless tuned): mu tile
+// 32 x 16 RPT, collision region 32 x 16 RPT around a 30 x (16 RPT - 2) tile.
+template <int RPT>
+struct Tile2 {
+  static constexpr int M2Y = 16 * RPT, C2Y = 16 * RPT, T2Y = C2Y - 2, C2N = C2X * C2Y;
+};
+constexpr int RPT_DEFAULT = 2;
 
-template <int S>
+template <int S, int RPT = RPT_DEFAULT>
 struct Split2DShape {
+  static constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, C2N = Tile2<RPT>::C2N;
   static constexpr int R = Sch<S>::R;
   static constexpr int MW = M2X + 2 * R, MH = M2Y + 2 * R;      // mu pass: density region
   static constexpr int GW = C2X + 2 * R, GH = C2Y + 2 * R;      // collision: field region
@@ -42,10 +47,11 @@ struct Split2DShape {
 // buffer; the caller commits and waits) and a compute half, so that the batch
 // kernel can copy its next tile while computing the current one.
 
-template <int S>
+template <int S, int RPT>
 __device__ __forceinline__ void mu2d_load(const KParams& p, const float* __restrict__ rin, int x0, int y0,
                                           unsigned char* smem) {
-  using Sh = Split2DShape<S>;
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
+  using Sh = Split2DShape<S, RPT>;
   constexpr int R = Sh::R, MW = Sh::MW, MH = Sh::MH;
   static_assert(MW <= 64 && MW > 32, "two columns per lane");
   float* s = reinterpret_cast<float*>(smem);
@@ -61,10 +67,11 @@ __device__ __forceinline__ void mu2d_load(const KParams& p, const float* __restr
   }
 }
 
-template <int S>
+template <int S, int RPT>
 __device__ __forceinline__ void mu2d_compute(const KParams& p, float* __restrict__ mu, int x0, int y0,
                                              const unsigned char* smem) {
-  using Sh = Split2DShape<S>;
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
+  using Sh = Split2DShape<S, RPT>;
   constexpr int R = Sh::R, MW = Sh::MW;
   const float* s = reinterpret_cast<const float*>(smem);
   const int nx = p.nx, ny = p.ny;
@@ -81,11 +88,12 @@ __device__ __forceinline__ void mu2d_compute(const KParams& p, float* __restrict
   }
 }
 
-template <int S>
+template <int S, int RPT>
 __device__ __forceinline__ void coll2d_load(const KParams& p, const float* __restrict__ fin,
                                             const float* __restrict__ rin, const float* __restrict__ muf, int x0,
                                             int y0, unsigned char* smem) {
-  using Sh = Split2DShape<S>;
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
+  using Sh = Split2DShape<S, RPT>;
   constexpr int Q = 9, R = Sh::R, GW = Sh::GW, GH = Sh::GH;
   float* s_ds = reinterpret_cast<float*>(smem);
   float* s_mu = reinterpret_cast<float*>(smem + Sh::off_mu);
@@ -124,12 +132,13 @@ __device__ __forceinline__ void coll2d_load(const KParams& p, const float* __res
   }
 }
 
-template <int S, bool TAU1>
+template <int S, bool TAU1, int RPT>
 __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restrict__ fout, float* __restrict__ rout,
                                                unsigned long long* bad, long long t, int x0, int y0,
                                                unsigned char* smem, const Mrt& mrt) {
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
   using L = Lattice<0>;
-  using Sh = Split2DShape<S>;
+  using Sh = Split2DShape<S, RPT>;
   constexpr int Q = 9, R = Sh::R, GW = Sh::GW;
   const float* s_ds = reinterpret_cast<const float*>(smem);
   const float* s_mu = reinterpret_cast<const float*>(smem + Sh::off_mu);
@@ -225,8 +234,9 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
 // same persistent launch (by other CTAs, before a device-wide barrier with
 // acquire semantics), so they are read with ordinary coherent loads, never
 // through the non-coherent read-only path (no __ldg, no __restrict__).
-template <int S>
+template <int S, int RPT>
 __device__ __forceinline__ void mu2d_direct(const KParams& p, const float* rin, float* mu, int x0, int y0) {
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
   using Sc = Sch<S>;
   constexpr int R = Sc::R;
   const int nx = p.nx, ny = p.ny;
@@ -333,41 +343,45 @@ __global__ void __launch_bounds__(YMT) k_mu2d_ym(const KParams p, const float* _
 }
 
 // whole tiles (load, wait, compute) for the single-case kernels
-template <int S>
+template <int S, int RPT>
 __device__ __forceinline__ void mu2d_tile(const KParams& p, const float* __restrict__ rin, float* __restrict__ mu,
                                           int x0, int y0, unsigned char* smem) {
-  mu2d_load<S>(p, rin, x0, y0, smem);
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
+  mu2d_load<S, RPT>(p, rin, x0, y0, smem);
   cpa_commit();
   cpa_wait_all();
   __syncthreads();
-  mu2d_compute<S>(p, mu, x0, y0, smem);
+  mu2d_compute<S, RPT>(p, mu, x0, y0, smem);
 }
 
-template <int S, bool TAU1>
+template <int S, bool TAU1, int RPT>
 __device__ __forceinline__ void coll2d_tile(const KParams& p, const float* __restrict__ fin, float* __restrict__ fout,
                                             const float* __restrict__ rin, const float* __restrict__ muf,
                                             float* __restrict__ rout, unsigned long long* bad, long long t, int x0,
                                             int y0, unsigned char* smem, const Mrt& mrt) {
-  coll2d_load<S>(p, fin, rin, muf, x0, y0, smem);
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
+  coll2d_load<S, RPT>(p, fin, rin, muf, x0, y0, smem);
   cpa_commit();
   cpa_wait_all();
   __syncthreads();
-  coll2d_compute<S, TAU1>(p, fout, rout, bad, t, x0, y0, smem, mrt);
+  coll2d_compute<S, TAU1, RPT>(p, fout, rout, bad, t, x0, y0, smem, mrt);
 }
 
-template <int S>
+template <int S, int RPT>
 __global__ void __launch_bounds__(NT2S) k_mu2d(const KParams p, const float* __restrict__ rin, float* __restrict__ mu) {
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
   extern __shared__ __align__(16) unsigned char smem[];
-  mu2d_tile<S>(p, rin, mu, blockIdx.x * M2X, blockIdx.y * M2Y, smem);
+  mu2d_tile<S, RPT>(p, rin, mu, blockIdx.x * M2X, blockIdx.y * M2Y, smem);
 }
 
-template <int S, bool TAU1>
+template <int S, bool TAU1, int RPT>
 __global__ void __launch_bounds__(NT2S) k_coll2d(const KParams p, const float* __restrict__ fin,
                                                  float* __restrict__ fout, const float* __restrict__ rin,
                                                  const float* __restrict__ mu, float* __restrict__ rout,
                                                  const StepAux aux, const Mrt mrt) {
+  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
   extern __shared__ __align__(16) unsigned char smem[];
-  coll2d_tile<S, TAU1>(p, fin, fout, rin, mu, rout, aux.bad_step, aux.t, blockIdx.x * T2X, blockIdx.y * T2Y, smem,
+  coll2d_tile<S, TAU1, RPT>(p, fin, fout, rin, mu, rout, aux.bad_step, aux.t, blockIdx.x * T2X, blockIdx.y * T2Y, smem,
                        mrt);
 }
 

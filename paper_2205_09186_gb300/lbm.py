@@ -94,6 +94,8 @@ SIGNATURES = {
     "lbm_batch_get_step": (C.c_longlong, [_h]),
     "lbm_batch_size": (C.c_int, [_h, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lbm_batch_inject_stall": (C.c_int, [_h, C.c_int]),
+    "lbm_batch_set_tiles": (C.c_int, [_h, C.c_int]),
+    "lbm_batch_autotune": (C.c_int, [_h, C.c_int, C.POINTER(C.c_int)]),
     "lbm_mlp_create": (C.c_int, [C.POINTER(C.c_int), C.c_int, C.c_int, C.c_void_p, C.POINTER(lbm_allocator),
                                  C.POINTER(C.c_void_p)]),
     "lbm_mlp_destroy": (None, [_h]),
@@ -420,6 +422,37 @@ class Batch:
 
     def lbm_batch_inject_stall(self, cta):
         return check(lib().lbm_batch_inject_stall(self.h, cta), "lbm_batch_inject_stall")
+
+    def lbm_batch_set_tiles(self, rows_per_thread):
+        return check(lib().lbm_batch_set_tiles(self.h, int(rows_per_thread)), "lbm_batch_set_tiles")
+
+    def lbm_batch_autotune(self, steps=5, cache=None):
+        """Tile rows per thread (1, 2, 4) chosen by timing; the tuning steps
+        advance the state (initialise afterwards).  cache: path of a JSON file
+        of earlier choices keyed by the device and the cases' shapes; a hit
+        sets that choice without timing, a miss records the new one."""
+        key = None
+        if cache is not None:
+            import hashlib
+            import json
+            import os
+            import torch
+            shapes = [(p.nx, p.ny, p.scheme, p.precision, p.mu_fp64, p.collision) for p in self.params]
+            key = hashlib.sha1(json.dumps([torch.cuda.get_device_name(), shapes]).encode()).hexdigest()
+            table = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    table = json.load(f)
+            if key in table:
+                self.lbm_batch_set_tiles(table[key])
+                return table[key]
+        r = C.c_int()
+        check(lib().lbm_batch_autotune(self.h, int(steps), C.byref(r)), "lbm_batch_autotune")
+        if key is not None:
+            table[key] = r.value
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return r.value
 
 
 def _f32(a):

@@ -93,3 +93,46 @@ def test_stalled_barrier_times_out(L):
     s.lbm_init_droplet(CASES[0]["r"])
     s.lbm_step(5)
     assert s.lbm_observables()["status"] == 0
+
+
+def test_tile_shapes_give_identical_results(L):
+    # the same arithmetic per node in every tile shape: bitwise equal states
+    cases = CASES[:4]
+    dens = {}
+    for rows in (1, 2, 4):
+        b = L.Batch([params(L, c, 1) for c in cases])
+        b.lbm_batch_set_tiles(rows)
+        b.lbm_batch_init_droplets([c["r"] for c in cases])
+        b.lbm_batch_step(25)
+        dens[rows] = [b.lbm_batch_get_density(i) for i in range(len(cases))]
+        nc, nitems, grid = b.lbm_batch_size()
+        assert nc == len(cases) and nitems > 0 and grid > 0
+        b.close()
+    for rows in (1, 4):
+        for a, d in zip(dens[rows], dens[2]):
+            assert np.array_equal(a, d), rows
+
+
+def test_autotune_keeps_a_shape_and_caches_it(L, tmp_path):
+    cases = CASES[:4]
+    cache = str(tmp_path / "tiles.json")
+    b = L.Batch([params(L, c, 1) for c in cases])
+    rows = b.lbm_batch_autotune(steps=2, cache=cache)
+    assert rows in (1, 2, 4)
+    b.lbm_batch_init_droplets([c["r"] for c in cases])
+    b.lbm_batch_step(10)
+    ref = L.Batch([params(L, c, 1) for c in cases])
+    ref.lbm_batch_init_droplets([c["r"] for c in cases])
+    ref.lbm_batch_step(10)
+    for i in range(len(cases)):
+        assert np.array_equal(b.lbm_batch_get_density(i), ref.lbm_batch_get_density(i))
+    # a second batch of the same shapes takes the cached choice
+    c2 = L.Batch([params(L, c, 1) for c in cases])
+    assert c2.lbm_batch_autotune(steps=2, cache=cache) == rows
+    import json
+    assert list(json.load(open(cache)).values()) == [rows]
+    with pytest.raises(L.LBMError) as e:
+        b.lbm_batch_set_tiles(3)
+    assert e.value.code == L.LBM_EINVAL
+    for x in (b, ref, c2):
+        x.close()
