@@ -185,7 +185,10 @@ def run_batch(L, steps=50, warmup=10, ncases=512):
     params = [L.make_params(lattice=L.LBM_D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1,
                             scheme=c["scheme"], precision=L.LBM_FP32DEV) for c in cases]
     b = L.Batch(params)
-    rows = b.lbm_batch_autotune(steps=5)  # tile shape by timing (advances the state: initialise after)
+    # tile shape by timing on the initial droplets (the tuning advances the
+    # state: initialise again afterwards)
+    b.lbm_batch_init_droplets([c["r"] for c in cases])
+    rows = b.lbm_batch_autotune(steps=10)
     b.lbm_batch_init_droplets([c["r"] for c in cases])
     nodes = sum(c["nx"] * c["ny"] for c in cases)
     b.lbm_batch_step(warmup)

@@ -391,7 +391,8 @@ int lbm_batch_inject_stall(lbm_batch* b, int cta);
  * it; lbm_batch_autotune times `steps` steps of every shape that has a
  * resident launch configuration (after one captured warm-up launch each) and
  * keeps the fastest, reported in *rows_out.  The tuning steps run on the
- * batch's state, which they advance: initialise after tuning.  The shapes
+ * batch's state, which they advance: initialise before tuning (the timing
+ * is only representative of a physical state) and again after it.  The shapes
  * give identical results (same arithmetic per node).  Errors: LBM_EINVAL,
  * LBM_ENOTSUP (not an FP32-deviation batch), LBM_ECUDA. */
 int lbm_batch_set_tiles(lbm_batch* b, int rows_per_thread);

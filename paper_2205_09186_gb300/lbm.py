@@ -428,7 +428,7 @@ class Batch:
 
     def lbm_batch_autotune(self, steps=5, cache=None):
         """Tile rows per thread (1, 2, 4) chosen by timing; the tuning steps
-        advance the state (initialise afterwards).  cache: path of a JSON file
+        advance the state (initialise before tuning, and again afterwards).  cache: path of a JSON file
         of earlier choices keyed by the device and the cases' shapes; a hit
         sets that choice without timing, a miss records the new one."""
         key = None
