@@ -117,6 +117,7 @@ def test_autotune_keeps_a_shape_and_caches_it(L, tmp_path):
     cases = CASES[:4]
     cache = str(tmp_path / "tiles.json")
     b = L.Batch([params(L, c, 1) for c in cases])
+    b.lbm_batch_init_droplets([c["r"] for c in cases])
     rows = b.lbm_batch_autotune(steps=2, cache=cache)
     assert rows in (1, 2, 4)
     b.lbm_batch_init_droplets([c["r"] for c in cases])
