@@ -1,9 +1,11 @@
 // Batched D2Q9 droplets of uneven sizes and parameters in one persistent
-// launch.  The (case, tile) work items of all cases are fetched dynamically
-// by resident CTAs (an atomic counter per step); steps are separated by a
-// device-wide barrier whose waits are bounded (about one second), after which
-// the kernel records LBM_ETIMEOUT and returns.  lbm_batch_step captures the
-// launch (plus the counter reset) in a CUDA graph and replays it.
+// launch.  FP32-deviation batches (k_batch_split) deal the (case, tile) work
+// items of each phase to the resident CTAs in contiguous runs; other
+// precisions (k_batch_persistent) fetch them from an atomic counter per step.
+// Steps and phases are separated by a device-wide barrier whose waits are
+// bounded (about one second), after which the kernel records LBM_ETIMEOUT and
+// returns.  lbm_batch_step captures the launch (plus the counter reset) in a
+// CUDA graph and replays it; lbm_batch_autotune picks the tile shape.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,7 +35,7 @@ struct CaseDev {
   int scheme;
   int tiles_x, tiles_y;
   int item_begin, item_end;      // observation / single-phase items
-  int mtiles_x, ctiles_x;        // split path: mu tiles (32 x 16) and collision tiles (30 x 14) per row
+  int mtiles_x, ctiles_x;        // split path: mu tiles (32 wide) and collision tiles (30 wide) per row
   Mrt mrt;                       // collision operator of the case
 };
 

@@ -1,15 +1,16 @@
 // D2Q9 FP32-deviation step as two passes (the 2D counterpart of
 // step3d_split.cuh):
 //
-//  mu2d_tile    mu = k^2 psi'(rho) - kappa lap rho (Eq. 16) for one 32 x 32
-//               tile (halo R staged in shared memory).
+//  mu2d_tile    mu = k^2 psi'(rho) - kappa lap rho (Eq. 16) for one
+//               32 x 16 RPT tile (halo R staged in shared memory).
 //  coll2d_tile  grad mu, grad rho (Eq. 17-25) -> F (Eq. 12) -> BGK + EDM
 //               (Eq. 1, 6, 8) -> push streaming and the next density for a
-//               30 x 30 tile; its 32 x 32 tile-plus-ring region maps one warp
-//               to two rows, w and w + 16 (512 threads, two collisions per
-//               thread: the per-tile staging, barriers and bookkeeping are
-//               shared by twice the nodes of a 30 x 14 tile, and the ring is
-//               6% of the region's rows instead of 12%).
+//               30 x (16 RPT - 2) tile; its 32 x 16 RPT tile-plus-ring region
+//               maps one warp to RPT rows, w, w + 16, ... (512 threads, RPT
+//               collisions per thread: with RPT = 2, the default, the
+//               per-tile staging, barriers and bookkeeping are shared by twice
+//               the nodes of RPT = 1, and the ring is 6% of the region's rows
+//               instead of 12%).
 //
 // Both are device functions so that the single-case kernels and the
 // persistent batch kernel share them.
