@@ -236,12 +236,15 @@ def run_2d(L, steps=200, warmup=20):
     s = L.Sim(L.make_params(lattice=L.LBM_D2Q9, nx=4096, ny=4096, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
                             precision=L.LBM_FP32DEV))
     s.lbm_init_droplet(800.0)
+    rows = s.lbm_autotune()  # tile rows by timing (leaves the state undefined)
+    s.lbm_init_droplet(800.0)
     s.lbm_step(5)
     torch.cuda.synchronize()
     ms = s.lbm_step_timed(20)
     n = 4096 * 4096
     out["bgk_4096"] = {"mlups": n * 20 / (ms[2] * 1e-3) / 1e6, "ms_per_step": ms[2] / 20, "coll_ms": ms[1] / 20,
                        "mu_ms": ms[0] / 20, "coll_frac": 84 * n / (ms[1] / 20 * 1e-3) / 1e9 / measured_peak()[0],
+                       "tile_rows_per_thread": rows,
                        "status": s.lbm_observables()["status"]}
     s.close()
     # the same droplet sitting on a flat wall of 8 rows (Appendix A), wall

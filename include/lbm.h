@@ -257,15 +257,19 @@ long long lbm_get_step(const lbm_handle* h);
  * next lbm_step. */
 int lbm_device_state(lbm_handle* h, void** f, void** rho);
 
-/* Work decomposition of the D3Q19 FP32DEV step (explicit schemes): each CTA
- * marches through a chunk of zc planes.  lbm_set_zchunk fixes zc (0 = the
+/* Work decomposition.  D3Q19 FP32DEV step (explicit schemes): each CTA
+ * marches through a chunk of zc planes; lbm_set_zchunk fixes zc (0 = the
  * built-in heuristic, which balances the last wave of CTAs against the
- * per-chunk prologue).  lbm_autotune times the candidate chunk lengths over a
- * few steps each on this handle's lattice and keeps the fastest; the steps
- * run on the handle's state, which is left undefined (initialise after
- * tuning).  *zc_out receives the choice, 0 if the handle has nothing to
- * tune. */
+ * per-chunk prologue).  D2Q9 FP32DEV split step (explicit and isotropic
+ * schemes, no walls): tiles of 16 x rows-per-thread rows; lbm_set_tile_rows
+ * fixes rows per thread (1, 2 or 4; 0 = 2).  lbm_autotune times the
+ * candidates (chunk lengths, or tile rows) over a few steps each on this
+ * handle's lattice and keeps the fastest; the steps run on the handle's
+ * state, which is left undefined (initialise after tuning).  *zc_out
+ * receives the choice (the z chunk, or the tile rows per thread), 0 if the
+ * handle has nothing to tune.  The choices give identical results. */
 int lbm_set_zchunk(lbm_handle* h, int zc);
+int lbm_set_tile_rows(lbm_handle* h, int rows_per_thread);
 int lbm_autotune(lbm_handle* h, int* zc_out);
 
 /* Carnahan-Starling critical point for constants (a, b, R), solving

@@ -46,6 +46,7 @@ struct lbm_handle {
   double mu_w = 0.0;             // wall chemical potential
   alignas(64) unsigned char tmap[2][128];  // D3Q19 FP32DEV: tensor maps (CUtensorMap) of f[0], f[1]
   bool has_tmap = false;
+  int rpt2d = 0;  // D2Q9 FP32DEV split tiles: rows per thread (0 = default)
 };
 
 // ------------------------------------------------------------------ allocation
@@ -740,6 +741,7 @@ static Launch make_launch(lbm_handle* h, int out_buf) {
   c.mu = h->mu;
   c.mrt = h->mrt;
   c.tmap = h->has_tmap ? h->tmap[h->cur] : nullptr;
+  c.rpt2d = h->rpt2d;
   return c;
 }
 
@@ -764,9 +766,43 @@ extern "C" int lbm_set_zchunk(lbm_handle* h, int zc) {
   return LBM_OK;
 }
 
+extern "C" int lbm_set_tile_rows(lbm_handle* h, int rows) {
+  if (!h || (rows != 0 && rows != 1 && rows != 2 && rows != 4)) return LBM_EINVAL;
+  h->rpt2d = rows;
+  return LBM_OK;
+}
+
+// the D2Q9 FP32DEV split step runs on tiles of 16 x rows-per-thread rows
+static bool tunable2d(const lbm_handle* h) { return h->D == 2 && h->prec == 1 && h->mu && !h->compact && !h->layer; }
+
 extern "C" int lbm_autotune(lbm_handle* h, int* zc_out) {
   if (!h) return LBM_EINVAL;
   if (zc_out) *zc_out = 0;
+  if (tunable2d(h)) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LBM_ECUDA; }
+    const long long t_saved = h->t;
+    int best = 0, rc = LBM_OK;
+    float best_ms = 1e30f;
+    for (const int rows : {1, 2, 4}) {
+      h->rpt2d = rows;
+      if ((rc = lbm_step(h, 2)) != LBM_OK) break;  // warm up
+      cudaEventRecord(e0, h->stream);
+      if ((rc = lbm_step(h, 5)) != LBM_OK) break;
+      cudaEventRecord(e1, h->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LBM_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best = rows; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->t = t_saved;
+    h->rpt2d = best;
+    if (zc_out) *zc_out = best;
+    return rc != LBM_OK ? rc : (best > 0 ? LBM_OK : LBM_ECUDA);
+  }
   if (!tunable(h)) return LBM_OK;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LBM_ECUDA;

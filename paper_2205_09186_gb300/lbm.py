@@ -80,6 +80,7 @@ SIGNATURES = {
     "lbm_bulk_mu": (C.c_int, [C.POINTER(lbm_params), C.c_double, _dp]),
     "lbm_lattice_q": (C.c_int, [C.c_int]),
     "lbm_set_zchunk": (C.c_int, [_h, C.c_int]),
+    "lbm_set_tile_rows": (C.c_int, [_h, C.c_int]),
     "lbm_autotune": (C.c_int, [_h, C.POINTER(C.c_int)]),
     "lbm_strerror": (C.c_char_p, [C.c_int]),
     "lbm_observables_noalloc": (C.c_int, [C.POINTER(lbm_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong,
@@ -356,7 +357,12 @@ class Sim:
     def lbm_set_zchunk(self, zc):
         return check(lib().lbm_set_zchunk(self.h, zc), "lbm_set_zchunk")
 
+    def lbm_set_tile_rows(self, rows_per_thread):
+        return check(lib().lbm_set_tile_rows(self.h, int(rows_per_thread)), "lbm_set_tile_rows")
+
     def lbm_autotune(self):
+        """z chunk (D3Q19) or tile rows per thread (D2Q9 split step) chosen by
+        timing; 0 if nothing to tune.  The state is left undefined."""
         zc = C.c_int()
         check(lib().lbm_autotune(self.h, C.byref(zc)), "lbm_autotune")
         return zc.value

@@ -265,3 +265,23 @@ def test_fp32dev_2d_mu_variants_against_oracle(L, shape, scheme):
     assert o.step(40) == 0
     err = np.max(np.abs(g.lbm_get_density() - o.density())) / 0.15
     assert err < TOL32, err
+
+
+@pytest.mark.parametrize("scheme", ["EFDS6", "E8"])
+def test_d2q9_tile_rows_give_identical_results(L, scheme):
+    # the split D2Q9 step on tiles of 16, 32 and 64 rows: the same arithmetic
+    # per node, bitwise equal states; the tuner picks one of them
+    kw = dict(lattice=L.LBM_D2Q9, nx=100, ny=90, Tr=0.8, k=0.25, kappa=0.1, scheme=scheme,
+              precision=L.LBM_FP32DEV)
+    out = {}
+    for rows in (1, 2, 4):
+        s = L.Sim(L.make_params(**kw))
+        s.lbm_set_tile_rows(rows)
+        s.lbm_init_droplet(20.0)
+        s.lbm_step(30)
+        out[rows] = s.lbm_get_density()
+    assert np.array_equal(out[1], out[2]) and np.array_equal(out[4], out[2])
+    s = L.Sim(L.make_params(**kw))
+    assert s.lbm_autotune() in (1, 2, 4)
+    with pytest.raises(L.LBMError):
+        s.lbm_set_tile_rows(3)
