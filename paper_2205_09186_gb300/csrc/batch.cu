@@ -197,18 +197,20 @@ __device__ void split_load(const CaseDev& cd, int tile, long long t, int phase, 
   }
 }
 
+// one warp's mu unit: rows part * MU_UNIT_ROWS .. + MU_UNIT_ROWS - 1 of a mu tile
 template <int RPT>
-__device__ void mu_direct(const CaseDev& cd, int tile, long long t) {
+__device__ void mu_unit(const CaseDev& cd, int tile, int part, long long t, int lane) {
   constexpr int M2Y = Tile2<RPT>::M2Y;
   const int par = int(t & 1);
   const float* rin = static_cast<const float*>(cd.rho[par]);
-  const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
+  const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y + part * MU_UNIT_ROWS;
+  if (y0 >= cd.kp.ny) return;
   switch (cd.scheme) {
-    case S_EFDS2: mu2d_direct<S_EFDS2, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
-    case S_EFDS4: mu2d_direct<S_EFDS4, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
-    case S_EFDS6: mu2d_direct<S_EFDS6, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
-    case S_E4: mu2d_direct<S_E4, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
-    case S_E8: mu2d_direct<S_E8, RPT>(cd.kp, rin, cd.mu, x0, y0); break;
+    case S_EFDS2: mu2d_rows<S_EFDS2>(cd.kp, rin, cd.mu, x0, y0, lane); break;
+    case S_EFDS4: mu2d_rows<S_EFDS4>(cd.kp, rin, cd.mu, x0, y0, lane); break;
+    case S_EFDS6: mu2d_rows<S_EFDS6>(cd.kp, rin, cd.mu, x0, y0, lane); break;
+    case S_E4: mu2d_rows<S_E4>(cd.kp, rin, cd.mu, x0, y0, lane); break;
+    case S_E8: mu2d_rows<S_E8>(cd.kp, rin, cd.mu, x0, y0, lane); break;
     default: break;
   }
 }
@@ -249,68 +251,127 @@ __device__ void split_compute(const CaseDev& cd, int tile, long long t, int phas
 #undef LBM_SPLIT_CASE
 }
 
-// Items of a phase are dealt in contiguous runs (CTA b takes items
-// [n b / grid, n (b + 1) / grid)): they are tiles of nearly equal cost, so the
-// static deal is balanced to one item; consecutive items mostly belong to one
-// case, so its descriptor stays in L1 and neighbouring tiles share halos in L2;
-// and knowing the next items in advance lets the copies of the next NBUF - 1
-// items be in flight while the current one is computed.
+// Items of a phase are dealt dynamically in guided runs: a CTA claims a run of
+// consecutive items from the phase's counter, up to 16 while much work is
+// left and shrinking to single items at the end.  Item costs differ by scheme
+// (E8's 5 x 5 stencils against EFDS2's 3-point lines) and by how much of a
+// ragged tile lies on the lattice, so equal static shares left the average CTA
+// waiting 29% of the step at the grid barriers; runs keep neighbouring tiles of
+// one case on one CTA (halo lines reused from L1).  In the collision phase
+// the claimant is the CTA: thread 0 claims its next run when it starts the
+// current one, so the atomic's round trip is hidden, and each item's index
+// reaches the other threads through a two-slot shared queue at the barrier
+// every item already has.  The mu phase needs no CTA barrier: each warp claims
+// units of eight tile rows itself (lane 0, broadcast by a shuffle), which
+// also balances the warps of a CTA.  Phase k of a launch (k = 2 step +
+// phase) counts on work[k % 4]; block 0 zeroes work[(k + 2) % 4], last used
+// two phases back, before it arrives at the phase's barrier, and the launch
+// starts from zeroed counters.
 // Dynamic shared memory: NBUF buffers of buf_bytes (a multiple of 16); two
 // 30 x 30 tiles' buffers (~48 KB each) keep two CTAs resident per SM.
 constexpr int NBUF = 2;
+
+// one claimant's claims in a phase of n units: the run [lo, hi) being worked
+// through and the run of nc units from nlo claimed after it
+constexpr int RUN_MU = 16, RUN_COLL = 16, RUN_DIV = 4;
+struct Claims {
+  int lo, hi, nlo, nc, cap, g;
+  // a run: 1/RUN_DIV of an equal share (over g claimants) of what is left, 1..cap units
+  __device__ int size(int n, int v) const {
+    const int share = (n - v) / (RUN_DIV * g);
+    return share < 1 ? 1 : (share > cap ? cap : share);
+  }
+  __device__ void start(unsigned* ctr, int n, int run_cap, int claimants) {
+    cap = run_cap;
+    g = claimants;
+    const int c = size(n, 0);
+    lo = int(atomicAdd(ctr, unsigned(c)));
+    hi = lo + c;
+    nc = size(n, lo);
+    nlo = int(atomicAdd(ctr, unsigned(nc)));
+  }
+  // the next item index (>= n: the phase has no more work for this CTA)
+  __device__ int next(unsigned* ctr, int n) {
+    if (lo >= hi) {
+      lo = nlo;
+      hi = nlo + nc;
+      nc = size(n, lo);
+      nlo = int(atomicAdd(ctr, unsigned(nc)));
+    }
+    return lo++;
+  }
+};
 
 template <int RPT>  // rows per thread of the tiles (1, 2, 4)
 __global__ void __launch_bounds__(NT2S, RPT >= 4 ? 1 : 2) k_batch_split(const CaseDev* __restrict__ cases,
                                                       const Item* __restrict__ mitems, int nmu,
                                                       const Item* __restrict__ citems, int ncoll, int nsteps,
                                                       BatchCtl* ctl, unsigned long long timeout_ns, int buf_bytes) {
+  static_assert(NBUF == 2, "one item in flight: the claim queue has two slots");
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_q[2];
+  __shared__ Claims s_cl[NT2S / 32];  // in shared memory: registers are at the cap
   const long long t0 = *((volatile long long*)&ctl->t);
-  const int G = int(gridDim.x);
   for (int s = 0; s < nsteps; ++s) {
     const long long t = t0 + s;
     for (int phase = 0; phase < 2; ++phase) {
       const Item* items = phase == 0 ? mitems : citems;
       const int nitems = phase == 0 ? nmu : ncoll;
-      const int i0 = int((long long)nitems * blockIdx.x / G), i1 = int((long long)nitems * (blockIdx.x + 1) / G);
+      const int k = 2 * s + phase;
+      unsigned* ctr = &ctl->work[k & 3];
       if (phase == 0) {
-        // mu items: every thread reads its stencils with cached global loads;
-        // no staging, no CTA barrier
-        for (int it = i0; it < i1; ++it) {
-          const Item itm = items[it];
-          mu_direct<RPT>(cases[itm.c], itm.tile, t);
+        // mu: each warp claims units of MU_UNIT_ROWS rows of a mu tile and
+        // reads their stencils with cached global loads; no staging, no CTA barrier
+        constexpr int UPI = Tile2<RPT>::M2Y / MU_UNIT_ROWS;
+        const int n = nitems * UPI, lane = int(threadIdx.x) & 31;
+        Claims& cl = s_cl[threadIdx.x / 32];  // lane 0's
+        if (lane == 0) cl.start(ctr, n, RUN_MU, int(gridDim.x) * (NT2S / 32));
+        for (;;) {
+          int u = 0;
+          if (lane == 0) u = cl.next(ctr, n);
+          u = __shfl_sync(0xffffffffu, u, 0);
+          if (u >= n) break;
+          const Item itm = items[u / UPI];
+          mu_unit<RPT>(cases[itm.c], itm.tile, u % UPI, t, lane);
         }
-        if (!grid_barrier(ctl, timeout_ns)) return;
-        continue;
-      }
-      // prologue: copies of the first NBUF - 1 items (one group each, empty past the end)
-#pragma unroll
-      for (int j = 0; j < NBUF - 1; ++j) {
-        const int it = i0 + j;
-        if (it < i1) {
-          const Item itm = items[it];
-          split_load<RPT>(cases[itm.c], itm.tile, t, phase, smem + j * buf_bytes);
+      } else {
+        Claims& cl = s_cl[0];  // thread 0's
+        if (threadIdx.x == 0) {
+          cl.start(ctr, nitems, RUN_COLL, int(gridDim.x));
+          s_q[0] = cl.next(ctr, nitems);
         }
-        cpa_commit();
-      }
-      int b = 0;
-      for (int it = i0; it < i1; ++it) {
-        // this item's copies (the oldest group) have landed, and every thread
-        // is past the computation of the item before: one barrier covers both
-        // the data and the reuse of that item's buffer
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(NBUF - 2) : "memory");
         __syncthreads();
-        const int ahead = it + NBUF - 1;
-        if (ahead < i1) {
-          const Item itm = items[ahead];
-          split_load<RPT>(cases[itm.c], itm.tile, t, phase, smem + ring(b + NBUF - 1, NBUF) * buf_bytes);
+        int cur = s_q[0], q = 1;
+        // a slot is rewritten two items after it was read, by thread 0 past
+        // the barrier that every reader reached after reading it
+        int b = 0;
+        if (cur < nitems) {
+          const Item itm = items[cur];
+          split_load<RPT>(cases[itm.c], itm.tile, t, phase, smem);
         }
         cpa_commit();
-        const Item itm = items[it];
-        split_compute<RPT>(cases[itm.c], itm.tile, t, phase, smem + b * buf_bytes);
-        b = ring(b + 1, NBUF);
+        while (cur < nitems) {
+          if (threadIdx.x == 0) s_q[q] = cl.next(ctr, nitems);
+          // this item's copies have landed, every thread is past the
+          // computation of the item before, and the next index is published:
+          // one barrier covers the data, the reuse of the other buffer and the claim
+          cpa_wait_all();
+          __syncthreads();
+          const int nxt = s_q[q];
+          q ^= 1;
+          if (nxt < nitems) {
+            const Item itm = items[nxt];
+            split_load<RPT>(cases[itm.c], itm.tile, t, phase, smem + (b ^ 1) * buf_bytes);
+          }
+          cpa_commit();
+          const Item itm = items[cur];
+          split_compute<RPT>(cases[itm.c], itm.tile, t, phase, smem + b * buf_bytes);
+          cur = nxt;
+          b ^= 1;
+        }
+        cpa_wait_all();
       }
-      cpa_wait_all();
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[(k + 2) & 3] = 0u;
       if (!grid_barrier(ctl, timeout_ns)) return;
     }
   }

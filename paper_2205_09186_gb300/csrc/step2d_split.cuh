@@ -228,30 +228,39 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
   }
 }
 
-// mu of one 32 x 32 tile straight from global memory: each thread its two
-// nodes (rows w and w + 16 of warp w), every stencil value an L1-cached load.
-// No shared memory and no barrier, so that the persistent batch kernel deals
-// mu items without CTA synchronisation.  The inputs are written earlier in the
-// same persistent launch (by other CTAs, before a device-wide barrier with
-// acquire semantics), so they are read with ordinary coherent loads, never
-// through the non-coherent read-only path (no __ldg, no __restrict__).
-template <int S, int RPT>
-__device__ __forceinline__ void mu2d_direct(const KParams& p, const float* rin, float* mu, int x0, int y0) {
-  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
+// mu of 8 rows x 32 columns of a mu tile straight from global memory, for
+// one warp (lane l: column x0 + l), every stencil value an L1-cached load.
+// The stencil rows come from one table of wrapped row offsets, so a value that
+// several of the eight rows use is loaded once, and the results are stored
+// after the last load (with the buffers not marked __restrict__, a store
+// between them would keep later loads behind it).  No shared memory and no
+// barrier: the persistent batch kernel deals these units to warps.  The inputs
+// are written earlier in the same persistent launch (by other CTAs, before a
+// device-wide barrier with acquire semantics), so they are read with ordinary
+// coherent loads, never through the non-coherent read-only path (no __ldg, no
+// __restrict__).
+constexpr int MU_UNIT_ROWS = 8;
+
+template <int S>
+__device__ __forceinline__ void mu2d_rows(const KParams& p, const float* rin, float* mu, int x0, int y0, int lane) {
   using Sc = Sch<S>;
-  constexpr int R = Sc::R;
+  constexpr int R = Sc::R, U = MU_UNIT_ROWS;
   const int nx = p.nx, ny = p.ny;
-  const int gx = x0 + int(threadIdx.x) % M2X;
+  const int gx = x0 + lane;
   if (gx >= nx) return;
+  const int nr = min(U, ny - y0);
   int xo[2 * R + 1];  // wrapped x of the stencil columns
 #pragma unroll
   for (int d = -R; d <= R; ++d) xo[d + R] = wrapi(gx + d, nx);
-  const float k2 = float(p.k2), kap = float(p.kappa), rref = float(p.rho_ref);
+  int ro[U + 2 * R];  // wrapped row offsets of rows y0 - R .. y0 + U + R - 1
 #pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    const int gy = y0 + int(threadIdx.x) / M2X + r * (NT2S / M2X);
-    if (gy >= ny) break;
-    auto at = [&](int dx, int dy) { return (*(rin + wrapi(gy + dy, ny) * nx + xo[dx + R])); };
+  for (int k = 0; k < U + 2 * R; ++k) ro[k] = wrapn(y0 - R + k, ny) * nx;
+  const float k2 = float(p.k2), kap = float(p.kappa), rref = float(p.rho_ref);
+  const EosF ef = eos_f(p);
+  float res[U];
+#pragma unroll
+  for (int r = 0; r < U; ++r) {
+    auto at = [&](int dx, int dy) { return rin[ro[r + R + dy] + xo[dx + R]]; };
     const float c = at(0, 0);
     float lap;
     if constexpr (Sc::ISO) {
@@ -268,8 +277,11 @@ __device__ __forceinline__ void mu2d_direct(const KParams& p, const float* rin, 
 #pragma unroll
       for (int m = 1; m <= R; ++m) lap += float(Sc::l(m)) * ((at(m, 0) + at(-m, 0)) + (at(0, m) + at(0, -m)));
     }
-    mu[gy * nx + gx] = k2 * eos_mu_f(rref + c, eos_f(p)) - kap * lap;
+    res[r] = k2 * eos_mu_f(rref + c, ef) - kap * lap;
   }
+#pragma unroll
+  for (int r = 0; r < U; ++r)
+    if (r < nr) mu[(y0 + r) * nx + gx] = res[r];
 }
 
 // y-marching vector mu pass (line schemes EFDS2/4/6, nx % 4 == 0, 16-byte
