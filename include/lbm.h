@@ -393,8 +393,9 @@ int lbm_batch_inject_stall(lbm_batch* b, int cta);
  * 30 x (16 rows - 2) and mu tiles of 32 x 16 rows, rows = 16 x (rows per
  * thread), rows per thread 1, 2 (default) or 4.  lbm_batch_set_tiles fixes
  * it; lbm_batch_autotune times `steps` steps of every shape that has a
- * resident launch configuration (after one captured warm-up launch each) and
- * keeps the fastest, reported in *rows_out.  The tuning steps run on the
+ * resident launch configuration (after one captured warm-up launch each), in
+ * three interleaved rounds, and keeps the shape with the fastest launch,
+ * reported in *rows_out (18 launches of `steps` steps).  The tuning steps run on the
  * batch's state, which they advance: initialise before tuning (the timing
  * is only representative of a physical state) and again after it.  The shapes
  * give identical results (same arithmetic per node).  Errors: LBM_EINVAL,

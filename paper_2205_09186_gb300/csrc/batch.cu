@@ -816,22 +816,32 @@ extern "C" int lbm_batch_autotune(lbm_batch* b, int steps, int* rows_out) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LBM_ECUDA; }
-  int best = 0, rc = LBM_OK;
-  float best_ms = 1e30f;
-  for (const int r : {1, 2, 4}) {
-    if (setup_split(b, r) != LBM_OK) continue;  // shape without a resident configuration
-    if ((rc = lbm_batch_step(b, steps)) != LBM_OK) break;  // capture and warm up
-    cudaEventRecord(e0, b->stream);
-    if ((rc = lbm_batch_step(b, steps)) != LBM_OK) break;
-    cudaEventRecord(e1, b->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LBM_ECUDA; break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = r; }
+  // three interleaved rounds, each shape's fastest launch counting: shapes
+  // a few percent apart are otherwise ordered by noise and by the state each
+  // launch happens to step through
+  const int shapes[3] = {1, 2, 4};
+  float shape_ms[3] = {1e30f, 1e30f, 1e30f};
+  int rc = LBM_OK;
+  for (int round = 0; round < 3 && rc == LBM_OK; ++round) {
+    for (int j = 0; j < 3; ++j) {
+      if (setup_split(b, shapes[j]) != LBM_OK) continue;  // shape without a resident configuration
+      if ((rc = lbm_batch_step(b, steps)) != LBM_OK) break;  // capture and warm up
+      cudaEventRecord(e0, b->stream);
+      if ((rc = lbm_batch_step(b, steps)) != LBM_OK) break;
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LBM_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      shape_ms[j] = std::min(shape_ms[j], ms);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != LBM_OK) return rc;
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int j = 0; j < 3; ++j)
+    if (shape_ms[j] < best_ms) { best_ms = shape_ms[j]; best = shapes[j]; }
   if (best == 0) return LBM_ECUDA;
   if ((rc = setup_split(b, best)) != LBM_OK) return rc;
   if (rows_out) *rows_out = best;
