@@ -222,6 +222,8 @@ def run_2d(L, steps=200, warmup=20):
         s = L.Sim(L.make_params(lattice=L.LBM_D2Q9, nx=512, ny=512, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
                                 precision=L.LBM_FP32DEV, collision=col))
         s.lbm_init_droplet(100.0)
+        rows = s.lbm_autotune()  # tile rows by timing (leaves the state undefined)
+        s.lbm_init_droplet(100.0)
         s.lbm_step(warmup)
         torch.cuda.synchronize()
         ms = s.lbm_step_timed(steps)
@@ -230,7 +232,7 @@ def run_2d(L, steps=200, warmup=20):
         out[col.lower()] = {"mlups": n * steps / (ms[2] * 1e-3) / 1e6, "ms_per_step": ms[2] / steps,
                             "coll_ms": coll_ms, "mu_ms": ms[0] / steps,
                             "coll_frac": 84 * n / (coll_ms * 1e-3) / 1e9 / measured_peak()[0],
-                            "status": s.lbm_observables()["status"]}
+                            "tile_rows_per_thread": rows, "status": s.lbm_observables()["status"]}
         s.close()
     # a lattice larger than L2: 4096^2 (1.2 GB of populations), r0 = 800
     s = L.Sim(L.make_params(lattice=L.LBM_D2Q9, nx=4096, ny=4096, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",

@@ -263,8 +263,9 @@ int lbm_device_state(lbm_handle* h, void** f, void** rho);
  * per-chunk prologue).  D2Q9 FP32DEV split step (explicit and isotropic
  * schemes, no walls): tiles of 16 x rows-per-thread rows; lbm_set_tile_rows
  * fixes rows per thread (1, 2 or 4; 0 = 2).  lbm_autotune times the
- * candidates (chunk lengths, or tile rows) over a few steps each on this
- * handle's lattice and keeps the fastest; the steps run on the handle's
+ * candidates on this handle's lattice and keeps the fastest: chunk lengths
+ * over a few steps each, tile rows in three interleaved rounds of ten steps
+ * (each shape's fastest round counting); the steps run on the handle's
  * state, which is left undefined (initialise after tuning).  *zc_out
  * receives the choice (the z chunk, or the tile rows per thread), 0 if the
  * handle has nothing to tune.  The choices give identical results. */

@@ -783,21 +783,30 @@ extern "C" int lbm_autotune(lbm_handle* h, int* zc_out) {
     if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LBM_ECUDA; }
     const long long t_saved = h->t;
-    int best = 0, rc = LBM_OK;
-    float best_ms = 1e30f;
-    for (const int rows : {1, 2, 4}) {
-      h->rpt2d = rows;
-      if ((rc = lbm_step(h, 2)) != LBM_OK) break;  // warm up
-      cudaEventRecord(e0, h->stream);
-      if ((rc = lbm_step(h, 5)) != LBM_OK) break;
-      cudaEventRecord(e1, h->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LBM_ECUDA; break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) { best_ms = ms; best = rows; }
+    // three interleaved rounds, each shape's fastest counting (shapes a few
+    // percent apart, and small lattices' short steps, are otherwise ordered by noise)
+    const int shapes[3] = {1, 2, 4};
+    float shape_ms[3] = {1e30f, 1e30f, 1e30f};
+    int rc = LBM_OK;
+    for (int round = 0; round < 3 && rc == LBM_OK; ++round) {
+      for (int j = 0; j < 3; ++j) {
+        h->rpt2d = shapes[j];
+        if ((rc = lbm_step(h, 2)) != LBM_OK) break;  // warm up
+        cudaEventRecord(e0, h->stream);
+        if ((rc = lbm_step(h, 10)) != LBM_OK) break;
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LBM_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        shape_ms[j] = std::min(shape_ms[j], ms);
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int j = 0; j < 3; ++j)
+      if (shape_ms[j] < best_ms) { best_ms = shape_ms[j]; best = shapes[j]; }
     h->t = t_saved;
     h->rpt2d = best;
     if (zc_out) *zc_out = best;
