@@ -137,3 +137,39 @@ def test_autotune_keeps_a_shape_and_caches_it(L, tmp_path):
     assert e.value.code == L.LBM_EINVAL
     for x in (b, ref, c2):
         x.close()
+
+
+def test_many_cases_dealt_dynamically_match_single_runs(L):
+    # enough work that every CTA claims several guided runs of collision items
+    # and every warp several mu units, across phases, steps and graph replays;
+    # seed 11, 48 cases of 128..384 nodes a side, all five schemes, stable T_r
+    rng = np.random.default_rng(11)
+    schemes = ["EFDS2", "EFDS4", "EFDS6", "E4", "E8"]
+    cases = []
+    for i in range(48):
+        nx, ny = int(rng.integers(128, 385)), int(rng.integers(128, 385))
+        cases.append(dict(nx=nx, ny=ny, Tr=float(rng.uniform(0.8, 0.95)), k=float(rng.uniform(0.15, 0.35)),
+                          scheme=schemes[i % 5], r=float(rng.uniform(8, min(nx, ny) / 4))))
+    dens = {}
+    for rows in (2, 1):
+        b = L.Batch([params(L, c, 1) for c in cases])
+        b.lbm_batch_set_tiles(rows)
+        b.lbm_batch_init_droplets([c["r"] for c in cases])
+        for _ in range(3):
+            b.lbm_batch_step(8)
+        assert b.lbm_batch_get_step() == 24
+        _, nitems, grid = b.lbm_batch_size()
+        assert nitems > 4 * grid
+        rc, obs = b.lbm_batch_observables(raise_errors=False)
+        assert rc == 0 and all(o["status"] == 0 for o in obs)
+        dens[rows] = [b.lbm_batch_get_density(i) for i in range(len(cases))]
+        b.close()
+    for a, d in zip(dens[1], dens[2]):
+        assert np.array_equal(a, d)
+    for i, c in enumerate(cases):
+        s = L.Sim(params(L, c, 1))
+        s.lbm_init_droplet(c["r"])
+        s.lbm_step(24)
+        rs = s.lbm_get_density()
+        assert np.max(np.abs(dens[2][i] - rs)) / np.max(rs) < 1e-6, c
+        s.close()
