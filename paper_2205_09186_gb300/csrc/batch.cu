@@ -290,7 +290,7 @@ struct Claims {
     nc = size(n, lo);
     nlo = int(atomicAdd(ctr, unsigned(nc)));
   }
-  // the next item index (>= n: the phase has no more work for this CTA)
+  // the next unit index (>= n: the phase has no more work for this claimant)
   __device__ int next(unsigned* ctr, int n) {
     if (lo >= hi) {
       lo = nlo;
