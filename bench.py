@@ -188,7 +188,7 @@ def run_batch(L, steps=50, warmup=10, ncases=512):
     # tile shape by timing on the initial droplets (the tuning advances the
     # state: initialise again afterwards)
     b.lbm_batch_init_droplets([c["r"] for c in cases])
-    rows = b.lbm_batch_autotune(steps=10)
+    rows = b.lbm_batch_autotune(steps=steps)  # launches as long as the timed one
     b.lbm_batch_init_droplets([c["r"] for c in cases])
     nodes = sum(c["nx"] * c["ny"] for c in cases)
     b.lbm_batch_step(warmup)
