@@ -134,17 +134,31 @@ __global__ void __launch_bounds__(LT) k_lines(int axis, int nx, int ny, int nz, 
     for (int i = i0; i < L; i += di) A[j * LP + i] = ok ? T(in[b + i * stride]) : T(0);
     __syncthreads();
   }
-  const T A1 = T(lc.A1), A2 = T(lc.A2), A3 = T(lc.A3);
-  for (int j = warp; j < LPB; j += LT / 32) {
-    // explicit side: a (f[i+1]-f[i-1])/2 + b (f[i+2]-f[i-2])/4 + c (f[i+3]-f[i-3])/6
-    const T* f = A + j * LP;
-    for (int i = lane; i < L; i += 32) {
-      auto at = [&](int k) { return f[k < 0 ? k + L : (k >= L ? k - L : k)]; };
-      T r = A1 * (at(i + 1) - at(i - 1));
-      if (lc.A2 != 0.0) r += A2 * (at(i + 2) - at(i - 2));
-      if (lc.A3 != 0.0) r += A3 * (at(i + 3) - at(i - 3));
-      B[j * LP + i] = r;
+  // element loops outside, the warp's lines inside: a wrapped position is
+  // computed once for all the lines of the warp (index arithmetic, not the
+  // few flops, dominated the per-element cost)
+  constexpr int NW = LT / 32;
+  auto for_lines = [&](auto&& fn) {
+    if (LPB == 4 * NW) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fn(warp + q * NW);
+    } else {
+      for (int j = warp; j < LPB; j += NW) fn(j);
     }
+  };
+  const T A1 = T(lc.A1), A2 = T(lc.A2), A3 = T(lc.A3);
+  const bool has2 = lc.A2 != 0.0, has3 = lc.A3 != 0.0;
+  for (int i = lane; i < L; i += 32) {
+    // explicit side: a (f[i+1]-f[i-1])/2 + b (f[i+2]-f[i-2])/4 + c (f[i+3]-f[i-3])/6
+    auto wr = [&](int k) { return k < 0 ? k + L : (k >= L ? k - L : k); };
+    const int p1 = wr(i + 1), m1 = wr(i - 1), p2 = wr(i + 2), m2 = wr(i - 2), p3 = wr(i + 3), m3 = wr(i - 3);
+    for_lines([&](int j) {
+      const T* f = A + j * LP;
+      T r = A1 * (f[p1] - f[m1]);
+      if (has2) r += A2 * (f[p2] - f[m2]);
+      if (has3) r += A3 * (f[p3] - f[m3]);
+      B[j * LP + i] = r;
+    });
   }
   __syncwarp();
   T* cur = B;
@@ -152,13 +166,13 @@ __global__ void __launch_bounds__(LT) k_lines(int axis, int nx, int ny, int nz, 
   int s = 1 % L;
   for (int k = 0; k < lc.nlev; ++k) {
     const T al = T(lc.alpha[k]), iv = T(lc.inv[k]);
-    for (int j = warp; j < LPB; j += LT / 32) {
-      const T* d = cur + j * LP;
-      for (int i = lane; i < L; i += 32) {
-        int ip = i + s; if (ip >= L) ip -= L;
-        int im = i - s; if (im < 0) im += L;
+    for (int i = lane; i < L; i += 32) {
+      int ip = i + s; if (ip >= L) ip -= L;
+      int im = i - s; if (im < 0) im += L;
+      for_lines([&](int j) {
+        const T* d = cur + j * LP;
         nxt[j * LP + i] = (d[i] - al * (d[im] + d[ip])) * iv;
-      }
+      });
     }
     __syncwarp();
     T* t = cur; cur = nxt; nxt = t;
