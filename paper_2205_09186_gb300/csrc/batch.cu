@@ -1,7 +1,8 @@
 // Batched D2Q9 droplets of uneven sizes and parameters in one persistent
-// launch.  FP32-deviation batches (k_batch_split) deal the (case, tile) work
-// items of each phase to the resident CTAs in contiguous runs; other
-// precisions (k_batch_persistent) fetch them from an atomic counter per step.
+// launch.  In FP32-deviation batches (k_batch_split) the CTAs (collision
+// items) and warps (mu units) claim the work of each phase from an atomic
+// counter in guided runs; other precisions (k_batch_persistent) fetch their
+// (case, tile) items one at a time from an atomic counter per step.
 // Steps and phases are separated by a device-wide barrier whose waits are
 // bounded (about one second), after which the kernel records LBM_ETIMEOUT and
 // returns.  lbm_batch_step captures the launch (plus the counter reset) in a
@@ -46,7 +47,7 @@ struct Item {
 struct BatchCtl {
   unsigned int count;
   unsigned int gen;
-  unsigned int work[4];  // [phase * 2 + step parity]
+  unsigned int work[4];  // k_batch_split: [(2 step + phase) % 4]; k_batch_persistent: [step parity]
   int status;
   int skip_block;  // fault injection for tests: this CTA never arrives (-1: none)
   long long t;     // step counter of the batch
@@ -163,28 +164,16 @@ __global__ void __launch_bounds__(NT2) k_batch_persistent(const CaseDev* __restr
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t = t0 + nsteps;
 }
 
-// FP32DEV: per step a mu phase over all cases' mu tiles and a collision phase
-// over their collision tiles, each followed by the bounded device barrier.
-// Within a phase a CTA works through its items in a two-stage pipeline: the
-// copies of the next item (and the fetch of the item after it) are in flight
-// while the current item is computed from the other shared-memory buffer.
+// FP32DEV: per step a mu phase over all cases' mu tiles (warp units of eight
+// rows, read straight from global memory) and a collision phase over their
+// collision tiles, each followed by the bounded device barrier.  A collision
+// item is staged in shared memory: the copies of the next item are in flight
+// while the current one is computed from the other buffer.
 template <int RPT>
-__device__ void split_load(const CaseDev& cd, int tile, long long t, int phase, unsigned char* buf) {
-  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, T2Y = Tile2<RPT>::T2Y;
+__device__ void coll_load(const CaseDev& cd, int tile, long long t, unsigned char* buf) {
+  constexpr int T2Y = Tile2<RPT>::T2Y;
   const int par = int(t & 1);
   const float* rin = static_cast<const float*>(cd.rho[par]);
-  if (phase == 0) {
-    const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
-    switch (cd.scheme) {
-      case S_EFDS2: mu2d_load<S_EFDS2, RPT>(cd.kp, rin, x0, y0, buf); break;
-      case S_EFDS4: mu2d_load<S_EFDS4, RPT>(cd.kp, rin, x0, y0, buf); break;
-      case S_EFDS6: mu2d_load<S_EFDS6, RPT>(cd.kp, rin, x0, y0, buf); break;
-      case S_E4: mu2d_load<S_E4, RPT>(cd.kp, rin, x0, y0, buf); break;
-      case S_E8: mu2d_load<S_E8, RPT>(cd.kp, rin, x0, y0, buf); break;
-      default: break;
-    }
-    return;
-  }
   const int x0 = (tile % cd.ctiles_x) * T2X, y0 = (tile / cd.ctiles_x) * T2Y;
   const float* fin = static_cast<const float*>(cd.f[par]);
   switch (cd.scheme) {
@@ -216,21 +205,9 @@ __device__ void mu_unit(const CaseDev& cd, int tile, int part, long long t, int 
 }
 
 template <int RPT>
-__device__ void split_compute(const CaseDev& cd, int tile, long long t, int phase, unsigned char* buf) {
-  [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, T2Y = Tile2<RPT>::T2Y;
+__device__ void coll_compute(const CaseDev& cd, int tile, long long t, unsigned char* buf) {
+  constexpr int T2Y = Tile2<RPT>::T2Y;
   const int par = int(t & 1);
-  if (phase == 0) {
-    const int x0 = (tile % cd.mtiles_x) * M2X, y0 = (tile / cd.mtiles_x) * M2Y;
-    switch (cd.scheme) {
-      case S_EFDS2: mu2d_compute<S_EFDS2, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
-      case S_EFDS4: mu2d_compute<S_EFDS4, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
-      case S_EFDS6: mu2d_compute<S_EFDS6, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
-      case S_E4: mu2d_compute<S_E4, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
-      case S_E8: mu2d_compute<S_E8, RPT>(cd.kp, cd.mu, x0, y0, buf); break;
-      default: break;
-    }
-    return;
-  }
   const int x0 = (tile % cd.ctiles_x) * T2X, y0 = (tile / cd.ctiles_x) * T2Y;
   float* fout = static_cast<float*>(cd.f[par ^ 1]);
   float* rout = static_cast<float*>(cd.rho[par ^ 1]);
@@ -347,7 +324,7 @@ __global__ void __launch_bounds__(NT2S, RPT >= 4 ? 1 : 2) k_batch_split(const Ca
         int b = 0;
         if (cur < nitems) {
           const Item itm = items[cur];
-          split_load<RPT>(cases[itm.c], itm.tile, t, phase, smem);
+          coll_load<RPT>(cases[itm.c], itm.tile, t, smem);
         }
         cpa_commit();
         while (cur < nitems) {
@@ -361,11 +338,11 @@ __global__ void __launch_bounds__(NT2S, RPT >= 4 ? 1 : 2) k_batch_split(const Ca
           q ^= 1;
           if (nxt < nitems) {
             const Item itm = items[nxt];
-            split_load<RPT>(cases[itm.c], itm.tile, t, phase, smem + (b ^ 1) * buf_bytes);
+            coll_load<RPT>(cases[itm.c], itm.tile, t, smem + (b ^ 1) * buf_bytes);
           }
           cpa_commit();
           const Item itm = items[cur];
-          split_compute<RPT>(cases[itm.c], itm.tile, t, phase, smem + b * buf_bytes);
+          coll_compute<RPT>(cases[itm.c], itm.tile, t, smem + b * buf_bytes);
           cur = nxt;
           b ^= 1;
         }
