@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(LT) k_lines(int axis, int nx, int ny, int nz, 
   T* nxt = A;
   int s = 1 % L;
   for (int k = 0; k < lc.nlev; ++k) {
-    const T al = T(lc.alpha[k]), iv = T(lc.inv[k]);
+    const T al = sizeof(T) == 4 ? T(lc.alpha_f[k]) : T(lc.alpha[k]);
+    const T iv = sizeof(T) == 4 ? T(lc.inv_f[k]) : T(lc.inv[k]);
     for (int i = lane; i < L; i += 32) {
       int ip = i + s; if (ip >= L) ip -= L;
       int im = i - s; if (im < 0) im += L;
@@ -224,6 +225,10 @@ cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T*
     int k = 0;
     while (k < lc.nlev && std::fabs(lc.alpha[k]) > 9.3e-10) ++k;
     lf.nlev = k;
+  }
+  for (int k = 0; k < 16; ++k) {
+    lf.alpha_f[k] = float(lf.alpha[k]);
+    lf.inv_f[k] = float(lf.inv[k]);
   }
   k_lines<Tin, T><<<grid, LT, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, in, out, lf, LPB, sh);
   return cudaGetLastError();

@@ -15,6 +15,7 @@ struct LineCoef {
   double A1, A2, A3;  // a/2, b/4, c/6 of the explicit side of Eq. 21
   int nlev;           // PCR levels until |alpha_k| < 1e-17
   double alpha[16], inv[16];
+  float alpha_f[16], inv_f[16];  // the same rounded to float (FP32 lines: no FP64 conversion per level)
 };
 
 struct CompactBufs {
