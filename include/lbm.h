@@ -325,7 +325,10 @@ const char* lbm_strerror(int code);
  * stall or fail.  The paper has no counterpart; it is an interface choice.
  *
  *  p                 the parameters the state was produced with (explicit and
- *                    isotropic schemes only: compact schemes -> LBM_ENOTSUP)
+ *                    isotropic schemes only: compact schemes -> LBM_ENOTSUP;
+ *                    a state without walls: the pass has no wall mask, so
+ *                    the wall nodes of a lbm_set_solid state would enter the
+ *                    mass and the velocity maxima)
  *  d_f, d_rho        device pointers to the populations and density field in
  *                    the stored form of lbm_device_state (read only)
  *  d_rho_prev        density field of an earlier step (stored form) for
@@ -337,10 +340,14 @@ const char* lbm_strerror(int code);
  * The reduction's partial results live in a fixed file-scope device array of
  * 65536 x 4 doubles plus 16 result words (about 2 MiB), held by every GPU that
  * loads the library until the process exits.  Lattices whose observation pass
- * needs more than 65536 CTAs (D2Q9 above about 16.7 M nodes, D3Q19 above
- * about 537 M nodes) return LBM_ESCRATCH.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
+ * needs more than 65536 CTAs (D2Q9 above about 16.7 M nodes) return
+ * LBM_ESCRATCH.  On D3Q19 the node limit of 2^31 / 19 (about 113 M nodes,
+ * 32-bit population indexing; LBM_EINVAL) comes first, except for very thin
+ * lattices (a few nodes across x and y, millions along z).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for that device; make that first call
+ * before any stream capture.  After a cudaDeviceReset the library is not
+ * usable on that device again in the same process.  All calls share the array and it keeps the last
  * call's contents: calls that overlap on the GPU race and must be serialised.
  * Returns LBM_OK, or LBM_EUNSTABLE (out->status too) if a density is
  * non-positive or NaN. */

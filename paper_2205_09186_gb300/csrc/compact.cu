@@ -205,12 +205,7 @@ cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T*
   while (LPB > 1 && size_t(2) * LPB * (L + 1) * sizeof(T) > 200 * 1024) { LPB /= 2; --sh; }
   const size_t smem = size_t(2) * LPB * (L + 1) * sizeof(T);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
-  static int set_bytes = 0;
-  if (int(smem) > set_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_lines<Tin, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    if (e != cudaSuccess) return e;
-    set_bytes = 220 * 1024;
-  }
+  if (cudaError_t e = ensure_smem(k_lines<Tin, T>, size_t(220) * 1024); e != cudaSuccess) return e;
   unsigned grid;
   if (axis == 0) {
     grid = unsigned(((long long)kp.ny * kp.nz + LPB - 1) / LPB);
@@ -245,12 +240,7 @@ cudaError_t launch_gf(const Launch& c, int D, int* nblocks) {
   if (D == 2) {
     using Sh = Step2DShape<S_CFDS4, P, TXc, TYc>;
     auto k = k_step2d<S_CFDS4, P, TXc, TYc, MODE>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    if (cudaError_t e = ensure_smem(k, Sh::bytes); e != cudaSuccess) return e;
     dim3 grid((c.kp.nx + TXc - 1) / TXc, (c.kp.ny + TYc - 1) / TYc, 1);
     if (nblocks) *nblocks = int(grid.x * grid.y);
     k<<<grid, NT2, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), rin, rout,
@@ -258,12 +248,7 @@ cudaError_t launch_gf(const Launch& c, int D, int* nblocks) {
   } else {
     using Sh = Step3DShape<S_CFDS4, P, TXc, TYc>;
     auto k = k_step3d<S_CFDS4, P, TXc, TYc, ZCc, MODE>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    if (cudaError_t e = ensure_smem(k, Sh::bytes); e != cudaSuccess) return e;
     dim3 grid((c.kp.nx + TXc - 1) / TXc, (c.kp.ny + TYc - 1) / TYc, (c.kp.nz + ZCc - 1) / ZCc);
     if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
     k<<<grid, NT3, Sh::bytes, c.stream>>>(c.kp, static_cast<const Tf*>(c.fin), static_cast<Tf*>(c.fout), rin, rout,

@@ -17,12 +17,7 @@ template <int S, class P, int MODE>
 cudaError_t launch_mode(const Launch& c, int* nblocks) {
   using Sh = Step2DShape<S, P, TX2, TY2>;
   auto k = k_step2d<S, P, TX2, TY2, MODE>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (cudaError_t e = ensure_smem(k, Sh::bytes); e != cudaSuccess) return e;
   dim3 grid((c.kp.nx + TX2 - 1) / TX2, (c.kp.ny + TY2 - 1) / TY2, 1);
   if (nblocks) *nblocks = int(grid.x * grid.y);
   using Tf = typename P::Tf;
@@ -39,24 +34,13 @@ template <int S, bool TAU1, int RPT>
 cudaError_t launch_split2d_t(const Launch& c, int* nblocks) {
   using Sh = Split2DShape<S, RPT>;
   constexpr int M2Y = Tile2<RPT>::M2Y, T2Y = Tile2<RPT>::T2Y;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mu2d<S, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_coll2d<S, TAU1, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (cudaError_t e = ensure_smem(k_mu2d<S, RPT>, Sh::bytes); e != cudaSuccess) return e;
+  if (cudaError_t e = ensure_smem(k_coll2d<S, TAU1, RPT>, Sh::bytes); e != cudaSuccess) return e;
   if constexpr (!Sch<S>::ISO) {
     if (c.kp.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(c.rin) & 15) == 0 && (reinterpret_cast<uintptr_t>(c.mu) & 15) == 0) {
       // rows per thread: about four CTAs of 8 warps per SM, 2..32 rows
       const int gx = (c.kp.nx + 63) / 64;
-      static int sms = 0;
-      if (!sms) {
-        int d = 0;
-        cudaGetDevice(&d);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms < 1) sms = 1;
-      }
+      const int sms = device_sms();
       const int want_gy = (4 * sms + gx - 1) / gx;
       int rows = (c.kp.ny + 16 * want_gy - 1) / (16 * want_gy);
       rows = rows < 2 ? 2 : (rows > 32 ? 32 : rows);

@@ -12,16 +12,7 @@
 
 namespace lbmd {
 
-static int num_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return sms;
-}
+static int num_sms() { return device_sms(); }
 
 bool split3d_scheme(int scheme, int prec) {
   return prec == 1 && (scheme == S_EFDS2 || scheme == S_EFDS4 || scheme == S_EFDS6);
@@ -70,12 +61,7 @@ template <int S, class P, int MODE>
 cudaError_t launch_mode(const Launch& c, int* nblocks) {
   using Sh = Step3DShape<S, P, TX3, TY3>;
   auto k = k_step3d<S, P, TX3, TY3, ZC3, MODE>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (cudaError_t e = ensure_smem(k, Sh::bytes); e != cudaSuccess) return e;
   dim3 grid((c.kp.nx + TX3 - 1) / TX3, (c.kp.ny + TY3 - 1) / TY3, (c.kp.nz + ZC3 - 1) / ZC3);
   if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
   using Tf = typename P::Tf;
@@ -91,12 +77,7 @@ template <int S, bool TAU1>
 cudaError_t launch_fast(const Launch& c, int* nblocks) {
   using Sh = FastShape<S>;
   auto k = k_step3d_fast<S, TAU1>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::bytes));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (cudaError_t e = ensure_smem(k, Sh::bytes); e != cudaSuccess) return e;
   const int zc = c.zc > 0 ? c.zc : fast_zchunk_heuristic(c.kp, Sh::R);
   dim3 grid((c.kp.nx + FT - 1) / FT, (c.kp.ny + FT - 1) / FT, (c.kp.nz + zc - 1) / zc);
   if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
@@ -115,12 +96,7 @@ cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
     if (!c.tmap) return cudaErrorInvalidValue;
     tm = *static_cast<const CUtensorMap*>(c.tmap);
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(by));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (cudaError_t e = ensure_smem(kc, by); e != cudaSuccess) return e;
   kc<<<grid, CNT, by, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
                                          static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
                                          static_cast<float*>(c.rout), c.aux, zc,
@@ -224,15 +200,17 @@ long long step3d_obs_ctas(const KParams& kp) {
 
 bool make_coll3d_tmap(const void* f, const KParams& kp, void* out) {
   if (kp.nx % 4 != 0 || (reinterpret_cast<uintptr_t>(f) & 15) != 0) return false;
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // the driver's encoder, looked up once (a function-local static is
+  // initialised once even when several host threads get here together)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return false;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
   const cuuint64_t dims[4] = {cuuint64_t(kp.nx), cuuint64_t(kp.ny), cuuint64_t(kp.nz), 19};
   const cuuint64_t strides[3] = {cuuint64_t(kp.nx) * 4, cuuint64_t(kp.nx) * kp.ny * 4, cuuint64_t(kp.n) * 4};
   const cuuint32_t box[4] = {cuuint32_t(FW), cuuint32_t(CY), 1, 19};

@@ -67,6 +67,19 @@ cudaError_t mu3d_pass(const Launch& c, int order);
 // not allow the vector variant.
 cudaError_t coll3d_gf_step(const Launch& c, int* nblocks);
 
+// Raise kernel fn's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The attribute belongs to one device (context): it is set
+// once per device and kernel, under a lock, so handles on several GPUs and
+// several host threads may launch.  A cudaDeviceReset drops every attribute
+// (and every handle's memory) of that device: the library is not usable on it
+// again in the same process.
+cudaError_t ensure_smem(const void* fn, size_t bytes);
+template <class K>
+inline cudaError_t ensure_smem(K* fn, size_t bytes) { return ensure_smem(reinterpret_cast<const void*>(fn), bytes); }
+
+// multiprocessor count of the current device (looked up once per device)
+int device_sms();
+
 // number of CTAs (hence partial results) of the observation pass
 long long step2d_obs_ctas(const KParams& kp);
 long long step3d_obs_ctas(const KParams& kp);

@@ -9,6 +9,9 @@
 #include <cstring>
 #include <new>
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -484,6 +487,38 @@ __global__ void k_obs_final(const double* part, int nb, const Tr* rho, double rh
 inline unsigned grid1(long long n, int bs) { return unsigned((n + bs - 1) / bs); }
 
 }  // namespace
+
+namespace lbmd {
+
+cudaError_t ensure_smem(const void* fn, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;  // (device, kernel) -> limit set
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find({dev, fn});
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess) done[{dev, fn}] = bytes;
+  return e;
+}
+
+int device_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  static std::mutex mu;
+  static std::map<int, int> sms;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = sms.find(dev);
+  if (it != sms.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  sms[dev] = n;
+  return n;
+}
+
+}  // namespace lbmd
 
 static int ck(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
 

@@ -13,9 +13,16 @@
 // call shares it and it keeps the previous call's contents: the status word is
 // cleared by each call, the partials and results are overwritten.  Calls whose
 // work overlaps on the GPU (different streams, or host threads without
-// ordering) race on the array; serialise them.
+// ordering) race on the array; serialise them.  The address cached per device
+// belongs to the device's context: after a cudaDeviceReset the library is not
+// usable on that device again in the same process.
+//
+// The observation pass is the periodic one, with no wall mask: a state
+// produced with walls (lbm_set_solid) would count its wall nodes in the mass
+// and the velocity maxima, so this entry point is for states without walls.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <climits>
 #include <cstring>
 
@@ -32,7 +39,10 @@ constexpr long long kResults = kMaxCtas * 4;     // offset of the 16 result word
 static __device__ __align__(256) double g_obs_scratch[kMaxCtas * 4 + 16];
 
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};         // device address of the array, per device
+// device address of the array, per device: looked up by the first call on
+// that device; atomic, since host threads may make their first calls together
+// (each finds the same address)
+std::atomic<double*> g_scratch_addr[kMaxDevices] = {};
 
 // fixed-order reduction of the per-CTA partials (max, max, sum, max)
 template <typename Tr>
@@ -90,12 +100,11 @@ extern "C" int lbm_observables_noalloc(const lbm_params* p, const void* d_f, con
   // once per device: the device address of the scratch array
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ECUDA;
-  if (!g_scratch_addr[dev]) {
-    double* ptr = nullptr;
-    if (cudaGetSymbolAddress((void**)&ptr, g_obs_scratch) != cudaSuccess || !ptr) return LBM_ECUDA;
-    g_scratch_addr[dev] = ptr;
+  double* scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!scratch) {
+    if (cudaGetSymbolAddress((void**)&scratch, g_obs_scratch) != cudaSuccess || !scratch) return LBM_ECUDA;
+    g_scratch_addr[dev].store(scratch, std::memory_order_release);
   }
-  double* scratch = g_scratch_addr[dev];
   double* res = scratch + kResults;
   unsigned long long* bad = reinterpret_cast<unsigned long long*>(res + 8);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -94,7 +94,11 @@ __device__ __forceinline__ void grad3d_pair(const float2* sdm, const int* base, 
 
 // mbarrier helpers of the tensor-copy staging.  Waits are bounded: after about
 // a second of polling the wait gives up (the caller records an error) instead
-// of hanging the GPU.
+// of hanging the GPU.  A copy that did not complete in time may still be
+// writing into the CTA's shared memory, so k_coll3d then issues no further
+// copy and, before the CTA exits, its issuing thread waits once more (again
+// bounded) for that copy; the march in between computes on whatever arrived,
+// in a step already marked bad.
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -163,7 +167,10 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   }
   __syncthreads();
   unsigned bar_phase = 0;  // bit b: parity of the next completion of s_bar[b]
-  bool tma_lost = false;   // a wait ran out: later waits are skipped (the step is already marked bad)
+  // a wait ran out: later waits are skipped and no copy is issued after it
+  // (the step is already marked bad); the copy awaited then is lost_bar/lost_par
+  bool tma_lost = false;
+  unsigned lost_bar = 0, lost_par = 0;
 
   // the x-y part of the global offset of each of this thread's field nodes
   // (fixed for the whole z march; the shared offset of node e is e) and, VEC,
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
     }
     if constexpr (VEC) {
       if (fl && tcta) {
-        if (tid == 0) {
+        if (tid == 0 && !tma_lost) {
           // the buffer's previous contents were read and written through the
           // generic proxy before the barrier that precedes this call
           const unsigned bar = smem_u32(&s_bar[pc & 1]);
@@ -278,6 +285,8 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       if (!tma_lost && !mbar_wait_bounded(smem_u32(&s_bar[b]), (bar_phase >> b) & 1u)) {
         atomicMin(aux.bad_step, 0ull);
         tma_lost = true;
+        lost_bar = smem_u32(&s_bar[b]);
+        lost_par = (bar_phase >> b) & 1u;
       }
       bar_phase ^= 1u << b;
       // this thread's generic accesses to the other buffer (the previous
@@ -452,6 +461,9 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
     }
     sc = ring(sc + 1, NS);
   }
+  // the issuing thread keeps the CTA (and its shared memory) alive until a
+  // copy that missed its wait has landed, or a second bounded wait runs out
+  if (tcta && tid == 0 && tma_lost) (void)mbar_wait_bounded(lost_bar, lost_par);
   if constexpr (OBS)
     block_obs_reduce<CNT>(0.5 * sqrt(double(o_v2)), sqrt(double(o_u2)), double(o_n) * p.rho_ref + double(o_m), double(o_d),
                           aux.partials + 4 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));

@@ -26,6 +26,14 @@ def L():
 KEYS = ("max_v", "max_u", "mass", "rho_center", "rho_corner")
 
 
+class _DeviceArray:
+    """A library-owned device buffer seen by torch (no copy)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2}
+
+
 @pytest.mark.parametrize("lattice,shape,precision,scheme", [
     (0, (72, 40, 1), 0, "EFDS6"),
     (1, (40, 36, 44), 1, "EFDS6"),
@@ -55,6 +63,43 @@ def test_noalloc_matches_allocating_observables(L, lattice, shape, precision, sc
     rc, o = L.lbm_observables_noalloc(s.params, d_f, d_rho, d_rho_prev=d_rho, steps_since_prev=5, step=20,
                                       stream=stream)
     assert rc == L.LBM_OK and o["max_drho"] == 0.0
+
+
+@pytest.mark.parametrize("lattice,shape,precision", [
+    (0, (72, 40, 1), 0), (0, (72, 40, 1), 1), (1, (40, 36, 44), 0), (1, (40, 36, 44), 1),
+])
+def test_noalloc_max_drho_against_earlier_density(L, lattice, shape, precision):
+    # the caller keeps a copy of the density at step 20, runs 5 more steps and
+    # asks for max |rho(25) - rho(20)| / 5; the handle's own lbm_observables,
+    # whose previous observation was at step 20, reports the same quantity
+    import torch
+    nx, ny, nz = shape
+    p = L.make_params(lattice=lattice, nx=nx, ny=ny, nz=nz, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
+                      precision=precision)
+    s = L.Sim(p)
+    s.lbm_init_droplet(8.0)
+    s.lbm_step(20)
+    s.lbm_observables()  # the handle's snapshot at step 20
+    _, d_rho20 = s.lbm_device_state()
+    n = nx * ny * nz
+    # the caller's own copy of the stored density field (device to device)
+    stored = torch.as_tensor(_DeviceArray(d_rho20, n, "<f8" if precision == 0 else "<f4"), device="cuda")
+    prev = stored.clone()
+    stream = torch.cuda.current_stream()
+    s.lbm_step(5)
+    ref = s.lbm_observables()
+    assert ref["step"] == 25 and ref["max_drho"] > 0
+    d_f, d_rho = s.lbm_device_state()
+    for _ in range(2):
+        rc, o = L.lbm_observables_noalloc(s.params, d_f, d_rho, d_rho_prev=prev.data_ptr(), steps_since_prev=5,
+                                          step=25, stream=stream.cuda_stream)
+        assert rc == L.LBM_OK and o["status"] == 0
+        if precision == 0:
+            assert o["max_drho"] == pytest.approx(ref["max_drho"], rel=1e-12)
+        else:
+            # the same float pairs differenced; the passes round the maxima
+            # alike up to the FP32 rounding of one density value over dt
+            assert abs(o["max_drho"] - ref["max_drho"]) <= 1e-6 * ref["rho_center"] / 5
 
 
 def test_noalloc_rejects_oversized_and_compact(L):
