@@ -77,13 +77,14 @@ def test_fused_observation_matches_oracle(L):
     oo = o.observables()
     assert ob["step"] == oo["step"] == 15
     # FP32 deviation storage against the FP64 oracle (the parity tolerance of the
-    # densities; velocities relative to their own scale)
+    # densities; velocities to 1e-3 of their own scale: max |v| here is ~1e-2,
+    # above 1e3 times the FP32 noise floor measured on flat slabs, ~5e-7)
     rl = O.maxwell_tr(0.8)[1]
     for k in ("rho_center", "rho_corner"):
         assert abs(ob[k] - oo[k]) < 1e-5 * rl, k
     assert ob["mass"] == pytest.approx(oo["mass"], rel=1e-6)
     for k in ("max_v", "max_u"):
-        assert ob[k] == pytest.approx(oo[k], rel=2e-3, abs=1e-7), k
+        assert ob[k] == pytest.approx(oo[k], rel=1e-3, abs=1e-7), k
 
 
 @pytest.mark.parametrize("shape,kw", [((48, 40, 1), dict(precision=0)), ((48, 40, 1), dict()),
