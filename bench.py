@@ -4,9 +4,12 @@
 Workload (one step = one full time step of the hot path over the lattice):
 D3Q19, 256^3 periodic, droplet r0 = 60, Carnahan-Starling EOS (a=1, b=4,
 R=1), T_r = 0.8, k = 0.25, kappa = 0.1, tau = 1, sixth-order central
-differences (EFDS6), populations stored in FP32 as deviations from w_i rho_g
-with an FP64 density field.  The f arrays (1.27 GB) are far larger than L2,
-so no flush is needed between steps.
+differences (EFDS6), populations stored in FP32 as deviations from w_i rho_g,
+the density field as an FP32 deviation from rho_g, the chemical potential in
+FP32 (reductions in FP64).  The f arrays (1.27 GB) are far larger than L2, so
+no flush is needed between steps.  Extra legs: the same droplet at T_r 0.5
+and 0.2 and with the FP64 chemical potential, the 512-case D2Q9 batch, D2Q9
+512^2 / 4096^2, the compact schemes, the warm start.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead,
 on a bounded sample of the same workload.
@@ -288,6 +291,72 @@ def run_compact(L, steps=20, warmup=5, n=192):
     return out
 
 
+def run_cfg3_legs(L, zc, steps=20, warmup=5, n=256, check_steps=300):
+    """The 256^3 droplet (r0 = 60, EFDS6, FP32 deviation storage) at the other
+    temperatures of the configuration and with the FP64 chemical potential:
+    MLUPS, the step's HBM fraction at 168 B per lattice update, and the status
+    after check_steps steps (first bad step if unstable).  At T_r 0.2 the
+    k = 0.25 droplet goes unstable (the oracle on the same droplet scaled to
+    96^3 fails at the same step as the GPU there); it is recorded, and the
+    T_r 0.2 leg also runs at k = 0.15, inside the paper's 0.1-0.4 range."""
+    import torch
+    peak = measured_peak()[0]
+    out = {"workload": "D3Q19 %d^3 droplet r0=60, EFDS6, kappa 0.1, FP32DEV, tau 1" % n}
+    legs = [("Tr0.5", 0.5, 0.25, 0), ("Tr0.2_k0.25", 0.2, 0.25, 0), ("Tr0.2_k0.15", 0.2, 0.15, 0),
+            ("Tr0.8_mu_fp64", 0.8, 0.25, 1), ("Tr0.2_k0.15_mu_fp64", 0.2, 0.15, 1)]
+    for name, Tr, k, mu64 in legs:
+        s = L.Sim(L.make_params(lattice=L.LBM_D3Q19, nx=n, ny=n, nz=n, Tr=Tr, k=k, kappa=0.1, scheme="EFDS6",
+                                precision=L.LBM_FP32DEV, mu_fp64=mu64))
+        if zc:
+            s.lbm_set_zchunk(zc)
+        s.lbm_init_droplet(60.0 * n / 256)
+        s.lbm_step(warmup)
+        torch.cuda.synchronize()
+        ms = s.lbm_step_timed(steps)
+        s.lbm_step(check_steps - warmup - steps)
+        o = s.lbm_observables()
+        out[name] = {"Tr": Tr, "k": k, "mu": "fp64" if mu64 else "fp32", "mlups": n ** 3 * steps / (ms[2] * 1e-3) / 1e6,
+                     "ms_per_step": ms[2] / steps,
+                     "step_frac": B_ALG * n ** 3 / (ms[2] / steps * 1e-3) / 1e9 / peak,
+                     "status": o["status"], "steps_checked": check_steps,
+                     "first_bad_step": o["step"] if o["status"] != 0 else None,
+                     "rho_center": o["rho_center"], "rho_corner": o["rho_corner"], "max_v": o["max_v"]}
+        s.close()
+    return out
+
+
+def _oracle_replica(args):
+    """One oracle replica of the all-core CPU leg (a process of its own)."""
+    steps, n, barrier, q = args
+    import oracle as O
+    w = WORKLOAD
+    s = O.Sim(lattice=O.D3Q19, nx=n, ny=n, nz=n, Tr=w["Tr"], k=w["k"], kappa=w["kappa"], tau=w["tau"],
+              scheme=w["scheme"])
+    s.init_droplet(w["radius"] * n / w["nx"])
+    barrier.wait()
+    t0 = time.perf_counter()
+    rc = s.step(steps)
+    q.put((t0, time.perf_counter(), rc))
+
+
+def oracle_sample_all_cores(steps, n=SAMPLE_N):
+    """The oracle as it stands, one replica per host core (processes started
+    with spawn), all stepping the same n^3 sample at once: aggregate MLUPS."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    cores = os.cpu_count() or 1
+    barrier, q = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_replica, args=((steps, n, barrier, q),)) for _ in range(cores)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=600) for _ in procs]
+    for p in procs:
+        p.join()
+    assert all(r[2] == 0 for r in res)
+    wall = max(r[1] for r in res) - min(r[0] for r in res)
+    return cores * n ** 3 * steps / wall / 1e6, wall, cores
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -398,6 +467,8 @@ def run_gpu(args):
 
     sim.close()
     extra = {}
+    if not args.no_cfg3:
+        extra["d3q19_256_legs"] = run_cfg3_legs(L, zc, n=w["nx"])
     if not args.no_batch:
         extra["batch2d"] = run_batch(L, steps=args.batch_steps, ncases=args.batch_cases)
         extra["d2q9_512"] = run_2d(L)
@@ -415,10 +486,15 @@ def run_gpu(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
+        # all host cores: one oracle replica per core on the same sample (the
+        # oracle is single-threaded as written); the single-core figure beside it
+        va, dta, cores = oracle_sample_all_cores(args.cpu_steps)
         v, dt = oracle_sample(args.cpu_steps)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d^3 lattice with the same parameters (r0 scaled), %d FP64 oracle steps, %.1f s"
-                         % (SAMPLE_N, args.cpu_steps, dt)}
+        cpu = {"value": va, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d replicas (one per host core, processes) of a %d^3 lattice with the same parameters "
+                         "(r0 scaled), %d FP64 oracle steps each, %.1f s" % (cores, SAMPLE_N, args.cpu_steps, dta),
+               "single_core": {"value": v, "unit": UNIT, "cores": 1,
+                               "sample": "one %d^3 replica, %d steps, %.1f s" % (SAMPLE_N, args.cpu_steps, dt)}}
     line = {"metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -453,6 +529,7 @@ def main():
     ap.add_argument("--batch-cases", type=int, default=512, help="cases of the batched 2D sweep (small: profiling)")
     ap.add_argument("--batch-steps", type=int, default=50, help="steps per timed launch of the batched 2D sweep")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start experiment")
+    ap.add_argument("--no-cfg3", action="store_true", help="skip the other-temperature and FP64-mu 256^3 legs")
     ap.add_argument("--zchunk", type=int, default=0, help="fix the z-chunk instead of autotuning (profiling runs)")
     ap.add_argument("--size", type=int, default=256,
                     help="lattice edge (profiling runs only; the benchmark workload is 256)")

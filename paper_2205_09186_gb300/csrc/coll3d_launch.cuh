@@ -1,0 +1,38 @@
+// Launcher of the D3Q19 FP32-deviation collision pass (k_coll3d) for one tile
+// shape: RY region rows (RY - 2 tile rows) and NB staged population planes.
+#pragma once
+#include <cuda.h>
+
+#include "launch.cuh"
+#include "step3d_split.cuh"
+
+namespace lbmd {
+
+template <int S, bool TAU1, bool VEC, bool OBS, int RY = CY, int NB = 2>
+cudaError_t launch_coll(const Launch& c, int zc) {
+  using Sh = CollShape<S, RY, NB>;
+  auto kc = k_coll3d<S, TAU1, VEC, OBS, RY, NB>;
+  constexpr size_t by = OBS ? Sh::bytes_obs : Sh::bytes;
+  static_assert(by <= size_t(227) * 1024, "shared memory of one CTA");
+  CUtensorMap tm{};
+  if constexpr (VEC) {
+    if (!c.tmap) return cudaErrorInvalidValue;
+    if constexpr (RY == CY) {
+      tm = *static_cast<const CUtensorMap*>(c.tmap);
+    } else {
+      // the handle keeps maps for the default box height; other shapes
+      // encode theirs (a host-side call) for the launch's populations
+      if (!make_coll3d_tmap(c.fin, c.kp, &tm, RY)) return cudaErrorInvalidValue;
+    }
+  }
+  if (cudaError_t e = ensure_smem(kc, by); e != cudaSuccess) return e;
+  const dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + Sh::TY - 1) / Sh::TY, (c.kp.nz + zc - 1) / zc);
+  kc<<<grid, Sh::NT, by, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
+                                     static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
+                                     static_cast<float*>(c.rout), c.aux, zc,
+                                     OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr, tm,
+                                     static_cast<const float*>(c.gi.gmu), static_cast<const float*>(c.gi.grho));
+  return cudaGetLastError();
+}
+
+}  // namespace lbmd

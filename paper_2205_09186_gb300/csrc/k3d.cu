@@ -9,6 +9,7 @@
 #include "step3d.cuh"
 #include "step3d_fast.cuh"
 #include "step3d_split.cuh"
+#include "coll3d_launch.cuh"
 
 namespace lbmd {
 
@@ -19,10 +20,11 @@ bool split3d_scheme(int scheme, int prec) {
 }
 
 // z-chunk for the split collision pass: last-wave balance against the
-// prologue (2R planes of field loads and two extra collided planes)
-static int split_zchunk_heuristic(const KParams& kp, int R) {
-  const long long tiles = (long long)((kp.nx + TXC - 1) / TXC) * ((kp.ny + TYC - 1) / TYC);
-  const long long slots = 2LL * num_sms();
+// prologue (2R planes of field loads and two extra collided planes) for tiles
+// of ty rows and per_sm resident CTAs per SM
+static int split_zchunk_heuristic(const KParams& kp, int R, int ty, int per_sm) {
+  const long long tiles = (long long)((kp.nx + TXC - 1) / TXC) * ((kp.ny + ty - 1) / ty);
+  const long long slots = (long long)per_sm * num_sms();
   double best = 1e300;
   int best_zc = kp.nz;
   for (int nzc = 1; nzc <= kp.nz && nzc <= 128; ++nzc) {
@@ -86,24 +88,6 @@ cudaError_t launch_fast(const Launch& c, int* nblocks) {
   return cudaGetLastError();
 }
 
-template <int S, bool TAU1, bool VEC, bool OBS>
-cudaError_t launch_coll(const Launch& c, dim3 grid, int zc) {
-  using Sh = CollShape<S>;
-  auto kc = k_coll3d<S, TAU1, VEC, OBS>;
-  constexpr size_t by = OBS ? Sh::bytes_obs : Sh::bytes;
-  CUtensorMap tm{};
-  if constexpr (VEC) {
-    if (!c.tmap) return cudaErrorInvalidValue;
-    tm = *static_cast<const CUtensorMap*>(c.tmap);
-  }
-  if (cudaError_t e = ensure_smem(kc, by); e != cudaSuccess) return e;
-  kc<<<grid, CNT, by, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
-                                         static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
-                                         static_cast<float*>(c.rout), c.aux, zc,
-                                         OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr, tm,
-                                         static_cast<const float*>(c.gi.gmu), static_cast<const float*>(c.gi.grho));
-  return cudaGetLastError();
-}
 
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
 
@@ -132,14 +116,13 @@ cudaError_t launch_mu(const Launch& c) {
 // collision pass also reduces the observables of the state it advances
 template <int S, bool TAU1>
 cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
-  using Sh = CollShape<S>;
   if (!c.mu) return cudaErrorInvalidValue;
-  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sh::R);
-  dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + TYC - 1) / TYC, (c.kp.nz + zc - 1) / zc);
+  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sch<S>::R, TYC, CollShape<S>::MINB);
+  const long long ctas = (long long)((c.kp.nx + TXC - 1) / TXC) * ((c.kp.ny + TYC - 1) / TYC) * ((c.kp.nz + zc - 1) / zc);
   if (nblocks) {
     // observation: the caller's partials buffer holds *nblocks entries
-    if (obs && (long long)grid.x * grid.y * grid.z > *nblocks) return cudaErrorNotSupported;
-    *nblocks = int(grid.x * grid.y * grid.z);
+    if (obs && ctas > *nblocks) return cudaErrorNotSupported;
+    *nblocks = int(ctas);
   } else if (obs) {
     return cudaErrorInvalidValue;
   }
@@ -149,8 +132,8 @@ cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   // 16-byte copies need rows of whole chunks and aligned bases
   const bool vec = c.kp.nx % 4 == 0 && aligned16(c.fin) && aligned16(c.rin) && aligned16(c.mu) && c.tmap;
   if (obs)
-    return vec ? launch_coll<S, TAU1, true, true>(c, grid, zc) : launch_coll<S, TAU1, false, true>(c, grid, zc);
-  return vec ? launch_coll<S, TAU1, true, false>(c, grid, zc) : launch_coll<S, TAU1, false, false>(c, grid, zc);
+    return vec ? launch_coll<S, TAU1, true, true>(c, zc) : launch_coll<S, TAU1, false, true>(c, zc);
+  return vec ? launch_coll<S, TAU1, true, false>(c, zc) : launch_coll<S, TAU1, false, false>(c, zc);
 }
 
 // observation pass of the split path: mu field, then the node-parallel reduction
@@ -198,7 +181,7 @@ long long step3d_obs_ctas(const KParams& kp) {
   return (long long)((kp.nx + TX3 - 1) / TX3) * ((kp.ny + TY3 - 1) / TY3) * ((kp.nz + ZC3 - 1) / ZC3);
 }
 
-bool make_coll3d_tmap(const void* f, const KParams& kp, void* out) {
+bool make_coll3d_tmap(const void* f, const KParams& kp, void* out, int rows) {
   if (kp.nx % 4 != 0 || (reinterpret_cast<uintptr_t>(f) & 15) != 0) return false;
   // the driver's encoder, looked up once (a function-local static is
   // initialised once even when several host threads get here together)
@@ -213,7 +196,8 @@ bool make_coll3d_tmap(const void* f, const KParams& kp, void* out) {
   if (!encode) return false;
   const cuuint64_t dims[4] = {cuuint64_t(kp.nx), cuuint64_t(kp.ny), cuuint64_t(kp.nz), 19};
   const cuuint64_t strides[3] = {cuuint64_t(kp.nx) * 4, cuuint64_t(kp.nx) * kp.ny * 4, cuuint64_t(kp.n) * 4};
-  const cuuint32_t box[4] = {cuuint32_t(FW), cuuint32_t(CY), 1, 19};
+  if (rows < 1 || rows > 32) return false;
+  const cuuint32_t box[4] = {cuuint32_t(FW), cuuint32_t(rows), 1, 19};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(f), dims, strides,
                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -223,11 +207,10 @@ bool make_coll3d_tmap(const void* f, const KParams& kp, void* out) {
 cudaError_t coll3d_gf_step(const Launch& c, int* nblocks) {
   if (c.kp.nx % 4 != 0 || !aligned16(c.fin) || !aligned16(c.rin) || !c.tmap || !c.gi.gmu || !c.gi.grho)
     return cudaErrorNotSupported;
-  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, 0);
-  dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + TYC - 1) / TYC, (c.kp.nz + zc - 1) / zc);
-  if (nblocks) *nblocks = int(grid.x * grid.y * grid.z);
-  return c.kp.omega == 1.0 ? launch_coll<S_CFDS4, true, true, false>(c, grid, zc)
-                           : launch_coll<S_CFDS4, false, true, false>(c, grid, zc);
+  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, 0, TYC, 2);
+  if (nblocks) *nblocks = int((long long)((c.kp.nx + TXC - 1) / TXC) * ((c.kp.ny + TYC - 1) / TYC) * ((c.kp.nz + zc - 1) / zc));
+  return c.kp.omega == 1.0 ? launch_coll<S_CFDS4, true, true, false>(c, zc)
+                           : launch_coll<S_CFDS4, false, true, false>(c, zc);
 }
 
 cudaError_t mu3d_pass(const Launch& c, int order) {

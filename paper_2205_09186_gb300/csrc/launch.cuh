@@ -51,10 +51,13 @@ StepFn step2d_fn(int scheme, int prec);
 StepFn step3d_fn(int scheme, int prec);
 
 // Tensor map of a D3Q19 FP32-deviation population array f[19][nz][ny][nx]
-// for the collision pass's tensor copies, written to out (a CUtensorMap, 128
-// bytes, 64-byte aligned).  False when the lattice or the pointer does not
-// allow one (nx % 4 != 0, unaligned base) or the driver refuses it.
-bool make_coll3d_tmap(const void* f, const KParams& kp, void* out);
+// for the collision pass's tensor copies (box 36 x rows x 1 x 19; rows = the
+// collision region's rows, 11 for the tiles the library launches), written to out (a
+// CUtensorMap, 128 bytes, 64-byte aligned).  False when the lattice or the
+// pointer does not allow one (nx % 4 != 0, unaligned base) or the driver
+// refuses it.
+bool make_coll3d_tmap(const void* f, const KParams& kp, void* out, int rows = 11);
+
 
 // D3Q19 FP32 mu field (Eq. 16) with the explicit central Laplacian of the
 // given order (4 or 6) from c.rin into c.mu (N floats): the mu pass of the

@@ -338,6 +338,9 @@ __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_gro
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 // all but the most recent group complete
 __device__ __forceinline__ void cpa_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+// all but the N most recent groups complete
+template <int N>
+__device__ __forceinline__ void cpa_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ int ring(int s, int n) { return s < 0 ? s + n : (s >= n ? s - n : s); }
 

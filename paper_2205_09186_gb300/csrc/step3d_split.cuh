@@ -25,7 +25,7 @@
 namespace lbmd {
 
 // ------------------------------------------------------------------ collision pass
-constexpr int CX = 32, CY = 11;     // collision region (tile + ring), one warp per row
+constexpr int CX = 32, CY = 11;     // default collision region (tile + ring), one warp per row
 constexpr int TXC = CX - 2, TYC = CY - 2;  // 30 x 9 tile
 constexpr int CNT = CX * CY;        // 352 threads
 constexpr int FW = 36;              // staged population row: 32 nodes + up to 3 of alignment
@@ -42,30 +42,40 @@ constexpr int FW = 36;              // staged population row: 32 nodes + up to 3
 // seam) stages it with one tensor copy (TMA) per plane: a 36 x 11 x 1 x 19 box
 // of the populations viewed as a 4-D tensor (x, y, z, i) lands in exactly this
 // layout; the buffers are 1 KB aligned for it.
-template <int S>
+//
+// RY rows of the region (RY - 2 tile rows, one warp each) and NB staged planes
+// of populations: the copies of plane z + NB - 1 are issued while plane z is
+// collided, so NB - 1 planes are in flight per CTA.  The field ring holds the
+// 2R + 1 planes of the stencil plus the NB - 1 in flight.
+template <int S, int RY_ = CY, int NB_ = 2>
 struct CollShape {
   static constexpr int R = Sch<S>::R;
-  static constexpr int GW = CX + 2 * R, GH = CY + 2 * R;  // field region (ring + stencil halo)
-  static constexpr int NS = 2 * R + 2;                    // ring of planes (one in flight)
+  static constexpr int RY = RY_, TY = RY_ - 2, NT = CX * RY_, NB = NB_;
+  static_assert(NB >= 2 && NB <= 4, "two to four staged planes");
+  static constexpr int GW = CX + 2 * R, GH = RY + 2 * R;  // field region (ring + stencil halo)
+  static constexpr int NS = 2 * R + NB;                   // ring of planes (NB - 1 in flight)
   static constexpr int plane = GH * GW;                   // float2 per field plane
-  static constexpr int FPL = CY * FW;                     // staged populations of one i
+  static constexpr int FPL = RY * FW;                     // staged populations of one i
   static constexpr int fbuf = (19 * FPL + 255) / 256 * 256;  // buffer stride (floats), 1 KB multiple
   static constexpr unsigned box_bytes = 19u * FPL * 4u;       // one tensor copy
   // compact schemes (GF): per collided node the density deviation and the six
-  // derivative values (grad mu, grad rho) of its own plane, double-buffered
+  // derivative values (grad mu, grad rho) of its own plane, one set per staged plane
   static constexpr int NG = 7;
-  static constexpr size_t fields_bytes = Sch<S>::GF ? size_t(2) * NG * CNT * 4 : size_t(NS) * plane * 8;
+  static constexpr size_t fields_bytes = Sch<S>::GF ? size_t(NB) * NG * NT * 4 : size_t(NS) * plane * 8;
   static constexpr size_t off_f = (fields_bytes + 1023) / 1024 * 1024;
-  static constexpr size_t bytes = off_f + size_t(2) * fbuf * 4;
+  static constexpr size_t bytes = off_f + size_t(NB) * fbuf * 4;
   // OBS: the snapshot values of the collided plane, one per thread, staged
-  // like the populations (double-buffered by plane parity)
+  // like the populations (one set per staged plane)
   static constexpr size_t off_snap = bytes;
-  static constexpr size_t bytes_obs = bytes + size_t(2) * CNT * 4;
+  static constexpr size_t bytes_obs = bytes + size_t(NB) * NT * 4;
   // field nodes per plane, and per thread; 16-byte population chunks, and per thread
   static constexpr int DE = plane;
-  static constexpr int KD = (DE + CNT - 1) / CNT;
-  static constexpr int FCH = 19 * CY * (FW / 4);
-  static constexpr int KF = (FCH + CNT - 1) / CNT;
+  static constexpr int KD = (DE + NT - 1) / NT;
+  static constexpr int FCH = 19 * RY * (FW / 4);
+  static constexpr int KF = (FCH + NT - 1) / NT;
+  // resident CTAs per SM the launch bounds ask for: two when two fit in the
+  // SM's 228 KB of shared memory (1 KB of it reserved per CTA)
+  static constexpr int MINB = 2 * (bytes_obs + 2048) <= size_t(228) * 1024 ? 2 : 1;
 };
 
 // grad rho and grad mu of a line scheme together from the interleaved field
@@ -117,34 +127,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
 // (component-major, N each) of the line solves; no stencil halo.
 // VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations),
 // and tensor copies of the populations for CTAs away from the periodic seams
-// (tmf: the populations as a 4-D tensor (nx, ny, nz, 19), box (FW, CY, 1, 19)).
+// (tmf: the populations as a 4-D tensor (nx, ny, nz, 19), box (FW, RY, 1, 19)).
 // OBS: also reduce the observables of the state being advanced (max |v| with
 // v = u + F / (2 rho), max |u|, mass, max |rho - snap|) into aux.partials, one
 // set per CTA, and overwrite snap with this state's density deviation.
-template <int S, bool TAU1, bool VEC, bool OBS>
-__global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float* __restrict__ fin,
+template <int S, bool TAU1, bool VEC, bool OBS, int RY_ = CY, int NB_ = 2>
+__global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_coll3d(const KParams p, const float* __restrict__ fin,
                                                     float* __restrict__ fout, const float* __restrict__ rin,
                                                     const float* __restrict__ muf, float* __restrict__ rout,
                                                     const StepAux aux, const int zc, float* __restrict__ snap,
                                                     const __grid_constant__ CUtensorMap tmf,
                                                     const float* __restrict__ gmu, const float* __restrict__ grho) {
   using L = Lattice<1>;
-  using Sh = CollShape<S>;
+  using Sh = CollShape<S, RY_, NB_>;
   constexpr int Q = 19, R = Sh::R, GW = Sh::GW, NS = Sh::NS, FPL = Sh::FPL;
+  constexpr int RY = Sh::RY, TY = Sh::TY, NT = Sh::NT, NB = Sh::NB;
   extern __shared__ __align__(1024) unsigned char smem_c3[];  // (own name: other kernels align theirs to 16)
   unsigned char* smem = smem_c3;
-  __shared__ __align__(8) unsigned long long s_bar[2];  // tensor copies: one mbarrier per buffer
+  __shared__ __align__(8) unsigned long long s_bar[NB];  // tensor copies: one mbarrier per buffer
   constexpr bool GF = Sch<S>::GF;
   float2* s_dm = reinterpret_cast<float2*>(smem);
-  float* s_g = reinterpret_cast<float*>(smem);  // GF: [2][NG][CNT]
+  float* s_g = reinterpret_cast<float*>(smem);  // GF: [NB][NG][NT]
   float* s_f = reinterpret_cast<float*>(smem + Sh::off_f);
   float* s_snap = reinterpret_cast<float*>(smem + Sh::off_snap);  // OBS only
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int N = int(p.n), NXY = nx * ny;
-  const int x0 = blockIdx.x * TXC, y0 = blockIdx.y * TYC, z0 = blockIdx.z * zc;
+  const int x0 = blockIdx.x * TXC, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
   const int z1 = min(z0 + zc, nz);
-  const int VW = min(TXC, nx - x0), VH = min(TYC, ny - y0);
+  const int VW = min(TXC, nx - x0), VH = min(TY, ny - y0);
   const int tid = threadIdx.x;
   const int cy = tid / CX, cx = tid - cy * CX;  // one warp per row
   const int lx = cx - 1, ly = cy - 1;
@@ -153,16 +164,19 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
   const float omega = float(p.omega), rref = float(p.rho_ref);
   const int pc_first = z0 - 1, pc_last = z1;
+  // staging buffer (populations, GF derivatives, OBS snapshot) of plane pc
+  auto bsel = [&](int pc) { return int(unsigned(pc - pc_first) % unsigned(NB)); };
   // first population column of the region in shared memory
   const int of = VEC ? (x0 - 1) & 3 : 0;
   // tensor copies when the population region (36 columns from the aligned
-  // start, 11 rows) needs no periodic wrap
+  // start, RY rows) needs no periodic wrap
   // (and the staging buffers 128-byte aligned, as tensor copies require)
-  const bool tcta = VEC && x0 - 1 - of >= 0 && x0 - 1 - of + FW <= nx && y0 - 1 >= 0 && y0 - 1 + CY <= ny &&
+  const bool tcta = VEC && x0 - 1 - of >= 0 && x0 - 1 - of + FW <= nx && y0 - 1 >= 0 && y0 - 1 + RY <= ny &&
                     (smem_u32(s_f) & 127u) == 0 && ((Sh::fbuf * 4) & 127) == 0;
   if (tcta && tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[1])) : "memory");
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[b])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -178,7 +192,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   int dofs[Sh::KD], fofs[VEC ? Sh::KF : 1];
 #pragma unroll
   for (int k = 0; k < Sh::KD; ++k) {
-    const int e = tid + k * CNT;
+    const int e = tid + k * NT;
     const int ry = e / GW, rx = e - ry * GW;
     dofs[k] = e < Sh::DE ? wrapn(y0 - 1 - R + ry, ny) * nx + wrapn(x0 - 1 - R + rx, nx) : 0;
   }
@@ -186,37 +200,38 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
     const int xaf = x0 - 1 - of;  // aligned start (may be negative)
 #pragma unroll
     for (int k = 0; k < Sh::KF; ++k) {
-      const int c = tid + k * CNT, i = c / (CY * (FW / 4));  // population of chunk c
-      const int r = c - i * (CY * FW / 4), ry = r / (FW / 4), j = r - ry * (FW / 4);
+      const int c = tid + k * NT, i = c / (RY * (FW / 4));  // population of chunk c
+      const int r = c - i * (RY * FW / 4), ry = r / (FW / 4), j = r - ry * (FW / 4);
       fofs[k] = i * N + wrapn(y0 - 1 + ry, ny) * nx + wrapn(xaf + 4 * j, nx);
     }
   }
 
   // field planes q (density deviation and mu) -> ring slot; populations of
-  // plane q - R (if collided) -> staging buffer of its parity
+  // plane q - R (if collided) -> its staging buffer
   auto issue = [&](int q, int slot) {
     const int zo = wrapi(q, nz) * NXY;  // q in [z0 - 1 - R, z1 + R]: one period at most
     float2* dd = s_dm + slot * Sh::plane;
     const int pc = q - R;
     const bool fl = pc >= pc_first && pc <= pc_last;
     const int zf = wrapi(pc, nz) * NXY;
-    float* fd = s_f + (pc & 1) * Sh::fbuf;
+    const int pb = bsel(pc);
+    float* fd = s_f + pb * Sh::fbuf;
     if constexpr (GF) {
       // this node's deviation and derivatives in plane pc (R = 0: q = pc)
       if (fl && cnode) {
-        float* gd = s_g + (pc & 1) * Sh::NG * CNT + tid;
+        float* gd = s_g + pb * Sh::NG * NT + tid;
         const int o = zf + gy * nx + gx;
         cpa4(gd, rin + o);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          cpa4(gd + (1 + a) * CNT, gmu + a * N + o);
-          cpa4(gd + (4 + a) * CNT, grho + a * N + o);
+          cpa4(gd + (1 + a) * NT, gmu + a * N + o);
+          cpa4(gd + (4 + a) * NT, grho + a * N + o);
         }
       }
     } else {
 #pragma unroll
       for (int k = 0; k < Sh::KD; ++k) {
-        const int e = tid + k * CNT;
+        const int e = tid + k * NT;
         if (e < Sh::DE) {
           cpa4(&dd[e].x, rin + zo + dofs[k]);
           cpa4(&dd[e].y, muf + zo + dofs[k]);
@@ -228,7 +243,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
         if (tid == 0 && !tma_lost) {
           // the buffer's previous contents were read and written through the
           // generic proxy before the barrier that precedes this call
-          const unsigned bar = smem_u32(&s_bar[pc & 1]);
+          const unsigned bar = smem_u32(&s_bar[pb]);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(Sh::box_bytes)
                        : "memory");
@@ -242,7 +257,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       } else if (fl) {
 #pragma unroll
         for (int k = 0; k < Sh::KF; ++k) {
-          const int c = tid + k * CNT;
+          const int c = tid + k * NT;
           if (c < Sh::FCH) cpa16(fd + 4 * c, fin + zf + fofs[k]);
         }
       }
@@ -256,32 +271,32 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
     }
     if constexpr (OBS) {
       // the snapshot of this thread's node in plane pc (push planes only)
-      if (interior && pc >= z0 && pc < z1) cpa4(s_snap + (pc & 1) * CNT + tid, snap + pc * NXY + gy * nx + gx);
+      if (interior && pc >= z0 && pc < z1) cpa4(s_snap + pb * NT + tid, snap + pc * NXY + gy * nx + gx);
     }
     cpa_commit();
   };
 
-  // prologue: planes pc_first - R .. pc_first + R
+  // prologue: field planes pc_first - R .. pc_first + R + NB - 2 (populations
+  // of planes pc_first .. pc_first + NB - 2), one copy group per plane
   int slot = 0;  // ring slot of plane pc_first - R + (number issued)
-  for (int q = pc_first - R; q <= pc_first + R - 1; ++q) {
+  for (int q = pc_first - R; q <= pc_first + R + NB - 2; ++q) {
     issue(q, slot);
     slot = ring(slot + 1, NS);
   }
   int sc = R;  // ring slot of the collision plane
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-  issue(pc_first + R, slot);
-  slot = ring(slot + 1, NS);
   const int fme = cy * FW + of + cx;  // this node in a staged population plane
   float o_v2 = 0.f, o_u2 = 0.f, o_d = 0.f;  // OBS: running maxima (4 |v|^2, |u|^2, |rho - snap|)
   float o_m = 0.f;                           // OBS: sum of this thread's density deviations
   int o_n = 0;                               // OBS: nodes counted
   const int snap_xy = gy * nx + gx;  // OBS: this thread's node in a plane
   for (int pc = pc_first; pc <= pc_last; ++pc) {
-    cpa_wait_all();
+    // one copy group per plane, the NB - 2 latest may still be in flight
+    cpa_wait_n<NB - 2>();
     if (tcta) {
       // this plane's tensor copy has landed (bounded wait; on time-out the
       // step is marked bad and the march goes on with whatever arrived)
-      const int b = pc & 1;
+      const int b = bsel(pc);
       if (!tma_lost && !mbar_wait_bounded(smem_u32(&s_bar[b]), (bar_phase >> b) & 1u)) {
         atomicMin(aux.bad_step, 0ull);
         tma_lost = true;
@@ -294,11 +309,14 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (pc < pc_last) {
-      issue(pc + R + 1, slot);
+    if (pc + NB - 1 <= pc_last) {
+      issue(pc + R + NB - 1, slot);
       slot = ring(slot + 1, NS);
+    } else {
+      cpa_commit();  // an empty group: the wait above counts one group per plane
     }
-    float* fb = s_f + (pc & 1) * Sh::fbuf;
+    const int fbi = bsel(pc);
+    float* fb = s_f + fbi * Sh::fbuf;
     float own0 = 0.f, ownp = 0.f, ownm = 0.f;  // this node's populations with e_x = e_y = 0
     if (cnode) {
       int base[2 * R + 1];
@@ -308,7 +326,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
 #pragma unroll
       for (int i = 0; i < Q; ++i) fv[i] = fb[i * FPL + fme];
       const int c = (cy + R) * GW + cx + R;
-      const float* gq = s_g + (pc & 1) * Sh::NG * CNT + tid;  // GF
+      const float* gq = s_g + fbi * Sh::NG * NT + tid;  // GF
       const float dsv = GF ? gq[0] : s_dm[base[R] + c].x;
       const float rc = rref + dsv;
       // momentum from the differences of opposite populations (e_{i+1} = -e_i
@@ -325,9 +343,9 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
       const float ux = jx * irc, uy = jy * irc, uz = jz * irc;
       float2 g2x, g2y, g2z;
       if constexpr (GF) {
-        g2x = make_float2(gq[4 * CNT], gq[1 * CNT]);
-        g2y = make_float2(gq[5 * CNT], gq[2 * CNT]);
-        g2z = make_float2(gq[6 * CNT], gq[3 * CNT]);
+        g2x = make_float2(gq[4 * NT], gq[1 * NT]);
+        g2y = make_float2(gq[5 * NT], gq[2 * NT]);
+        g2z = make_float2(gq[6 * NT], gq[3 * NT]);
       } else {
         grad3d_pair<S>(s_dm, base, GW, cx + R, cy + R, g2x, g2y, g2z);
       }
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
           o_u2 = fmaxf(o_u2, ux * ux + uy * uy + uz * uz);
           // the staged snapshot value was copied in before this plane's
           // barrier; it is overwritten with this state's deviation
-          o_d = fmaxf(o_d, fabsf(dsv - s_snap[(pc & 1) * CNT + tid]));
+          o_d = fmaxf(o_d, fabsf(dsv - s_snap[fbi * NT + tid]));
           snap[pc * NXY + snap_xy] = dsv;  // push planes lie in [z0, z1): no wrap
           o_m += dsv;  // at most one z-chunk of deviations per thread: FP32 suffices
           ++o_n;
@@ -465,7 +483,7 @@ __global__ void __launch_bounds__(CNT, 2) k_coll3d(const KParams p, const float*
   // copy that missed its wait has landed, or a second bounded wait runs out
   if (tcta && tid == 0 && tma_lost) (void)mbar_wait_bounded(lost_bar, lost_par);
   if constexpr (OBS)
-    block_obs_reduce<CNT>(0.5 * sqrt(double(o_v2)), sqrt(double(o_u2)), double(o_n) * p.rho_ref + double(o_m), double(o_d),
+    block_obs_reduce<NT>(0.5 * sqrt(double(o_v2)), sqrt(double(o_u2)), double(o_n) * p.rho_ref + double(o_m), double(o_d),
                           aux.partials + 4 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }
 

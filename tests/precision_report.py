@@ -11,11 +11,14 @@ markdown table:
   FP64 storage mode for reference;
 * equilibrium rows: D2Q9 64^2 droplet (r0 = 16) relaxed for 5000 steps, with
   the FP32 noise floor of max |v| measured on a 16 x 64 flat slab after 15000
-  steps (the oracle's slab velocity having decayed below it).
+  steps (the oracle's slab velocity having decayed below it), and one droplet
+  run for 40000 steps.
 
 Columns: relative errors of max |v|, max |u|, rho at the centre node, rho at the
 corner node (the gas), total mass and max |d rho / dt| (over the last 100 steps
-for transients, 1000 for equilibrium), and the node-wise max |drho| / rho_l.
+for transients, 1000 for equilibrium; where the oracle's has converged below
+1e-9 per step both absolute values are shown), and the node-wise
+max |drho| / rho_l.
 """
 import os
 import sys
@@ -89,6 +92,10 @@ def main(out=None):
     for scheme, Tr in (("EFDS6", 0.8), ("OCFDS4", 0.8), ("EFDS6", 0.5)):
         cases.append((2, (64, 64, 1), Tr, scheme, 0.25, ("droplet", 16.0), 5000, 1000,
                       "D2Q9 64^2 %s T_r %g k 0.25, equilibrium (5000 steps)" % (scheme, Tr)))
+    # a long run: the slow drift that FP32 rounding of the chemical potential
+    # leaves in the equilibrium, and that the FP64 chemical potential removes
+    cases.append((2, (64, 64, 1), 0.8, "EFDS6", 0.25, ("droplet", 16.0), 40000, 1000,
+                  "D2Q9 64^2 EFDS6 T_r 0.8 k 0.25, 40000 steps"))
     for lat, shape, Tr, scheme, k, init, steps, last, name in cases:
         rg, rl = O.maxwell_tr(Tr)
         rc, ro, oo = run_oracle(lat, shape, Tr, scheme, k, init, steps, last)
@@ -100,7 +107,10 @@ def main(out=None):
             if og["status"] != 0:
                 lines.append("| %s | %s | unstable | | | | | | |" % (name, mname))
                 continue
-            errs = ["%.1e" % rel(og[k_], oo[k_]) for k_ in KEYS]
+            # a converged max |d rho / dt| (the oracle's ~1e-13 per step) has
+            # no meaningful relative error: both absolute values are shown
+            errs = [("%.1e" % rel(og[k_], oo[k_])) if not (k_ == "max_drho" and abs(oo[k_]) < 1e-9)
+                    else "abs %.0e vs %.0e" % (og[k_], oo[k_]) for k_ in KEYS]
             lines.append("| %s | %s | %s | %.1e |" % (name, mname, " | ".join(errs),
                                                       float(np.max(np.abs(rho - ro))) / rl))
         if steps == 5000:
