@@ -358,7 +358,10 @@ int lbm_observables_noalloc(const lbm_params* p, const void* d_f, const void* d_
  * Many independent D2Q9 droplets of different sizes and parameters advanced
  * together (the parameter sweeps of Sec. 3.3-3.4 run as one job).  All cases
  * must share lattice (LBM_D2Q9), precision and mu_fp64; schemes may differ
- * among LBM_EFDS2/4/6, LBM_E4, LBM_E8 (compact schemes: LBM_ENOTSUP).  Each
+ * freely, the compact ones included (Eq. 21-24 and OCFDS4 of Sec. 3.1: their
+ * steps add a chemical-potential phase where the precision needs one, and a
+ * phase of periodic tridiagonal line solves along x and y, groups of lines
+ * being work items of the same launch, each phase behind the barrier).  Each
  * case owns its own populations and density; lbm_batch_step runs n steps of
  * every case in ONE persistent kernel launch whose resident CTAs fetch
  * (case, tile) work items dynamically and meet at a device-wide barrier

@@ -2,7 +2,13 @@
 // launch.  In FP32-deviation batches (k_batch_split) the CTAs (collision
 // items) and warps (mu units) claim the work of each phase from an atomic
 // counter in guided runs; other precisions (k_batch_persistent) fetch their
-// (case, tile) items one at a time from an atomic counter per step.
+// (case, tile) items one at a time from an atomic counter per phase.
+// Compact-scheme cases (Eq. 21-24, OCFDS4 of Sec. 3.1) add phases to every
+// step: their chemical-potential field (k_batch_persistent; the mu phase of
+// k_batch_split already has one), then the periodic tridiagonal line solves
+// for grad mu and grad rho along x and y (groups of lines as work items), each
+// behind the same bounded barrier, before the collision reads the derivative
+// fields.
 // Steps and phases are separated by a device-wide barrier whose waits are
 // bounded (about one second), after which the kernel records LBM_ETIMEOUT and
 // returns.  lbm_batch_step captures the launch (plus the counter reset) in a
@@ -16,6 +22,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "compact_dev.cuh"
 #include "launch.cuh"
 #include "step2d.cuh"
 #include "step2d_split.cuh"
@@ -38,7 +45,20 @@ struct CaseDev {
   int item_begin, item_end;      // observation / single-phase items
   int mtiles_x, ctiles_x;        // split path: mu tiles (32 wide) and collision tiles (30 wide) per row
   Mrt mrt;                       // collision operator of the case
+  // compact schemes: order of the explicit Laplacian (4, 6, 8; 0 = not
+  // compact), line coefficients (row of c_lines), mu field (type P::Tm; the
+  // split path's mu), grad mu (P::Tm) and grad rho (P::Tc), 2 N each
+  int lap, lci;
+  void* cmu;
+  void* gmu;
+  void* grho;
 };
+
+// line coefficients of CFDS4, CFDS6, CFDS8, OCFDS4: [0] all PCR levels (FP64
+// lines), [1] the levels that move a float (FP32 lines)
+__constant__ LineCoef c_lines[2][4];
+
+__device__ __forceinline__ bool is_compact(int scheme) { return scheme >= S_CFDS4 && scheme <= S_OCFDS4; }
 
 struct Item {
   int c, tile;
@@ -115,7 +135,7 @@ __device__ void run_item(const CaseDev& cd, int tile, long long t, unsigned char
   aux.partials = nullptr;
   aux.rho_snap = cd.snap;
   FieldOut fo{nullptr, nullptr};
-  GradIn gi{nullptr, nullptr, nullptr};
+  GradIn gi{cd.gmu, cd.grho, cd.cmu};
   const Tf* fin = static_cast<const Tf*>(cd.f[par]);
   Tf* fout = static_cast<Tf*>(cd.f[par ^ 1]);
   const Tr* rin = static_cast<const Tr*>(cd.rho[par]);
@@ -133,33 +153,96 @@ __device__ void run_item(const CaseDev& cd, int tile, long long t, unsigned char
     LBM_ITEM_CASE(S_EFDS6)
     LBM_ITEM_CASE(S_E4)
     LBM_ITEM_CASE(S_E8)
-    default: break;
+    default:
+      if (is_compact(cd.scheme)) {  // derivatives from the line solves of this step
+        if (mode == MODE_STEP)
+          step2d_tile<S_CFDS4, P, TXB, TYB, MODE_STEP>(cd.kp, fin, fout, rin, rout, aux, fo, gi, cd.mrt, x0, y0, smem,
+                                                        partial);
+        else
+          step2d_tile<S_CFDS4, P, TXB, TYB, MODE_OBS>(cd.kp, fin, fout, rin, rout, aux, fo, gi, cd.mrt, x0, y0, smem,
+                                                       partial);
+      }
+      break;
   }
 #undef LBM_ITEM_CASE
 }
 
+// compact case: mu of one 32 x 8 tile (one node per thread of NT2)
+template <class P>
+__device__ void cmu_tile(const CaseDev& cd, int tile, long long t) {
+  using Tm = typename P::Tm;
+  using Tr = typename P::Tr;
+  const Tr* rin = static_cast<const Tr*>(cd.rho[int(t & 1)]);
+  const int x = (tile % cd.tiles_x) * TXB + int(threadIdx.x) % TXB;
+  const int y = (tile / cd.tiles_x) * TYB + int(threadIdx.x) / TXB;
+  if (x < cd.kp.nx && y < cd.kp.ny) {
+    const long long n = (long long)y * cd.kp.nx + x;
+    static_cast<Tm*>(cd.cmu)[n] = mu_field_node_order<Tm, Tr>(cd.lap, cd.kp, 2, P::DEV, rin, n);
+  }
+}
+
+// compact case: one group of lines (code = group * 4 + set; set = 2 axis +
+// field, field 0 mu -> grad mu, 1 rho -> grad rho) by a CTA of NTH threads
+template <int NTH, class P>
+__device__ void line_item(const CaseDev& cd, int code, long long t, int lpb, int lpb_shift, unsigned char* smem) {
+  using Tm = typename P::Tm;
+  using Tr = typename P::Tr;
+  using Tc = typename P::Tc;
+  const int set = code & 3, grp = code >> 2, axis = set >> 1;
+  const long long N = cd.kp.n;
+  const int nx = cd.kp.nx, ny = cd.kp.ny;
+  if ((set & 1) == 0) {
+    lines_block<NTH, Tm, Tm>(axis, nx, ny, 1, static_cast<const Tm*>(cd.cmu), static_cast<Tm*>(cd.gmu) + axis * N,
+                             c_lines[sizeof(Tm) == 4][cd.lci], lpb, lpb_shift, grp, smem);
+  } else {
+    lines_block<NTH, Tr, Tc>(axis, nx, ny, 1, static_cast<const Tr*>(cd.rho[int(t & 1)]),
+                             static_cast<Tc*>(cd.grho) + axis * N, c_lines[sizeof(Tc) == 4][cd.lci], lpb, lpb_shift,
+                             grp, smem);
+  }
+}
+
+// Every step: [mu tiles of the compact cases] -> [their line groups] -> the
+// step items of all cases, each phase followed by the bounded barrier.  Phase
+// k of a launch counts on work[k % 4]; block 0 zeroes work[(k + 2) % 4], last
+// used two phases back, before it arrives at the phase's barrier (the launch
+// starts from zeroed counters).
 template <class P>
 __global__ void __launch_bounds__(NT2) k_batch_persistent(const CaseDev* __restrict__ cases,
                                                           const Item* __restrict__ items, int nitems, int nsteps,
-                                                          BatchCtl* ctl, unsigned long long timeout_ns) {
+                                                          BatchCtl* ctl, unsigned long long timeout_ns,
+                                                          const Item* __restrict__ cmu_items, int ncmu,
+                                                          const Item* __restrict__ line_items, int nline, int lpb,
+                                                          int lpb_shift) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   const long long t0 = *((volatile long long*)&ctl->t);
-  for (int s = 0; s < nsteps; ++s) {
-    const long long t = t0 + s;
+  int k = 0;  // phase of the launch
+  // items of one phase, fetched one at a time by the CTAs; false if the
+  // barrier after it failed
+  auto phase = [&](const Item* its, int n, auto&& fn) {
+    unsigned* ctr = &ctl->work[k & 3];
     for (;;) {
-      if (threadIdx.x == 0) s_item = int(atomicAdd(&ctl->work[s & 1], 1u));
+      if (threadIdx.x == 0) s_item = int(atomicAdd(ctr, 1u));
       __syncthreads();
       const int it = s_item;
       __syncthreads();
-      if (it >= nitems) break;
-      const Item itm = items[it];
-      run_item<P>(cases[itm.c], itm.tile, t, smem, MODE_STEP, nullptr);
+      if (it >= n) break;
+      fn(its[it]);
       __syncthreads();
     }
-    // the counter of the next step was last used two steps ago: reset it
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[(s + 1) & 1] = 0u;
-    if (!grid_barrier(ctl, timeout_ns)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[(k + 2) & 3] = 0u;
+    ++k;
+    return grid_barrier(ctl, timeout_ns);
+  };
+  for (int s = 0; s < nsteps; ++s) {
+    const long long t = t0 + s;
+    if (ncmu > 0 && !phase(cmu_items, ncmu, [&](const Item& itm) { cmu_tile<P>(cases[itm.c], itm.tile, t); })) return;
+    if (nline > 0 && !phase(line_items, nline, [&](const Item& itm) {
+          line_item<NT2, P>(cases[itm.c], itm.tile, t, lpb, lpb_shift, smem);
+        }))
+      return;
+    if (!phase(items, nitems, [&](const Item& itm) { run_item<P>(cases[itm.c], itm.tile, t, smem, MODE_STEP, nullptr); }))
+      return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t = t0 + nsteps;
 }
@@ -182,7 +265,11 @@ __device__ void coll_load(const CaseDev& cd, int tile, long long t, unsigned cha
     case S_EFDS6: coll2d_load<S_EFDS6, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
     case S_E4: coll2d_load<S_E4, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
     case S_E8: coll2d_load<S_E8, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf); break;
-    default: break;
+    default:
+      if (is_compact(cd.scheme))
+        coll2d_load<S_CFDS4, RPT>(cd.kp, fin, rin, cd.mu, x0, y0, buf, static_cast<const float*>(cd.gmu),
+                                  static_cast<const float*>(cd.grho));
+      break;
   }
 }
 
@@ -200,7 +287,18 @@ __device__ void mu_unit(const CaseDev& cd, int tile, int part, long long t, int 
     case S_EFDS6: mu2d_rows<S_EFDS6>(cd.kp, rin, cd.mu, x0, y0, lane); break;
     case S_E4: mu2d_rows<S_E4>(cd.kp, rin, cd.mu, x0, y0, lane); break;
     case S_E8: mu2d_rows<S_E8>(cd.kp, rin, cd.mu, x0, y0, lane); break;
-    default: break;
+    default:
+      if (is_compact(cd.scheme)) {
+        // the compact scheme's chemical potential, node by node as in the
+        // single-case path (explicit Laplacian of the scheme's order)
+        const int gx = x0 + lane;
+        if (gx >= cd.kp.nx) break;
+        for (int r = 0; r < MU_UNIT_ROWS && y0 + r < cd.kp.ny; ++r) {
+          const long long n = (long long)(y0 + r) * cd.kp.nx + gx;
+          cd.mu[n] = mu_field_node_order<float, float>(cd.lap, cd.kp, 2, true, rin, n);
+        }
+      }
+      break;
   }
 }
 
@@ -223,7 +321,12 @@ __device__ void coll_compute(const CaseDev& cd, int tile, long long t, unsigned 
     LBM_SPLIT_CASE(S_EFDS6)
     LBM_SPLIT_CASE(S_E4)
     LBM_SPLIT_CASE(S_E8)
-    default: break;
+    default:
+      if (is_compact(cd.scheme)) {
+        if (tau1) coll2d_compute<S_CFDS4, true, RPT>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf, cd.mrt);
+        else coll2d_compute<S_CFDS4, false, RPT>(cd.kp, fout, rout, cd.bad, t, x0, y0, buf, cd.mrt);
+      }
+      break;
   }
 #undef LBM_SPLIT_CASE
 }
@@ -283,20 +386,35 @@ template <int RPT>  // rows per thread of the tiles (1, 2, 4)
 __global__ void __launch_bounds__(NT2S, RPT >= 4 ? 1 : 2) k_batch_split(const CaseDev* __restrict__ cases,
                                                       const Item* __restrict__ mitems, int nmu,
                                                       const Item* __restrict__ citems, int ncoll, int nsteps,
-                                                      BatchCtl* ctl, unsigned long long timeout_ns, int buf_bytes) {
+                                                      BatchCtl* ctl, unsigned long long timeout_ns, int buf_bytes,
+                                                      const Item* __restrict__ litems, int nline, int lpb,
+                                                      int lpb_shift) {
   static_assert(NBUF == 2, "one item in flight: the claim queue has two slots");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_q[2];
   __shared__ Claims s_cl[NT2S / 32];  // in shared memory: registers are at the cap
   const long long t0 = *((volatile long long*)&ctl->t);
+  int k = 0;  // phase of the launch: mu, [lines,] collision per step
   for (int s = 0; s < nsteps; ++s) {
     const long long t = t0 + s;
-    for (int phase = 0; phase < 2; ++phase) {
-      const Item* items = phase == 0 ? mitems : citems;
-      const int nitems = phase == 0 ? nmu : ncoll;
-      const int k = 2 * s + phase;
+    for (int phase = 0; phase < 3; ++phase) {
+      if (phase == 1 && nline == 0) continue;
+      const Item* items = phase == 0 ? mitems : (phase == 1 ? litems : citems);
+      const int nitems = phase == 0 ? nmu : (phase == 1 ? nline : ncoll);
       unsigned* ctr = &ctl->work[k & 3];
-      if (phase == 0) {
+      if (phase == 1) {
+        // line groups of the compact cases, one at a time per CTA
+        for (;;) {
+          if (threadIdx.x == 0) s_q[0] = int(atomicAdd(ctr, 1u));
+          __syncthreads();
+          const int it = s_q[0];
+          __syncthreads();
+          if (it >= nitems) break;
+          const Item itm = items[it];
+          line_item<NT2S, PrecF32>(cases[itm.c], itm.tile, t, lpb, lpb_shift, smem);
+          __syncthreads();
+        }
+      } else if (phase == 0) {
         // mu: each warp claims units of MU_UNIT_ROWS rows of a mu tile and
         // reads their stencils with cached global loads; no staging, no CTA barrier
         constexpr int UPI = Tile2<RPT>::M2Y / MU_UNIT_ROWS;
@@ -349,10 +467,27 @@ __global__ void __launch_bounds__(NT2S, RPT >= 4 ? 1 : 2) k_batch_split(const Ca
         cpa_wait_all();
       }
       if (blockIdx.x == 0 && threadIdx.x == 0) ctl->work[(k + 2) & 3] = 0u;
+      ++k;
       if (!grid_barrier(ctl, timeout_ns)) return;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t = t0 + nsteps;
+}
+
+// derivative fields of the compact cases for the current state (before an
+// observation pass): mu tiles, then line groups, one CTA per item
+template <class P>
+__global__ void __launch_bounds__(NT2) k_batch_cmu(const CaseDev* __restrict__ cases, const Item* __restrict__ items,
+                                                   const BatchCtl* ctl) {
+  const Item itm = items[blockIdx.x];
+  cmu_tile<P>(cases[itm.c], itm.tile, ctl->t);
+}
+template <class P>
+__global__ void __launch_bounds__(NT2) k_batch_clines(const CaseDev* __restrict__ cases, const Item* __restrict__ items,
+                                                      const BatchCtl* ctl, int lpb, int lpb_shift) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Item itm = items[blockIdx.x];
+  line_item<NT2, P>(cases[itm.c], itm.tile, ctl->t, lpb, lpb_shift, smem);
 }
 
 // observation pass: one CTA per work item (not persistent)
@@ -418,7 +553,8 @@ __global__ void k_batch_snap(const CaseDev* __restrict__ cases, const BatchCtl* 
 
 template <class P>
 size_t batch_smem() {
-  size_t m = Step2DShape<S_EFDS2, P, TXB, TYB>::bytes;
+  size_t m = Step2DShape<S_CFDS4, P, TXB, TYB>::bytes;
+  m = std::max(m, Step2DShape<S_EFDS2, P, TXB, TYB>::bytes);
   m = std::max(m, Step2DShape<S_EFDS4, P, TXB, TYB>::bytes);
   m = std::max(m, Step2DShape<S_EFDS6, P, TXB, TYB>::bytes);
   m = std::max(m, Step2DShape<S_E4, P, TXB, TYB>::bytes);
@@ -456,8 +592,42 @@ struct lbm_batch {
   int rpt = 0;        // split kernel: tile rows per thread (1, 2, 4)
   int item_cap = 0;   // capacity of d_mitems and of d_citems
   std::vector<int> case_order;  // split path: cases in work-list order
+  // compact-scheme cases: their mu tiles (TXB x TYB), their line groups
+  // (rebuilt with the group size lpb of the tile shape), longest line
+  bool compact = false;
+  Item* d_cmu = nullptr;
+  int ncmu = 0;
+  Item* d_litems = nullptr;
+  int nline = 0, line_cap = 0, lpb = 8, lpb_shift = 3, lmax = 0;
   std::vector<std::pair<void*, size_t>> blocks;
 };
+
+// line groups of the compact cases for groups of lpb lines: code = group * 4
+// + 2 axis + field (field 0: mu, 1: rho)
+static int build_line_items(lbm_batch* b, int lpb) {
+  int sh = 0;
+  while ((1 << sh) < lpb) ++sh;
+  std::vector<Item> li;
+  for (const int c : b->case_order) {
+    const CaseDev& cd = b->host_cases[c];
+    if (!cd.lap) continue;
+    for (int axis = 0; axis < 2; ++axis) {
+      const int lines = axis == 0 ? b->p[c].ny : b->p[c].nx;
+      const int groups = (lines + lpb - 1) / lpb;
+      for (int g = 0; g < groups; ++g)
+        for (int field = 0; field < 2; ++field) li.push_back({c, g * 4 + 2 * axis + field});
+    }
+  }
+  if (int(li.size()) > b->line_cap) return LBM_ECUDA;
+  if (!li.empty() && cudaMemcpyAsync(b->d_litems, li.data(), sizeof(Item) * li.size(), cudaMemcpyHostToDevice,
+                                     b->stream) != cudaSuccess)
+    return LBM_ECUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBM_ECUDA;
+  b->nline = int(li.size());
+  b->lpb = lpb;
+  b->lpb_shift = sh;
+  return LBM_OK;
+}
 
 static void* balloc(lbm_batch* b, size_t bytes) {
   void* p = b->alloc.alloc(bytes ? bytes : 256, b->alloc.ctx);
@@ -503,6 +673,14 @@ static int setup_split_t(lbm_batch* b) {
   m = std::max(m, Split2DShape<S_EFDS6, RPT>::bytes);
   m = std::max(m, Split2DShape<S_E4, RPT>::bytes);
   m = std::max(m, Split2DShape<S_E8, RPT>::bytes);
+  if (b->compact) m = std::max(m, Split2DShape<S_CFDS4, RPT>::bytes);
+  // compact cases: groups of up to 16 lines (one per warp) whose two float
+  // line buffers fit the items' shared memory
+  int lpb = 16;
+  if (b->compact) {
+    while (lpb > 1 && size_t(2) * lpb * (b->lmax + 1) * 4 > NBUF * m) lpb /= 2;
+    m = std::max(m, (size_t(2) * lpb * (b->lmax + 1) * 4 + NBUF - 1) / NBUF);
+  }
   const int buf = int((m + 15) / 16 * 16);
   const size_t smem = NBUF * size_t(buf);  // items in flight
   int dev = 0, sms = 0, ps = 0;
@@ -511,6 +689,7 @@ static int setup_split_t(lbm_batch* b) {
   if (cudaFuncSetAttribute(k_batch_split<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_batch_split<RPT>, NT2S, smem) != cudaSuccess || ps < 1)
     return LBM_ENOTSUP;
+  if (b->compact && build_line_items(b, lpb) != LBM_OK) return LBM_ECUDA;
   b->nmu = int(mitems.size());
   b->ncoll = int(citems.size());
   b->buf_split = buf;
@@ -543,9 +722,7 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     if (!(q.a > 0 && q.b > 0 && q.R > 0 && q.Tr > 0 && q.k > 0 && q.kappa >= 0 && q.tau > 0.5)) return LBM_EINVAL;
     if (q.precision != prec0 || q.mu_fp64 != mu0 || (q.precision != LBM_FP64 && q.precision != LBM_FP32DEV))
       return LBM_EINVAL;
-    if (!(q.scheme == LBM_EFDS2 || q.scheme == LBM_EFDS4 || q.scheme == LBM_EFDS6 || q.scheme == LBM_E4 ||
-          q.scheme == LBM_E8))
-      return LBM_ENOTSUP;
+    if (q.scheme < LBM_EFDS2 || q.scheme > LBM_E8) return LBM_EINVAL;
     if (q.collision != LBM_BGK && q.collision != LBM_MRT) return LBM_EINVAL;
     if (q.eos < LBM_EOS_CS || q.eos > LBM_EOS_RKS) return LBM_EINVAL;
   }
@@ -566,8 +743,11 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     if (cases[x].scheme != cases[y].scheme) return cases[x].scheme < cases[y].scheme;
     return (long long)cases[x].nx * cases[x].ny > (long long)cases[y].nx * cases[y].ny;
   });
-  std::vector<Item> items;
+  std::vector<Item> items, cmu_items;
   const size_t fs = prec0 == LBM_FP64 ? 8 : 4;
+  // compact cases: mu type (float only in FP32DEV with FP32 mu), gradient types
+  const size_t tm = (prec0 == LBM_FP32DEV && !mu0) ? 4 : 8, tc = prec0 == LBM_FP64 ? 8 : 4;
+  long long line_cap = 0;
   bool ok = true;
   for (int k = 0; k < n && ok; ++k) {
     const int c = idx[k];
@@ -594,14 +774,50 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     cd.ctiles_x = (q.nx + T2X - 1) / T2X;
     if (prec0 == LBM_FP32DEV && !mu0) cd.mu = static_cast<float*>(balloc(b, size_t(N) * 4));
     ok = cd.f[0] && cd.f[1] && cd.rho[0] && cd.rho[1] && cd.snap && cd.bad && (cd.mu || prec0 != LBM_FP32DEV || mu0);
+    cd.lap = cd.lci = 0;
+    cd.cmu = cd.gmu = cd.grho = nullptr;
+    if (ok && q.scheme >= LBM_CFDS4 && q.scheme <= LBM_OCFDS4) {
+      b->compact = true;
+      cd.lap = q.scheme == LBM_CFDS6 ? 6 : (q.scheme == LBM_CFDS8 ? 8 : 4);
+      cd.lci = q.scheme - LBM_CFDS4;
+      cd.cmu = cd.mu ? static_cast<void*>(cd.mu) : balloc(b, size_t(N) * tm);
+      cd.gmu = balloc(b, size_t(2) * N * tm);
+      cd.grho = balloc(b, size_t(2) * N * tc);
+      ok = cd.cmu && cd.gmu && cd.grho;
+      for (int tl = cd.item_begin; tl < cd.item_end; ++tl) cmu_items.push_back(items[tl]);
+      line_cap += 2LL * (q.nx + q.ny);
+      b->lmax = std::max(b->lmax, std::max(q.nx, q.ny));
+    }
   }
   if (!ok) { lbm_batch_destroy(b); return LBM_ENOMEM; }
   b->nitems = int(items.size());
   b->split = prec0 == LBM_FP32DEV && !mu0;
+  b->case_order.assign(idx.begin(), idx.end());
+  if (b->compact) {
+    // the line coefficients of the four compact schemes (the same for every batch)
+    LineCoef lc[2][4];
+    for (int j = 0; j < 4; ++j) {
+      const LineCoef full = make_line_coef(S_CFDS4 + j);
+      lc[0][j] = line_coef_for(full, false);
+      lc[1][j] = line_coef_for(full, true);
+    }
+    b->ncmu = int(cmu_items.size());
+    b->line_cap = int(line_cap);
+    b->d_cmu = static_cast<Item*>(balloc(b, sizeof(Item) * cmu_items.size()));
+    b->d_litems = static_cast<Item*>(balloc(b, sizeof(Item) * line_cap));
+    if (!b->d_cmu || !b->d_litems ||
+        cudaMemcpyToSymbolAsync(c_lines, lc, sizeof(lc), 0, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_cmu, cmu_items.data(), sizeof(Item) * cmu_items.size(), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess) {
+      lbm_batch_destroy(b);
+      return LBM_ECUDA;
+    }
+    // the persistent kernel of FP64 (and FP64-mu) batches: groups of 8 lines
+    if (!b->split && build_line_items(b, 8) != LBM_OK) { lbm_batch_destroy(b); return LBM_ECUDA; }
+  }
   if (b->split) {
     // work lists are rebuilt per tile shape; the shortest tiles (one row per
     // thread) give the longest lists
-    b->case_order.assign(idx.begin(), idx.end());
     long long cap = 0;
     for (int k = 0; k < n; ++k) {
       const int c = idx[k];
@@ -634,11 +850,13 @@ extern "C" int lbm_batch_create(const lbm_params* cases, int n, void* stream, co
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT2, smem);
   };
-  if (b->prec == 0) { b->smem = batch_smem<PrecF64>(); setup(k_batch_persistent<PrecF64>, b->smem);
+  // line groups of 8 lines of 8-byte values beside the step tiles (compact cases)
+  const size_t line_bytes = b->compact ? size_t(2) * 8 * (b->lmax + 1) * 8 : 0;
+  if (b->prec == 0) { b->smem = std::max(batch_smem<PrecF64>(), line_bytes); setup(k_batch_persistent<PrecF64>, b->smem);
                       cudaFuncSetAttribute(k_batch_obs<PrecF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)); }
-  else if (b->prec == 1) { b->smem = batch_smem<PrecF32>(); setup(k_batch_persistent<PrecF32>, b->smem);
+  else if (b->prec == 1) { b->smem = std::max(batch_smem<PrecF32>(), line_bytes); setup(k_batch_persistent<PrecF32>, b->smem);
                            cudaFuncSetAttribute(k_batch_obs<PrecF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)); }
-  else { b->smem = batch_smem<PrecF32M64>(); setup(k_batch_persistent<PrecF32M64>, b->smem);
+  else { b->smem = std::max(batch_smem<PrecF32M64>(), line_bytes); setup(k_batch_persistent<PrecF32M64>, b->smem);
          cudaFuncSetAttribute(k_batch_obs<PrecF32M64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)); }
   b->grid = std::max(1, std::min(per_sm * sms, b->nitems));
   if (b->split && e == cudaSuccess && setup_split(b, RPT_DEFAULT) != LBM_OK) {
@@ -728,7 +946,8 @@ static cudaError_t launch_persistent(lbm_batch* b, int nsteps) {
     cs.numAttrs = 1;
     auto kern = b->rpt == 1 ? k_batch_split<1> : (b->rpt == 4 ? k_batch_split<4> : k_batch_split<2>);
     return cudaLaunchKernelEx(&cs, kern, (const CaseDev*)b->d_cases, (const Item*)b->d_mitems, b->nmu,
-                              (const Item*)b->d_citems, b->ncoll, nsteps, b->ctl, timeout_ns, b->buf_split);
+                              (const Item*)b->d_citems, b->ncoll, nsteps, b->ctl, timeout_ns, b->buf_split,
+                              (const Item*)b->d_litems, b->nline, b->lpb, b->lpb_shift);
   }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(unsigned(b->grid));
@@ -740,14 +959,16 @@ static cudaError_t launch_persistent(lbm_batch* b, int nsteps) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const Item* cmu = b->d_cmu;
+  const Item* li = b->d_litems;
   if (b->prec == 0)
     return cudaLaunchKernelEx(&cfg, k_batch_persistent<PrecF64>, (const CaseDev*)b->d_cases, (const Item*)b->d_items,
-                              b->nitems, nsteps, b->ctl, timeout_ns);
+                              b->nitems, nsteps, b->ctl, timeout_ns, cmu, b->ncmu, li, b->nline, b->lpb, b->lpb_shift);
   if (b->prec == 1)
     return cudaLaunchKernelEx(&cfg, k_batch_persistent<PrecF32>, (const CaseDev*)b->d_cases, (const Item*)b->d_items,
-                              b->nitems, nsteps, b->ctl, timeout_ns);
+                              b->nitems, nsteps, b->ctl, timeout_ns, cmu, b->ncmu, li, b->nline, b->lpb, b->lpb_shift);
   return cudaLaunchKernelEx(&cfg, k_batch_persistent<PrecF32M64>, (const CaseDev*)b->d_cases, (const Item*)b->d_items,
-                            b->nitems, nsteps, b->ctl, timeout_ns);
+                            b->nitems, nsteps, b->ctl, timeout_ns, cmu, b->ncmu, li, b->nline, b->lpb, b->lpb_shift);
 }
 
 // n steps = one persistent launch (preceded by the reset of the barrier and
@@ -825,9 +1046,23 @@ extern "C" int lbm_batch_autotune(lbm_batch* b, int steps, int* rows_out) {
   return LBM_OK;
 }
 
+// compact cases: mu and derivative fields of the current state
+template <class P>
+static cudaError_t compact_fields(lbm_batch* b) {
+  if (!b->compact) return cudaSuccess;
+  const size_t lb = size_t(2) * b->lpb * (b->lmax + 1) * 8;
+  if (cudaError_t e = ensure_smem(k_batch_clines<P>, lb); e != cudaSuccess) return e;
+  if (b->ncmu > 0) k_batch_cmu<P><<<b->ncmu, NT2, 0, b->stream>>>(b->d_cases, b->d_cmu, b->ctl);
+  if (b->nline > 0)
+    k_batch_clines<P><<<b->nline, NT2, lb, b->stream>>>(b->d_cases, b->d_litems, b->ctl, b->lpb, b->lpb_shift);
+  return cudaGetLastError();
+}
+
 extern "C" int lbm_batch_observables(lbm_batch* b, lbm_obs* out) {
   if (!b || !out) return LBM_EINVAL;
-  cudaError_t e;
+  cudaError_t e = b->prec == 0 ? compact_fields<PrecF64>(b)
+                               : (b->prec == 1 ? compact_fields<PrecF32>(b) : compact_fields<PrecF32M64>(b));
+  if (e != cudaSuccess) return LBM_ECUDA;
   if (b->prec == 0) k_batch_obs<PrecF64><<<b->nitems, NT2, b->smem, b->stream>>>(b->d_cases, b->d_items, b->ctl, b->d_partials);
   else if (b->prec == 1) k_batch_obs<PrecF32><<<b->nitems, NT2, b->smem, b->stream>>>(b->d_cases, b->d_items, b->ctl, b->d_partials);
   else k_batch_obs<PrecF32M64><<<b->nitems, NT2, b->smem, b->stream>>>(b->d_cases, b->d_items, b->ctl, b->d_partials);
@@ -891,7 +1126,7 @@ extern "C" int lbm_batch_inject_stall(lbm_batch* b, int cta) {
 extern "C" int lbm_batch_size(const lbm_batch* b, int* ncases, int* nitems, int* grid) {
   if (!b) return LBM_EINVAL;
   if (ncases) *ncases = b->n;
-  if (nitems) *nitems = b->split ? b->nmu + b->ncoll : b->nitems;
+  if (nitems) *nitems = (b->split ? b->nmu + b->ncoll : b->nitems + b->ncmu) + b->nline;
   if (grid) *grid = b->split ? b->grid_split : b->grid;
   return LBM_OK;
 }

@@ -38,8 +38,12 @@ struct Split2DShape {
   static constexpr int MW = M2X + 2 * R, MH = M2Y + 2 * R;      // mu pass: density region
   static constexpr int GW = C2X + 2 * R, GH = C2Y + 2 * R;      // collision: field region
   static constexpr size_t mu_bytes = size_t(MW) * MH * 4;
-  static constexpr size_t off_mu = size_t(GW) * GH * 4;
-  static constexpr size_t off_f = (off_mu + size_t(GW) * GH * 4 + 15) / 16 * 16;
+  // compact schemes (GF): per collided node its density deviation (at 0) and
+  // its four derivative values d_x mu, d_y mu, d_x rho, d_y rho (at off_mu,
+  // component-major) instead of the two halo regions
+  static constexpr bool GF = Sch<S>::GF;
+  static constexpr size_t off_mu = GF ? size_t(C2N) * 4 : size_t(GW) * GH * 4;
+  static constexpr size_t off_f = GF ? size_t(5) * C2N * 4 : (off_mu + size_t(GW) * GH * 4 + 15) / 16 * 16;
   static constexpr size_t coll_bytes = off_f + size_t(9) * C2N * 4;
   static constexpr size_t bytes = coll_bytes > mu_bytes ? coll_bytes : mu_bytes;
 };
@@ -89,10 +93,13 @@ __device__ __forceinline__ void mu2d_compute(const KParams& p, float* __restrict
   }
 }
 
+// S a compact scheme (GF): gmu and grho are the derivative fields of the line
+// solves (component-major, 2 N each); muf is not read.
 template <int S, int RPT>
 __device__ __forceinline__ void coll2d_load(const KParams& p, const float* __restrict__ fin,
                                             const float* __restrict__ rin, const float* __restrict__ muf, int x0,
-                                            int y0, unsigned char* smem) {
+                                            int y0, unsigned char* smem, const float* gmu = nullptr,
+                                            const float* grho = nullptr) {
   [[maybe_unused]] constexpr int M2Y = Tile2<RPT>::M2Y, C2Y = Tile2<RPT>::C2Y, T2Y = Tile2<RPT>::T2Y, C2N = Tile2<RPT>::C2N;
   using Sh = Split2DShape<S, RPT>;
   constexpr int Q = 9, R = Sh::R, GW = Sh::GW, GH = Sh::GH;
@@ -107,14 +114,25 @@ __device__ __forceinline__ void coll2d_load(const KParams& p, const float* __res
     const int node = tid + r * NT2S;  // region rows w and w + 16 of warp w
     const int cy = node / C2X, cx = node - cy * C2X;
     if (cx - 1 <= VW && cy - 1 <= VH) {  // collided node: stage its populations
-      const float* fs = fin + wrapi(y0 + cy - 1, ny) * nx + wrapi(x0 + cx - 1, nx);
+      const int g = wrapi(y0 + cy - 1, ny) * nx + wrapi(x0 + cx - 1, nx);
+      const float* fs = fin + g;
 #pragma unroll
       for (int i = 0; i < Q; ++i) cpa4(s_f + i * C2N + node, fs + i * N);
+      if constexpr (Sch<S>::GF) {
+        // its density deviation and derivative values
+        cpa4(s_ds + node, rin + g);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          cpa4(s_mu + a * C2N + node, gmu + a * N + g);
+          cpa4(s_mu + (2 + a) * C2N + node, grho + a * N + g);
+        }
+      }
     }
   }
+  if constexpr (Sch<S>::GF) return;
   // fields: warp w copies rows w, w + 16, ...; lane l columns l and 32 + l
   // (the region of a ragged tile only as far as its collided nodes reach)
-  static_assert(GW <= 64 && GW > 32, "two columns per lane");
+  static_assert(Sch<S>::GF || (GW <= 64 && GW > 32), "two columns per lane");
   const int lane = tid & 31, warp = tid >> 5;
   const int xa = wrapi(x0 - 1 - R + lane, nx);
   const bool two = lane + 32 < GW && lane + 32 < VW + 2 + 2 * R;
@@ -170,8 +188,15 @@ __device__ __forceinline__ void coll2d_compute(const KParams& p, float* __restri
     const float irc = __fdividef(1.f, rc);
     const float ux = jx * irc, uy = jy * irc;
     float gmx, gmy, grx, gry;
-    grad2d<S, float>(s_mu, GW, cx + R, cy + R, gmx, gmy);
-    grad2d<S, float>(s_ds, GW, cx + R, cy + R, grx, gry);
+    if constexpr (Sch<S>::GF) {
+      gmx = s_mu[node];
+      gmy = s_mu[C2N + node];
+      grx = s_mu[2 * C2N + node];
+      gry = s_mu[3 * C2N + node];
+    } else {
+      grad2d<S, float>(s_mu, GW, cx + R, cy + R, gmx, gmy);
+      grad2d<S, float>(s_ds, GW, cx + R, cy + R, grx, gry);
+    }
     const float Fx = -rc * gmx + grx * (1.f / 3.f), Fy = -rc * gmy + gry * (1.f / 3.f);
     const float vx = ux + Fx * irc, vy = uy + Fy * irc;
     if (interior && !(rc > 0.f)) atomicMin(bad, (unsigned long long)t);

@@ -173,3 +173,77 @@ def test_many_cases_dealt_dynamically_match_single_runs(L):
         rs = s.lbm_get_density()
         assert np.max(np.abs(dens[2][i] - rs)) / np.max(rs) < 1e-6, c
         s.close()
+
+
+# compact schemes (Eq. 21-24; OCFDS4 of Sec. 3.1) inside the persistent launch:
+# mu field, line solves for grad mu and grad rho along x and y as work items,
+# then the collision reading the derivative fields, each phase behind the
+# bounded barrier; mixed with an explicit case and uneven, ragged sizes
+COMPACT = [dict(nx=64, ny=48, Tr=0.8, k=0.25, scheme="OCFDS4", r=12.0),
+           dict(nx=40, ny=72, Tr=0.85, k=0.3, scheme="CFDS4", r=10.0),
+           dict(nx=96, ny=80, Tr=0.8, k=0.2, scheme="CFDS6", r=18.0),
+           dict(nx=36, ny=44, Tr=0.9, k=0.25, scheme="CFDS8", r=8.0),
+           dict(nx=48, ny=48, Tr=0.8, k=0.25, scheme="EFDS6", r=10.0)]
+
+
+def oracle_density(c, steps):
+    o = O.Sim(lattice=O.D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1, scheme=c["scheme"])
+    o.init_droplet(c["r"])
+    assert o.step(steps) == 0
+    return o.density(), o
+
+
+def test_batch_compact_fp64_matches_oracle(L):
+    b = L.Batch([params(L, c, 0) for c in COMPACT])
+    b.lbm_batch_init_droplets([c["r"] for c in COMPACT])
+    b.lbm_batch_step(15)
+    b.lbm_batch_step(10)  # a replay continues the run
+    rc, obs = b.lbm_batch_observables(raise_errors=False)
+    assert rc == 0
+    for i, c in enumerate(COMPACT):
+        ro, o = oracle_density(c, 25)
+        assert np.max(np.abs(b.lbm_batch_get_density(i) - ro)) / np.max(ro) < 1e-12, c
+        oo = o.observables()
+        assert obs[i]["status"] == 0
+        for key in ("max_v", "max_u", "mass", "rho_center", "rho_corner"):
+            assert obs[i][key] == pytest.approx(oo[key], rel=1e-10, abs=1e-300), (c, key)
+
+
+@pytest.mark.parametrize("mu_fp64", [0, 1])
+def test_batch_compact_fp32_matches_oracle_and_single_case(L, mu_fp64):
+    ps = [L.make_params(lattice=L.LBM_D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1,
+                        scheme=c["scheme"], precision=L.LBM_FP32DEV, mu_fp64=mu_fp64) for c in COMPACT]
+    b = L.Batch(ps)
+    b.lbm_batch_init_droplets([c["r"] for c in COMPACT])
+    b.lbm_batch_step(25)
+    rc, obs = b.lbm_batch_observables(raise_errors=False)
+    assert rc == 0
+    for i, c in enumerate(COMPACT):
+        ro, o = oracle_density(c, 25)
+        rl = O.maxwell_tr(c["Tr"])[1]
+        rb = b.lbm_batch_get_density(i)
+        assert np.max(np.abs(rb - ro)) / rl < 1e-5, c
+        s = L.Sim(ps[i])
+        s.lbm_init_droplet(c["r"])
+        s.lbm_step(25)
+        rs = s.lbm_get_density()
+        assert np.max(np.abs(rb - rs)) / np.max(rs) < 1e-6, c
+        so = s.lbm_observables()
+        for key in ("max_v", "max_u", "mass", "rho_center", "rho_corner"):
+            assert obs[i][key] == pytest.approx(so[key], rel=1e-3), (c, key)
+        s.close()
+
+
+def test_batch_compact_tile_shapes_identical(L):
+    dens = {}
+    ps = [params(L, c, 1) for c in COMPACT]
+    for rows in (1, 2, 4):
+        b = L.Batch(ps)
+        b.lbm_batch_set_tiles(rows)
+        b.lbm_batch_init_droplets([c["r"] for c in COMPACT])
+        b.lbm_batch_step(20)
+        dens[rows] = [b.lbm_batch_get_density(i) for i in range(len(COMPACT))]
+        b.close()
+    for rows in (1, 4):
+        for a, d in zip(dens[rows], dens[2]):
+            assert np.array_equal(a, d), rows
