@@ -161,14 +161,17 @@ def oracle_sample(steps, n=SAMPLE_N):
     return n ** 3 * steps / dt / 1e6, dt
 
 
-def batch_cases(n=512, seed=2205):
+SWEEP_SCHEMES = ["EFDS2", "EFDS4", "EFDS6", "E4", "E8", "OCFDS4"]
+
+
+def batch_cases(n=512, seed=2205, schemes=None):
     """Seeded sweep of D2Q9 droplets: sizes uniform in {64..512}^2, radius uniform
     in [8, L/4], T_r uniform in [0.2, 0.95], k log-uniform in [0.1, 0.4], scheme
     uniform over the sweep set: second-, fourth- and sixth-order central,
     isotropic E4 and E8, and the optimised compact OCFDS4 (Sec. 3.1)."""
     import numpy as np
     rng = np.random.default_rng(seed)
-    schemes = ["EFDS2", "EFDS4", "EFDS6", "E4", "E8", "OCFDS4"]
+    schemes = schemes or SWEEP_SCHEMES
     out = []
     for _ in range(n):
         lx, ly = int(rng.integers(64, 513)), int(rng.integers(64, 513))
@@ -180,12 +183,12 @@ def batch_cases(n=512, seed=2205):
     return out
 
 
-def run_batch(L, steps=50, warmup=10, ncases=512):
+def run_batch(L, steps=50, warmup=10, ncases=512, schemes=None):
     """ncases (512) D2Q9 droplets of uneven sizes in one persistent graph-captured
     launch per lbm_batch_step (FP32 deviation storage); returns MLUPS and case
     counts."""
     import torch
-    cases = batch_cases(ncases)
+    cases = batch_cases(ncases, schemes=schemes)
     params = [L.make_params(lattice=L.LBM_D2Q9, nx=c["nx"], ny=c["ny"], Tr=c["Tr"], k=c["k"], kappa=0.1,
                             scheme=c["scheme"], precision=L.LBM_FP32DEV) for c in cases]
     b = L.Batch(params)
@@ -484,14 +487,20 @@ def run_gpu(args):
         extra["d3q19_256_legs"] = run_cfg3_legs(L, zc, n=w["nx"])
     if not args.no_batch:
         extra["batch2d"] = run_batch(L, steps=args.batch_steps, ncases=args.batch_cases)
+        # the same seeded sweep over the explicit and isotropic schemes only
+        extra["batch2d_explicit"] = run_batch(L, steps=args.batch_steps, ncases=args.batch_cases,
+                                              schemes=SWEEP_SCHEMES[:5])
         extra["d2q9_512"] = run_2d(L)
         extra["d3q19_compact"] = run_compact(L)
     if not args.no_warmstart:
         from paper_2205_09186_gb300 import warmstart as W
-        # the plain arm (FP64 storage, tanh start) on the first 4 test cases
-        res, _ = W.experiment(n_train=32, n_test=12, n=80, tol=1e-7, iters=4000, plain=4)
-        res["device_s_ratio_cold_over_warm"] = (res["cold_device_s"] / res["warm_device_s"]
-                                                if res["warm_device_s"] else None)
+        # the plain arm (FP64 storage, tanh start) on the first 4 test cases;
+        # --warmstart-full: 64 held-out droplets on 192^3 lattices
+        if args.warmstart_full:
+            res, _ = W.experiment(n_train=32, n_test=64, n=192, tol=1e-10, iters=4000, plain=4, R=(30.0, 50.0),
+                                  max_steps=100000)
+        else:
+            res, _ = W.experiment(n_train=32, n_test=12, n=80, tol=1e-10, iters=4000, plain=4)
         extra["warmstart"] = res
     if rank != 0:
         if dist:
@@ -543,6 +552,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=50, help="steps per timed launch of the batched 2D sweep")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start experiment")
     ap.add_argument("--no-cfg3", action="store_true", help="skip the other-temperature and FP64-mu 256^3 legs")
+    ap.add_argument("--warmstart-full", action="store_true",
+                    help="the warm-start experiment at full size (64 held-out 192^3 droplets; tens of minutes)")
     ap.add_argument("--zchunk", type=int, default=0, help="fix the z-chunk instead of autotuning (profiling runs)")
     ap.add_argument("--size", type=int, default=256,
                     help="lattice edge (profiling runs only; the benchmark workload is 256)")

@@ -8,10 +8,9 @@
 
 namespace lbmd {
 
-__device__ __forceinline__ int lmod(long long a, int n) {
-  long long r = a % n;
-  return int(r < 0 ? r + n : r);
-}
+// a + d wrapped into [0, n) for |d| <= 4 < n (one period at most: a
+// compare and an add, not an integer division)
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // mu = k^2 psi'(rho) - kappa lap rho at node n, with the explicit central
 // second derivative of order LO along each axis (the compact scheme's
@@ -22,18 +21,19 @@ __device__ __forceinline__ Tm mu_field_node(const KParams& p, int D, bool dev, c
   const double l0 = LO == 4 ? -2.5 : (LO == 6 ? -49.0 / 18.0 : -205.0 / 72.0);
   const double lc[5] = {l0, LO == 4 ? 4.0 / 3.0 : (LO == 6 ? 1.5 : 1.6), LO == 4 ? -1.0 / 12.0 : (LO == 6 ? -0.15 : -0.2),
                         LO == 6 ? 1.0 / 90.0 : (LO == 8 ? 8.0 / 315.0 : 0.0), LO == 8 ? -1.0 / 560.0 : 0.0};
-  const int x = int(n % p.nx), y = int((n / p.nx) % p.ny), z = int(n / ((long long)p.nx * p.ny));
+  const long long nxy = (long long)p.nx * p.ny;
+  const int z = int(n / nxy);
+  const int rem = int(n - z * nxy), y = rem / p.nx, x = rem - y * p.nx;
   const Tm c0 = Tm(rho[n]);
   Tm lap = Tm(D * lc[0]) * c0;
+  const long long zo = z * nxy, row = zo + (long long)y * p.nx;
 #pragma unroll
   for (int m = 1; m <= R; ++m) {
-    const long long row = (long long)z * p.nx * p.ny + (long long)y * p.nx;
-    Tm s = Tm(rho[row + lmod(x + m, p.nx)]) + Tm(rho[row + lmod(x - m, p.nx)]);
-    s += Tm(rho[(long long)z * p.nx * p.ny + (long long)lmod(y + m, p.ny) * p.nx + x]) +
-         Tm(rho[(long long)z * p.nx * p.ny + (long long)lmod(y - m, p.ny) * p.nx + x]);
+    Tm s = Tm(rho[row + wrap1(x + m, p.nx)]) + Tm(rho[row + wrap1(x - m, p.nx)]);
+    s += Tm(rho[zo + (long long)wrap1(y + m, p.ny) * p.nx + x]) + Tm(rho[zo + (long long)wrap1(y - m, p.ny) * p.nx + x]);
     if (D == 3)
-      s += Tm(rho[(long long)lmod(z + m, p.nz) * p.nx * p.ny + (long long)y * p.nx + x]) +
-           Tm(rho[(long long)lmod(z - m, p.nz) * p.nx * p.ny + (long long)y * p.nx + x]);
+      s += Tm(rho[wrap1(z + m, p.nz) * nxy + (long long)y * p.nx + x]) +
+           Tm(rho[wrap1(z - m, p.nz) * nxy + (long long)y * p.nx + x]);
     lap += Tm(lc[m]) * s;
   }
   const Tm rfull = dev ? Tm(p.rho_ref) + Tm(rho[n]) : Tm(rho[n]);

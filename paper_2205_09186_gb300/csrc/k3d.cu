@@ -15,8 +15,10 @@ namespace lbmd {
 
 static int num_sms() { return device_sms(); }
 
+// FP32DEV with the FP32 chemical potential (prec 1) or with the EOS part of
+// it evaluated in FP64 (prec 2) in the mu pass; the collision pass is the same
 bool split3d_scheme(int scheme, int prec) {
-  return prec == 1 && (scheme == S_EFDS2 || scheme == S_EFDS4 || scheme == S_EFDS6);
+  return (prec == 1 || prec == 2) && (scheme == S_EFDS2 || scheme == S_EFDS4 || scheme == S_EFDS6);
 }
 
 // z-chunk for the split collision pass: last-wave balance against the
@@ -93,7 +95,7 @@ static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 
 
 
 // the mu pass: the vector kernel when rows are whole 16-byte chunks
-template <int S>
+template <int S, bool M64 = false>
 cudaError_t launch_mu(const Launch& c) {
   if (c.kp.nx % 4 == 0 && aligned16(c.rin) && aligned16(c.mu)) {
     // z chunks: enough CTAs for several waves, at least 8 planes per chunk
@@ -103,18 +105,18 @@ cudaError_t launch_mu(const Launch& c) {
                                                                     (c.kp.nz + 7) / 8)));
     const int zc = (c.kp.nz + nzc - 1) / nzc;
     dim3 g(gx, gy, (c.kp.nz + zc - 1) / zc);
-    k_mu3d_zm<S><<<g, MZT, MuZShape<S>::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin),
-                                                           static_cast<float*>(c.mu), zc);
+    k_mu3d_zm<S, M64><<<g, MZT, MuZShape<S>::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin),
+                                                                static_cast<float*>(c.mu), zc);
   } else {
     dim3 g((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
-    k_mu3d<S><<<g, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+    k_mu3d<S, M64><<<g, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
   }
   return cudaGetLastError();
 }
 
 // mu pass + collision pass (line schemes, FP32DEV, FP32 mu); with obs the
 // collision pass also reduces the observables of the state it advances
-template <int S, bool TAU1>
+template <int S, bool TAU1, bool M64 = false>
 cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   if (!c.mu) return cudaErrorInvalidValue;
   const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sch<S>::R, TYC, CollShape<S>::MINB);
@@ -126,7 +128,7 @@ cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   } else if (obs) {
     return cudaErrorInvalidValue;
   }
-  cudaError_t em = launch_mu<S>(c);
+  cudaError_t em = launch_mu<S, M64>(c);
   if (em != cudaSuccess) return em;
   if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
   // 16-byte copies need rows of whole chunks and aligned bases
@@ -137,9 +139,9 @@ cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
 }
 
 // observation pass of the split path: mu field, then the node-parallel reduction
-template <int S>
+template <int S, bool M64 = false>
 cudaError_t launch_obs_split(const Launch& c, int* nblocks) {
-  cudaError_t em = launch_mu<S>(c);
+  cudaError_t em = launch_mu<S, M64>(c);
   if (em != cudaSuccess) return em;
   // at most 8192 CTAs: the handle's partials buffer holds at least that many
   const int nb = int(std::min<long long>(std::min<long long>((long long)c.kp.ny * c.kp.nz, 8LL * num_sms()), 8192LL));
@@ -153,6 +155,17 @@ template <int S, class P>
 cudaError_t launch(const Launch& c, int mode, int* nblocks) {
   if constexpr (std::is_same<P, PrecF32>::value && !Sch<S>::ISO) {
     if (mode == MODE_OBS && c.mu) return launch_obs_split<S>(c, nblocks);
+  }
+  if constexpr (std::is_same<P, PrecF32M64>::value && !Sch<S>::ISO && !Sch<S>::GF) {
+    // line schemes with the FP64 EOS chemical potential: the split path
+    if (c.mu) {
+      if (mode == MODE_OBS) return launch_obs_split<S, true>(c, nblocks);
+      if (mode == MODE_STEP || mode == MODE_STEP_OBS) {
+        const bool obs = mode == MODE_STEP_OBS;
+        return c.kp.omega == 1.0 ? launch_split<S, true, true>(c, nblocks, obs)
+                                 : launch_split<S, false, true>(c, nblocks, obs);
+      }
+    }
   }
   if constexpr (std::is_same<P, PrecF32>::value) {
     if (mode == MODE_STEP || mode == MODE_STEP_OBS) {

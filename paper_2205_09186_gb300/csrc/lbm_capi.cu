@@ -613,7 +613,7 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
   }
   // tensor maps of both population buffers for the D3Q19 FP32DEV collision
   // pass's copies (split explicit schemes and compact schemes)
-  if (ok && h->D == 3 && h->prec == 1)
+  if (ok && h->D == 3 && (h->prec == 1 || h->prec == 2))
     h->has_tmap = make_coll3d_tmap(h->f[0], h->kp, h->tmap[0]) && make_coll3d_tmap(h->f[1], h->kp, h->tmap[1]);
   if (ok && h->compact) {
     rc = compact_alloc(h->cb, h->kp, h->D, params->scheme, h->prec, [&](size_t b) { return dalloc(h, b); });
@@ -791,7 +791,7 @@ static cudaError_t run_pass(lbm_handle* h, const Launch& c, int mode, int* nb) {
 }
 
 static bool tunable(const lbm_handle* h) {
-  return h->D == 3 && h->prec == 1 && !h->compact && !h->layer &&
+  return h->D == 3 && (h->prec == 1 || (h->prec == 2 && h->mu)) && !h->compact && !h->layer &&
          (h->p.scheme == LBM_EFDS2 || h->p.scheme == LBM_EFDS4 || h->p.scheme == LBM_EFDS6 || h->p.scheme == LBM_E4);
 }
 

@@ -16,8 +16,20 @@ namespace lbmd {
 // through the 8 planes with the z neighbours in a register queue.
 constexpr int MUX = 32, MUY = 8, MUZ = 8, MUT = MUX * MUY;
 
+// M64: the EOS chemical potential k^2 psi'(rho) evaluated in FP64 from
+// rho = rho_ref + deviation (FP64 division and logarithm), the Laplacian term
+// in FP32 as with M64 off, the sum rounded once to the float mu field.
+template <bool M64>
+__device__ __forceinline__ float mu_value(const KParams& p, const EosF& ef, float k2, float kap, float rref, float dev,
+                                          float lap) {
+  if constexpr (M64)
+    return float(p.k2 * eos_mu<double>(p.rho_ref + double(dev), p) - p.kappa * double(lap));
+  else
+    return k2 * eos_mu_f(rref + dev, ef) - kap * lap;
+}
+
 // line schemes only (the isotropic 3D Laplacian needs diagonal neighbours)
-template <int S>
+template <int S, bool M64 = false>
 __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __restrict__ rin,
                                               float* __restrict__ mu) {
   static_assert(!Sch<S>::ISO, "line schemes only");
@@ -73,7 +85,7 @@ __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __re
       for (int m = 1; m <= R; ++m)
         lap += float(Sch<S>::l(m)) * ((blk[pz][cy][cx + m] + blk[pz][cy][cx - m]) +
                                       (blk[pz][cy + m][cx] + blk[pz][cy - m][cx]) + (q[R + m] + q[R - m]));
-      out[dz * NXY] = k2 * eos_mu_f(rref + c, ef) - kap * lap;
+      out[dz * NXY] = mu_value<M64>(p, ef, k2, kap, rref, c, lap);
     }
   }
 }
@@ -99,7 +111,7 @@ struct MuZShape {
   static constexpr size_t bytes = size_t(2) * PCH * 16;
 };
 
-template <int S>
+template <int S, bool M64 = false>
 __global__ void __launch_bounds__(MZT) k_mu3d_zm(const KParams p, const float* __restrict__ rin,
                                                  float* __restrict__ mu, const int zc) {
   static_assert(!Sch<S>::ISO, "line schemes only");
@@ -177,7 +189,7 @@ __global__ void __launch_bounds__(MZT) k_mu3d_zm(const KParams p, const float* _
       float lap = float(3.0 * Sch<S>::l(0)) * cv;
 #pragma unroll
       for (int m = 1; m <= R; ++m) lap += float(Sch<S>::l(m)) * ((row[4 + k + m] + row[4 + k - m]) + yz[k][m - 1]);
-      res[k] = k2 * eos_mu_f(rref + cv, ef) - kap * lap;
+      res[k] = mu_value<M64>(p, ef, k2, kap, rref, cv, lap);
     }
     *reinterpret_cast<float4*>(mu + z * NXY + col) = make_float4(res[0], res[1], res[2], res[3]);
   }

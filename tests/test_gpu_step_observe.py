@@ -42,10 +42,12 @@ def close(a, b, rel, keys=KEYS):
         assert a[k] == pytest.approx(b[k], rel=rel, abs=1e-12 * max(1.0, abs(b[k]))), k
 
 
-# nx % 4 == 0 takes the 16-byte copy variant of the collision pass, 42 the 4-byte one
-@pytest.mark.parametrize("shape,scheme", [((48, 40, 44), "EFDS6"), ((42, 36, 40), "EFDS4"), ((40, 40, 40), "EFDS2")])
-def test_fused_observation_matches_observe_then_step(L, shape, scheme):
-    a, b = make(L, shape, scheme=scheme), make(L, shape, scheme=scheme)
+# nx % 4 == 0 takes the 16-byte copy variant of the collision pass, 42 the 4-byte one;
+# mu_fp64 = 1: the same passes with the EOS chemical potential evaluated in FP64
+@pytest.mark.parametrize("shape,scheme,mu_fp64", [((48, 40, 44), "EFDS6", 0), ((42, 36, 40), "EFDS4", 0),
+                                                  ((40, 40, 40), "EFDS2", 0), ((48, 40, 44), "EFDS6", 1)])
+def test_fused_observation_matches_observe_then_step(L, shape, scheme, mu_fp64):
+    a, b = make(L, shape, scheme=scheme, mu_fp64=mu_fp64), make(L, shape, scheme=scheme, mu_fp64=mu_fp64)
     t_prev = 0
     for n in (12, 5):  # two cycles: the second max |d rho / dt| uses the fused kernel's snapshot
         a.lbm_step(n - 1)

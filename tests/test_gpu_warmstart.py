@@ -1,7 +1,9 @@
 """Learned warm start: the solver generates converged profiles, the library's
 MLP kernels fit them, and a predicted profile starts a held-out droplet closer
 to its converged state than the tanh profile of Eq. 26; the warm-started run
-relaxes to the same densities as the cold-started one."""
+relaxes to the same densities as the cold-started one (both relaxed until
+max |d rho / dt| stagnates at the FP32 rounding floor: the benchmark spec's 1e-5
+agreement on densities)."""
 import numpy as np
 import pytest
 
@@ -25,7 +27,7 @@ def test_warm_start_gain_and_agreement(W):
     train = [dict(Tr=tr, k=k, R=R, scheme="EFDS6") for tr in (0.65, 0.75) for k in (0.25, 0.35) for R in (11.0, 14.0)]
     X, Y, info = W.generate(train, n=n, tol=1e-6, max_steps=6000, check_every=200)
     assert len(X) >= 6
-    net, loss = W.train(X, Y, iters=1500, lr=2e-3)
+    net, loss, _ = W.train(X, Y, iters=1500, lr=2e-3)
     assert loss < 0.02
     case = dict(Tr=0.7, k=0.3, R=12.5, scheme="EFDS6")
     # cold start: tanh profile; relax and take the converged profile
@@ -34,7 +36,7 @@ def test_warm_start_gain_and_agreement(W):
     c = (n // 2, n // 2, n // 2)
     r = W.window(case["R"])
     cold0 = W.radial_profile(sim.lbm_get_density(), c, r)
-    steps_c, _, ok_c, obs_c = W.relax(sim, 1e-6, 6000, 200)
+    steps_c, _, ok_c, obs_c, _ = W.relax(sim, 1e-10, 40000, 200, fp32_floor=True)
     conv = W.radial_profile(sim.lbm_get_density(), c, r)
     assert ok_c
     # warm start from the network
@@ -43,10 +45,10 @@ def test_warm_start_gain_and_agreement(W):
     sim2.lbm_init_profile(rr, rho)
     warm0 = W.radial_profile(sim2.lbm_get_density(), c, r)
     assert np.linalg.norm(warm0 - conv) < np.linalg.norm(cold0 - conv)
-    steps_w, _, ok_w, obs_w = W.relax(sim2, 1e-6, 6000, 200)
+    steps_w, _, ok_w, obs_w, _ = W.relax(sim2, 1e-10, 40000, 200, fp32_floor=True)
     assert ok_w
     # the droplet survives (centre is liquid) and both starts reach the same state
     rl = L.lbm_maxwell(p)[1]
     assert obs_c["rho_center"] > 0.5 * rl
-    assert abs(obs_w["rho_center"] - obs_c["rho_center"]) / rl < 2e-3
-    assert abs(obs_w["rho_corner"] - obs_c["rho_corner"]) / rl < 2e-3
+    assert abs(obs_w["rho_center"] - obs_c["rho_center"]) / rl < 1e-5
+    assert abs(obs_w["rho_corner"] - obs_c["rho_corner"]) / rl < 1e-5
