@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include <type_traits>
+#include <utility>
 
 #include "compact.cuh"
 #include "compact_dev.cuh"
@@ -93,6 +94,192 @@ cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T*
   return cudaGetLastError();
 }
 
+// FP32 lines whose length is a multiple of 32, L = 32 LW (LW = 2..16): one
+// warp holds a whole line in registers (element i = lane + 32 k in v[k]).  A
+// shift by s < 32 elements is one shuffle per register and a select (lanes
+// past the end of a 32-element row take the neighbouring register, wrapping
+// around the periodic line); a shift by a multiple of 32 is a renaming of
+// registers.  The right side of Eq. 21 and every PCR level are formed that way,
+// with the same arithmetic as k_lines.  x lines are read and written straight
+// from global memory (a warp's accesses are 32 consecutive floats); y and z
+// lines of 32 consecutive x go through a padded shared-memory tile (33 columns:
+// the column reads of the warps are free of bank conflicts).  One launch does
+// both fields of an axis: blocks of the first half take mu, of the second rho.
+constexpr int LRT = 256;  // 8 warps
+
+template <int LW>
+struct RegLine {
+  float v[LW];
+  // element i + s (or i - s), s < 32
+  __device__ __forceinline__ void shift_small(int s, int lane, bool fwd, float* out) const {
+    const int src = fwd ? ((lane + s) & 31) : ((lane - s) & 31);
+    float a[LW];
+#pragma unroll
+    for (int k = 0; k < LW; ++k) a[k] = __shfl_sync(0xffffffffu, v[k], src);
+    if (fwd) {
+      const bool same = lane + s < 32;
+#pragma unroll
+      for (int k = 0; k < LW; ++k) out[k] = same ? a[k] : a[(k + 1) % LW];
+    } else {
+      const bool same = lane >= s;
+#pragma unroll
+      for (int k = 0; k < LW; ++k) out[k] = same ? a[k] : a[(k + LW - 1) % LW];
+    }
+  }
+};
+
+// stride of PCR level lev on a periodic line of L elements: 2^lev mod L
+__host__ __device__ constexpr int pcr_stride(int lev, int L) {
+  int s = 1 % L;
+  for (int k = 0; k < lev; ++k) {
+    s *= 2;
+    if (s >= L) s -= L;
+  }
+  return s;
+}
+
+template <int LW, int LEV>
+__device__ __forceinline__ void pcr_level(RegLine<LW>& d, int lane, const LineCoef& lc) {
+  constexpr int L = 32 * LW, S = pcr_stride(LEV, L);
+  const float al = lc.alpha_f[LEV], iv = lc.inv_f[LEV];
+  float m[LW], p[LW];
+  if constexpr (S % 32 == 0) {
+    constexpr int Q = S / 32;
+#pragma unroll
+    for (int k = 0; k < LW; ++k) {
+      p[k] = d.v[(k + Q) % LW];
+      m[k] = d.v[(k + LW - Q % LW) % LW];
+    }
+  } else {
+    d.shift_small(S, lane, true, p);
+    d.shift_small(S, lane, false, m);
+  }
+#pragma unroll
+  for (int k = 0; k < LW; ++k) d.v[k] = (d.v[k] - al * (m[k] + p[k])) * iv;
+}
+
+template <int LW, int... LEV>
+__device__ __forceinline__ void pcr_levels(RegLine<LW>& d, int lane, const LineCoef& lc,
+                                           std::integer_sequence<int, LEV...>) {
+  ((LEV < lc.nlev ? pcr_level<LW, LEV>(d, lane, lc) : void()), ...);
+}
+
+template <int LW>
+__device__ __forceinline__ void solve_line(RegLine<LW>& f, int lane, const LineCoef& lc) {
+  const float A1 = float(lc.A1), A2 = float(lc.A2), A3 = float(lc.A3);
+  const bool has2 = lc.A2 != 0.0, has3 = lc.A3 != 0.0;
+  float p1[LW], m1[LW];
+  f.shift_small(1, lane, true, p1);
+  f.shift_small(1, lane, false, m1);
+  RegLine<LW> r;
+#pragma unroll
+  for (int k = 0; k < LW; ++k) r.v[k] = A1 * (p1[k] - m1[k]);
+  if (has2) {
+    f.shift_small(2, lane, true, p1);
+    f.shift_small(2, lane, false, m1);
+#pragma unroll
+    for (int k = 0; k < LW; ++k) r.v[k] += A2 * (p1[k] - m1[k]);
+  }
+  if (has3) {
+    f.shift_small(3, lane, true, p1);
+    f.shift_small(3, lane, false, m1);
+#pragma unroll
+    for (int k = 0; k < LW; ++k) r.v[k] += A3 * (p1[k] - m1[k]);
+  }
+  pcr_levels<LW>(r, lane, lc, std::make_integer_sequence<int, 16>{});
+  f = r;
+}
+
+// blocks: axis 0: 2 fields x ceil(lines / 8), one line per warp; axes 1, 2:
+// 2 fields x ceil(nx / 32) x (nz or ny), 32 lines of consecutive x per block
+template <int LW>
+__global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int nz, const float* __restrict__ mu,
+                                                   const float* __restrict__ rho, float* __restrict__ gmu,
+                                                   float* __restrict__ grho, const LineCoef lc, unsigned half) {
+  constexpr int L = 32 * LW;
+  extern __shared__ __align__(16) float tile[];  // [L][33] (axes 1, 2)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool second = blockIdx.x >= half;
+  const unsigned b = second ? blockIdx.x - half : blockIdx.x;
+  const float* in = second ? rho : mu;
+  float* out = second ? grho : gmu;
+  const long long NXY = (long long)nx * ny;
+  RegLine<LW> f;
+  if (axis == 0) {
+    const long long row = (long long)b * (LRT / 32) + warp;
+    if (row >= (long long)ny * nz) return;  // whole warps only: no CTA barrier in this branch
+    const float* src = in + row * nx;
+#pragma unroll
+    for (int k = 0; k < LW; ++k) f.v[k] = src[lane + 32 * k];
+    solve_line<LW>(f, lane, lc);
+    float* dst = out + row * nx;
+#pragma unroll
+    for (int k = 0; k < LW; ++k) dst[lane + 32 * k] = f.v[k];
+    return;
+  }
+  const int gxs = (nx + 31) / 32;
+  const int x0 = int(b % gxs) * 32;
+  const long long r = b / gxs;  // z (axis 1) or y (axis 2)
+  const long long base = axis == 1 ? r * NXY + x0 : r * nx + x0;
+  const long long stride = axis == 1 ? nx : NXY;
+  const bool xin = x0 + lane < nx;
+  for (int i = warp; i < L; i += LRT / 32) tile[i * 33 + lane] = xin ? in[base + i * stride + lane] : 0.f;
+  __syncthreads();
+  for (int j = warp; j < 32; j += LRT / 32) {
+#pragma unroll
+    for (int k = 0; k < LW; ++k) f.v[k] = tile[(lane + 32 * k) * 33 + j];
+    solve_line<LW>(f, lane, lc);
+#pragma unroll
+    for (int k = 0; k < LW; ++k) tile[(lane + 32 * k) * 33 + j] = f.v[k];
+  }
+  __syncthreads();
+  if (xin)
+    for (int i = warp; i < L; i += LRT / 32) out[base + i * stride + lane] = tile[i * 33 + lane];
+}
+
+template <int LW>
+cudaError_t launch_lines_reg(int axis, const KParams& kp, const float* mu, const float* rho, float* gmu, float* grho,
+                             const LineCoef& lf, cudaStream_t st) {
+  constexpr int L = 32 * LW;
+  unsigned half;
+  size_t smem = 0;
+  if (axis == 0) {
+    half = unsigned(((long long)kp.ny * kp.nz + LRT / 32 - 1) / (LRT / 32));
+  } else {
+    half = unsigned((long long)((kp.nx + 31) / 32) * (axis == 1 ? kp.nz : kp.ny));
+    smem = size_t(L) * 33 * 4;
+  }
+  if (cudaError_t e = ensure_smem(k_lines_reg<LW>, smem); e != cudaSuccess) return e;
+  k_lines_reg<LW><<<2 * half, LRT, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, mu, rho, gmu, grho, lf, half);
+  return cudaGetLastError();
+}
+
+// grad mu and grad rho along one axis of FP32 fields: the register kernel
+// when the line length is a multiple of 32 (64 .. 512), else k_lines per field
+cudaError_t run_lines_pair_f32(int axis, const KParams& kp, const float* mu, const float* rho, float* gmu,
+                               float* grho, const LineCoef& lc, cudaStream_t st) {
+  const int L = axis == 0 ? kp.nx : (axis == 1 ? kp.ny : kp.nz);
+  const LineCoef lf = line_coef_for(lc, true);
+  if (L % 32 == 0 && lf.nlev <= 16) {
+    switch (L / 32) {
+      case 2: return launch_lines_reg<2>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 3: return launch_lines_reg<3>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 4: return launch_lines_reg<4>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 5: return launch_lines_reg<5>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 6: return launch_lines_reg<6>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 7: return launch_lines_reg<7>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 8: return launch_lines_reg<8>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 10: return launch_lines_reg<10>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 12: return launch_lines_reg<12>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 16: return launch_lines_reg<16>(axis, kp, mu, rho, gmu, grho, lf, st);
+      default: break;
+    }
+  }
+  cudaError_t e = run_lines<float, float>(axis, kp, mu, 0.0, gmu, lc, st);
+  if (e != cudaSuccess) return e;
+  return run_lines<float, float>(axis, kp, rho, 0.0, grho, lc, st);
+}
+
 constexpr int TXc = 32, TYc = 8, ZCc = 32;
 
 template <class P, int MODE>
@@ -147,6 +334,11 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   Tm* gmu = static_cast<Tm*>(cb.gmu);
   Tc* grho = static_cast<Tc*>(cb.grho);
   for (int ax = 0; ax < D; ++ax) {
+    if constexpr (std::is_same<P, PrecF32>::value) {
+      e = run_lines_pair_f32(ax, kp, mu, rin, gmu + size_t(ax) * kp.n, grho + size_t(ax) * kp.n, cb.lc, c.stream);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     e = run_lines<Tm, Tm>(ax, kp, mu, 0.0, gmu + size_t(ax) * kp.n, cb.lc, c.stream);
     if (e != cudaSuccess) return e;
     e = run_lines<Tr, Tc>(ax, kp, rin, 0.0, grho + size_t(ax) * kp.n, cb.lc, c.stream);

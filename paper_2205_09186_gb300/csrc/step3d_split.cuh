@@ -47,13 +47,16 @@ constexpr int FW = 36;              // staged population row: 32 nodes + up to 3
 // of populations: the copies of plane z + NB - 1 are issued while plane z is
 // collided, so NB - 1 planes are in flight per CTA.  The field ring holds the
 // 2R + 1 planes of the stencil plus the NB - 1 in flight.
+__host__ __device__ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 1) / 2); }
+
 template <int S, int RY_ = CY, int NB_ = 2>
 struct CollShape {
   static constexpr int R = Sch<S>::R;
   static constexpr int RY = RY_, TY = RY_ - 2, NT = CX * RY_, NB = NB_;
   static_assert(NB >= 2 && NB <= 4, "two to four staged planes");
   static constexpr int GW = CX + 2 * R, GH = RY + 2 * R;  // field region (ring + stencil halo)
-  static constexpr int NS = 2 * R + NB;                   // ring of planes (NB - 1 in flight)
+  // ring of planes (NB - 1 in flight), a power of two so that a slot is a mask
+  static constexpr int NS = pow2_at_least(2 * R + NB);
   static constexpr int plane = GH * GW;                   // float2 per field plane
   static constexpr int FPL = RY * FW;                     // staged populations of one i
   static constexpr int fbuf = (19 * FPL + 255) / 256 * 256;  // buffer stride (floats), 1 KB multiple
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
   int slot = 0;  // ring slot of plane pc_first - R + (number issued)
   for (int q = pc_first - R; q <= pc_first + R + NB - 2; ++q) {
     issue(q, slot);
-    slot = ring(slot + 1, NS);
+    slot = (slot + 1) & (NS - 1);
   }
   int sc = R;  // ring slot of the collision plane
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
     __syncthreads();
     if (pc + NB - 1 <= pc_last) {
       issue(pc + R + NB - 1, slot);
-      slot = ring(slot + 1, NS);
+      slot = (slot + 1) & (NS - 1);
     } else {
       cpa_commit();  // an empty group: the wait above counts one group per plane
     }
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
     if (cnode) {
       int base[2 * R + 1];
 #pragma unroll
-      for (int d = -R; d <= R; ++d) base[d + R] = ring(sc + d, NS) * Sh::plane;
+      for (int d = -R; d <= R; ++d) base[d + R] = ((sc + d) & (NS - 1)) * Sh::plane;
       float fv[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) fv[i] = fb[i * FPL + fme];
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
       acc1 = acc2;
       acc2 = 0.f;
     }
-    sc = ring(sc + 1, NS);
+    sc = (sc + 1) & (NS - 1);
   }
   // the issuing thread keeps the CTA (and its shared memory) alive until a
   // copy that missed its wait has landed, or a second bounded wait runs out

@@ -231,8 +231,10 @@ def test_zchunk_and_autotune_do_not_change_results(L):
 # compact schemes in 3D with FP32 deviation storage: z-marching mu pass (orders
 # 4 and 6; the node-parallel one for CFDS8), line solves, and the tiled
 # collision pass reading the derivative fields (64: tensor-copy and 16-byte
-# variants by tile; 42: the 4-byte variant everywhere)
-@pytest.mark.parametrize("shape", [(64, 40, 36), (42, 26, 20)])
+# variants by tile; 42: the 4-byte variant everywhere).  Lines whose length is
+# a multiple of 32 are solved in registers (64 x 96 x 64: every axis; 64 x 40
+# x 36: x only), the others in shared memory.
+@pytest.mark.parametrize("shape", [(64, 40, 36), (42, 26, 20), (64, 96, 64)])
 @pytest.mark.parametrize("scheme", ["OCFDS4", "CFDS6", "CFDS8"])
 def test_fp32dev_compact_3d_against_oracle(L, shape, scheme):
     nx, ny, nz = shape
