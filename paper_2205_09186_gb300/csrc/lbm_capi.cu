@@ -368,20 +368,24 @@ __device__ double init_density(const InitSpec& s, int x, int y, int z, long long
 }
 
 // f_i = w_i rho0 (u = 0); the density field is the sum of the stored populations
-template <typename Tf>
-__global__ void k_init(KParams p, int Q, InitSpec s, Tf* f, Tf* rho) {
+// (Q a template parameter: the population loop unrolls, its weights and
+// population offsets become constants)
+template <typename Tf, int Q>
+__global__ void k_init(KParams p, InitSpec s, Tf* f, Tf* rho) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= p.n) return;
   // (a density array needs no coordinates: skip the 64-bit divisions)
   const int x = s.kind == 3 ? 0 : int(n % p.nx), y = s.kind == 3 ? 0 : int((n / p.nx) % p.ny);
   const int z = s.kind == 3 ? 0 : int(n / ((long long)p.nx * p.ny));
   const double r0 = init_density(s, x, y, z, n);
+  Tf* fn = f + n;
   if constexpr (sizeof(Tf) == 8) {
     const double* w = Q == 9 ? c_w9 : c_w19;
     double acc = 0;
+#pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double fi = w[i] * r0;
-      f[i * p.n + n] = Tf(fi);
+      fn[i * p.n] = Tf(fi);
       acc += fi;
     }
     rho[n] = acc;
@@ -391,9 +395,10 @@ __global__ void k_init(KParams p, int Q, InitSpec s, Tf* f, Tf* rho) {
     const float dv = float(r0 - p.rho_ref);
     const float* w = Q == 9 ? c_w9f : c_w19f;
     FSum acc;
+#pragma unroll
     for (int i = 0; i < Q; ++i) {
       const float d = w[i] * dv;
-      f[i * p.n + n] = d;
+      fn[i * p.n] = d;
       acc.add(d);
     }
     rho[n] = acc.fvalue();
@@ -636,12 +641,17 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
 // ------------------------------------------------------------------ init
 static int run_init(lbm_handle* h, const InitSpec& s) {
   const int bs = 256;
-  if (h->p.precision == LBM_FP64)
-    k_init<double><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, s, static_cast<double*>(h->f[0]),
-                                                          static_cast<double*>(h->rho[0]));
-  else
-    k_init<float><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, h->Q, s, static_cast<float*>(h->f[0]),
-                                                         static_cast<float*>(h->rho[0]));
+  double* fd = static_cast<double*>(h->f[0]);
+  double* rd = static_cast<double*>(h->rho[0]);
+  float* ff = static_cast<float*>(h->f[0]);
+  float* rf = static_cast<float*>(h->rho[0]);
+  if (h->p.precision == LBM_FP64) {
+    if (h->Q == 9) k_init<double, 9><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, s, fd, rd);
+    else k_init<double, 19><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, s, fd, rd);
+  } else {
+    if (h->Q == 9) k_init<float, 9><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, s, ff, rf);
+    else k_init<float, 19><<<grid1(h->N, bs), bs, 0, h->stream>>>(h->kp, s, ff, rf);
+  }
   h->cur = 0;
   h->t = 0;
   h->t_snap = 0;
