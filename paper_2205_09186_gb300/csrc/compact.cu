@@ -95,38 +95,37 @@ cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T*
 }
 
 // FP32 lines whose length is a multiple of 32, L = 32 LW (LW = 2..16): one
-// warp holds a whole line in registers (element i = lane + 32 k in v[k]).  A
-// shift by s < 32 elements is one shuffle per register and a select (lanes
-// past the end of a 32-element row take the neighbouring register, wrapping
-// around the periodic line); a shift by a multiple of 32 is a renaming of
-// registers.  The right side of Eq. 21 and every PCR level are formed that way,
-// with the same arithmetic as k_lines.  x lines are read and written straight
-// from global memory (a warp's accesses are 32 consecutive floats); y and z
-// lines of 32 consecutive x go through a padded shared-memory tile (33 columns:
-// the column reads of the warps are free of bank conflicts).  One launch does
-// both fields of an axis: blocks of the first half take mu, of the second rho.
+// warp holds a whole line in registers, lane l the block of elements
+// l LW .. l LW + LW - 1 (element i in v[i % LW] of lane i / LW).  The value at
+// offset o from element l LW + k is element (l + q) LW + r of the periodic
+// line, with q and r fixed by k and o: register r of lane (l + q) mod 32, one
+// shuffle when q is not a multiple of 32, a register of the lane itself when
+// it is.  A PCR level of stride s needs min(LW, s) shuffles per direction (one
+// per register that looks past its lane's block), the right side of Eq. 21
+// 1 + 2 + 3 per direction; no selects.  The arithmetic is that of k_lines.
+// Lines are staged in shared memory to switch between the coalesced global
+// layout and the blocked one: x lines one row per warp, y and z lines a padded
+// tile of 32 lines of consecutive x.  One launch does both fields of an axis:
+// blocks of the first half take mu, of the second rho.
 constexpr int LRT = 256;  // 8 warps
 
 template <int LW>
-struct RegLine {
+struct BlkLine {
   float v[LW];
-  // element i + s (or i - s), s < 32
-  __device__ __forceinline__ void shift_small(int s, int lane, bool fwd, float* out) const {
-    const int src = fwd ? ((lane + s) & 31) : ((lane - s) & 31);
-    float a[LW];
-#pragma unroll
-    for (int k = 0; k < LW; ++k) a[k] = __shfl_sync(0xffffffffu, v[k], src);
-    if (fwd) {
-      const bool same = lane + s < 32;
-#pragma unroll
-      for (int k = 0; k < LW; ++k) out[k] = same ? a[k] : a[(k + 1) % LW];
-    } else {
-      const bool same = lane >= s;
-#pragma unroll
-      for (int k = 0; k < LW; ++k) out[k] = same ? a[k] : a[(k + LW - 1) % LW];
-    }
-  }
 };
+
+// value at offset O (|O| < L) from each of the lane's elements
+template <int LW, int O>
+__device__ __forceinline__ void blk_shift(const BlkLine<LW>& f, int lane, float* out) {
+  constexpr int L = 32 * LW;
+#pragma unroll
+  for (int k = 0; k < LW; ++k) {
+    const int j = ((k + O) % L + L) % L;  // compile-time: k is unrolled
+    const int q = j / LW, r = j % LW;
+    if (q % 32 == 0) out[k] = f.v[r];
+    else out[k] = __shfl_sync(0xffffffffu, f.v[r], (lane + q) & 31);
+  }
+}
 
 // stride of PCR level lev on a periodic line of L elements: 2^lev mod L
 __host__ __device__ constexpr int pcr_stride(int lev, int L) {
@@ -139,52 +138,43 @@ __host__ __device__ constexpr int pcr_stride(int lev, int L) {
 }
 
 template <int LW, int LEV>
-__device__ __forceinline__ void pcr_level(RegLine<LW>& d, int lane, const LineCoef& lc) {
-  constexpr int L = 32 * LW, S = pcr_stride(LEV, L);
+__device__ __forceinline__ void pcr_level(BlkLine<LW>& d, int lane, const LineCoef& lc) {
+  constexpr int S = pcr_stride(LEV, 32 * LW);
   const float al = lc.alpha_f[LEV], iv = lc.inv_f[LEV];
   float m[LW], p[LW];
-  if constexpr (S % 32 == 0) {
-    constexpr int Q = S / 32;
-#pragma unroll
-    for (int k = 0; k < LW; ++k) {
-      p[k] = d.v[(k + Q) % LW];
-      m[k] = d.v[(k + LW - Q % LW) % LW];
-    }
-  } else {
-    d.shift_small(S, lane, true, p);
-    d.shift_small(S, lane, false, m);
-  }
+  blk_shift<LW, S>(d, lane, p);
+  blk_shift<LW, -S>(d, lane, m);
 #pragma unroll
   for (int k = 0; k < LW; ++k) d.v[k] = (d.v[k] - al * (m[k] + p[k])) * iv;
 }
 
 template <int LW, int... LEV>
-__device__ __forceinline__ void pcr_levels(RegLine<LW>& d, int lane, const LineCoef& lc,
+__device__ __forceinline__ void pcr_levels(BlkLine<LW>& d, int lane, const LineCoef& lc,
                                            std::integer_sequence<int, LEV...>) {
   ((LEV < lc.nlev ? pcr_level<LW, LEV>(d, lane, lc) : void()), ...);
 }
 
 template <int LW>
-__device__ __forceinline__ void solve_line(RegLine<LW>& f, int lane, const LineCoef& lc) {
+__device__ __forceinline__ void solve_line(BlkLine<LW>& f, int lane, const LineCoef& lc) {
   const float A1 = float(lc.A1), A2 = float(lc.A2), A3 = float(lc.A3);
   const bool has2 = lc.A2 != 0.0, has3 = lc.A3 != 0.0;
-  float p1[LW], m1[LW];
-  f.shift_small(1, lane, true, p1);
-  f.shift_small(1, lane, false, m1);
-  RegLine<LW> r;
+  float p[LW], m[LW];
+  BlkLine<LW> r;
+  blk_shift<LW, 1>(f, lane, p);
+  blk_shift<LW, -1>(f, lane, m);
 #pragma unroll
-  for (int k = 0; k < LW; ++k) r.v[k] = A1 * (p1[k] - m1[k]);
+  for (int k = 0; k < LW; ++k) r.v[k] = A1 * (p[k] - m[k]);
   if (has2) {
-    f.shift_small(2, lane, true, p1);
-    f.shift_small(2, lane, false, m1);
+    blk_shift<LW, 2>(f, lane, p);
+    blk_shift<LW, -2>(f, lane, m);
 #pragma unroll
-    for (int k = 0; k < LW; ++k) r.v[k] += A2 * (p1[k] - m1[k]);
+    for (int k = 0; k < LW; ++k) r.v[k] += A2 * (p[k] - m[k]);
   }
   if (has3) {
-    f.shift_small(3, lane, true, p1);
-    f.shift_small(3, lane, false, m1);
+    blk_shift<LW, 3>(f, lane, p);
+    blk_shift<LW, -3>(f, lane, m);
 #pragma unroll
-    for (int k = 0; k < LW; ++k) r.v[k] += A3 * (p1[k] - m1[k]);
+    for (int k = 0; k < LW; ++k) r.v[k] += A3 * (p[k] - m[k]);
   }
   pcr_levels<LW>(r, lane, lc, std::make_integer_sequence<int, 16>{});
   f = r;
@@ -197,24 +187,32 @@ __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int
                                                    const float* __restrict__ rho, float* __restrict__ gmu,
                                                    float* __restrict__ grho, const LineCoef lc, unsigned half) {
   constexpr int L = 32 * LW;
-  extern __shared__ __align__(16) float tile[];  // [L][33] (axes 1, 2)
+  extern __shared__ __align__(16) float tile[];  // axis 0: [8][L]; axes 1, 2: [L][33]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool second = blockIdx.x >= half;
   const unsigned b = second ? blockIdx.x - half : blockIdx.x;
   const float* in = second ? rho : mu;
   float* out = second ? grho : gmu;
   const long long NXY = (long long)nx * ny;
-  RegLine<LW> f;
+  BlkLine<LW> f;
   if (axis == 0) {
     const long long row = (long long)b * (LRT / 32) + warp;
-    if (row >= (long long)ny * nz) return;  // whole warps only: no CTA barrier in this branch
+    if (row >= (long long)ny * nz) return;  // whole warps only: the warp's own row of the tile, no CTA barrier
+    float* t = tile + warp * L;
     const float* src = in + row * nx;
 #pragma unroll
-    for (int k = 0; k < LW; ++k) f.v[k] = src[lane + 32 * k];
+    for (int k = 0; k < LW; ++k) t[lane + 32 * k] = src[lane + 32 * k];
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < LW; ++k) f.v[k] = t[lane * LW + k];
     solve_line<LW>(f, lane, lc);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < LW; ++k) t[lane * LW + k] = f.v[k];
+    __syncwarp();
     float* dst = out + row * nx;
 #pragma unroll
-    for (int k = 0; k < LW; ++k) dst[lane + 32 * k] = f.v[k];
+    for (int k = 0; k < LW; ++k) dst[lane + 32 * k] = t[lane + 32 * k];
     return;
   }
   const int gxs = (nx + 31) / 32;
@@ -227,10 +225,10 @@ __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int
   __syncthreads();
   for (int j = warp; j < 32; j += LRT / 32) {
 #pragma unroll
-    for (int k = 0; k < LW; ++k) f.v[k] = tile[(lane + 32 * k) * 33 + j];
+    for (int k = 0; k < LW; ++k) f.v[k] = tile[(lane * LW + k) * 33 + j];
     solve_line<LW>(f, lane, lc);
 #pragma unroll
-    for (int k = 0; k < LW; ++k) tile[(lane + 32 * k) * 33 + j] = f.v[k];
+    for (int k = 0; k < LW; ++k) tile[(lane * LW + k) * 33 + j] = f.v[k];
   }
   __syncthreads();
   if (xin)
@@ -245,6 +243,7 @@ cudaError_t launch_lines_reg(int axis, const KParams& kp, const float* mu, const
   size_t smem = 0;
   if (axis == 0) {
     half = unsigned(((long long)kp.ny * kp.nz + LRT / 32 - 1) / (LRT / 32));
+    smem = size_t(LRT / 32) * L * 4;
   } else {
     half = unsigned((long long)((kp.nx + 31) / 32) * (axis == 1 ? kp.nz : kp.ny));
     smem = size_t(L) * 33 * 4;
