@@ -495,9 +495,10 @@ def run_gpu(args):
     if not args.no_warmstart:
         from paper_2205_09186_gb300 import warmstart as W
         # the plain arm (FP64 storage, tanh start) on the first 4 test cases;
-        # --warmstart-full: 64 held-out droplets on 192^3 lattices
+        # --warmstart-full: 64 held-out droplets on 192^3 lattices, warm against
+        # cold FP32 only (FP64 storage at this size takes ~17 ms per step here)
         if args.warmstart_full:
-            res, _ = W.experiment(n_train=32, n_test=64, n=192, tol=1e-10, iters=4000, plain=4, R=(30.0, 50.0),
+            res, _ = W.experiment(n_train=32, n_test=64, n=192, tol=1e-10, iters=4000, plain=0, R=(30.0, 50.0),
                                   max_steps=100000)
         else:
             res, _ = W.experiment(n_train=32, n_test=12, n=80, tol=1e-10, iters=4000, plain=4)
@@ -552,6 +553,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=50, help="steps per timed launch of the batched 2D sweep")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the warm-start experiment")
     ap.add_argument("--no-cfg3", action="store_true", help="skip the other-temperature and FP64-mu 256^3 legs")
+    ap.add_argument("--compact-only", action="store_true",
+                    help="profiling: only the D3Q19 192^3 compact-scheme leg (one JSON line of its own)")
     ap.add_argument("--warmstart-full", action="store_true",
                     help="the warm-start experiment at full size (64 held-out 192^3 droplets; tens of minutes)")
     ap.add_argument("--zchunk", type=int, default=0, help="fix the z-chunk instead of autotuning (profiling runs)")
@@ -560,6 +563,11 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.compact_only:
+        import paper_2205_09186_gb300 as pkg
+        pkg.build()
+        from paper_2205_09186_gb300 import lbm as L
+        print(json.dumps({"d3q19_compact": run_compact(L, steps=args.steps, warmup=args.warmup)}), flush=True)
     else:
         run_gpu(args)
 

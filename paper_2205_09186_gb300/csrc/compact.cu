@@ -137,15 +137,19 @@ __host__ __device__ constexpr int pcr_stride(int lev, int L) {
   return s;
 }
 
+// A PCR level divides every row by 1 - 2 alpha^2, the same number for every
+// element of every line: the register kernel leaves those divisions out and
+// takes their product into the right side instead (lc.A1..A3 arrive scaled by
+// it, see run_lines_pair_f32), two flops per element and level.
 template <int LW, int LEV>
 __device__ __forceinline__ void pcr_level(BlkLine<LW>& d, int lane, const LineCoef& lc) {
   constexpr int S = pcr_stride(LEV, 32 * LW);
-  const float al = lc.alpha_f[LEV], iv = lc.inv_f[LEV];
+  const float al = lc.alpha_f[LEV];
   float m[LW], p[LW];
   blk_shift<LW, S>(d, lane, p);
   blk_shift<LW, -S>(d, lane, m);
 #pragma unroll
-  for (int k = 0; k < LW; ++k) d.v[k] = (d.v[k] - al * (m[k] + p[k])) * iv;
+  for (int k = 0; k < LW; ++k) d.v[k] = d.v[k] - al * (m[k] + p[k]);
 }
 
 template <int LW, int... LEV>
@@ -259,18 +263,25 @@ cudaError_t run_lines_pair_f32(int axis, const KParams& kp, const float* mu, con
                                float* grho, const LineCoef& lc, cudaStream_t st) {
   const int L = axis == 0 ? kp.nx : (axis == 1 ? kp.ny : kp.nz);
   const LineCoef lf = line_coef_for(lc, true);
+  // the register kernel: the levels' row scalings folded into the right side
+  LineCoef lr = lf;
+  double scale = 1.0;
+  for (int k = 0; k < lf.nlev; ++k) scale *= lf.inv[k];
+  lr.A1 = lf.A1 * scale;
+  lr.A2 = lf.A2 * scale;
+  lr.A3 = lf.A3 * scale;
   if (L % 32 == 0 && lf.nlev <= 16) {
     switch (L / 32) {
-      case 2: return launch_lines_reg<2>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 3: return launch_lines_reg<3>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 4: return launch_lines_reg<4>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 5: return launch_lines_reg<5>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 6: return launch_lines_reg<6>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 7: return launch_lines_reg<7>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 8: return launch_lines_reg<8>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 10: return launch_lines_reg<10>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 12: return launch_lines_reg<12>(axis, kp, mu, rho, gmu, grho, lf, st);
-      case 16: return launch_lines_reg<16>(axis, kp, mu, rho, gmu, grho, lf, st);
+      case 2: return launch_lines_reg<2>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 3: return launch_lines_reg<3>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 4: return launch_lines_reg<4>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 5: return launch_lines_reg<5>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 6: return launch_lines_reg<6>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 7: return launch_lines_reg<7>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 8: return launch_lines_reg<8>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 10: return launch_lines_reg<10>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 12: return launch_lines_reg<12>(axis, kp, mu, rho, gmu, grho, lr, st);
+      case 16: return launch_lines_reg<16>(axis, kp, mu, rho, gmu, grho, lr, st);
       default: break;
     }
   }
