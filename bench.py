@@ -230,6 +230,35 @@ def run_batch(L, steps=50, warmup=10, ncases=512, schemes=None):
             "resident_ctas": grid, "tile_rows_per_thread": rows, "status": rc}
 
 
+def run_cfg2_sweep(L, steps=50, warmup=5):
+    """The 512^2 droplet sweep (r0 = 100): schemes {EFDS2, EFDS4, EFDS6, E4, E8,
+    OCFDS4} x T_r {0.9, 0.7, 0.5, 0.3, 0.2} x k {0.1, 0.4}, each half of the
+    storage choice (FP32 deviations, FP64) as one persistent batch: MLUPS of
+    each half and the cases still stable after warmup + steps."""
+    import torch
+    out = {"workload": "D2Q9 512^2 droplets r0=100, 6 schemes x 5 T_r x 2 k, per storage mode one batch"}
+    for name, prec in (("fp32dev", L.LBM_FP32DEV), ("fp64", L.LBM_FP64)):
+        params = [L.make_params(lattice=L.LBM_D2Q9, nx=512, ny=512, Tr=tr, k=k, kappa=0.1, scheme=sch, precision=prec)
+                  for sch in SWEEP_SCHEMES for tr in (0.9, 0.7, 0.5, 0.3, 0.2) for k in (0.1, 0.4)]
+        b = L.Batch(params)
+        b.lbm_batch_init_droplets([100.0] * len(params))
+        b.lbm_batch_step(warmup)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.lbm_batch_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rc, obs = b.lbm_batch_observables(raise_errors=False)
+        nodes = 512 * 512 * len(params)
+        out[name] = {"cases": len(params), "steps": steps, "ms": ms, "mlups": nodes * steps / (ms * 1e-3) / 1e6,
+                     "stable_cases": sum(1 for o in obs if o["status"] == 0), "status": rc}
+        b.close()
+    return out
+
+
 def run_2d(L, steps=200, warmup=20):
     """D2Q9 512^2 droplet (r0 = 100, T_r = 0.8, k = 0.25, EFDS6, FP32 deviation
     storage): BGK and the MRT operator of Eq. 1, 3-5; MLUPS and the roofline of
@@ -491,6 +520,7 @@ def run_gpu(args):
         extra["batch2d_explicit"] = run_batch(L, steps=args.batch_steps, ncases=args.batch_cases,
                                               schemes=SWEEP_SCHEMES[:5])
         extra["d2q9_512"] = run_2d(L)
+        extra["d2q9_512_sweep_batched"] = run_cfg2_sweep(L)
         extra["d3q19_compact"] = run_compact(L)
     if not args.no_warmstart:
         from paper_2205_09186_gb300 import warmstart as W

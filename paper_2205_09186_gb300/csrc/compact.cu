@@ -225,6 +225,8 @@ __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int
   const long long base = axis == 1 ? r * NXY + x0 : r * nx + x0;
   const long long stride = axis == 1 ? nx : NXY;
   const bool xin = x0 + lane < nx;
+  // every row load of the warp in flight before the first is used
+#pragma unroll
   for (int i = warp; i < L; i += LRT / 32) tile[i * 33 + lane] = xin ? in[base + i * stride + lane] : 0.f;
   __syncthreads();
   for (int j = warp; j < 32; j += LRT / 32) {
@@ -235,8 +237,10 @@ __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int
     for (int k = 0; k < LW; ++k) tile[(lane * LW + k) * 33 + j] = f.v[k];
   }
   __syncthreads();
-  if (xin)
+  if (xin) {
+#pragma unroll
     for (int i = warp; i < L; i += LRT / 32) out[base + i * stride + lane] = tile[i * 33 + lane];
+  }
 }
 
 template <int LW>
