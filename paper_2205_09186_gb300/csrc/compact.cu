@@ -104,9 +104,10 @@ cudaError_t run_lines(int axis, const KParams& kp, const Tin* in, double ref, T*
 // per register that looks past its lane's block), the right side of Eq. 21
 // 1 + 2 + 3 per direction; no selects.  The arithmetic is that of k_lines.
 // Lines are staged in shared memory to switch between the coalesced global
-// layout and the blocked one: x lines one row per warp, y and z lines a padded
-// tile of 32 lines of consecutive x.  One launch does both fields of an axis:
-// blocks of the first half take mu, of the second rho.
+// layout and the blocked one: x lines one row per warp, y and z lines padded
+// tiles of 32 lines of consecutive x.  One launch does both fields of an axis:
+// for x lines the first half of the blocks takes mu, the second rho; a block
+// of y or z lines takes the same 32 lines of both fields.
 constexpr int LRT = 256;  // 8 warps
 
 template <int LW>
@@ -185,13 +186,13 @@ __device__ __forceinline__ void solve_line(BlkLine<LW>& f, int lane, const LineC
 }
 
 // blocks: axis 0: 2 fields x ceil(lines / 8), one line per warp; axes 1, 2:
-// 2 fields x ceil(nx / 32) x (nz or ny), 32 lines of consecutive x per block
+// ceil(nx / 32) x (nz or ny), 32 lines of consecutive x of both fields per block
 template <int LW>
 __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int nz, const float* __restrict__ mu,
                                                    const float* __restrict__ rho, float* __restrict__ gmu,
                                                    float* __restrict__ grho, const LineCoef lc, unsigned half) {
   constexpr int L = 32 * LW;
-  extern __shared__ __align__(16) float tile[];  // axis 0: [8][L]; axes 1, 2: [L][33]
+  extern __shared__ __align__(16) float tile[];  // axis 0: [8][L]; axes 1, 2: 2 x [L][33]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool second = blockIdx.x >= half;
   const unsigned b = second ? blockIdx.x - half : blockIdx.x;
@@ -219,27 +220,40 @@ __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int
     for (int k = 0; k < LW; ++k) dst[lane + 32 * k] = t[lane + 32 * k];
     return;
   }
+  // y and z lines: both fields of the same 32 lines in one block (two tiles),
+  // so that twice the row loads are in flight while the block waits for them
+  const unsigned bb = blockIdx.x;
   const int gxs = (nx + 31) / 32;
-  const int x0 = int(b % gxs) * 32;
-  const long long r = b / gxs;  // z (axis 1) or y (axis 2)
+  const int x0 = int(bb % gxs) * 32;
+  const long long r = bb / gxs;  // z (axis 1) or y (axis 2)
   const long long base = axis == 1 ? r * NXY + x0 : r * nx + x0;
   const long long stride = axis == 1 ? nx : NXY;
   const bool xin = x0 + lane < nx;
+  float* t0 = tile;
+  float* t1 = tile + L * 33;
   // every row load of the warp in flight before the first is used
 #pragma unroll
-  for (int i = warp; i < L; i += LRT / 32) tile[i * 33 + lane] = xin ? in[base + i * stride + lane] : 0.f;
+  for (int i = warp; i < L; i += LRT / 32) {
+    t0[i * 33 + lane] = xin ? mu[base + i * stride + lane] : 0.f;
+    t1[i * 33 + lane] = xin ? rho[base + i * stride + lane] : 0.f;
+  }
   __syncthreads();
-  for (int j = warp; j < 32; j += LRT / 32) {
+  for (int j = warp; j < 64; j += LRT / 32) {
+    float* t = j < 32 ? t0 : t1;
+    const int jj = j & 31;
 #pragma unroll
-    for (int k = 0; k < LW; ++k) f.v[k] = tile[(lane * LW + k) * 33 + j];
+    for (int k = 0; k < LW; ++k) f.v[k] = t[(lane * LW + k) * 33 + jj];
     solve_line<LW>(f, lane, lc);
 #pragma unroll
-    for (int k = 0; k < LW; ++k) tile[(lane * LW + k) * 33 + j] = f.v[k];
+    for (int k = 0; k < LW; ++k) t[(lane * LW + k) * 33 + jj] = f.v[k];
   }
   __syncthreads();
   if (xin) {
 #pragma unroll
-    for (int i = warp; i < L; i += LRT / 32) out[base + i * stride + lane] = tile[i * 33 + lane];
+    for (int i = warp; i < L; i += LRT / 32) {
+      gmu[base + i * stride + lane] = t0[i * 33 + lane];
+      grho[base + i * stride + lane] = t1[i * 33 + lane];
+    }
   }
 }
 
@@ -254,10 +268,13 @@ cudaError_t launch_lines_reg(int axis, const KParams& kp, const float* mu, const
     smem = size_t(LRT / 32) * L * 4;
   } else {
     half = unsigned((long long)((kp.nx + 31) / 32) * (axis == 1 ? kp.nz : kp.ny));
-    smem = size_t(L) * 33 * 4;
+    smem = size_t(2) * L * 33 * 4;
   }
   if (cudaError_t e = ensure_smem(k_lines_reg<LW>, smem); e != cudaSuccess) return e;
-  k_lines_reg<LW><<<2 * half, LRT, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, mu, rho, gmu, grho, lf, half);
+  // axis 0: the first half of the blocks takes mu, the second rho; y and z:
+  // every block takes both
+  const unsigned blocks = axis == 0 ? 2 * half : half;
+  k_lines_reg<LW><<<blocks, LRT, smem, st>>>(axis, kp.nx, kp.ny, kp.nz, mu, rho, gmu, grho, lf, half);
   return cudaGetLastError();
 }
 
