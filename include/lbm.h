@@ -91,7 +91,11 @@ extern "C" {
  *  scheme    LBM_EFDS2 .. LBM_E8
  *  precision LBM_FP64 or LBM_FP32DEV
  *  mu_fp64   FP32DEV only: evaluate the EOS chemical potential in FP64
- *            (slower on GB300, whose FP64 rate is a small fraction of FP32)
+ *            (slower on GB300, whose FP64 rate is a small fraction of FP32).
+ *            D3Q19 with LBM_EFDS2/4/6: k^2 psi'(rho) in FP64 from rho_ref +
+ *            the float deviation, the mu field then rounded to float for the
+ *            stencils (3.5x the step time at 256^3); elsewhere mu and its
+ *            gradient stay in FP64 in the kernels
  *  rho_ref   FP32DEV only: reference density of the stored deviations;
  *            <= 0 selects the Maxwell gas density at Tr
  *  collision LBM_BGK, or LBM_MRT (D2Q9; LBM_ENOTSUP on D3Q19)

@@ -321,6 +321,12 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
     const int fbi = bsel(pc);
     float* fb = s_f + fbi * Sh::fbuf;
     float own0 = 0.f, ownp = 0.f, ownm = 0.f;  // this node's populations with e_x = e_y = 0
+    // post-collision populations moving along the row (e_y = 0, e_x != 0): they
+    // reach their target in the same warp and go there by shuffle, not through
+    // shared memory (only the six entries with e_y = 0, e_x != 0 are used)
+    float xmv[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) xmv[i] = 0.f;
     if (cnode) {
       int base[2 * R + 1];
 #pragma unroll
@@ -404,9 +410,13 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
           if (L::ey(i) != 0 && (L::ey(i) > 0) == up) fb[i * FPL + fme] = post(i);
       } else {
         auto keep = [&](const int i, const float fs) {
-          // populations that stay in this x-y column are gathered from registers
+          // populations that stay in this x-y column are gathered from
+          // registers, those moving along the row by shuffle, the others
+          // through shared memory
           if (L::ex(i) == 0 && L::ey(i) == 0) {
             if (L::ez(i) == 0) own0 = fs; else if (L::ez(i) > 0) ownp = fs; else ownm = fs;
+          } else if (L::ey(i) == 0) {
+            xmv[i] = fs;
           } else {
             fb[i * FPL + fme] = fs;
           }
@@ -458,13 +468,23 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
         }
       }
     }
+    if (ly >= 0 && ly < VH) {
+      // a tile row (a whole warp): the node at lane cx takes the row movers of
+      // lane cx - e_x (ring columns included; lanes past the region hold zeros)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (L::ey(i) != 0 || L::ex(i) == 0) continue;
+        const float v = __shfl_sync(0xffffffffu, xmv[i], (cx - L::ex(i)) & 31);
+        if (L::ez(i) < 0) ownm += v; else if (L::ez(i) == 0) own0 += v; else ownp += v;
+      }
+    }
     __syncthreads();
     // gather for the tile's own node of this thread
     if (interior) {
       float s_m = ownm, s_0 = own0, s_p = ownp;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        if (L::ex(i) == 0 && L::ey(i) == 0) continue;
+        if (L::ey(i) == 0) continue;  // own column and row movers are in the registers
         const float v = fb[i * FPL + fme - L::ey(i) * FW - L::ex(i)];
         if (L::ez(i) < 0) s_m += v; else if (L::ez(i) == 0) s_0 += v; else s_p += v;
       }
