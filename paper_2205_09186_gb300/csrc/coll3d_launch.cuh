@@ -1,5 +1,7 @@
 // Launcher of the D3Q19 FP32-deviation collision pass (k_coll3d) for one tile
-// shape: RY region rows (RY - 2 tile rows) and NB staged population planes.
+// shape: bands of RY rows (RowBands) and NB staged population planes.  The
+// pass adds into the edge rows of its output density: the mu pass of the same
+// step (launch_mu with an EdgeZero of the same RY) must have zeroed them.
 #pragma once
 #include <cuda.h>
 
@@ -26,7 +28,7 @@ cudaError_t launch_coll(const Launch& c, int zc) {
     }
   }
   if (cudaError_t e = ensure_smem(kc, by); e != cudaSuccess) return e;
-  const dim3 grid((c.kp.nx + TXC - 1) / TXC, (c.kp.ny + Sh::TY - 1) / Sh::TY, (c.kp.nz + zc - 1) / zc);
+  const dim3 grid((c.kp.nx + TXC - 1) / TXC, RowBands(c.kp.ny, RY).nb, (c.kp.nz + zc - 1) / zc);
   kc<<<grid, Sh::NT, by, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
                                      static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
                                      static_cast<float*>(c.rout), c.aux, zc,

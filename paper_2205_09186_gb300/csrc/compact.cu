@@ -350,16 +350,22 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   const unsigned g = unsigned((kp.n + bs - 1) / bs);
   Tm* mu = static_cast<Tm*>(cb.mu);
   cudaError_t e;
+  // D3Q19 FP32 steps collide on the tiled z-marching kernel when the lattice
+  // allows it; its output density's band edge rows are zeroed first
+  const bool gf3 = std::is_same<P, PrecF32>::value && D == 3 && mode == MODE_STEP && coll3d_gf_ok(c);
   if (std::is_same<P, PrecF32>::value && D == 3 && (cb.lap_order == 4 || cb.lap_order == 6)) {
     // FP32 mu in 3D: the z-marching mu pass of the split path
     Launch cm = c;
     cm.mu = mu;
-    e = mu3d_pass(cm, cb.lap_order);
+    e = mu3d_pass(cm, cb.lap_order, gf3);
   } else {
     if (cb.lap_order == 4) k_mu_field<Tm, Tr, 4><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
     else if (cb.lap_order == 6) k_mu_field<Tm, Tr, 6><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
     else k_mu_field<Tm, Tr, 8><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
     e = cudaGetLastError();
+    if constexpr (std::is_same<P, PrecF32>::value)
+      if (e == cudaSuccess && gf3)
+        e = coll3d_zero_edges(kp, rin, static_cast<float*>(c.rout), c.aux.bad_step, c.aux.t, c.stream);
   }
   if (e != cudaSuccess) return e;
   Tm* gmu = static_cast<Tm*>(cb.gmu);
@@ -378,10 +384,7 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   c.gi.gmu = gmu;
   c.gi.grho = grho;
   c.gi.mu = mu;
-  if (std::is_same<P, PrecF32>::value && D == 3 && mode == MODE_STEP) {
-    e = coll3d_gf_step(c, nblocks);
-    if (e != cudaErrorNotSupported) return e;
-  }
+  if (gf3) return coll3d_gf_step(c, nblocks);
   if (mode == MODE_STEP) return launch_gf<P, MODE_STEP>(c, D, nblocks);
   if (mode == MODE_OBS) return launch_gf<P, MODE_OBS>(c, D, nblocks);
   return launch_gf<P, MODE_FIELDS>(c, D, nblocks);

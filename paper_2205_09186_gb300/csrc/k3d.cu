@@ -40,6 +40,11 @@ static int split_zchunk_heuristic(const KParams& kp, int R, int ty, int per_sm) 
   return best_zc;
 }
 
+// CTAs of one collision pass (k_coll3d): 30-column tiles x row bands x z chunks
+static long long coll3d_ctas(const KParams& kp, int zc) {
+  return (long long)((kp.nx + TXC - 1) / TXC) * RowBands(kp.ny, CY).nb * ((kp.nz + zc - 1) / zc);
+}
+
 int fast_zchunk_heuristic(const KParams& kp, int R) {
   const int sms = num_sms();
   const long long tiles = (long long)((kp.nx + FT - 1) / FT) * ((kp.ny + FT - 1) / FT);
@@ -94,9 +99,12 @@ cudaError_t launch_fast(const Launch& c, int* nblocks) {
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
 
 
-// the mu pass: the vector kernel when rows are whole 16-byte chunks
+// the mu pass: the vector kernel when rows are whole 16-byte chunks; with
+// zero_edges it also prepares c.rout for the collision pass (EdgeZero)
 template <int S, bool M64 = false>
-cudaError_t launch_mu(const Launch& c) {
+cudaError_t launch_mu(const Launch& c, bool zero_edges = false) {
+  const EdgeZero ez{zero_edges ? static_cast<float*>(c.rout) : nullptr, CY, c.aux.bad_step, c.aux.t};
+  if (zero_edges && !c.rout) return cudaErrorInvalidValue;
   if (c.kp.nx % 4 == 0 && aligned16(c.rin) && aligned16(c.mu)) {
     // z chunks: enough CTAs for several waves, at least 8 planes per chunk
     const int gx = (c.kp.nx + MZX - 1) / MZX, gy = (c.kp.ny + MZY - 1) / MZY;
@@ -106,10 +114,10 @@ cudaError_t launch_mu(const Launch& c) {
     const int zc = (c.kp.nz + nzc - 1) / nzc;
     dim3 g(gx, gy, (c.kp.nz + zc - 1) / zc);
     k_mu3d_zm<S, M64><<<g, MZT, MuZShape<S>::bytes, c.stream>>>(c.kp, static_cast<const float*>(c.rin),
-                                                                static_cast<float*>(c.mu), zc);
+                                                                static_cast<float*>(c.mu), zc, ez);
   } else {
     dim3 g((c.kp.nx + MUX - 1) / MUX, (c.kp.ny + MUY - 1) / MUY, (c.kp.nz + MUZ - 1) / MUZ);
-    k_mu3d<S, M64><<<g, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu));
+    k_mu3d<S, M64><<<g, MUT, 0, c.stream>>>(c.kp, static_cast<const float*>(c.rin), static_cast<float*>(c.mu), ez);
   }
   return cudaGetLastError();
 }
@@ -120,7 +128,7 @@ template <int S, bool TAU1, bool M64 = false>
 cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   if (!c.mu) return cudaErrorInvalidValue;
   const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sch<S>::R, TYC, CollShape<S>::MINB);
-  const long long ctas = (long long)((c.kp.nx + TXC - 1) / TXC) * ((c.kp.ny + TYC - 1) / TYC) * ((c.kp.nz + zc - 1) / zc);
+  const long long ctas = coll3d_ctas(c.kp, zc);
   if (nblocks) {
     // observation: the caller's partials buffer holds *nblocks entries
     if (obs && ctas > *nblocks) return cudaErrorNotSupported;
@@ -128,7 +136,7 @@ cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   } else if (obs) {
     return cudaErrorInvalidValue;
   }
-  cudaError_t em = launch_mu<S, M64>(c);
+  cudaError_t em = launch_mu<S, M64>(c, true);
   if (em != cudaSuccess) return em;
   if (c.ev_mid) cudaEventRecord(c.ev_mid, c.stream);
   // 16-byte copies need rows of whole chunks and aligned bases
@@ -217,18 +225,44 @@ bool make_coll3d_tmap(const void* f, const KParams& kp, void* out, int rows) {
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+namespace {
+// one thread per node of the band edge rows: blockIdx.y = 2 band + (0: first row, 1: last row)
+__global__ void k_zero_edges(const KParams p, const float* __restrict__ rin, float* __restrict__ rout,
+                             unsigned long long* bad, long long t) {
+  const RowBands bands(p.ny, CY);
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int b = int(blockIdx.y) >> 1;
+  const int y = (blockIdx.y & 1) ? bands.start(b + 1) - 1 : bands.start(b);
+  const long long o = (long long)blockIdx.z * p.nx * p.ny + (long long)y * p.nx + x;
+  rout[o] = 0.f;
+  if (!(float(p.rho_ref) + rin[o] > 0.f)) atomicMin(bad, (unsigned long long)t);
+}
+}  // namespace
+
+cudaError_t coll3d_zero_edges(const KParams& kp, const float* rin, float* rout, unsigned long long* bad, long long t,
+                              cudaStream_t st) {
+  if (!rin || !rout || !bad || kp.nz > 65535) return cudaErrorInvalidValue;
+  const dim3 g((kp.nx + 127) / 128, 2 * RowBands(kp.ny, CY).nb, kp.nz);
+  k_zero_edges<<<g, 128, 0, st>>>(kp, rin, rout, bad, t);
+  return cudaGetLastError();
+}
+
+bool coll3d_gf_ok(const Launch& c) {
+  return c.kp.nx % 4 == 0 && aligned16(c.fin) && aligned16(c.rin) && c.tmap && c.rout;
+}
+
 cudaError_t coll3d_gf_step(const Launch& c, int* nblocks) {
-  if (c.kp.nx % 4 != 0 || !aligned16(c.fin) || !aligned16(c.rin) || !c.tmap || !c.gi.gmu || !c.gi.grho)
-    return cudaErrorNotSupported;
+  if (!coll3d_gf_ok(c) || !c.gi.gmu || !c.gi.grho) return cudaErrorNotSupported;
   const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, 0, TYC, 2);
-  if (nblocks) *nblocks = int((long long)((c.kp.nx + TXC - 1) / TXC) * ((c.kp.ny + TYC - 1) / TYC) * ((c.kp.nz + zc - 1) / zc));
+  if (nblocks) *nblocks = int(coll3d_ctas(c.kp, zc));
   return c.kp.omega == 1.0 ? launch_coll<S_CFDS4, true, true, false>(c, zc)
                            : launch_coll<S_CFDS4, false, true, false>(c, zc);
 }
 
-cudaError_t mu3d_pass(const Launch& c, int order) {
-  if (order == 4) return launch_mu<S_EFDS4>(c);
-  if (order == 6) return launch_mu<S_EFDS6>(c);
+cudaError_t mu3d_pass(const Launch& c, int order, bool zero_edges) {
+  if (order == 4) return launch_mu<S_EFDS4>(c, zero_edges);
+  if (order == 6) return launch_mu<S_EFDS6>(c, zero_edges);
   return cudaErrorNotSupported;
 }
 

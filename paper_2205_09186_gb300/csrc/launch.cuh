@@ -61,13 +61,24 @@ bool make_coll3d_tmap(const void* f, const KParams& kp, void* out, int rows = 11
 
 // D3Q19 FP32 mu field (Eq. 16) with the explicit central Laplacian of the
 // given order (4 or 6) from c.rin into c.mu (N floats): the mu pass of the
-// split path, shared with the compact schemes.
-cudaError_t mu3d_pass(const Launch& c, int order);
+// split path, shared with the compact schemes.  zero_edges: also zero the
+// rows of c.rout that the collision pass completes by atomic addition (the
+// edge rows of its row bands), as coll3d_gf_step needs.
+cudaError_t mu3d_pass(const Launch& c, int order, bool zero_edges);
+
+// Zero the edge rows of the collision pass's row bands in rout (N floats)
+// and flag step t in bad where the density rin is not positive there: what
+// mu3d_pass does with zero_edges, for a mu field computed otherwise.
+cudaError_t coll3d_zero_edges(const KParams& kp, const float* rin, float* rout, unsigned long long* bad, long long t,
+                              cudaStream_t st);
 
 // D3Q19 FP32DEV collision pass of the compact schemes on the tiled z-marching
-// kernel, the derivatives read from c.gi (gmu, grho: 3 x N floats each);
-// cudaErrorNotSupported (nothing launched) when the lattice or the buffers do
-// not allow the vector variant.
+// kernel, the derivatives read from c.gi (gmu, grho: 3 x N floats each).
+// coll3d_gf_ok tells whether the lattice and buffers allow it; when they do,
+// the edge rows of c.rout must have been zeroed in this step (mu3d_pass with
+// zero_edges, or coll3d_zero_edges) before coll3d_gf_step runs.  Otherwise
+// cudaErrorNotSupported, nothing launched.
+bool coll3d_gf_ok(const Launch& c);
 cudaError_t coll3d_gf_step(const Launch& c, int* nblocks);
 
 // Raise kernel fn's dynamic shared-memory limit to at least `bytes` on the

@@ -9,6 +9,43 @@
 
 namespace lbmd {
 
+// ------------------------------------------------------------------ row bands
+// The collision pass (k_coll3d) cuts the lattice's rows into bands of ry rows
+// (the last band may be shorter); band b holds rows [start(b), start(b + 1)).
+// A last band of a single row takes one row from the band before it, so that
+// every band has two distinct edge rows unless ny = 1.  The next density of a
+// band's first and last rows is completed by two atomic additions onto zero:
+// one from the band itself and one from the band that streams into the row
+// from the other side.  The mu pass that precedes the collision pass in the
+// same step zeroes those rows of the output density (EdgeZero below).
+struct RowBands {
+  int ny, ry, nb, adj;
+  __host__ __device__ RowBands(int ny_, int ry_) : ny(ny_), ry(ry_), nb((ny_ + ry_ - 1) / ry_), adj(0) {
+    if (nb >= 2 && ny - (nb - 1) * ry == 1) adj = 1;
+  }
+  __host__ __device__ int start(int b) const { return b >= nb ? ny : b * ry - (b == nb - 1 ? adj : 0); }
+  __host__ __device__ int band(int y) const {
+    const int b = y / ry < nb - 1 ? y / ry : nb - 1;
+    return (adj && b == nb - 2 && y >= start(nb - 1)) ? nb - 1 : b;
+  }
+  __host__ __device__ bool edge(int y) const {
+    const int b = band(y);
+    return y == start(b) || y == start(b + 1) - 1;
+  }
+};
+
+// What the mu pass does for the collision pass that follows it: zero the edge
+// rows of the collision pass's output density rz (bands of ry rows), and flag
+// step t in bad when the density of an edge-row node is not positive (the
+// collision pass checks the other rows of the density it produces, flagging
+// the same step index).  rz == nullptr: nothing.
+struct EdgeZero {
+  float* rz;
+  int ry;
+  unsigned long long* bad;
+  long long t;
+};
+
 // ------------------------------------------------------------------ mu pass
 // One CTA: a 32 x 8 x 8 block of nodes.  The block and its stencil halo are
 // copied to shared memory in one asynchronous batch (every copy of the CTA in
@@ -31,7 +68,7 @@ __device__ __forceinline__ float mu_value(const KParams& p, const EosF& ef, floa
 // line schemes only (the isotropic 3D Laplacian needs diagonal neighbours)
 template <int S, bool M64 = false>
 __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __restrict__ rin,
-                                              float* __restrict__ mu) {
+                                              float* __restrict__ mu, const EdgeZero ez) {
   static_assert(!Sch<S>::ISO, "line schemes only");
   constexpr int R = Sch<S>::R;
   constexpr int PW = MUX + 2 * R, PH = MUY + 2 * R, PD = MUZ + 2 * R;
@@ -72,6 +109,7 @@ __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __re
   for (int d = 0; d < 2 * R; ++d) q[d + 1] = blk[d][cy][cx];
   const int zend = min(MUZ, nz - z0);
   float* out = mu + z0 * NXY + (y0 + ty) * nx + x0 + tx;
+  const bool erow = ez.rz && RowBands(ny, ez.ry).edge(y0 + ty);
 #pragma unroll
   for (int dz = 0; dz < MUZ; ++dz) {
 #pragma unroll
@@ -86,6 +124,10 @@ __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __re
         lap += float(Sch<S>::l(m)) * ((blk[pz][cy][cx + m] + blk[pz][cy][cx - m]) +
                                       (blk[pz][cy + m][cx] + blk[pz][cy - m][cx]) + (q[R + m] + q[R - m]));
       out[dz * NXY] = mu_value<M64>(p, ef, k2, kap, rref, c, lap);
+      if (erow) {
+        ez.rz[(out - mu) + dz * NXY] = 0.f;
+        if (!(rref + c > 0.f)) atomicMin(ez.bad, (unsigned long long)ez.t);
+      }
     }
   }
 }
@@ -113,7 +155,7 @@ struct MuZShape {
 
 template <int S, bool M64 = false>
 __global__ void __launch_bounds__(MZT) k_mu3d_zm(const KParams p, const float* __restrict__ rin,
-                                                 float* __restrict__ mu, const int zc) {
+                                                 float* __restrict__ mu, const int zc, const EdgeZero ez) {
   static_assert(!Sch<S>::ISO, "line schemes only");
   using Sh = MuZShape<S>;
   constexpr int R = Sh::R, NCH = Sh::NCH, PH = Sh::PH, PCH = Sh::PCH, KC = (PCH + MZT - 1) / MZT;
@@ -147,6 +189,8 @@ __global__ void __launch_bounds__(MZT) k_mu3d_zm(const KParams p, const float* _
   const int tx = tid % (MZX / 4), ty = tid / (MZX / 4);
   const bool own = x0 + 4 * tx < nx && y0 + ty < ny;  // nx % 4 == 0: all four nodes or none
   const int col = own ? (y0 + ty) * nx + x0 + 4 * tx : 0;
+  const bool erow = ez.rz && own && RowBands(ny, ez.ry).edge(y0 + ty);
+  bool ebad = false;
   auto ld = [&](int z) { return __ldg(reinterpret_cast<const float4*>(rin + wrapi(z, nz) * NXY + col)); };
   const float k2 = float(p.k2), kap = float(p.kappa);
   const EosF ef = eos_f(p);
@@ -192,6 +236,13 @@ __global__ void __launch_bounds__(MZT) k_mu3d_zm(const KParams p, const float* _
       res[k] = mu_value<M64>(p, ef, k2, kap, rref, cv, lap);
     }
     *reinterpret_cast<float4*>(mu + z * NXY + col) = make_float4(res[0], res[1], res[2], res[3]);
+    if (erow) ebad |= !(rref + c4.x > 0.f && rref + c4.y > 0.f && rref + c4.z > 0.f && rref + c4.w > 0.f);
+  }
+  // the edge rows' zeroes after the march (inside it they cost the march its
+  // registers)
+  if (erow) {
+    for (int z = z0; z < z1; ++z) *reinterpret_cast<float4*>(ez.rz + z * NXY + col) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ebad) atomicMin(ez.bad, (unsigned long long)ez.t);
   }
 }
 

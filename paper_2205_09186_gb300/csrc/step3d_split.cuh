@@ -4,7 +4,8 @@
 //              (step3d_mu.cuh).
 //  k_coll3d    grad mu, grad rho (Eq. 17-25) -> F (Eq. 12) -> BGK + EDM
 //              (Eq. 1, 6, 8) -> push streaming, plus the next density, for
-//              a 30 x 9 tile and its one-node ring marching through z.
+//              a band of 11 rows x 30 columns (and the column on each side)
+//              marching through z.
 //
 // Compared with evaluating mu inside the collision kernel (where the halo
 // makes each CTA recompute it ~2.3 times per node and the recomputation
@@ -25,8 +26,8 @@
 namespace lbmd {
 
 // ------------------------------------------------------------------ collision pass
-constexpr int CX = 32, CY = 11;     // default collision region (tile + ring), one warp per row
-constexpr int TXC = CX - 2, TYC = CY - 2;  // 30 x 9 tile
+constexpr int CX = 32, CY = 11;     // default collision region (tile + ring columns), one warp per row
+constexpr int TXC = CX - 2, TYC = CY;  // 30 x 11 tile
 constexpr int CNT = CX * CY;        // 352 threads
 constexpr int FW = 36;              // staged population row: 32 nodes + up to 3 of alignment
 
@@ -43,18 +44,19 @@ constexpr int FW = 36;              // staged population row: 32 nodes + up to 3
 // of the populations viewed as a 4-D tensor (x, y, z, i) lands in exactly this
 // layout; the buffers are 1 KB aligned for it.
 //
-// RY rows of the region (RY - 2 tile rows, one warp each) and NB staged planes
-// of populations: the copies of plane z + NB - 1 are issued while plane z is
-// collided, so NB - 1 planes are in flight per CTA.  The field ring holds the
-// 2R + 1 planes of the stencil plus the NB - 1 in flight.
+// RY rows of the region (all of them tile rows, one warp each: the rows of one
+// band of RowBands) and NB staged planes of populations: the copies of plane
+// z + NB - 1 are issued while plane z is collided, so NB - 1 planes are in
+// flight per CTA.  The field ring holds the 2R + 1 planes of the stencil plus
+// the NB - 1 in flight.
 __host__ __device__ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 1) / 2); }
 
 template <int S, int RY_ = CY, int NB_ = 2>
 struct CollShape {
   static constexpr int R = Sch<S>::R;
-  static constexpr int RY = RY_, TY = RY_ - 2, NT = CX * RY_, NB = NB_;
+  static constexpr int RY = RY_, TY = RY_, NT = CX * RY_, NB = NB_;
   static_assert(NB >= 2 && NB <= 4, "two to four staged planes");
-  static constexpr int GW = CX + 2 * R, GH = RY + 2 * R;  // field region (ring + stencil halo)
+  static constexpr int GW = CX + 2 * R, GH = RY + 2 * R;  // field region (region + stencil halo)
   // ring of planes (NB - 1 in flight), a power of two so that a slot is a mask
   static constexpr int NS = pow2_at_least(2 * R + NB);
   static constexpr int plane = GH * GW;                   // float2 per field plane
@@ -134,6 +136,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
 // OBS: also reduce the observables of the state being advanced (max |v| with
 // v = u + F / (2 rho), max |u|, mass, max |rho - snap|) into aux.partials, one
 // set per CTA, and overwrite snap with this state's density deviation.
+// The CTA (blockIdx.y = band b of RowBands(ny, RY)) collides the nodes of its
+// band's rows in the columns x0 - 1 .. x0 + 30 (the outer two recomputed by the
+// neighbouring CTAs in x as their own) and gathers the next density of its 30
+// columns.  Rows inside the band get every incoming population from the band
+// and are stored; the band's first and last rows lack the populations that
+// come from the neighbouring bands, and the band's populations leaving through
+// those rows are summed per target node: both go into rout by atomic
+// addition onto the zeroes the mu pass wrote there.
 template <int S, bool TAU1, bool VEC, bool OBS, int RY_ = CY, int NB_ = 2>
 __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_coll3d(const KParams p, const float* __restrict__ fin,
                                                     float* __restrict__ fout, const float* __restrict__ rin,
@@ -156,15 +166,20 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int N = int(p.n), NXY = nx * ny;
-  const int x0 = blockIdx.x * TXC, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+  const RowBands bands(ny, RY);
+  const int x0 = blockIdx.x * TXC, y0 = bands.start(blockIdx.y), z0 = blockIdx.z * zc;
   const int z1 = min(z0 + zc, nz);
-  const int VW = min(TXC, nx - x0), VH = min(TY, ny - y0);
+  const int VW = min(TXC, nx - x0), VH = bands.start(blockIdx.y + 1) - y0;
   const int tid = threadIdx.x;
   const int cy = tid / CX, cx = tid - cy * CX;  // one warp per row
-  const int lx = cx - 1, ly = cy - 1;
-  const bool cnode = lx <= VW && ly <= VH;
-  const bool interior = lx >= 0 && lx < VW && ly >= 0 && ly < VH;
+  const int lx = cx - 1, ly = cy;
+  const bool crow = ly < VH;  // a row of the band (warp-uniform)
+  const bool cnode = lx <= VW && crow;
+  const bool interior = lx >= 0 && lx < VW && crow;
+  const bool top = ly == 0, bot = ly == VH - 1;  // edge rows (both when VH = 1)
   const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
+  // the row beyond this warp's edge (ny = 1: the row itself, whichever side)
+  const int yo = top ? wrapn(y0 - 1, ny) : wrapn(y0 + VH, ny);
   const float omega = float(p.omega), rref = float(p.rho_ref);
   const int pc_first = z0 - 1, pc_last = z1;
   // staging buffer (populations, GF derivatives, OBS snapshot) of plane pc
@@ -174,7 +189,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
   // tensor copies when the population region (36 columns from the aligned
   // start, RY rows) needs no periodic wrap
   // (and the staging buffers 128-byte aligned, as tensor copies require)
-  const bool tcta = VEC && x0 - 1 - of >= 0 && x0 - 1 - of + FW <= nx && y0 - 1 >= 0 && y0 - 1 + RY <= ny &&
+  const bool tcta = VEC && x0 - 1 - of >= 0 && x0 - 1 - of + FW <= nx && y0 + RY <= ny &&
                     (smem_u32(s_f) & 127u) == 0 && ((Sh::fbuf * 4) & 127) == 0;
   if (tcta && tid == 0) {
 #pragma unroll
@@ -197,7 +212,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
   for (int k = 0; k < Sh::KD; ++k) {
     const int e = tid + k * NT;
     const int ry = e / GW, rx = e - ry * GW;
-    dofs[k] = e < Sh::DE ? wrapn(y0 - 1 - R + ry, ny) * nx + wrapn(x0 - 1 - R + rx, nx) : 0;
+    dofs[k] = e < Sh::DE ? wrapn(y0 - R + ry, ny) * nx + wrapn(x0 - 1 - R + rx, nx) : 0;
   }
   if constexpr (VEC) {
     const int xaf = x0 - 1 - of;  // aligned start (may be negative)
@@ -205,7 +220,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
     for (int k = 0; k < Sh::KF; ++k) {
       const int c = tid + k * NT, i = c / (RY * (FW / 4));  // population of chunk c
       const int r = c - i * (RY * FW / 4), ry = r / (FW / 4), j = r - ry * (FW / 4);
-      fofs[k] = i * N + wrapn(y0 - 1 + ry, ny) * nx + wrapn(xaf + 4 * j, nx);
+      fofs[k] = i * N + wrapn(y0 + ry, ny) * nx + wrapn(xaf + 4 * j, nx);
     }
   }
 
@@ -253,7 +268,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
           asm volatile(
               "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
               " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(fd)),
-              "l"(reinterpret_cast<unsigned long long>(&tmf)), "r"(x0 - 1 - of), "r"(y0 - 1), "r"(wrapi(pc, nz)),
+              "l"(reinterpret_cast<unsigned long long>(&tmf)), "r"(x0 - 1 - of), "r"(y0), "r"(wrapi(pc, nz)),
               "r"(0), "r"(bar)
               : "memory");
         }
@@ -287,7 +302,8 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
     slot = (slot + 1) & (NS - 1);
   }
   int sc = R;  // ring slot of the collision plane
-  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;     // next density of this node, planes pc - 1 .. pc + 1
+  float oacc0 = 0.f, oacc1 = 0.f, oacc2 = 0.f;  // edge rows: of the node beyond, planes pc - 1 .. pc + 1
   const int fme = cy * FW + of + cx;  // this node in a staged population plane
   float o_v2 = 0.f, o_u2 = 0.f, o_d = 0.f;  // OBS: running maxima (4 |v|^2, |u|^2, |rho - snap|)
   float o_m = 0.f;                           // OBS: sum of this thread's density deviations
@@ -320,14 +336,11 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
     }
     const int fbi = bsel(pc);
     float* fb = s_f + fbi * Sh::fbuf;
-    float own0 = 0.f, ownp = 0.f, ownm = 0.f;  // this node's populations with e_x = e_y = 0
-    // post-collision populations moving along the row (e_y = 0, e_x != 0): they
-    // reach their target in the same warp and go there by shuffle, not through
-    // shared memory (only the six entries with e_y = 0, e_x != 0 are used)
-    float xmv[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) xmv[i] = 0.f;
-    if (cnode) {
+    float own0 = 0.f, ownp = 0.f, ownm = 0.f;  // this node's incoming populations with e_y = 0
+    if (crow) {
+      // every lane of a band row collides (lanes past a ragged region on staged
+      // values that nothing reads back), so that the exchanges by shuffle see a
+      // converged warp; shared-memory stores are masked by cnode, pushes by push
       int base[2 * R + 1];
 #pragma unroll
       for (int d = -R; d <= R; ++d) base[d + R] = ((sc + d) & (NS - 1)) * Sh::plane;
@@ -401,29 +414,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
           return (1.f - omega) * fv[i] + omega * wd + wr * (omega * Au + Av - Au);
         }
       };
-      if (ly < 0 || ly == VH) {
-        // ring row (a whole warp): the neighbouring tile row gathers only the
-        // five populations moving towards it
-        const bool up = ly < 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-          if (L::ey(i) != 0 && (L::ey(i) > 0) == up) fb[i * FPL + fme] = post(i);
-      } else {
-        auto keep = [&](const int i, const float fs) {
-          // populations that stay in this x-y column are gathered from
-          // registers, those moving along the row by shuffle, the others
-          // through shared memory
-          if (L::ex(i) == 0 && L::ey(i) == 0) {
-            if (L::ez(i) == 0) own0 = fs; else if (L::ez(i) > 0) ownp = fs; else ownm = fs;
-          } else if (L::ey(i) == 0) {
-            xmv[i] = fs;
-          } else {
-            fb[i * FPL + fme] = fs;
-          }
-        };
-        // Away from the periodic seams the target offset of population i is
-        // i N + e_x + e_y nx + e_z nx ny for every thread: a warp none of whose
-        // pushing nodes lies on a seam stores with these common offsets.
+      {
         // all 19 post-collision values first; at tau = 1 the pairs (i, i + 1)
         // of opposite velocities (e_{i+1} = -e_i for odd i) share e_i . v and
         // are evaluated two at a time by packed FMAs
@@ -445,46 +436,61 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
 #pragma unroll
           for (int i = 0; i < Q; ++i) pst[i] = post(i);
         }
-        const bool seam = push && (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1 || pz == 0 || pz == nz - 1);
-        if (!__any_sync(__activemask(), seam)) {
+        // populations that stay in this x-y column are gathered from
+        // registers; those moving along the row (e_y = 0, e_x != 0) reach a
+        // lane of this warp, which takes them by shuffle (ring columns
+        // included); in an edge row, those leaving the band are summed per
+        // target column the same way (oacc); the others go through shared memory
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (L::ey(i) != 0) continue;
+          const float v = L::ex(i) == 0 ? pst[i] : __shfl_sync(0xffffffffu, pst[i], (cx - L::ex(i)) & 31);
+          if (L::ez(i) < 0) ownm += v; else if (L::ez(i) == 0) own0 += v; else ownp += v;
+        }
+        if (top || bot) {
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
-            const float fs = pst[i];
-            keep(i, fs);
-            if (push) fo[i * N + L::ex(i) + L::ey(i) * nx + L::ez(i) * NXY] = fs;
+            if (!((L::ey(i) < 0 && top) || (L::ey(i) > 0 && bot))) continue;
+            const float v = L::ex(i) == 0 ? pst[i] : __shfl_sync(0xffffffffu, pst[i], (cx - L::ex(i)) & 31);
+            if (L::ez(i) < 0) oacc0 += v; else if (L::ez(i) == 0) oacc1 += v; else oacc2 += v;
           }
+        }
+        if (cnode) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            if (L::ey(i) == 0 || (L::ey(i) < 0 && top) || (L::ey(i) > 0 && bot)) continue;
+            fb[i * FPL + fme] = pst[i];
+          }
+        }
+        // Away from the periodic seams the target offset of population i is
+        // i N + e_x + e_y nx + e_z nx ny for every thread: a warp none of whose
+        // pushing nodes lies on a seam stores with these common offsets.
+        const bool seam = push && (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1 || pz == 0 || pz == nz - 1);
+        if (!__any_sync(0xffffffffu, seam)) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i)
+            if (push) fo[i * N + L::ex(i) + L::ey(i) * nx + L::ez(i) * NXY] = pst[i];
         } else {
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
-            const float fs = pst[i];
-            keep(i, fs);
             if (push) {
               const int d = (L::ex(i) > 0 ? dxp : (L::ex(i) < 0 ? dxm : 0)) +
                             (L::ey(i) > 0 ? dyp : (L::ey(i) < 0 ? dym : 0)) +
                             (L::ez(i) > 0 ? dzp : (L::ez(i) < 0 ? dzm : 0));
-              fo[i * N + d] = fs;
+              fo[i * N + d] = pst[i];
             }
           }
         }
       }
     }
-    if (ly >= 0 && ly < VH) {
-      // a tile row (a whole warp): the node at lane cx takes the row movers of
-      // lane cx - e_x (ring columns included; lanes past the region hold zeros)
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (L::ey(i) != 0 || L::ex(i) == 0) continue;
-        const float v = __shfl_sync(0xffffffffu, xmv[i], (cx - L::ex(i)) & 31);
-        if (L::ez(i) < 0) ownm += v; else if (L::ez(i) == 0) own0 += v; else ownp += v;
-      }
-    }
     __syncthreads();
-    // gather for the tile's own node of this thread
+    // gather for the band's own node of this thread
     if (interior) {
       float s_m = ownm, s_0 = own0, s_p = ownp;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         if (L::ey(i) == 0) continue;  // own column and row movers are in the registers
+        if ((L::ey(i) > 0 && top) || (L::ey(i) < 0 && bot)) continue;  // from the neighbouring band
         const float v = fb[i * FPL + fme - L::ey(i) * FW - L::ex(i)];
         if (L::ez(i) < 0) s_m += v; else if (L::ez(i) == 0) s_0 += v; else s_p += v;
       }
@@ -493,12 +499,22 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
       acc2 += s_p;
       const int zt = pc - 1;
       if (zt >= z0 && zt < z1) {
-        rout[zt * NXY + (y0 + ly) * nx + x0 + lx] = acc0;
-        if (!(rref + acc0 > 0.f)) atomicMin(aux.bad_step, (unsigned long long)(aux.t + 1));
+        float* dst = rout + zt * NXY + (y0 + ly) * nx + x0 + lx;
+        if (top || bot) {
+          // completed by the neighbouring band's addition (positivity: the mu pass)
+          atomicAdd(dst, acc0);
+          atomicAdd(rout + zt * NXY + yo * nx + x0 + lx, oacc0);
+        } else {
+          *dst = acc0;
+          if (!(rref + acc0 > 0.f)) atomicMin(aux.bad_step, (unsigned long long)(aux.t + 1));
+        }
       }
       acc0 = acc1;
       acc1 = acc2;
       acc2 = 0.f;
+      oacc0 = oacc1;
+      oacc1 = oacc2;
+      oacc2 = 0.f;
     }
     sc = (sc + 1) & (NS - 1);
   }
