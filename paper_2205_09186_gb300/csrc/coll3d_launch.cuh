@@ -10,10 +10,10 @@
 
 namespace lbmd {
 
-template <int S, bool TAU1, bool VEC, bool OBS, int RY = CY, int NB = 2>
+template <int S, bool TAU1, bool VEC, bool OBS, int RY = CY, int NB = 2, int FD = (Sch<S>::GF ? 1 : COLL_FD)>
 cudaError_t launch_coll(const Launch& c, int zc) {
-  using Sh = CollShape<S, RY, NB>;
-  auto kc = k_coll3d<S, TAU1, VEC, OBS, RY, NB>;
+  using Sh = CollShape<S, RY, NB, FD>;
+  auto kc = k_coll3d<S, TAU1, VEC, OBS, RY, NB, FD>;
   constexpr size_t by = OBS ? Sh::bytes_obs : Sh::bytes;
   static_assert(by <= size_t(227) * 1024, "shared memory of one CTA");
   CUtensorMap tm{};

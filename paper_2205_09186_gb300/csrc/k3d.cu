@@ -127,7 +127,7 @@ cudaError_t launch_mu(const Launch& c, bool zero_edges = false) {
 template <int S, bool TAU1, bool M64 = false>
 cudaError_t launch_split(const Launch& c, int* nblocks, bool obs) {
   if (!c.mu) return cudaErrorInvalidValue;
-  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sch<S>::R, TYC, CollShape<S>::MINB);
+  const int zc = c.zc > 0 ? c.zc : split_zchunk_heuristic(c.kp, Sch<S>::R, TYC, CollShape<S, CY, 2, COLL_FD>::MINB);
   const long long ctas = coll3d_ctas(c.kp, zc);
   if (nblocks) {
     // observation: the caller's partials buffer holds *nblocks entries

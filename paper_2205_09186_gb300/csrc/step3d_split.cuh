@@ -30,6 +30,7 @@ constexpr int CX = 32, CY = 11;     // default collision region (tile + ring col
 constexpr int TXC = CX - 2, TYC = CY;  // 30 x 11 tile
 constexpr int CNT = CX * CY;        // 352 threads
 constexpr int FW = 36;              // staged population row: 32 nodes + up to 3 of alignment
+constexpr int COLL_FD = 1;          // field planes issued this many planes ahead (1 or 2)
 
 // Field planes: the density deviation and mu of a node side by side (one
 // float2, x = deviation, y = mu), copied in by two 4-byte copies per node, so
@@ -51,14 +52,17 @@ constexpr int FW = 36;              // staged population row: 32 nodes + up to 3
 // the NB - 1 in flight.
 __host__ __device__ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 1) / 2); }
 
-template <int S, int RY_ = CY, int NB_ = 2>
+template <int S, int RY_ = CY, int NB_ = 2, int FD_ = 1>
 struct CollShape {
   static constexpr int R = Sch<S>::R;
-  static constexpr int RY = RY_, TY = RY_, NT = CX * RY_, NB = NB_;
+  static constexpr int RY = RY_, TY = RY_, NT = CX * RY_, NB = NB_, FD = FD_;
   static_assert(NB >= 2 && NB <= 4, "two to four staged planes");
+  static_assert(FD == 1 || (FD == 2 && NB == 2 && !Sch<S>::GF), "field planes one or two planes ahead");
   static constexpr int GW = CX + 2 * R, GH = RY + 2 * R;  // field region (region + stencil halo)
-  // ring of planes (NB - 1 in flight), a power of two so that a slot is a mask
-  static constexpr int NS = pow2_at_least(2 * R + NB);
+  // ring of field planes: FD = 1, the stencil's 2R + 1 and the NB - 1 in
+  // flight, rounded up to a power of two so that a slot is a mask; FD = 2, the
+  // stencil's and two more (one landed or in flight, one being issued)
+  static constexpr int NS = FD == 1 ? pow2_at_least(2 * R + NB) : 2 * R + 1 + FD;
   static constexpr int plane = GH * GW;                   // float2 per field plane
   static constexpr int FPL = RY * FW;                     // staged populations of one i
   static constexpr int fbuf = (19 * FPL + 255) / 256 * 256;  // buffer stride (floats), 1 KB multiple
@@ -144,17 +148,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
 // come from the neighbouring bands, and the band's populations leaving through
 // those rows are summed per target node: both go into rout by atomic
 // addition onto the zeroes the mu pass wrote there.
-template <int S, bool TAU1, bool VEC, bool OBS, int RY_ = CY, int NB_ = 2>
-__global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_coll3d(const KParams p, const float* __restrict__ fin,
+template <int S, bool TAU1, bool VEC, bool OBS, int RY_ = CY, int NB_ = 2, int FD_ = COLL_FD>
+__global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) k_coll3d(const KParams p, const float* __restrict__ fin,
                                                     float* __restrict__ fout, const float* __restrict__ rin,
                                                     const float* __restrict__ muf, float* __restrict__ rout,
                                                     const StepAux aux, const int zc, float* __restrict__ snap,
                                                     const __grid_constant__ CUtensorMap tmf,
                                                     const float* __restrict__ gmu, const float* __restrict__ grho) {
   using L = Lattice<1>;
-  using Sh = CollShape<S, RY_, NB_>;
+  using Sh = CollShape<S, RY_, NB_, FD_>;
   constexpr int Q = 19, R = Sh::R, GW = Sh::GW, NS = Sh::NS, FPL = Sh::FPL;
-  constexpr int RY = Sh::RY, TY = Sh::TY, NT = Sh::NT, NB = Sh::NB;
+  constexpr int RY = Sh::RY, TY = Sh::TY, NT = Sh::NT, NB = Sh::NB, FD = Sh::FD;
   extern __shared__ __align__(1024) unsigned char smem_c3[];  // (own name: other kernels align theirs to 16)
   unsigned char* smem = smem_c3;
   __shared__ __align__(8) unsigned long long s_bar[NB];  // tensor copies: one mbarrier per buffer
@@ -226,27 +230,11 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
 
   // field planes q (density deviation and mu) -> ring slot; populations of
   // plane q - R (if collided) -> its staging buffer
-  auto issue = [&](int q, int slot) {
-    const int zo = wrapi(q, nz) * NXY;  // q in [z0 - 1 - R, z1 + R]: one period at most
-    float2* dd = s_dm + slot * Sh::plane;
-    const int pc = q - R;
-    const bool fl = pc >= pc_first && pc <= pc_last;
-    const int zf = wrapi(pc, nz) * NXY;
-    const int pb = bsel(pc);
-    float* fd = s_f + pb * Sh::fbuf;
-    if constexpr (GF) {
-      // this node's deviation and derivatives in plane pc (R = 0: q = pc)
-      if (fl && cnode) {
-        float* gd = s_g + pb * Sh::NG * NT + tid;
-        const int o = zf + gy * nx + gx;
-        cpa4(gd, rin + o);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          cpa4(gd + (1 + a) * NT, gmu + a * N + o);
-          cpa4(gd + (4 + a) * NT, grho + a * N + o);
-        }
-      }
-    } else {
+  // the field plane q (density deviation and mu) into ring slot `slot`
+  auto issue_fields = [&](int q, int slot) {
+    if constexpr (!GF) {
+      const int zo = wrapi(q, nz) * NXY;  // q in [z0 - 1 - R, z1 + R]: one period at most
+      float2* dd = s_dm + slot * Sh::plane;
 #pragma unroll
       for (int k = 0; k < Sh::KD; ++k) {
         const int e = tid + k * NT;
@@ -256,8 +244,28 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
         }
       }
     }
+  };
+  // the populations of plane pc (and, GF, this node's derivatives; OBS, its
+  // snapshot value) into the plane's staging buffer
+  auto issue_plane = [&](int pc) {
+    const int zf = wrapi(pc, nz) * NXY;
+    const int pb = bsel(pc);
+    float* fd = s_f + pb * Sh::fbuf;
+    if constexpr (GF) {
+      // this node's deviation and derivatives in plane pc
+      if (cnode) {
+        float* gd = s_g + pb * Sh::NG * NT + tid;
+        const int o = zf + gy * nx + gx;
+        cpa4(gd, rin + o);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          cpa4(gd + (1 + a) * NT, gmu + a * N + o);
+          cpa4(gd + (4 + a) * NT, grho + a * N + o);
+        }
+      }
+    }
     if constexpr (VEC) {
-      if (fl && tcta) {
+      if (tcta) {
         if (tid == 0 && !tma_lost) {
           // the buffer's previous contents were read and written through the
           // generic proxy before the barrier that precedes this call
@@ -272,7 +280,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
               "r"(0), "r"(bar)
               : "memory");
         }
-      } else if (fl) {
+      } else {
 #pragma unroll
         for (int k = 0; k < Sh::KF; ++k) {
           const int c = tid + k * NT;
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
         }
       }
     } else {
-      if (fl && cnode) {
+      if (cnode) {
         const float* fs = fin + zf + gy * nx + gx;
         float* fo = fd + cy * FW + cx;
 #pragma unroll
@@ -291,15 +299,38 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
       // the snapshot of this thread's node in plane pc (push planes only)
       if (interior && pc >= z0 && pc < z1) cpa4(s_snap + pb * NT + tid, snap + pc * NXY + gy * nx + gx);
     }
-    cpa_commit();
+  };
+  auto ring = [&](int v) {  // a slot index in [-NS, 2 NS) into [0, NS)
+    if constexpr ((NS & (NS - 1)) == 0) return v & (NS - 1);
+    else return v < 0 ? v + NS : (v >= NS ? v - NS : v);
   };
 
-  // prologue: field planes pc_first - R .. pc_first + R + NB - 2 (populations
-  // of planes pc_first .. pc_first + NB - 2), one copy group per plane
+  // prologue.  FD = 1: field planes pc_first - R .. pc_first + R + NB - 2 with
+  // the populations of planes pc_first .. pc_first + NB - 2, one copy group per
+  // plane.  FD = 2: the stencil's field planes (one group), the populations of
+  // plane pc_first (one group), field plane pc_first + R + 1 (one group); every
+  // plane then commits two groups, its next plane's populations and the field
+  // plane two planes ahead, so that waiting for all but the latest group leaves
+  // that field plane in flight.
   int slot = 0;  // ring slot of plane pc_first - R + (number issued)
-  for (int q = pc_first - R; q <= pc_first + R + NB - 2; ++q) {
-    issue(q, slot);
-    slot = (slot + 1) & (NS - 1);
+  if constexpr (FD == 1) {
+    for (int q = pc_first - R; q <= pc_first + R + NB - 2; ++q) {
+      issue_fields(q, slot);
+      if (q - R >= pc_first) issue_plane(q - R);
+      cpa_commit();
+      slot = ring(slot + 1);
+    }
+  } else {
+    for (int q = pc_first - R; q <= pc_first + R; ++q) {
+      issue_fields(q, slot);
+      slot = ring(slot + 1);
+    }
+    cpa_commit();
+    issue_plane(pc_first);
+    cpa_commit();
+    issue_fields(pc_first + R + 1, slot);
+    slot = ring(slot + 1);
+    cpa_commit();
   }
   int sc = R;  // ring slot of the collision plane
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;     // next density of this node, planes pc - 1 .. pc + 1
@@ -310,8 +341,9 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
   int o_n = 0;                               // OBS: nodes counted
   const int snap_xy = gy * nx + gx;  // OBS: this thread's node in a plane
   for (int pc = pc_first; pc <= pc_last; ++pc) {
-    // one copy group per plane, the NB - 2 latest may still be in flight
-    cpa_wait_n<NB - 2>();
+    // FD = 1: one copy group per plane, the NB - 2 latest may still be in
+    // flight; FD = 2: the latest group (a field plane) may
+    cpa_wait_n<FD == 1 ? NB - 2 : 1>();
     if (tcta) {
       // this plane's tensor copy has landed (bounded wait; on time-out the
       // step is marked bad and the march goes on with whatever arrived)
@@ -328,11 +360,21 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (pc + NB - 1 <= pc_last) {
-      issue(pc + R + NB - 1, slot);
-      slot = (slot + 1) & (NS - 1);
+    if constexpr (FD == 1) {
+      if (pc + NB - 1 <= pc_last) {
+        issue_fields(pc + R + NB - 1, slot);
+        issue_plane(pc + NB - 1);
+        slot = ring(slot + 1);
+      }
+      cpa_commit();  // (empty at the end: the wait above counts one group per plane)
     } else {
-      cpa_commit();  // an empty group: the wait above counts one group per plane
+      if (pc + 1 <= pc_last) issue_plane(pc + 1);
+      cpa_commit();
+      if (pc + 2 <= pc_last) {
+        issue_fields(pc + R + 2, slot);
+        slot = ring(slot + 1);
+      }
+      cpa_commit();
     }
     const int fbi = bsel(pc);
     float* fb = s_f + fbi * Sh::fbuf;
@@ -343,7 +385,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
       // converged warp; shared-memory stores are masked by cnode, pushes by push
       int base[2 * R + 1];
 #pragma unroll
-      for (int d = -R; d <= R; ++d) base[d + R] = ((sc + d) & (NS - 1)) * Sh::plane;
+      for (int d = -R; d <= R; ++d) base[d + R] = ring(sc + d) * Sh::plane;
       float fv[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) fv[i] = fb[i * FPL + fme];
@@ -516,7 +558,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_>::MINB)) k_col
       oacc1 = oacc2;
       oacc2 = 0.f;
     }
-    sc = (sc + 1) & (NS - 1);
+    sc = ring(sc + 1);
   }
   // the issuing thread keeps the CTA (and its shared memory) alive until a
   // copy that missed its wait has landed, or a second bounded wait runs out
