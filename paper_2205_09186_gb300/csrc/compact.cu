@@ -185,44 +185,43 @@ __device__ __forceinline__ void solve_line(BlkLine<LW>& f, int lane, const LineC
   f = r;
 }
 
-// blocks: axis 0: 2 fields x ceil(lines / 8), one line per warp; axes 1, 2:
-// ceil(nx / 32) x (nz or ny), 32 lines of consecutive x of both fields per block
+// x lines: 8 lines of one field per block, one line per warp, staged per
+// warp in a row of the shared tile (tile: [8][L] floats)
 template <int LW>
-__global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int nz, const float* __restrict__ mu,
-                                                   const float* __restrict__ rho, float* __restrict__ gmu,
-                                                   float* __restrict__ grho, const LineCoef lc, unsigned half) {
+__device__ __forceinline__ void lines_reg_x(unsigned b, int nx, int ny, int nz, const float* __restrict__ in,
+                                            float* __restrict__ out, const LineCoef& lc, float* tile) {
   constexpr int L = 32 * LW;
-  extern __shared__ __align__(16) float tile[];  // axis 0: [8][L]; axes 1, 2: 2 x [L][33]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool second = blockIdx.x >= half;
-  const unsigned b = second ? blockIdx.x - half : blockIdx.x;
-  const float* in = second ? rho : mu;
-  float* out = second ? grho : gmu;
-  const long long NXY = (long long)nx * ny;
+  const long long row = (long long)b * (LRT / 32) + warp;
+  if (row >= (long long)ny * nz) return;  // whole warps only: the warp's own row of the tile, no CTA barrier
+  float* t = tile + warp * L;
+  const float* src = in + row * nx;
   BlkLine<LW> f;
-  if (axis == 0) {
-    const long long row = (long long)b * (LRT / 32) + warp;
-    if (row >= (long long)ny * nz) return;  // whole warps only: the warp's own row of the tile, no CTA barrier
-    float* t = tile + warp * L;
-    const float* src = in + row * nx;
 #pragma unroll
-    for (int k = 0; k < LW; ++k) t[lane + 32 * k] = src[lane + 32 * k];
-    __syncwarp();
+  for (int k = 0; k < LW; ++k) t[lane + 32 * k] = src[lane + 32 * k];
+  __syncwarp();
 #pragma unroll
-    for (int k = 0; k < LW; ++k) f.v[k] = t[lane * LW + k];
-    solve_line<LW>(f, lane, lc);
-    __syncwarp();
+  for (int k = 0; k < LW; ++k) f.v[k] = t[lane * LW + k];
+  solve_line<LW>(f, lane, lc);
+  __syncwarp();
 #pragma unroll
-    for (int k = 0; k < LW; ++k) t[lane * LW + k] = f.v[k];
-    __syncwarp();
-    float* dst = out + row * nx;
+  for (int k = 0; k < LW; ++k) t[lane * LW + k] = f.v[k];
+  __syncwarp();
+  float* dst = out + row * nx;
 #pragma unroll
-    for (int k = 0; k < LW; ++k) dst[lane + 32 * k] = t[lane + 32 * k];
-    return;
-  }
-  // y and z lines: both fields of the same 32 lines in one block (two tiles),
-  // so that twice the row loads are in flight while the block waits for them
-  const unsigned bb = blockIdx.x;
+  for (int k = 0; k < LW; ++k) dst[lane + 32 * k] = t[lane + 32 * k];
+}
+
+// y (axis 1) or z (axis 2) lines: block bb = (32 consecutive x) x (z or y);
+// both fields of the same 32 lines in one block (tile: 2 x [L][33] floats), so
+// that twice the row loads are in flight while the block waits for them
+template <int LW>
+__device__ __forceinline__ void lines_reg_yz(int axis, unsigned bb, int nx, int ny, const float* __restrict__ mu,
+                                             const float* __restrict__ rho, float* __restrict__ gmu,
+                                             float* __restrict__ grho, const LineCoef& lc, float* tile) {
+  constexpr int L = 32 * LW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long NXY = (long long)nx * ny;
   const int gxs = (nx + 31) / 32;
   const int x0 = int(bb % gxs) * 32;
   const long long r = bb / gxs;  // z (axis 1) or y (axis 2)
@@ -231,6 +230,7 @@ __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int
   const bool xin = x0 + lane < nx;
   float* t0 = tile;
   float* t1 = tile + L * 33;
+  BlkLine<LW> f;
   // every row load of the warp in flight before the first is used
 #pragma unroll
   for (int i = warp; i < L; i += LRT / 32) {
@@ -257,6 +257,47 @@ __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int
   }
 }
 
+// one axis: axis 0, 2 fields x ceil(lines / 8) blocks (the first `half` take
+// mu); axes 1, 2, ceil(nx / 32) x (nz or ny) blocks of both fields
+template <int LW>
+__global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int nz, const float* __restrict__ mu,
+                                                   const float* __restrict__ rho, float* __restrict__ gmu,
+                                                   float* __restrict__ grho, const LineCoef lc, unsigned half) {
+  extern __shared__ __align__(16) float tile[];
+  if (axis == 0) {
+    const bool second = blockIdx.x >= half;
+    lines_reg_x<LW>(second ? blockIdx.x - half : blockIdx.x, nx, ny, nz, second ? rho : mu, second ? grho : gmu, lc,
+                    tile);
+  } else {
+    lines_reg_yz<LW>(axis, blockIdx.x, nx, ny, mu, rho, gmu, grho, lc, tile);
+  }
+}
+
+// the three axes of a lattice whose edges are all L = 32 LW long, in one
+// launch: blocks [0, nyz) the z lines, [nyz, 2 nyz) the y lines, then the x
+// lines (2 xh blocks, the first xh taking mu); the derivative fields are
+// component-major (3 x N floats).  One launch instead of three: the blocks of
+// all axes share the reads of mu and rho through L2, and the tail of one axis
+// overlaps the others.
+template <int LW>
+__global__ void __launch_bounds__(LRT) k_lines_reg3(int n, const float* __restrict__ mu,
+                                                    const float* __restrict__ rho, float* __restrict__ gmu,
+                                                    float* __restrict__ grho, const LineCoef lc, unsigned nyz,
+                                                    unsigned xh) {
+  extern __shared__ __align__(16) float tile[];
+  const long long N = (long long)n * n * n;
+  const unsigned b = blockIdx.x;
+  if (b < nyz) {
+    lines_reg_yz<LW>(2, b, n, n, mu, rho, gmu + 2 * N, grho + 2 * N, lc, tile);
+  } else if (b < 2 * nyz) {
+    lines_reg_yz<LW>(1, b - nyz, n, n, mu, rho, gmu + N, grho + N, lc, tile);
+  } else {
+    const unsigned bx = b - 2 * nyz;
+    const bool second = bx >= xh;
+    lines_reg_x<LW>(second ? bx - xh : bx, n, n, n, second ? rho : mu, second ? grho : gmu, lc, tile);
+  }
+}
+
 template <int LW>
 cudaError_t launch_lines_reg(int axis, const KParams& kp, const float* mu, const float* rho, float* gmu, float* grho,
                              const LineCoef& lf, cudaStream_t st) {
@@ -278,20 +319,61 @@ cudaError_t launch_lines_reg(int axis, const KParams& kp, const float* mu, const
   return cudaGetLastError();
 }
 
-// grad mu and grad rho along one axis of FP32 fields: the register kernel
-// when the line length is a multiple of 32 (64 .. 512), else k_lines per field
-cudaError_t run_lines_pair_f32(int axis, const KParams& kp, const float* mu, const float* rho, float* gmu,
-                               float* grho, const LineCoef& lc, cudaStream_t st) {
-  const int L = axis == 0 ? kp.nx : (axis == 1 ? kp.ny : kp.nz);
+// coefficients of the register kernels: the levels' row scalings folded into
+// the right side
+static LineCoef reg_coef(const LineCoef& lc) {
   const LineCoef lf = line_coef_for(lc, true);
-  // the register kernel: the levels' row scalings folded into the right side
   LineCoef lr = lf;
   double scale = 1.0;
   for (int k = 0; k < lf.nlev; ++k) scale *= lf.inv[k];
   lr.A1 = lf.A1 * scale;
   lr.A2 = lf.A2 * scale;
   lr.A3 = lf.A3 * scale;
-  if (L % 32 == 0 && lf.nlev <= 16) {
+  return lr;
+}
+
+template <int LW>
+cudaError_t launch_lines_reg3(const KParams& kp, const float* mu, const float* rho, float* gmu, float* grho,
+                              const LineCoef& lr, cudaStream_t st) {
+  constexpr int L = 32 * LW;
+  const unsigned nyz = unsigned((long long)((L + 31) / 32) * L);
+  const unsigned xh = unsigned(((long long)L * L + LRT / 32 - 1) / (LRT / 32));
+  const size_t smem = size_t(2) * L * 33 * 4;
+  if (cudaError_t e = ensure_smem(k_lines_reg3<LW>, smem); e != cudaSuccess) return e;
+  k_lines_reg3<LW><<<2 * nyz + 2 * xh, LRT, smem, st>>>(L, mu, rho, gmu, grho, lr, nyz, xh);
+  return cudaGetLastError();
+}
+
+// grad mu and grad rho along all three axes of FP32 fields on a cubic lattice
+// (gmu, grho component-major, 3 x N floats) in one launch, when its edge is a
+// multiple of 32 (64 .. 512); cudaErrorNotSupported (nothing launched) otherwise
+cudaError_t run_lines3_f32(const KParams& kp, const float* mu, const float* rho, float* gmu, float* grho,
+                           const LineCoef& lc, cudaStream_t st) {
+  if (kp.nx != kp.ny || kp.nx != kp.nz || kp.nx % 32 != 0) return cudaErrorNotSupported;
+  const LineCoef lr = reg_coef(lc);
+  if (lr.nlev > 16) return cudaErrorNotSupported;
+  switch (kp.nx / 32) {
+    case 2: return launch_lines_reg3<2>(kp, mu, rho, gmu, grho, lr, st);
+    case 3: return launch_lines_reg3<3>(kp, mu, rho, gmu, grho, lr, st);
+    case 4: return launch_lines_reg3<4>(kp, mu, rho, gmu, grho, lr, st);
+    case 5: return launch_lines_reg3<5>(kp, mu, rho, gmu, grho, lr, st);
+    case 6: return launch_lines_reg3<6>(kp, mu, rho, gmu, grho, lr, st);
+    case 7: return launch_lines_reg3<7>(kp, mu, rho, gmu, grho, lr, st);
+    case 8: return launch_lines_reg3<8>(kp, mu, rho, gmu, grho, lr, st);
+    case 10: return launch_lines_reg3<10>(kp, mu, rho, gmu, grho, lr, st);
+    case 12: return launch_lines_reg3<12>(kp, mu, rho, gmu, grho, lr, st);
+    case 16: return launch_lines_reg3<16>(kp, mu, rho, gmu, grho, lr, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+// grad mu and grad rho along one axis of FP32 fields: the register kernel
+// when the line length is a multiple of 32 (64 .. 512), else k_lines per field
+cudaError_t run_lines_pair_f32(int axis, const KParams& kp, const float* mu, const float* rho, float* gmu,
+                               float* grho, const LineCoef& lc, cudaStream_t st) {
+  const int L = axis == 0 ? kp.nx : (axis == 1 ? kp.ny : kp.nz);
+  const LineCoef lr = reg_coef(lc);
+  if (L % 32 == 0 && lr.nlev <= 16) {
     switch (L / 32) {
       case 2: return launch_lines_reg<2>(axis, kp, mu, rho, gmu, grho, lr, st);
       case 3: return launch_lines_reg<3>(axis, kp, mu, rho, gmu, grho, lr, st);
@@ -370,7 +452,15 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   if (e != cudaSuccess) return e;
   Tm* gmu = static_cast<Tm*>(cb.gmu);
   Tc* grho = static_cast<Tc*>(cb.grho);
-  for (int ax = 0; ax < D; ++ax) {
+  bool lines_done = false;
+  if constexpr (std::is_same<P, PrecF32>::value) {
+    if (D == 3) {
+      e = run_lines3_f32(kp, mu, rin, gmu, grho, cb.lc, c.stream);
+      if (e != cudaSuccess && e != cudaErrorNotSupported) return e;
+      lines_done = e == cudaSuccess;
+    }
+  }
+  for (int ax = 0; ax < D && !lines_done; ++ax) {
     if constexpr (std::is_same<P, PrecF32>::value) {
       e = run_lines_pair_f32(ax, kp, mu, rin, gmu + size_t(ax) * kp.n, grho + size_t(ax) * kp.n, cb.lc, c.stream);
       if (e != cudaSuccess) return e;

@@ -92,8 +92,12 @@ def test_fp32dev_against_oracle(L, lattice, shape, scheme, mu_fp64):
 
 # nx % 4 == 0 takes the 16-byte (vector) mu and collision kernels, other nx the
 # 4-byte ones; 68 = 64 + 4 leaves a 4-wide vector block, 8^3 wraps every halo
-# several times around the lattice
-@pytest.mark.parametrize("shape", [(68, 40, 36), (42, 26, 20), (8, 8, 8), (12, 9, 10)])
+# several times around the lattice.  The collision pass cuts the rows into
+# bands of 11 whose edge rows are completed by atomic additions: ny = 45 and
+# 12 leave a last band of one row, which takes a row from the band before it;
+# ny = 11 is one band whose two edge rows feed each other across the seam
+@pytest.mark.parametrize("shape", [(68, 40, 36), (42, 26, 20), (8, 8, 8), (12, 9, 10), (64, 45, 20), (36, 12, 10),
+                                   (40, 11, 12)])
 @pytest.mark.parametrize("scheme", ["EFDS2", "EFDS6"])
 def test_fp32dev_kernel_variants_against_oracle(L, shape, scheme):
     nx, ny, nz = shape
@@ -107,6 +111,21 @@ def test_fp32dev_kernel_variants_against_oracle(L, shape, scheme):
     assert o.step(30) == 0
     err = np.max(np.abs(g.lbm_get_density() - o.density())) / 0.15
     assert err < TOL32, err
+
+
+def test_fp32dev_split_step_is_bitwise_reproducible(L):
+    # the band edge rows receive exactly two atomic additions onto zero, whose
+    # result does not depend on their order: repeated runs agree bit for bit
+    kw = dict(lattice=L.LBM_D3Q19, nx=64, ny=45, nz=24, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
+              precision=L.LBM_FP32DEV)
+    outs = []
+    for _ in range(3):
+        g = L.Sim(L.make_params(**kw))
+        g.lbm_init_droplet(10.0)
+        g.lbm_step(25)
+        outs.append((g.lbm_get_f(), g.lbm_get_density()))
+    for f, r in outs[1:]:
+        assert np.array_equal(f, outs[0][0]) and np.array_equal(r, outs[0][1])
 
 
 def test_observables_parity(L):
@@ -233,8 +252,9 @@ def test_zchunk_and_autotune_do_not_change_results(L):
 # collision pass reading the derivative fields (64: tensor-copy and 16-byte
 # variants by tile; 42: the 4-byte variant everywhere).  Lines whose length is
 # a multiple of 32 are solved in registers (64 x 96 x 64: every axis; 64 x 40
-# x 36: x only), the others in shared memory.
-@pytest.mark.parametrize("shape", [(64, 40, 36), (42, 26, 20), (64, 96, 64)])
+# x 36: x only), the others in shared memory; a cube of such lines (64^3) has
+# all three axes solved in one launch.
+@pytest.mark.parametrize("shape", [(64, 40, 36), (42, 26, 20), (64, 96, 64), (64, 64, 64)])
 @pytest.mark.parametrize("scheme", ["OCFDS4", "CFDS6", "CFDS8"])
 def test_fp32dev_compact_3d_against_oracle(L, shape, scheme):
     nx, ny, nz = shape
