@@ -116,7 +116,8 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = ["paper_2205_09186_gb300/csrc/step3d_split.cuh", "paper_2205_09186_gb300/csrc/lbm_device.cuh",
-                  "paper_2205_09186_gb300/csrc/step3d_fast.cuh", "paper_2205_09186_gb300/csrc/step3d.cuh"]
+                  "paper_2205_09186_gb300/csrc/step3d_fast.cuh", "paper_2205_09186_gb300/csrc/step3d.cuh",
+                  "paper_2205_09186_gb300/csrc/step3d_mu.cuh", "paper_2205_09186_gb300/csrc/coll3d_launch.cuh"]
 TRAFFIC_FILE = "profiles/k_coll3d_d3q19_fp32dev_traffic.txt"
 
 

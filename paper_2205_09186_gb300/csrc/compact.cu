@@ -213,9 +213,10 @@ __device__ __forceinline__ void lines_reg_x(unsigned b, int nx, int ny, int nz, 
 }
 
 // y (axis 1) or z (axis 2) lines: block bb = (32 consecutive x) x (z or y);
-// both fields of the same 32 lines in one block (tile: 2 x [L][33] floats), so
-// that twice the row loads are in flight while the block waits for them
-template <int LW>
+// NF = 2: both fields of the same 32 lines in one block (tile: 2 x [L][33]
+// floats), so that twice the row loads are in flight while the block waits for
+// them; NF = 1: the first field only (mu, gmu)
+template <int LW, int NF = 2>
 __device__ __forceinline__ void lines_reg_yz(int axis, unsigned bb, int nx, int ny, const float* __restrict__ mu,
                                              const float* __restrict__ rho, float* __restrict__ gmu,
                                              float* __restrict__ grho, const LineCoef& lc, float* tile) {
@@ -235,10 +236,10 @@ __device__ __forceinline__ void lines_reg_yz(int axis, unsigned bb, int nx, int 
 #pragma unroll
   for (int i = warp; i < L; i += LRT / 32) {
     t0[i * 33 + lane] = xin ? mu[base + i * stride + lane] : 0.f;
-    t1[i * 33 + lane] = xin ? rho[base + i * stride + lane] : 0.f;
+    if (NF == 2) t1[i * 33 + lane] = xin ? rho[base + i * stride + lane] : 0.f;
   }
   __syncthreads();
-  for (int j = warp; j < 64; j += LRT / 32) {
+  for (int j = warp; j < 32 * NF; j += LRT / 32) {
     float* t = j < 32 ? t0 : t1;
     const int jj = j & 31;
 #pragma unroll
@@ -252,7 +253,7 @@ __device__ __forceinline__ void lines_reg_yz(int axis, unsigned bb, int nx, int 
 #pragma unroll
     for (int i = warp; i < L; i += LRT / 32) {
       gmu[base + i * stride + lane] = t0[i * 33 + lane];
-      grho[base + i * stride + lane] = t1[i * 33 + lane];
+      if (NF == 2) grho[base + i * stride + lane] = t1[i * 33 + lane];
     }
   }
 }
@@ -275,11 +276,12 @@ __global__ void __launch_bounds__(LRT) k_lines_reg(int axis, int nx, int ny, int
 
 // the three axes of a lattice whose edges are all L = 32 LW long, in one
 // launch: blocks [0, nyz) the z lines, [nyz, 2 nyz) the y lines, then the x
-// lines (2 xh blocks, the first xh taking mu); the derivative fields are
-// component-major (3 x N floats).  One launch instead of three: the blocks of
-// all axes share the reads of mu and rho through L2, and the tail of one axis
-// overlaps the others.
-template <int LW>
+// lines (NF xh blocks, the first xh taking the first field); the derivative
+// fields are component-major (3 x N floats).  NF = 2: both fields (mu, rho);
+// NF = 1: one field, passed as mu / gmu.  One launch instead of three: the
+// blocks of all axes share the field reads through L2, and the tail of one
+// axis overlaps the others.
+template <int LW, int NF>
 __global__ void __launch_bounds__(LRT) k_lines_reg3(int n, const float* __restrict__ mu,
                                                     const float* __restrict__ rho, float* __restrict__ gmu,
                                                     float* __restrict__ grho, const LineCoef lc, unsigned nyz,
@@ -288,9 +290,9 @@ __global__ void __launch_bounds__(LRT) k_lines_reg3(int n, const float* __restri
   const long long N = (long long)n * n * n;
   const unsigned b = blockIdx.x;
   if (b < nyz) {
-    lines_reg_yz<LW>(2, b, n, n, mu, rho, gmu + 2 * N, grho + 2 * N, lc, tile);
+    lines_reg_yz<LW, NF>(2, b, n, n, mu, rho, gmu + 2 * N, grho + 2 * N, lc, tile);
   } else if (b < 2 * nyz) {
-    lines_reg_yz<LW>(1, b - nyz, n, n, mu, rho, gmu + N, grho + N, lc, tile);
+    lines_reg_yz<LW, NF>(1, b - nyz, n, n, mu, rho, gmu + N, grho + N, lc, tile);
   } else {
     const unsigned bx = b - 2 * nyz;
     const bool second = bx >= xh;
@@ -319,6 +321,14 @@ cudaError_t launch_lines_reg(int axis, const KParams& kp, const float* mu, const
   return cudaGetLastError();
 }
 
+// lattices whose three axes the single-launch line kernel solves (a cube of
+// edge 32 LW, LW one of the register kernel's block lengths)
+static bool lines3_ok(const KParams& kp) {
+  const int lw = kp.nx / 32;
+  return kp.nx == kp.ny && kp.nx == kp.nz && kp.nx % 32 == 0 &&
+         (lw >= 2 && lw <= 8 || lw == 10 || lw == 12 || lw == 16);
+}
+
 // coefficients of the register kernels: the levels' row scalings folded into
 // the right side
 static LineCoef reg_coef(const LineCoef& lc) {
@@ -338,18 +348,25 @@ cudaError_t launch_lines_reg3(const KParams& kp, const float* mu, const float* r
   constexpr int L = 32 * LW;
   const unsigned nyz = unsigned((long long)((L + 31) / 32) * L);
   const unsigned xh = unsigned(((long long)L * L + LRT / 32 - 1) / (LRT / 32));
-  const size_t smem = size_t(2) * L * 33 * 4;
-  if (cudaError_t e = ensure_smem(k_lines_reg3<LW>, smem); e != cudaSuccess) return e;
-  k_lines_reg3<LW><<<2 * nyz + 2 * xh, LRT, smem, st>>>(L, mu, rho, gmu, grho, lr, nyz, xh);
+  if (rho) {
+    const size_t smem = size_t(2) * L * 33 * 4;
+    if (cudaError_t e = ensure_smem(k_lines_reg3<LW, 2>, smem); e != cudaSuccess) return e;
+    k_lines_reg3<LW, 2><<<2 * nyz + 2 * xh, LRT, smem, st>>>(L, mu, rho, gmu, grho, lr, nyz, xh);
+  } else {
+    const size_t smem = size_t(L) * 33 * 4;
+    if (cudaError_t e = ensure_smem(k_lines_reg3<LW, 1>, smem); e != cudaSuccess) return e;
+    k_lines_reg3<LW, 1><<<2 * nyz + xh, LRT, smem, st>>>(L, mu, nullptr, gmu, nullptr, lr, nyz, xh);
+  }
   return cudaGetLastError();
 }
 
 // grad mu and grad rho along all three axes of FP32 fields on a cubic lattice
 // (gmu, grho component-major, 3 x N floats) in one launch, when its edge is a
-// multiple of 32 (64 .. 512); cudaErrorNotSupported (nothing launched) otherwise
+// multiple of 32 (64 .. 512); cudaErrorNotSupported (nothing launched)
+// otherwise.  rho == nullptr: the first field only (mu into gmu).
 cudaError_t run_lines3_f32(const KParams& kp, const float* mu, const float* rho, float* gmu, float* grho,
                            const LineCoef& lc, cudaStream_t st) {
-  if (kp.nx != kp.ny || kp.nx != kp.nz || kp.nx % 32 != 0) return cudaErrorNotSupported;
+  if (!lines3_ok(kp)) return cudaErrorNotSupported;
   const LineCoef lr = reg_coef(lc);
   if (lr.nlev > 16) return cudaErrorNotSupported;
   switch (kp.nx / 32) {
@@ -435,6 +452,28 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   // D3Q19 FP32 steps collide on the tiled z-marching kernel when the lattice
   // allows it; its output density's band edge rows are zeroed first
   const bool gf3 = std::is_same<P, PrecF32>::value && D == 3 && mode == MODE_STEP && coll3d_gf_ok(c);
+  Tm* gmu = static_cast<Tm*>(cb.gmu);
+  Tc* grho = static_cast<Tc*>(cb.grho);
+  // D3Q19 FP32 on a cube of register-kernel lines: the density's line solves
+  // (which do not need mu) run on the side stream while this stream computes
+  // mu and then its line solves; the collision waits for both
+  bool forked = false;
+  if constexpr (std::is_same<P, PrecF32>::value) {
+    if (D == 3 && cb.side && lines3_ok(kp)) {
+      e = cudaEventRecord(cb.fork, c.stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cb.side, cb.fork, 0);
+      if (e != cudaSuccess) return e;
+      e = run_lines3_f32(kp, rin, nullptr, grho, nullptr, cb.lc, cb.side);
+      const cudaError_t ej = cudaEventRecord(cb.join, cb.side);
+      if (e == cudaSuccess && ej != cudaSuccess) e = ej;
+      if (e != cudaSuccess) {
+        cudaStreamWaitEvent(c.stream, cb.join, 0);
+        if (e != cudaErrorNotSupported) return e;
+      } else {
+        forked = true;
+      }
+    }
+  }
   if (std::is_same<P, PrecF32>::value && D == 3 && (cb.lap_order == 4 || cb.lap_order == 6)) {
     // FP32 mu in 3D: the z-marching mu pass of the split path
     Launch cm = c;
@@ -449,12 +488,19 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
       if (e == cudaSuccess && gf3)
         e = coll3d_zero_edges(kp, rin, static_cast<float*>(c.rout), c.aux.bad_step, c.aux.t, c.stream);
   }
-  if (e != cudaSuccess) return e;
-  Tm* gmu = static_cast<Tm*>(cb.gmu);
-  Tc* grho = static_cast<Tc*>(cb.grho);
+  if (e != cudaSuccess) {
+    if (forked) cudaStreamWaitEvent(c.stream, cb.join, 0);
+    return e;
+  }
   bool lines_done = false;
   if constexpr (std::is_same<P, PrecF32>::value) {
-    if (D == 3) {
+    if (forked) {
+      e = run_lines3_f32(kp, mu, nullptr, gmu, nullptr, cb.lc, c.stream);
+      const cudaError_t ej = cudaStreamWaitEvent(c.stream, cb.join, 0);
+      if (e == cudaSuccess) e = ej;
+      if (e != cudaSuccess) return e;
+      lines_done = true;
+    } else if (D == 3) {
       e = run_lines3_f32(kp, mu, rin, gmu, grho, cb.lc, c.stream);
       if (e != cudaSuccess && e != cudaErrorNotSupported) return e;
       lines_done = e == cudaSuccess;

@@ -25,6 +25,10 @@ struct CompactBufs {
   size_t mu_bytes = 0, gmu_bytes = 0, grho_bytes = 0;
   LineCoef lc{};
   int lap_order = 4;
+  // D3Q19 FP32: a second stream on which the density's line solves run while
+  // the handle's stream computes mu and its line solves (fork and join events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // coefficients (alpha, a, b, c) of the compact schemes; OCFDS4 takes the
@@ -45,7 +49,14 @@ int compact_alloc(CompactBufs& cb, const KParams& kp, int D, int scheme, int pre
   cb.grho = alloc(cb.grho_bytes);
   cb.lc = make_line_coef(scheme);
   cb.lap_order = (scheme == 4) ? 6 : (scheme == 5 ? 8 : 4);
-  return (cb.mu && cb.gmu && cb.grho) ? 0 : -2;
+  if (!(cb.mu && cb.gmu && cb.grho)) return -2;
+  if (prec == 1 && D == 3) {
+    if (cudaStreamCreateWithFlags(&cb.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cb.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cb.join, cudaEventDisableTiming) != cudaSuccess)
+      return -3;
+  }
+  return 0;
 }
 
 template <class FreeF>
@@ -54,6 +65,11 @@ void compact_free(CompactBufs& cb, FreeF fr) {
   if (cb.gmu) fr(cb.gmu, cb.gmu_bytes);
   if (cb.grho) fr(cb.grho, cb.grho_bytes);
   cb.mu = cb.gmu = cb.grho = nullptr;
+  if (cb.side) cudaStreamDestroy(cb.side);
+  if (cb.fork) cudaEventDestroy(cb.fork);
+  if (cb.join) cudaEventDestroy(cb.join);
+  cb.side = nullptr;
+  cb.fork = cb.join = nullptr;
 }
 
 cudaError_t compact_step(const CompactBufs& cb, Launch c, int D, int scheme, int prec, int mode, int* nblocks);
