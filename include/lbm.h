@@ -261,7 +261,8 @@ long long lbm_get_step(const lbm_handle* h);
  * next lbm_step. */
 int lbm_device_state(lbm_handle* h, void** f, void** rho);
 
-/* Work decomposition.  D3Q19 FP32DEV step (explicit schemes): each CTA
+/* Work decomposition.  D3Q19 FP32DEV step (explicit schemes, and the
+ * compact schemes' collision pass when nx % 4 == 0): each CTA
  * marches through a chunk of zc planes; lbm_set_zchunk fixes zc (0 = the
  * built-in heuristic, which balances the last wave of CTAs against the
  * per-chunk prologue).  D2Q9 FP32DEV split step (explicit and isotropic

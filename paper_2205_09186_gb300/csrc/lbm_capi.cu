@@ -800,8 +800,13 @@ static cudaError_t run_pass(lbm_handle* h, const Launch& c, int mode, int* nb) {
   return h->fn(c, mode, nb);
 }
 
+// handles whose D3Q19 collision pass marches z-chunks: the explicit FP32DEV
+// schemes, and the compact ones with FP32 mu (the tiled pass reading the
+// derivative fields)
 static bool tunable(const lbm_handle* h) {
-  return h->D == 3 && (h->prec == 1 || (h->prec == 2 && h->mu)) && !h->compact && !h->layer &&
+  if (h->D != 3 || h->layer) return false;
+  if (h->compact) return h->prec == 1 && h->has_tmap;
+  return (h->prec == 1 || (h->prec == 2 && h->mu)) &&
          (h->p.scheme == LBM_EFDS2 || h->p.scheme == LBM_EFDS4 || h->p.scheme == LBM_EFDS6 || h->p.scheme == LBM_E4);
 }
 

@@ -247,6 +247,25 @@ def test_zchunk_and_autotune_do_not_change_results(L):
         assert np.array_equal(o, outs[0])
 
 
+def test_compact_zchunk_and_autotune_do_not_change_results(L):
+    # the compact schemes' tiled collision pass marches z-chunks too; the
+    # tuner times them on the handle's lattice
+    kw = dict(lattice=L.LBM_D3Q19, nx=64, ny=40, nz=36, Tr=0.8, k=0.25, kappa=0.1, scheme="OCFDS4",
+              precision=L.LBM_FP32DEV)
+    outs = []
+    for zc in (0, 5, 11, 36, -1):
+        g = L.Sim(L.make_params(**kw))
+        if zc < 0:
+            assert g.lbm_autotune() > 0
+        else:
+            g.lbm_set_zchunk(zc)
+        g.lbm_init_droplet(9.0)
+        g.lbm_step(12)
+        outs.append(g.lbm_get_f())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
 # compact schemes in 3D with FP32 deviation storage: z-marching mu pass (orders
 # 4 and 6; the node-parallel one for CFDS8), line solves, and the tiled
 # collision pass reading the derivative fields (64: tensor-copy and 16-byte
