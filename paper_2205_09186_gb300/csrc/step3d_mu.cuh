@@ -236,14 +236,14 @@ __global__ void __launch_bounds__(MZT) k_mu3d_zm(const KParams p, const float* _
       res[k] = mu_value<M64>(p, ef, k2, kap, rref, cv, lap);
     }
     *reinterpret_cast<float4*>(mu + z * NXY + col) = make_float4(res[0], res[1], res[2], res[3]);
-    if (erow) ebad |= !(rref + c4.x > 0.f && rref + c4.y > 0.f && rref + c4.z > 0.f && rref + c4.w > 0.f);
+    if (erow) {
+      *reinterpret_cast<float4*>(ez.rz + z * NXY + col) = make_float4(0.f, 0.f, 0.f, 0.f);
+      ebad |= !(rref + c4.x > 0.f && rref + c4.y > 0.f && rref + c4.z > 0.f && rref + c4.w > 0.f);
+    }
   }
-  // the edge rows' zeroes after the march (inside it they cost the march its
-  // registers)
-  if (erow) {
-    for (int z = z0; z < z1; ++z) *reinterpret_cast<float4*>(ez.rz + z * NXY + col) = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ebad) atomicMin(ez.bad, (unsigned long long)ez.t);
-  }
+  // one flag per thread through the march, one atomic after it (an atomic
+  // inside the march cost it 30 registers)
+  if (erow && ebad) atomicMin(ez.bad, (unsigned long long)ez.t);
 }
 
 // ------------------------------------------------------------------ observation pass
