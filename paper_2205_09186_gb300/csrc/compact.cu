@@ -457,28 +457,36 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
   // D3Q19 FP32 on a cube of register-kernel lines: the density's line solves
   // (which do not need mu) run on the side stream while this stream computes
   // mu and then its line solves; the collision waits for both
-  bool forked = false;
+  // (the fork is recorded before the mu pass, whose launch is submitted
+  // first; the side stream's launch follows it)
+  bool fork_rec = false, forked = false;
   if constexpr (std::is_same<P, PrecF32>::value) {
     if (D == 3 && cb.side && lines3_ok(kp)) {
-      e = cudaEventRecord(cb.fork, c.stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(cb.side, cb.fork, 0);
-      if (e != cudaSuccess) return e;
-      e = run_lines3_f32(kp, rin, nullptr, grho, nullptr, cb.lc, cb.side);
-      const cudaError_t ej = cudaEventRecord(cb.join, cb.side);
-      if (e == cudaSuccess && ej != cudaSuccess) e = ej;
-      if (e != cudaSuccess) {
-        cudaStreamWaitEvent(c.stream, cb.join, 0);
-        if (e != cudaErrorNotSupported) return e;
-      } else {
-        forked = true;
-      }
+      if ((e = cudaEventRecord(cb.fork, c.stream)) != cudaSuccess) return e;
+      fork_rec = true;
     }
   }
+  auto fork_lines = [&]() -> cudaError_t {
+    if (!fork_rec) return cudaSuccess;
+    cudaError_t ef = cudaStreamWaitEvent(cb.side, cb.fork, 0);
+    if (ef != cudaSuccess) return ef;
+    ef = run_lines3_f32(kp, reinterpret_cast<const float*>(rin), nullptr, reinterpret_cast<float*>(grho), nullptr,
+                        cb.lc, cb.side);
+    const cudaError_t ej = cudaEventRecord(cb.join, cb.side);
+    if (ef == cudaSuccess && ej != cudaSuccess) ef = ej;
+    if (ef != cudaSuccess) {
+      cudaStreamWaitEvent(c.stream, cb.join, 0);
+      return ef == cudaErrorNotSupported ? cudaSuccess : ef;
+    }
+    forked = true;
+    return cudaSuccess;
+  };
   if (std::is_same<P, PrecF32>::value && D == 3 && (cb.lap_order == 4 || cb.lap_order == 6)) {
     // FP32 mu in 3D: the z-marching mu pass of the split path
     Launch cm = c;
     cm.mu = mu;
     e = mu3d_pass(cm, cb.lap_order, gf3);
+    if (e == cudaSuccess) e = fork_lines();
   } else {
     if (cb.lap_order == 4) k_mu_field<Tm, Tr, 4><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
     else if (cb.lap_order == 6) k_mu_field<Tm, Tr, 6><<<g, bs, 0, c.stream>>>(kp, D, P::DEV, rin, mu);
@@ -487,6 +495,7 @@ cudaError_t step_prec(const CompactBufs& cb, Launch c, int D, int mode, int* nbl
     if constexpr (std::is_same<P, PrecF32>::value)
       if (e == cudaSuccess && gf3)
         e = coll3d_zero_edges(kp, rin, static_cast<float*>(c.rout), c.aux.bad_step, c.aux.t, c.stream);
+    if (e == cudaSuccess) e = fork_lines();
   }
   if (e != cudaSuccess) {
     if (forked) cudaStreamWaitEvent(c.stream, cb.join, 0);

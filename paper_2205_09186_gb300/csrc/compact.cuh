@@ -51,7 +51,11 @@ int compact_alloc(CompactBufs& cb, const KParams& kp, int D, int scheme, int pre
   cb.lap_order = (scheme == 4) ? 6 : (scheme == 5 ? 8 : 4);
   if (!(cb.mu && cb.gmu && cb.grho)) return -2;
   if (prec == 1 && D == 3) {
-    if (cudaStreamCreateWithFlags(&cb.side, cudaStreamNonBlocking) != cudaSuccess ||
+    // the side stream at the lowest priority: the handle's stream carries the
+    // critical path (mu, then mu's line solves)
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&cb.side, cudaStreamNonBlocking, lo) != cudaSuccess ||
         cudaEventCreateWithFlags(&cb.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&cb.join, cudaEventDisableTiming) != cudaSuccess)
       return -3;
