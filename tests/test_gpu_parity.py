@@ -247,10 +247,11 @@ def test_zchunk_and_autotune_do_not_change_results(L):
         assert np.array_equal(o, outs[0])
 
 
-def test_compact_zchunk_and_autotune_do_not_change_results(L):
+@pytest.mark.parametrize("ny", [40, 48])
+def test_compact_zchunk_and_autotune_do_not_change_results(L, ny):
     # the compact schemes' tiled collision pass marches z-chunks too; the
     # tuner times them on the handle's lattice
-    kw = dict(lattice=L.LBM_D3Q19, nx=64, ny=40, nz=36, Tr=0.8, k=0.25, kappa=0.1, scheme="OCFDS4",
+    kw = dict(lattice=L.LBM_D3Q19, nx=64, ny=ny, nz=36, Tr=0.8, k=0.25, kappa=0.1, scheme="OCFDS4",
               precision=L.LBM_FP32DEV)
     outs = []
     for zc in (0, 5, 11, 36, -1):
