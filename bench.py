@@ -560,11 +560,13 @@ def run_gpu(args):
                            **WORKLOAD),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": captured_traffic(N), "peak_kind": peak_kind,
-                         "bytes_per_lu": B_COLL, "kernel": "k_coll3d (grad mu, grad rho, force, BGK+EDM, push, next density)",
+                         "bytes_per_lu": B_COLL,
+                         "kernel": "k_coll3d (grad mu, grad rho, force, BGK+EDM, push, next density)"
+                                   " + k_coll3d_corners (tile-corner densities), timed together",
                          "kernel_ms": coll_ms, "mu_pass": {"kernel": "k_mu3d_zm", "ms": mu_ms, "bytes_per_lu": B_MU,
                                                            "achieved": B_MU * N / (mu_ms * 1e-3) / 1e9 if mu_ms > 0 else None},
                          "step_bytes_per_lu": B_ALG, "step_frac": B_ALG * N / (total_ms / args.steps * 1e-3) / 1e9 / peak},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps,
             "clocks": clk.summary(), "check": {"status": obs["status"], "mass_rel_change": obs["mass"] / obs0["mass"] - 1,
                                                "ok": ok},
             "extra": extra}

@@ -1,9 +1,12 @@
 // Launcher of the D3Q19 FP32-deviation collision pass (k_coll3d) for one tile
-// shape: bands of RY rows (RowBands) and NB staged population planes.  The
-// pass adds into the edge rows of its output density: the mu pass of the same
+// shape: 32-column tiles (ColTiles), bands of RY rows (RowBands) and NB staged
+// population planes, followed by k_coll3d_corners.  The pass adds into the
+// edge rows and edge columns of its output density: the mu pass of the same
 // step (launch_mu with an EdgeZero of the same RY) must have zeroed them.
 #pragma once
 #include <cuda.h>
+
+#include <algorithm>
 
 #include "launch.cuh"
 #include "step3d_split.cuh"
@@ -27,13 +30,22 @@ cudaError_t launch_coll(const Launch& c, int zc) {
       if (!make_coll3d_tmap(c.fin, c.kp, &tm, RY)) return cudaErrorInvalidValue;
     }
   }
+  if (!c.qc || !(c.qscale > 0.f)) return cudaErrorInvalidValue;
   if (cudaError_t e = ensure_smem(kc, by); e != cudaSuccess) return e;
-  const dim3 grid((c.kp.nx + TXC - 1) / TXC, RowBands(c.kp.ny, RY).nb, (c.kp.nz + zc - 1) / zc);
+  const ColTiles tiles(c.kp.nx);
+  const RowBands bands(c.kp.ny, RY);
+  const dim3 grid(tiles.nt, bands.nb, (c.kp.nz + zc - 1) / zc);
   kc<<<grid, Sh::NT, by, c.stream>>>(c.kp, static_cast<const float*>(c.fin), static_cast<float*>(c.fout),
                                      static_cast<const float*>(c.rin), static_cast<const float*>(c.mu),
                                      static_cast<float*>(c.rout), c.aux, zc,
                                      OBS ? static_cast<float*>(const_cast<void*>(c.aux.rho_snap)) : nullptr, tm,
-                                     static_cast<const float*>(c.gi.gmu), static_cast<const float*>(c.gi.grho));
+                                     static_cast<const float*>(c.gi.gmu), static_cast<const float*>(c.gi.grho), c.qc,
+                                     c.qscale);
+  if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
+  const long long ncorner = 4LL * tiles.nt * bands.nb * c.kp.nz;
+  const int nblk = int(std::min<long long>((ncorner + 255) / 256, 4096LL));
+  k_coll3d_corners<<<nblk, 256, 0, c.stream>>>(c.kp, RY, c.qc, static_cast<float*>(c.rout), 1.f / c.qscale,
+                                               c.aux.bad_step, c.aux.t + 1);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // Instantiations of the fused 2.5D D3Q19 step for the explicit and isotropic schemes.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <type_traits>
 
@@ -25,7 +26,7 @@ bool split3d_scheme(int scheme, int prec) {
 // prologue (2R planes of field loads and two extra collided planes) for tiles
 // of ty rows and per_sm resident CTAs per SM
 static int split_zchunk_heuristic(const KParams& kp, int R, int ty, int per_sm) {
-  const long long tiles = (long long)((kp.nx + TXC - 1) / TXC) * ((kp.ny + ty - 1) / ty);
+  const long long tiles = (long long)ColTiles(kp.nx).nt * RowBands(kp.ny, ty).nb;
   const long long slots = (long long)per_sm * num_sms();
   double best = 1e300;
   int best_zc = kp.nz;
@@ -40,9 +41,22 @@ static int split_zchunk_heuristic(const KParams& kp, int R, int ty, int per_sm) 
   return best_zc;
 }
 
-// CTAs of one collision pass (k_coll3d): 30-column tiles x row bands x z chunks
+// CTAs of one collision pass (k_coll3d): 32-column tiles x row bands x z chunks
 static long long coll3d_ctas(const KParams& kp, int zc) {
-  return (long long)((kp.nx + TXC - 1) / TXC) * RowBands(kp.ny, CY).nb * ((kp.nz + zc - 1) / zc);
+  return (long long)ColTiles(kp.nx).nt * RowBands(kp.ny, CY).nb * ((kp.nz + zc - 1) / zc);
+}
+
+long long coll3d_corner_count(const KParams& kp) {
+  return 4LL * ColTiles(kp.nx).nt * RowBands(kp.ny, CY).nb * kp.nz;
+}
+
+float coll3d_corner_scale(int eos, double b) {
+  const double rmax = (eos == LBM_EOS_CS ? 4.0 : 1.0) / (b > 0 ? b : 1.0);
+  // |partial| <= 2 rmax <= 2^e; four of them: 4 * 2^e * 2^s <= 2^62
+  int e = 0;
+  while (std::ldexp(1.0, e) < 2.0 * rmax && e < 40) ++e;
+  const int s = std::min(60, 60 - e);
+  return float(std::ldexp(1.0, s));
 }
 
 int fast_zchunk_heuristic(const KParams& kp, int R) {
@@ -238,6 +252,18 @@ __global__ void k_zero_edges(const KParams p, const float* __restrict__ rin, flo
   rout[o] = 0.f;
   if (!(float(p.rho_ref) + rin[o] > 0.f)) atomicMin(bad, (unsigned long long)t);
 }
+// one thread per node of the tile edge columns: blockIdx.y = 2 tile + (0: first column, 1: last column)
+__global__ void k_zero_edge_cols(const KParams p, const float* __restrict__ rin, float* __restrict__ rout,
+                                 unsigned long long* bad, long long t) {
+  const ColTiles tiles(p.nx);
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= p.ny) return;
+  const int k = int(blockIdx.y) >> 1;
+  const int x = (blockIdx.y & 1) ? tiles.start(k + 1) - 1 : tiles.start(k);
+  const long long o = (long long)blockIdx.z * p.nx * p.ny + (long long)y * p.nx + x;
+  rout[o] = 0.f;
+  if (!(float(p.rho_ref) + rin[o] > 0.f)) atomicMin(bad, (unsigned long long)t);
+}
 }  // namespace
 
 cudaError_t coll3d_zero_edges(const KParams& kp, const float* rin, float* rout, unsigned long long* bad, long long t,
@@ -245,6 +271,9 @@ cudaError_t coll3d_zero_edges(const KParams& kp, const float* rin, float* rout, 
   if (!rin || !rout || !bad || kp.nz > 65535) return cudaErrorInvalidValue;
   const dim3 g((kp.nx + 127) / 128, 2 * RowBands(kp.ny, CY).nb, kp.nz);
   k_zero_edges<<<g, 128, 0, st>>>(kp, rin, rout, bad, t);
+  if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
+  const dim3 gc((kp.ny + 127) / 128, 2 * ColTiles(kp.nx).nt, kp.nz);
+  k_zero_edge_cols<<<gc, 128, 0, st>>>(kp, rin, rout, bad, t);
   return cudaGetLastError();
 }
 

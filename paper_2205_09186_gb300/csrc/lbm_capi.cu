@@ -49,6 +49,9 @@ struct lbm_handle {
   double mu_w = 0.0;             // wall chemical potential
   alignas(64) unsigned char tmap[2][128];  // D3Q19 FP32DEV: tensor maps (CUtensorMap) of f[0], f[1]
   bool has_tmap = false;
+  unsigned long long* qc = nullptr;  // D3Q19 FP32DEV: corner accumulators of the collision pass
+  long long n_qc = 0;
+  float qscale = 0.f;
   int rpt2d = 0;  // D2Q9 FP32DEV split tiles: rows per thread (0 = default)
 };
 
@@ -540,6 +543,7 @@ extern "C" void lbm_destroy(lbm_handle* h) {
   dfree(h, h->d_partials, size_t(h->n_partials) * 4 * 8);
   dfree(h, h->d_obs, 64 + sizeof(lbm_obs));
   dfree(h, h->mu, size_t(h->N) * 4);
+  dfree(h, h->qc, size_t(h->n_qc) * 8);
   dfree(h, h->layer, size_t(h->N));
   dfree(h, h->wmu, size_t(h->N) * 8);
   compact_free(h->cb, [&](void* p, size_t b) { dfree(h, p, b); });
@@ -618,8 +622,14 @@ extern "C" int lbm_create(const lbm_params* params, void* stream, const lbm_allo
   }
   // tensor maps of both population buffers for the D3Q19 FP32DEV collision
   // pass's copies (split explicit schemes and compact schemes)
-  if (ok && h->D == 3 && (h->prec == 1 || h->prec == 2))
+  if (ok && h->D == 3 && (h->prec == 1 || h->prec == 2)) {
     h->has_tmap = make_coll3d_tmap(h->f[0], h->kp, h->tmap[0]) && make_coll3d_tmap(h->f[1], h->kp, h->tmap[1]);
+    // corner accumulators of the tiled collision pass (zero between passes)
+    h->n_qc = coll3d_corner_count(h->kp);
+    h->qscale = coll3d_corner_scale(params->eos, params->b);
+    h->qc = static_cast<unsigned long long*>(dalloc(h, size_t(h->n_qc) * 8));
+    ok = h->qc != nullptr && cudaMemsetAsync(h->qc, 0, size_t(h->n_qc) * 8, h->stream) == cudaSuccess;
+  }
   if (ok && h->compact) {
     rc = compact_alloc(h->cb, h->kp, h->D, params->scheme, h->prec, [&](size_t b) { return dalloc(h, b); });
     if (rc != LBM_OK) ok = false;
@@ -787,6 +797,8 @@ static Launch make_launch(lbm_handle* h, int out_buf) {
   c.mrt = h->mrt;
   c.tmap = h->has_tmap ? h->tmap[h->cur] : nullptr;
   c.rpt2d = h->rpt2d;
+  c.qc = h->qc;
+  c.qscale = h->qscale;
   return c;
 }
 

@@ -34,11 +34,32 @@ struct RowBands {
   }
 };
 
-// What the mu pass does for the collision pass that follows it: zero the edge
-// rows of the collision pass's output density rz (bands of ry rows), and flag
-// step t in bad when the density of an edge-row node is not positive (the
-// collision pass checks the other rows of the density it produces, flagging
-// the same step index).  rz == nullptr: nothing.
+// Column tiles of the collision pass: 32 columns each (one warp lane per
+// column), the last one ragged.  A last tile of a single column (nx % 32 == 1,
+// odd nx, so never on the 16-byte paths) takes one column from the tile
+// before it, so that every tile has two distinct edge columns.
+struct ColTiles {
+  int nx, nt, adj;
+  __host__ __device__ explicit ColTiles(int nx_) : nx(nx_), nt((nx_ + 31) / 32), adj(0) {
+    if (nt >= 2 && nx - (nt - 1) * 32 == 1) adj = 1;
+  }
+  __host__ __device__ int start(int t) const { return t >= nt ? nx : 32 * t - (t == nt - 1 ? adj : 0); }
+  __host__ __device__ int tile(int x) const {
+    const int t = x / 32 < nt - 1 ? x / 32 : nt - 1;
+    return (adj && t == nt - 2 && x >= start(nt - 1)) ? nt - 1 : t;
+  }
+  __host__ __device__ bool edge(int x) const {
+    const int t = tile(x);
+    return x == start(t) || x == start(t + 1) - 1;
+  }
+};
+
+// What the mu pass does for the collision pass that follows it: zero the
+// nodes of the collision pass's output density rz that it completes by atomic
+// additions (the edge rows of its row bands of ry rows and the edge columns of
+// its column tiles), and flag step t in bad when the density of such a node is
+// not positive (the collision pass checks the other nodes of the density it
+// produces, flagging the same step index).  rz == nullptr: nothing.
 struct EdgeZero {
   float* rz;
   int ry;
@@ -109,7 +130,7 @@ __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __re
   for (int d = 0; d < 2 * R; ++d) q[d + 1] = blk[d][cy][cx];
   const int zend = min(MUZ, nz - z0);
   float* out = mu + z0 * NXY + (y0 + ty) * nx + x0 + tx;
-  const bool erow = ez.rz && RowBands(ny, ez.ry).edge(y0 + ty);
+  const bool enode = ez.rz && (RowBands(ny, ez.ry).edge(y0 + ty) || ColTiles(nx).edge(x0 + tx));
 #pragma unroll
   for (int dz = 0; dz < MUZ; ++dz) {
 #pragma unroll
@@ -124,7 +145,7 @@ __global__ void __launch_bounds__(MUT) k_mu3d(const KParams p, const float* __re
         lap += float(Sch<S>::l(m)) * ((blk[pz][cy][cx + m] + blk[pz][cy][cx - m]) +
                                       (blk[pz][cy + m][cx] + blk[pz][cy - m][cx]) + (q[R + m] + q[R - m]));
       out[dz * NXY] = mu_value<M64>(p, ef, k2, kap, rref, c, lap);
-      if (erow) {
+      if (enode) {
         ez.rz[(out - mu) + dz * NXY] = 0.f;
         if (!(rref + c > 0.f)) atomicMin(ez.bad, (unsigned long long)ez.t);
       }
@@ -189,7 +210,15 @@ __global__ void __launch_bounds__(MZT) k_mu3d_zm(const KParams p, const float* _
   const int tx = tid % (MZX / 4), ty = tid / (MZX / 4);
   const bool own = x0 + 4 * tx < nx && y0 + ty < ny;  // nx % 4 == 0: all four nodes or none
   const int col = own ? (y0 + ty) * nx + x0 + 4 * tx : 0;
-  const bool erow = ez.rz && own && RowBands(ny, ez.ry).edge(y0 + ty);
+  // this thread's four nodes hold a node of an edge row or an edge column:
+  // all four are zeroed (the others are stored by the collision pass before
+  // anything reads them) and checked
+  bool erow = ez.rz && own && RowBands(ny, ez.ry).edge(y0 + ty);
+  if (ez.rz && own && !erow) {
+    const ColTiles ct(nx);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) erow = erow || ct.edge(x0 + 4 * tx + k);
+  }
   bool ebad = false;
   auto ld = [&](int z) { return __ldg(reinterpret_cast<const float4*>(rin + wrapi(z, nz) * NXY + col)); };
   const float k2 = float(p.k2), kap = float(p.kappa);

@@ -4,8 +4,8 @@
 //              (step3d_mu.cuh).
 //  k_coll3d    grad mu, grad rho (Eq. 17-25) -> F (Eq. 12) -> BGK + EDM
 //              (Eq. 1, 6, 8) -> push streaming, plus the next density, for
-//              a band of 11 rows x 30 columns (and the column on each side)
-//              marching through z.
+//              a tile of 32 columns x a band of 11 rows marching through z.
+//  k_coll3d_corners  the next density of the tiles' corner nodes.
 //
 // Compared with evaluating mu inside the collision kernel (where the halo
 // makes each CTA recompute it ~2.3 times per node and the recomputation
@@ -13,8 +13,20 @@
 // write per node (168 instead of 160 bytes per lattice update) and removes
 // the mu phase, one block barrier per plane and most shared-memory loads from
 // the collision kernel.  In k_coll3d one warp owns one 32-wide row of the
-// collision region, so the stencil reads of a warp are contiguous (free of
-// bank conflicts).
+// tile, one lane per node, so the stencil reads of a warp are contiguous
+// (free of bank conflicts) and no lane recomputes a neighbouring tile's node.
+//
+// The next density of a node is the sum of the 19 populations pushed into it.
+// A node inside its tile receives them all from its own CTA.  A node in an
+// edge row of its band (or an edge column of its tile) receives some from the
+// band above or below (or the tile to the left or right): the two CTAs each
+// add their partial sum by an atomic addition onto a zero the mu pass wrote,
+// and since 0 + a + b does not depend on the order of the additions, the
+// result is the same bits on every run.  A corner node (edge row and edge
+// column) receives populations from up to four CTAs: their partial sums are
+// added as 64-bit fixed-point integers (exact, so again independent of order)
+// into an accumulator per corner, which k_coll3d_corners turns into the
+// float density after the pass and zeroes for the next one.
 #pragma once
 #include <cuda.h>  // CUtensorMap
 
@@ -26,27 +38,26 @@
 namespace lbmd {
 
 // ------------------------------------------------------------------ collision pass
-constexpr int CX = 32, CY = 11;     // default collision region (tile + ring columns), one warp per row
-constexpr int TXC = CX - 2, TYC = CY;  // 30 x 11 tile
+constexpr int CX = 32, CY = 11;     // default collision tile: 32 columns (lanes) x 11 rows (warps)
+constexpr int TXC = CX, TYC = CY;
 constexpr int CNT = CX * CY;        // 352 threads
-constexpr int FW = 36;              // staged population row: 32 nodes + up to 3 of alignment
+constexpr int FW = CX;              // staged population row: the tile's 32 columns
 constexpr int COLL_FD = 1;          // field planes issued this many planes ahead (1 or 2)
 
 // Field planes: the density deviation and mu of a node side by side (one
 // float2, x = deviation, y = mu), copied in by two 4-byte copies per node, so
 // that every stencil offset of the two gradients is one 8-byte shared load.
-// Staged populations: rows start at a 16-byte-aligned global x (x of the
-// region's first node rounded down to a multiple of 4), so that with
-// nx % 4 == 0 every row is a whole number of 16-byte chunks that never
-// straddle the periodic seam; the region's first node then sits at column of
-// (0..3).  The scalar path (any nx) uses the same layout with of = 0.  With
-// VEC a CTA whose population region lies inside the lattice (no periodic
-// seam) stages it with one tensor copy (TMA) per plane: a 36 x 11 x 1 x 19 box
-// of the populations viewed as a 4-D tensor (x, y, z, i) lands in exactly this
-// layout; the buffers are 1 KB aligned for it.
+// Staged populations: one row of 32 floats per tile row and population
+// (x0 of a tile is a multiple of 32, so with nx % 4 == 0 a row is eight
+// 16-byte chunks).  With VEC a CTA whose tile lies inside the lattice stages
+// them with one tensor copy (TMA) per plane: a 32 x 11 x 1 x 19 box of the
+// populations viewed as a 4-D tensor (x, y, z, i) lands in exactly this
+// layout; the buffers are 1 KB aligned for it.  A ragged last tile in x or a
+// short last band in y takes 16-byte copies that wrap around the periodic
+// seams instead (tensor boxes that cross the lattice edge were measured to
+// make those CTAs several times slower).
 //
-// RY rows of the region (all of them tile rows, one warp each: the rows of one
-// band of RowBands) and NB staged planes of populations: the copies of plane
+// RY rows of the tile (one warp each: the rows of one band of RowBands) and NB staged planes of populations: the copies of plane
 // z + NB - 1 are issued while plane z is collided, so NB - 1 planes are in
 // flight per CTA.  The field ring holds the 2R + 1 planes of the stencil plus
 // the NB - 1 in flight.
@@ -58,7 +69,7 @@ struct CollShape {
   static constexpr int RY = RY_, TY = RY_, NT = CX * RY_, NB = NB_, FD = FD_;
   static_assert(NB >= 2 && NB <= 4, "two to four staged planes");
   static_assert(FD == 1 || (FD == 2 && NB == 2 && !Sch<S>::GF), "field planes one or two planes ahead");
-  static constexpr int GW = CX + 2 * R, GH = RY + 2 * R;  // field region (region + stencil halo)
+  static constexpr int GW = CX + 2 * R, GH = RY + 2 * R;  // field region (tile + stencil halo)
   // ring of field planes: FD = 1, the stencil's 2R + 1 and the NB - 1 in
   // flight, rounded up to a power of two so that a slot is a mask; FD = 2, the
   // stencil's and two more (one landed or in flight, one being issued)
@@ -135,30 +146,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
 // S a compact scheme (GF): the derivatives come from the fields gmu and grho
 // (component-major, N each) of the line solves; no stencil halo.
 // VEC: 16-byte copies (nx % 4 == 0, 16-byte aligned fields and populations),
-// and tensor copies of the populations for CTAs away from the periodic seams
-// (tmf: the populations as a 4-D tensor (nx, ny, nz, 19), box (FW, RY, 1, 19)).
+// and tensor copies of the populations for CTAs whose tile lies inside the
+// lattice (tmf: the populations as a 4-D tensor (nx, ny, nz, 19), box
+// (FW, RY, 1, 19)).
 // OBS: also reduce the observables of the state being advanced (max |v| with
 // v = u + F / (2 rho), max |u|, mass, max |rho - snap|) into aux.partials, one
 // set per CTA, and overwrite snap with this state's density deviation.
-// The CTA (blockIdx.y = band b of RowBands(ny, RY)) collides the nodes of its
-// band's rows in the columns x0 - 1 .. x0 + 30 (the outer two recomputed by the
-// neighbouring CTAs in x as their own) and gathers the next density of its 30
-// columns.  Rows inside the band get every incoming population from the band
-// and are stored; the band's first and last rows lack the populations that
-// come from the neighbouring bands, and the band's populations leaving through
-// those rows are summed per target node: both go into rout by atomic
-// addition onto the zeroes the mu pass wrote there.
+// The CTA (blockIdx.x = tile of ColTiles(nx), blockIdx.y = band of
+// RowBands(ny, RY)) collides and pushes the nodes of its tile and band and
+// gathers their next density.  Interior nodes get every incoming population
+// from the CTA and are stored.  Edge-row and edge-column nodes lack those from
+// the neighbouring band or tile; the CTA sums, per target node, the
+// populations that leave through its edges (row by row across a band edge,
+// column by column across a tile edge) and both partial sums go into rout by
+// atomic addition onto the zeroes the mu pass wrote there.  Corner nodes and
+// the populations leaving through a tile's corners go, as fixed-point
+// integers (v * qscale rounded), into the corner accumulators qc
+// (k_coll3d_corners indexing); rout is not touched at corner nodes.
 template <int S, bool TAU1, bool VEC, bool OBS, int RY_ = CY, int NB_ = 2, int FD_ = COLL_FD>
 __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) k_coll3d(const KParams p, const float* __restrict__ fin,
                                                     float* __restrict__ fout, const float* __restrict__ rin,
                                                     const float* __restrict__ muf, float* __restrict__ rout,
                                                     const StepAux aux, const int zc, float* __restrict__ snap,
                                                     const __grid_constant__ CUtensorMap tmf,
-                                                    const float* __restrict__ gmu, const float* __restrict__ grho) {
+                                                    const float* __restrict__ gmu, const float* __restrict__ grho,
+                                                    unsigned long long* __restrict__ qc, const float qscale) {
   using L = Lattice<1>;
   using Sh = CollShape<S, RY_, NB_, FD_>;
   constexpr int Q = 19, R = Sh::R, GW = Sh::GW, NS = Sh::NS, FPL = Sh::FPL;
-  constexpr int RY = Sh::RY, TY = Sh::TY, NT = Sh::NT, NB = Sh::NB, FD = Sh::FD;
+  constexpr int RY = Sh::RY, NT = Sh::NT, NB = Sh::NB, FD = Sh::FD;
   extern __shared__ __align__(1024) unsigned char smem_c3[];  // (own name: other kernels align theirs to 16)
   unsigned char* smem = smem_c3;
   __shared__ __align__(8) unsigned long long s_bar[NB];  // tensor copies: one mbarrier per buffer
@@ -170,31 +186,40 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int N = int(p.n), NXY = nx * ny;
+  const ColTiles tiles(nx);
   const RowBands bands(ny, RY);
-  const int x0 = blockIdx.x * TXC, y0 = bands.start(blockIdx.y), z0 = blockIdx.z * zc;
+  const int tb = blockIdx.x, bb = blockIdx.y;
+  const int x0 = tiles.start(tb), y0 = bands.start(bb), z0 = blockIdx.z * zc;
   const int z1 = min(z0 + zc, nz);
-  const int VW = min(TXC, nx - x0), VH = bands.start(blockIdx.y + 1) - y0;
+  const int VW = tiles.start(tb + 1) - x0, VH = bands.start(bb + 1) - y0;
   const int tid = threadIdx.x;
-  const int cy = tid / CX, cx = tid - cy * CX;  // one warp per row
-  const int lx = cx - 1, ly = cy;
-  const bool crow = ly < VH;  // a row of the band (warp-uniform)
-  const bool cnode = lx <= VW && crow;
-  const bool interior = lx >= 0 && lx < VW && crow;
-  const bool top = ly == 0, bot = ly == VH - 1;  // edge rows (both when VH = 1)
-  const int gx = wrapi(x0 + lx, nx), gy = wrapi(y0 + ly, ny);
-  // the row beyond this warp's edge (ny = 1: the row itself, whichever side)
+  const int cy = tid / CX, cx = tid - cy * CX;  // one warp per row, one lane per column
+  const bool crow = cy < VH;                    // a row of the band (warp-uniform)
+  const bool cnode = cx < VW && crow;           // a node of the tile
+  const bool top = cy == 0, bot = cy == VH - 1;  // edge rows (VH >= 2: never both)
+  const bool lft = cx == 0, rgt = cx == VW - 1;  // edge columns (VW >= 2: never both)
+  const bool corner = (lft || rgt) && (top || bot);
+  const int gx = cx < VW ? x0 + cx : x0, gy = cy < VH ? y0 + cy : y0;
+  // the row beyond this warp's band edge, the columns beyond the tile's edges
   const int yo = top ? wrapn(y0 - 1, ny) : wrapn(y0 + VH, ny);
+  const int xo = lft ? wrapn(x0 - 1, nx) : wrapn(x0 + VW, nx);
+  // corner accumulators: plane z, band b, tile t, corner c (bit 0: last
+  // column of the tile, bit 1: last row of the band)
+  const int ntx = tiles.nt, nbd = bands.nb;
+  const int tm = tb == 0 ? ntx - 1 : tb - 1, tp = tb == ntx - 1 ? 0 : tb + 1;
+  const int bm = bb == 0 ? nbd - 1 : bb - 1, bp = bb == nbd - 1 ? 0 : bb + 1;
+  auto qadd = [&](int z, int b, int t, int c, float v) {
+    const long long k = (((long long)z * nbd + b) * ntx + t) * 4 + c;
+    atomicAdd(qc + k, (unsigned long long)__float2ll_rn(v * qscale));
+  };
   const float omega = float(p.omega), rref = float(p.rho_ref);
   const int pc_first = z0 - 1, pc_last = z1;
   // staging buffer (populations, GF derivatives, OBS snapshot) of plane pc
   auto bsel = [&](int pc) { return int(unsigned(pc - pc_first) % unsigned(NB)); };
-  // first population column of the region in shared memory
-  const int of = VEC ? (x0 - 1) & 3 : 0;
-  // tensor copies when the population region (36 columns from the aligned
-  // start, RY rows) needs no periodic wrap
+  // tensor copies when the tile (32 columns, RY rows) lies inside the lattice
   // (and the staging buffers 128-byte aligned, as tensor copies require)
-  const bool tcta = VEC && x0 - 1 - of >= 0 && x0 - 1 - of + FW <= nx && y0 + RY <= ny &&
-                    (smem_u32(s_f) & 127u) == 0 && ((Sh::fbuf * 4) & 127) == 0;
+  const bool tcta = VEC && x0 + FW <= nx && y0 + RY <= ny && (smem_u32(s_f) & 127u) == 0 &&
+                    ((Sh::fbuf * 4) & 127) == 0;
   if (tcta && tid == 0) {
 #pragma unroll
     for (int b = 0; b < NB; ++b)
@@ -216,15 +241,14 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
   for (int k = 0; k < Sh::KD; ++k) {
     const int e = tid + k * NT;
     const int ry = e / GW, rx = e - ry * GW;
-    dofs[k] = e < Sh::DE ? wrapn(y0 - R + ry, ny) * nx + wrapn(x0 - 1 - R + rx, nx) : 0;
+    dofs[k] = e < Sh::DE ? wrapn(y0 - R + ry, ny) * nx + wrapn(x0 - R + rx, nx) : 0;
   }
   if constexpr (VEC) {
-    const int xaf = x0 - 1 - of;  // aligned start (may be negative)
 #pragma unroll
     for (int k = 0; k < Sh::KF; ++k) {
       const int c = tid + k * NT, i = c / (RY * (FW / 4));  // population of chunk c
       const int r = c - i * (RY * FW / 4), ry = r / (FW / 4), j = r - ry * (FW / 4);
-      fofs[k] = i * N + wrapn(y0 + ry, ny) * nx + wrapn(xaf + 4 * j, nx);
+      fofs[k] = i * N + wrapn(y0 + ry, ny) * nx + wrapn(x0 + 4 * j, nx);
     }
   }
 
@@ -276,7 +300,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
           asm volatile(
               "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
               " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(fd)),
-              "l"(reinterpret_cast<unsigned long long>(&tmf)), "r"(x0 - 1 - of), "r"(y0), "r"(wrapi(pc, nz)),
+              "l"(reinterpret_cast<unsigned long long>(&tmf)), "r"(x0), "r"(y0), "r"(wrapi(pc, nz)),
               "r"(0), "r"(bar)
               : "memory");
         }
@@ -297,7 +321,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
     }
     if constexpr (OBS) {
       // the snapshot of this thread's node in plane pc (push planes only)
-      if (interior && pc >= z0 && pc < z1) cpa4(s_snap + pb * NT + tid, snap + pc * NXY + gy * nx + gx);
+      if (cnode && pc >= z0 && pc < z1) cpa4(s_snap + pb * NT + tid, snap + pc * NXY + gy * nx + gx);
     }
   };
   auto ring = [&](int v) {  // a slot index in [-NS, 2 NS) into [0, NS)
@@ -334,8 +358,9 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
   }
   int sc = R;  // ring slot of the collision plane
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;     // next density of this node, planes pc - 1 .. pc + 1
-  float oacc0 = 0.f, oacc1 = 0.f, oacc2 = 0.f;  // edge rows: of the node beyond, planes pc - 1 .. pc + 1
-  const int fme = cy * FW + of + cx;  // this node in a staged population plane
+  float oacc0 = 0.f, oacc1 = 0.f, oacc2 = 0.f;  // edge rows: of the node beyond the band, planes pc - 1 .. pc + 1
+  float cacc0 = 0.f, cacc1 = 0.f, cacc2 = 0.f;  // edge columns: of the node beyond the tile, planes pc - 1 .. pc + 1
+  const int fme = cy * FW + cx;  // this node in a staged population plane
   float o_v2 = 0.f, o_u2 = 0.f, o_d = 0.f;  // OBS: running maxima (4 |v|^2, |u|^2, |rho - snap|)
   float o_m = 0.f;                           // OBS: sum of this thread's density deviations
   int o_n = 0;                               // OBS: nodes counted
@@ -379,8 +404,9 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
     const int fbi = bsel(pc);
     float* fb = s_f + fbi * Sh::fbuf;
     float own0 = 0.f, ownp = 0.f, ownm = 0.f;  // this node's incoming populations with e_y = 0
+    const bool live = pc >= z0 && pc < z1;     // a plane of this chunk (not a z halo plane)
     if (crow) {
-      // every lane of a band row collides (lanes past a ragged region on staged
+      // every lane of a band row collides (lanes past a ragged tile on staged
       // values that nothing reads back), so that the exchanges by shuffle see a
       // converged warp; shared-memory stores are masked by cnode, pushes by push
       int base[2 * R + 1];
@@ -417,7 +443,7 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
       const float Fx = -rc * gmx + grx * (1.f / 3.f), Fy = -rc * gmy + gry * (1.f / 3.f),
                   Fz = -rc * gmz + grz * (1.f / 3.f);
       const float vx = ux + Fx * irc, vy = uy + Fy * irc, vz = uz + Fz * irc;
-      const bool push = interior && pc >= z0 && pc < z1;
+      const bool push = cnode && live;
       if (push && !(rc > 0.f)) atomicMin(aux.bad_step, (unsigned long long)aux.t);
       if constexpr (OBS) {
         if (push) {
@@ -480,21 +506,47 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
         }
         // populations that stay in this x-y column are gathered from
         // registers; those moving along the row (e_y = 0, e_x != 0) reach a
-        // lane of this warp, which takes them by shuffle (ring columns
-        // included); in an edge row, those leaving the band are summed per
-        // target column the same way (oacc); the others go through shared memory
+        // lane of this warp, which takes them by shuffle, except across the
+        // tile's edge columns (the lane they reach by the shuffle's wrap is
+        // not their target: the edge lane sums them for the tile beyond,
+        // cacc); in an edge row, those leaving the band are summed per target
+        // column the same way (oacc); the others go through shared memory
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           if (L::ey(i) != 0) continue;
-          const float v = L::ex(i) == 0 ? pst[i] : __shfl_sync(0xffffffffu, pst[i], (cx - L::ex(i)) & 31);
+          float v = pst[i];
+          if (L::ex(i) != 0) {
+            v = __shfl_sync(0xffffffffu, pst[i], (cx - L::ex(i)) & 31);
+            if ((L::ex(i) > 0 && lft) || (L::ex(i) < 0 && rgt)) v = 0.f;  // from the tile beyond
+          }
           if (L::ez(i) < 0) ownm += v; else if (L::ez(i) == 0) own0 += v; else ownp += v;
+        }
+        if (lft || rgt) {
+          // edge columns: the populations leaving the tile along the row
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            if (L::ey(i) != 0 || L::ex(i) == 0) continue;
+            if (!((L::ex(i) < 0 && lft) || (L::ex(i) > 0 && rgt))) continue;
+            if (L::ez(i) < 0) cacc0 += pst[i]; else if (L::ez(i) == 0) cacc1 += pst[i]; else cacc2 += pst[i];
+          }
         }
         if (top || bot) {
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
             if (!((L::ey(i) < 0 && top) || (L::ey(i) > 0 && bot))) continue;
-            const float v = L::ex(i) == 0 ? pst[i] : __shfl_sync(0xffffffffu, pst[i], (cx - L::ex(i)) & 31);
+            float v = pst[i];
+            if (L::ex(i) != 0) {
+              v = __shfl_sync(0xffffffffu, pst[i], (cx - L::ex(i)) & 31);
+              if ((L::ex(i) > 0 && lft) || (L::ex(i) < 0 && rgt)) v = 0.f;  // across a tile corner
+            }
             if (L::ez(i) < 0) oacc0 += v; else if (L::ez(i) == 0) oacc1 += v; else oacc2 += v;
+          }
+          // the in-plane diagonal population leaving through the tile's
+          // corner goes to the corner node of the diagonal neighbour
+          // (D3Q19: 7 = (1,1,0), 8 = (-1,-1,0), 9 = (1,-1,0), 10 = (-1,1,0))
+          if ((lft || rgt) && cnode && live) {
+            const float v = top ? (lft ? pst[8] : pst[9]) : (lft ? pst[10] : pst[7]);
+            qadd(pc, top ? bm : bp, lft ? tm : tp, (lft ? 1 : 0) | (top ? 2 : 0), v);
           }
         }
         if (cnode) {
@@ -526,29 +578,53 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
       }
     }
     __syncthreads();
-    // gather for the band's own node of this thread
-    if (interior) {
+    // gather for the tile's own node of this thread
+    if (cnode) {
       float s_m = ownm, s_0 = own0, s_p = ownp;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         if (L::ey(i) == 0) continue;  // own column and row movers are in the registers
         if ((L::ey(i) > 0 && top) || (L::ey(i) < 0 && bot)) continue;  // from the neighbouring band
+        if ((L::ex(i) > 0 && lft) || (L::ex(i) < 0 && rgt)) continue;  // from the neighbouring tile
         const float v = fb[i * FPL + fme - L::ey(i) * FW - L::ex(i)];
         if (L::ez(i) < 0) s_m += v; else if (L::ez(i) == 0) s_0 += v; else s_p += v;
       }
       acc0 += s_m;
       acc1 += s_0;
       acc2 += s_p;
+      if (lft || rgt) {
+        // edge columns: the in-plane diagonals leaving the tile from the
+        // rows above and below in this band, for the node beyond this row
+        float cv = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (L::ey(i) == 0 || L::ex(i) == 0) continue;
+          if (!((L::ex(i) < 0 && lft) || (L::ex(i) > 0 && rgt))) continue;
+          if ((L::ey(i) > 0 && top) || (L::ey(i) < 0 && bot)) continue;  // from the band beyond: a corner's
+          cv += fb[i * FPL + fme - L::ey(i) * FW];
+        }
+        cacc1 += cv;
+      }
       const int zt = pc - 1;
       if (zt >= z0 && zt < z1) {
-        float* dst = rout + zt * NXY + (y0 + ly) * nx + x0 + lx;
-        if (top || bot) {
-          // completed by the neighbouring band's addition (positivity: the mu pass)
-          atomicAdd(dst, acc0);
-          atomicAdd(rout + zt * NXY + yo * nx + x0 + lx, oacc0);
+        const int ro = zt * NXY + (y0 + cy) * nx;
+        if (corner) {
+          qadd(zt, bb, tb, (rgt ? 1 : 0) | (bot ? 2 : 0), acc0);
+        } else if (top || bot || lft || rgt) {
+          atomicAdd(rout + ro + x0 + cx, acc0);  // completed by the neighbour's addition (positivity: the mu pass)
         } else {
-          *dst = acc0;
+          rout[ro + x0 + cx] = acc0;
           if (!(rref + acc0 > 0.f)) atomicMin(aux.bad_step, (unsigned long long)(aux.t + 1));
+        }
+        if (top || bot) {
+          // the node beyond the band edge: a corner of that band at a tile edge
+          if (lft || rgt) qadd(zt, top ? bm : bp, tb, (top ? 2 : 0) | (rgt ? 1 : 0), oacc0);
+          else atomicAdd(rout + zt * NXY + yo * nx + x0 + cx, oacc0);
+        }
+        if (lft || rgt) {
+          // the node beyond the tile edge: a corner of that tile in an edge row
+          if (top || bot) qadd(zt, bb, lft ? tm : tp, (lft ? 1 : 0) | (bot ? 2 : 0), cacc0);
+          else atomicAdd(rout + ro + xo, cacc0);
         }
       }
       acc0 = acc1;
@@ -557,6 +633,9 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
       oacc0 = oacc1;
       oacc1 = oacc2;
       oacc2 = 0.f;
+      cacc0 = cacc1;
+      cacc1 = cacc2;
+      cacc2 = 0.f;
     }
     sc = ring(sc + 1);
   }
@@ -566,6 +645,35 @@ __global__ void __launch_bounds__(CX* RY_, (CollShape<S, RY_, NB_, FD_>::MINB)) 
   if constexpr (OBS)
     block_obs_reduce<NT>(0.5 * sqrt(double(o_v2)), sqrt(double(o_u2)), double(o_n) * p.rho_ref + double(o_m), double(o_d),
                           aux.partials + 4 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+}
+
+// The next density of the corner nodes of k_coll3d's tiles: accumulator k =
+// ((z nb + b) nt + t) 4 + c (nt tiles of ColTiles(nx), nb bands of
+// RowBands(ny, ry); corner c: bit 0 the tile's last column, bit 1 the band's
+// last row) holds the node's density deviation times qscale as a 64-bit
+// integer; it is written to rout as a float (one rounding), flagged in bad at
+// step t1 when the density is not positive, and zeroed for the next pass.
+__global__ void __launch_bounds__(256) k_coll3d_corners(const KParams p, int ry, unsigned long long* __restrict__ qc,
+                                                        float* __restrict__ rout, const float inv_qscale,
+                                                        unsigned long long* bad, long long t1) {
+  const ColTiles tiles(p.nx);
+  const RowBands bands(p.ny, ry);
+  const long long n = 4LL * tiles.nt * bands.nb * p.nz;
+  const float rref = float(p.rho_ref);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int c = int(k & 3);
+    const long long r = k >> 2;
+    const int t = int(r % tiles.nt);
+    const long long r2 = r / tiles.nt;
+    const int b = int(r2 % bands.nb), z = int(r2 / bands.nb);
+    const int x = (c & 1) ? tiles.start(t + 1) - 1 : tiles.start(t);
+    const int y = (c & 2) ? bands.start(b + 1) - 1 : bands.start(b);
+    const long long q = (long long)qc[k];
+    qc[k] = 0ull;
+    const float v = __ll2float_rn(q) * inv_qscale;
+    rout[(long long)z * p.nx * p.ny + (long long)y * p.nx + x] = v;
+    if (!(rref + v > 0.f)) atomicMin(bad, (unsigned long long)t1);
+  }
 }
 
 }  // namespace lbmd

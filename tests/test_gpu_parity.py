@@ -92,12 +92,15 @@ def test_fp32dev_against_oracle(L, lattice, shape, scheme, mu_fp64):
 
 # nx % 4 == 0 takes the 16-byte (vector) mu and collision kernels, other nx the
 # 4-byte ones; 68 = 64 + 4 leaves a 4-wide vector block, 8^3 wraps every halo
-# several times around the lattice.  The collision pass cuts the rows into
-# bands of 11 whose edge rows are completed by atomic additions: ny = 45 and
-# 12 leave a last band of one row, which takes a row from the band before it;
-# ny = 11 is one band whose two edge rows feed each other across the seam
+# several times around the lattice.  The collision pass cuts the lattice into
+# tiles of 32 columns and bands of 11 rows whose edge columns and rows are
+# completed by atomic additions and whose corners by fixed-point ones: ny = 45
+# and 12 leave a last band of one row, which takes a row from the band before
+# it; ny = 11 is one band whose two edge rows feed each other across the seam;
+# nx = 33 and 65 leave a last tile of one column, which takes a column from
+# the tile before it; nx < 32 is one tile whose edge columns feed each other
 @pytest.mark.parametrize("shape", [(68, 40, 36), (42, 26, 20), (8, 8, 8), (12, 9, 10), (64, 45, 20), (36, 12, 10),
-                                   (40, 11, 12)])
+                                   (40, 11, 12), (33, 20, 12), (65, 23, 10)])
 @pytest.mark.parametrize("scheme", ["EFDS2", "EFDS6"])
 def test_fp32dev_kernel_variants_against_oracle(L, shape, scheme):
     nx, ny, nz = shape
@@ -114,8 +117,9 @@ def test_fp32dev_kernel_variants_against_oracle(L, shape, scheme):
 
 
 def test_fp32dev_split_step_is_bitwise_reproducible(L):
-    # the band edge rows receive exactly two atomic additions onto zero, whose
-    # result does not depend on their order: repeated runs agree bit for bit
+    # the band edge rows and tile edge columns receive exactly two atomic
+    # additions onto zero, whose result does not depend on their order, and the
+    # tile corners exact integer additions: repeated runs agree bit for bit
     kw = dict(lattice=L.LBM_D3Q19, nx=64, ny=45, nz=24, Tr=0.8, k=0.25, kappa=0.1, scheme="EFDS6",
               precision=L.LBM_FP32DEV)
     outs = []
