@@ -43,9 +43,11 @@ def close(a, b, rel, keys=KEYS):
 
 
 # nx % 4 == 0 takes the 16-byte copy variant of the collision pass, 42 the 4-byte one;
-# mu_fp64 = 1: the same passes with the EOS chemical potential evaluated in FP64
+# mu_fp64 = 1: the same passes with the EOS chemical potential evaluated in FP64;
+# 65 and 33 leave a last tile of one column, which joins the tile before it
 @pytest.mark.parametrize("shape,scheme,mu_fp64", [((48, 40, 44), "EFDS6", 0), ((42, 36, 40), "EFDS4", 0),
-                                                  ((40, 40, 40), "EFDS2", 0), ((48, 40, 44), "EFDS6", 1)])
+                                                  ((40, 40, 40), "EFDS2", 0), ((48, 40, 44), "EFDS6", 1),
+                                                  ((65, 23, 20), "EFDS6", 0), ((33, 24, 22), "EFDS4", 0)])
 def test_fused_observation_matches_observe_then_step(L, shape, scheme, mu_fp64):
     a, b = make(L, shape, scheme=scheme, mu_fp64=mu_fp64), make(L, shape, scheme=scheme, mu_fp64=mu_fp64)
     t_prev = 0
