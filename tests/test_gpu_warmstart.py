@@ -2,8 +2,8 @@
 MLP kernels fit them, and a predicted profile starts a held-out droplet closer
 to its converged state than the tanh profile of Eq. 26; the warm-started run
 relaxes to the same densities as the cold-started one (both relaxed until
-max |d rho / dt| stagnates at the FP32 rounding floor: the benchmark spec's 1e-5
-agreement on densities)."""
+max |d rho / dt| stagnates at the FP32 rounding floor), to 1e-5 of the liquid
+density."""
 import numpy as np
 import pytest
 
