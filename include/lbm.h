@@ -205,7 +205,11 @@ int lbm_set_f(lbm_handle* h, const double* host_f);
  * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_set_solid(lbm_handle* h, const unsigned char* mask, double mu_w);
 
-/* Advance n >= 0 time steps; asynchronous on the handle's stream. */
+/* Advance n >= 0 time steps; asynchronous on the handle's stream.  The same
+ * handle parameters, initial state and n give the same bits on every run:
+ * where several thread blocks contribute to one node's next density, their
+ * partial sums are combined in an order-independent way (two floating-point
+ * additions onto zero, or exact 64-bit fixed-point additions). */
 int lbm_step(lbm_handle* h, long long n);
 
 /* As lbm_step (n <= 100000), timing every step on the handle's stream with
